@@ -1,0 +1,250 @@
+/*
+ * dsmc.h -- C ABI of the GB300 ensemble DSMC library (libdsmc.so).
+ *
+ * One call advances n statistically independent runs of an unsteady DSMC
+ * simulation from t = 0 (the outer loop of the sequential algorithm, Sec. 1.1
+ * of Bogdanov et al., "Algorithms of Two-Level Parallelization for DSMC of
+ * Unsteady Flows in Molecular Gasdynamics"), every time step made of the
+ * inner loop's subroutines (Sec. 1.1, Fig. 1):
+ *   Generation   particles enter through inflow boundaries;
+ *   Motion       free flight, specular / diffuse surface interaction, leavers
+ *                removed from P;
+ *   Enumeration, Indexing
+ *                particles counted per cell and the readdressing array LCR
+ *                built (one entry per particle, ordered by cell);
+ *   Interaction  collisions in every cell independently (no-time-counter
+ *                candidate count, hard-sphere / VHS cross section);
+ *   Sampling     cell macroparameters at the given moments, averaged over
+ *                the runs ("ensemble averaging", Sec. 1.1).
+ * All runs advance together on one GPU (the paper's independent-runs level,
+ * Sec. 1.3, mapped to a batch dimension; its data-parallel level, Sec. 1.4,
+ * mapped to GPU threads).
+ *
+ * Conventions for every entry point:
+ *  - Every struct starts with `struct_size` = sizeof(the struct) as the
+ *    caller compiled it; a smaller or zero value is rejected with
+ *    DSMC_E_INVALID.  The library copies every input struct and array; the
+ *    caller keeps ownership of what it passes in.
+ *  - Host pointers are plain host memory unless stated otherwise.
+ *  - No call throws; errors are returned as dsmc_status and described by
+ *    dsmc_last_error(ctx).  A context is used by one host thread at a time.
+ *  - Units are SI.  Geometry is a uniform Cartesian grid of n[0] x n[1]
+ *    (x n[2]) cells on [0, L_x) x [0, L_y) (x [0, L_z)); cell index
+ *    c = i + n[0] * (j + n[1] * k).  In 2-D, n[2] = 1 and extent[2] is the
+ *    depth (the third velocity component is carried, not the coordinate).
+ */
+#ifndef DSMC_H
+#define DSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DSMC_OK = 0,
+    DSMC_E_INVALID = 1,    /* bad argument; nothing was changed */
+    DSMC_E_OOM = 2,        /* device allocation failed */
+    DSMC_E_CUDA = 3,       /* a CUDA call failed (message in last_error) */
+    DSMC_E_CAPACITY = 4,   /* particle pool or a per-cell limit overflowed on
+                              the device; the run's results are incomplete */
+    DSMC_E_TIMEOUT = 5,    /* a bounded device wait expired (reserved) */
+    DSMC_E_STATE = 6       /* call out of order (e.g. samples before a run) */
+} dsmc_status;
+
+enum { DSMC_BC_OUTFLOW = 0, DSMC_BC_INFLOW = 1, DSMC_BC_SPECULAR = 2, DSMC_BC_DIFFUSE = 3 };
+enum { DSMC_FACE_XMIN = 0, DSMC_FACE_XMAX = 1, DSMC_FACE_YMIN = 2, DSMC_FACE_YMAX = 3,
+       DSMC_FACE_ZMIN = 4, DSMC_FACE_ZMAX = 5, DSMC_FACE_PLATE = 6 };
+enum { DSMC_MODE_BATCHED = 0, DSMC_MODE_PLAIN = 1 };
+enum { DSMC_FP32 = 0, DSMC_FP64 = 1 };
+
+typedef enum {
+    DSMC_Q_RAW_MOMENTS = 0,        /* [G][ncells][7] group sums, see below */
+    DSMC_Q_DENSITY = 1,            /* [ncells]   n (m^-3) */
+    DSMC_Q_VELOCITY = 2,           /* [ncells][3] mean velocity (m/s) */
+    DSMC_Q_TEMPERATURE = 3,        /* [ncells]   T (K) */
+    DSMC_Q_STDERR_DENSITY = 4,     /* [ncells]   batch-means standard errors */
+    DSMC_Q_STDERR_VELOCITY = 5,    /* [ncells][3] */
+    DSMC_Q_STDERR_TEMPERATURE = 6  /* [ncells] */
+} dsmc_quantity;
+
+#define DSMC_NMOM 7     /* N, sum u, sum v, sum w, sum u^2, sum v^2, sum w^2 */
+#define DSMC_MAX_BC 32
+#define DSMC_MAX_GROUPS 16
+
+/* Computational domain (the array C of Sec. 1.1 is built from it). */
+typedef struct {
+    uint32_t struct_size;
+    int32_t dim;            /* 2 or 3 */
+    double extent[3];       /* L_x, L_y, L_z (m); 2-D: extent[2] = depth */
+    int32_t fill;           /* 0: start empty; 1: start filled with a uniform
+                               freestream (fill_n, fill_T, fill_U) */
+    double fill_n, fill_T, fill_U[3];
+} dsmc_domain;
+
+typedef struct {
+    uint32_t struct_size;
+    int32_t n[3];           /* cells per axis; n[2] = 1 in 2-D */
+} dsmc_cells;
+
+/* Monatomic gas, variable-hard-sphere model:
+ *   sigma_T(c_r) = pi d_ref^2 (2 k T_ref / (m_r c_r^2))^(omega - 1/2)
+ *                  / Gamma(5/2 - omega),  m_r = mass / 2;
+ * omega = 0.5 is the hard sphere pi d_ref^2.  F_N = real molecules per
+ * simulated particle. */
+typedef struct {
+    uint32_t struct_size;
+    double mass, d_ref, T_ref, omega, F_N;
+} dsmc_gas;
+
+/* One boundary segment.  Faces: 2 * axis + side (side 0 at coordinate 0,
+ * side 1 at L).  [lo, hi) are cell ranges along the face's two tangential
+ * axes in increasing axis order (2-D: the second range is [0, 1)).  Where
+ * several segments cover a face cell at a step, the last listed active one
+ * applies; an uncovered face cell is open (outflow).  INFLOW injects a
+ * drifting Maxwellian (n, T, U) and removes particles leaving through it;
+ * OUTFLOW removes leavers; SPECULAR reflects; DIFFUSE re-emits at T.
+ * face = DSMC_FACE_PLATE describes a zero-thickness internal plate normal to
+ * `plate_axis` at coordinate plate_index * cell size, covering [lo, hi) of
+ * the tangential cells, SPECULAR or DIFFUSE on both sides.  A segment is
+ * active for steps step_from..step_to (1-based, inclusive; 0 = forever). */
+typedef struct {
+    uint32_t struct_size;
+    int32_t kind, face;
+    int32_t lo[2], hi[2];
+    int32_t step_from, step_to;
+    int32_t plate_axis, plate_index;
+    double n, T, U[3];
+} dsmc_boundary;
+
+/* Device memory callbacks (e.g. a framework's caching allocator).  `stream`
+ * is the cudaStream_t the memory will be used on.  alloc returns a device
+ * pointer aligned to at least 256 bytes, or NULL. */
+typedef void* (*dsmc_alloc_fn)(size_t bytes, void* user, void* stream);
+typedef void (*dsmc_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
+
+typedef struct {
+    uint32_t struct_size;
+    int32_t mode;             /* DSMC_MODE_BATCHED: all runs in one launch per
+                                 kernel per step (CUDA-graph captured);
+                                 DSMC_MODE_PLAIN: one run after another */
+    int32_t precision;        /* particle state / collision arithmetic:
+                                 DSMC_FP32 or DSMC_FP64 (sampling sums and the
+                                 NTC remainder are FP64 in both) */
+    double capacity_factor;   /* pool size = factor x estimate (0 -> 1.25) */
+    int64_t capacity_per_run; /* > 0 overrides the estimate */
+    dsmc_alloc_fn alloc;      /* NULL: cudaMalloc / cudaFree */
+    dsmc_free_fn free;
+    void* alloc_user;
+    void* stream;             /* cudaStream_t; NULL: the library's own stream */
+    int32_t use_graph;        /* batched mode: capture one step per graph */
+    int32_t debug;            /* keep per-cell candidate / accepted counts and
+                                 the LCR of the last step (test hooks) */
+    int32_t device;           /* CUDA device ordinal */
+    int32_t profile;          /* time every kernel with CUDA events (direct
+                                 launches, no graph); see dsmc_stats */
+} dsmc_options;
+
+typedef struct {
+    uint32_t struct_size;
+    uint64_t particle_steps;  /* sum over runs and steps of particles moved */
+    uint64_t generated, removed, wall_hits;
+    uint64_t candidates, collisions, clamps;   /* NTC counters; clamps: pairs
+                                                  with sigma c_r > max */
+    uint64_t bounce_limit, reject_limit;       /* numerical guards hit */
+    uint32_t error_word;      /* device error bits (DSMC_ERR_*) */
+    int32_t steps_done;
+    int64_t particles_now;    /* particles in all runs after the last step */
+    int64_t capacity;         /* particle pool capacity (all runs) */
+    double ms_steps;          /* device time of the last run's step loop */
+    double ms_kernel[12];     /* profile mode: device time per kernel kind */
+    int64_t launches_kernel[12];
+} dsmc_stats;
+
+/* device error bits */
+#define DSMC_ERR_POOL      0x1u   /* particle pool overflow */
+#define DSMC_ERR_GEN       0x2u   /* per-run generation buffer overflow */
+#define DSMC_ERR_BIGCELL   0x4u   /* a cell exceeded the per-cell limit */
+#define DSMC_ERR_BIGLIST   0x8u   /* too many large cells in one step */
+
+/* kernel kinds of dsmc_stats.ms_kernel */
+enum { DSMC_K_GENERATE = 0, DSMC_K_MOVE = 1, DSMC_K_SCAN = 2, DSMC_K_SCATTER = 3,
+       DSMC_K_CELL = 4, DSMC_K_CELL_BIG = 5, DSMC_K_REDUCE = 6, DSMC_K_OTHER = 7 };
+
+typedef struct dsmc_ctx dsmc_ctx;
+
+/* Create a context for one problem: domain and grid, gas model, `n_b`
+ * boundary segments (n_b <= DSMC_MAX_BC) and options (NULL: defaults).  No
+ * device memory is allocated until the first run.  *out receives the
+ * context; release it with dsmc_destroy.  Errors: DSMC_E_INVALID (bad
+ * geometry, gas or boundary description), DSMC_E_CUDA (device selection). */
+dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells,
+                        const dsmc_gas* gas, const dsmc_boundary* b, int n_b,
+                        const dsmc_options* opt, dsmc_ctx** out);
+
+/* Run n_runs independent runs for `steps` steps of length dt (s) from t = 0.
+ * Sample k is taken after step sample_steps[k] (1-based, strictly
+ * increasing, <= steps; at most 4096 samples), once Interaction of that step
+ * is done.  Run r draws every random number from Philox4x32-10 keyed by
+ * `seed` with (r, step, entity, purpose, draw) as the counter, so results do
+ * not depend on mode, launch shape or stream.  Blocks until the device is
+ * done.  Device memory is owned by the library (through the callbacks) and
+ * reused by later calls.  Errors: DSMC_E_INVALID, DSMC_E_OOM, DSMC_E_CUDA,
+ * DSMC_E_CAPACITY (results incomplete; rerun with a larger capacity). */
+dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                              const int32_t* sample_steps, int n_samples,
+                              uint64_t seed);
+
+/* Copy sample `sample_idx` of the last run into out[0 .. out_len).  The
+ * runs are split into G = min(n_runs, 16) groups (run r in group r mod G);
+ * RAW_MOMENTS gives the group sums [G][ncells][7] of N, sum v_a and
+ * sum v_a^2; the macroscopic quantities pool all groups:
+ *   n = sum N F_N / (n_runs V_c),  u = sum v / sum N,
+ *   T = m / (3 k) (sum |v|^2 / sum N - |u|^2)  (NaN where sum N = 0);
+ * STDERR_* are the standard deviations over the G group estimates divided
+ * by sqrt(G).  Errors: DSMC_E_INVALID (index or out_len too small),
+ * DSMC_E_STATE (no completed run). */
+dsmc_status dsmc_get_samples(dsmc_ctx* ctx, int sample_idx, dsmc_quantity q,
+                             double* out, size_t out_len);
+
+dsmc_status dsmc_get_stats(dsmc_ctx* ctx, dsmc_stats* out);
+void dsmc_destroy(dsmc_ctx* ctx);
+/* Message of the last failed call on ctx (static string if ctx is NULL). */
+const char* dsmc_last_error(const dsmc_ctx* ctx);
+
+/* ---- test hooks (step-level access for parity tests) ---------------- */
+
+/* Allocate for n_runs and set up the step-0 state (filled or empty) without
+ * running a step; the sample list is empty. */
+dsmc_status dsmc_debug_begin(dsmc_ctx* ctx, int n_runs, double dt, uint64_t seed);
+/* Advance every run by n_steps steps. */
+dsmc_status dsmc_debug_step(dsmc_ctx* ctx, int n_steps);
+/* Particles of `run` in the current P order (cell, id): x[n][3], v[n][3],
+ * id[n]; at most cap particles are written, *n_out gets the count. */
+dsmc_status dsmc_debug_get_state(dsmc_ctx* ctx, int run, double* x, double* v,
+                                 uint32_t* id, int64_t cap, int64_t* n_out);
+/* Replace the particles of `run` (any order; this order numbers the slots
+ * of the next step's LCR) and its next particle id. */
+dsmc_status dsmc_debug_set_state(dsmc_ctx* ctx, int run, int64_t n, const double* x,
+                                 const double* v, const uint32_t* id, uint32_t next_id);
+/* Last step's per-cell counts, NTC candidates and accepted collisions
+ * ([ncells] each; needs options.debug for cand/accepted/lcr) and its LCR:
+ * lcr[k] = pre-step slot (old particles 0..n_old-1 in their previous order,
+ * then the step's entrants in generation order) of the k-th particle. */
+dsmc_status dsmc_debug_get_cells(dsmc_ctx* ctx, int run, int32_t* count, int32_t* cand,
+                                 int32_t* accepted, int64_t* lcr, int64_t cap);
+dsmc_status dsmc_debug_get_cell_state(dsmc_ctx* ctx, int run, double* rem, double* smax);
+dsmc_status dsmc_debug_set_cell_state(dsmc_ctx* ctx, int run, const double* rem,
+                                      const double* smax);
+/* Moments [ncells][7] of `run`'s current particles (FP64). */
+dsmc_status dsmc_debug_sample(dsmc_ctx* ctx, int run, double* mom);
+/* The device Philox4x32-10 on n host (ctr[4], key[2]) pairs -> out[4n]. */
+dsmc_status dsmc_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* key,
+                              uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -597,6 +597,12 @@ int64_t orc_count(const orc_ctx* C, int run)
     return C->runs[run].n;
 }
 
+uint32_t orc_next_id(const orc_ctx* C, int run)
+{
+    if (!C || run < 0 || run >= C->n_runs) return 0;
+    return C->runs[run].next_id;
+}
+
 int orc_get_state(const orc_ctx* C, int run, double* x, double* v, uint32_t* id)
 {
     if (!C || run < 0 || run >= C->n_runs) return -1;

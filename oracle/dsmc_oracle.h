@@ -98,6 +98,7 @@ void orc_destroy(orc_ctx* c);
 int orc_init_run(orc_ctx* c, int run);                /* step-0 state */
 int orc_step(orc_ctx* c, int run, int step);          /* one DSMC step */
 int64_t orc_count(const orc_ctx* c, int run);
+uint32_t orc_next_id(const orc_ctx* c, int run);   /* ids handed out so far */
 int orc_get_state(const orc_ctx* c, int run, double* x, double* v, uint32_t* id);
 int orc_set_state(orc_ctx* c, int run, int64_t n, const double* x,
                   const double* v, const uint32_t* id, uint32_t next_id);

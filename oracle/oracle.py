@@ -92,6 +92,8 @@ def oracle_lib():
             lib.orc_step.argtypes = [P, C.c_int, C.c_int]
             lib.orc_count.restype = C.c_int64
             lib.orc_count.argtypes = [P, C.c_int]
+            lib.orc_next_id.restype = C.c_uint32
+            lib.orc_next_id.argtypes = [P, C.c_int]
             lib.orc_get_state.argtypes = [P, C.c_int, dp, dp, u32p]
             lib.orc_set_state.argtypes = [P, C.c_int, C.c_int64, dp, dp, u32p, C.c_uint32]
             lib.orc_get_cells.argtypes = [P, C.c_int, ip, ip, ip, i64p]
@@ -224,6 +226,9 @@ class Oracle:
 
     def count(self, run):
         return int(self.lib.orc_count(self.h, run))
+
+    def next_id(self, run):
+        return int(self.lib.orc_next_id(self.h, run))
 
     def get_state(self, run):
         n = self.count(run)

@@ -1,0 +1,1061 @@
+// dsmc_engine.cu -- host engine and C ABI of libdsmc.so.
+//
+// The engine owns the device buffers of one problem, sizes them from the
+// workload, and drives the step kernels either for all runs at once
+// (batched: one launch per kernel per step, one CUDA graph per step and
+// buffer parity) or one run after another (plain).  Everything a step
+// computes happens in the kernels of dsmc_kernels.cu; the host only derives
+// constants, allocates, launches and copies results out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dsmc_internal.cuh"
+
+using namespace dsmc;
+
+namespace {
+
+constexpr double kB = 1.380649e-23;
+
+struct DevBuf {
+    void* p;
+    size_t bytes;
+};
+
+struct AnyArgs {
+    StepArgs<float> f;
+    StepArgs<double> d;
+};
+
+}  // namespace
+
+struct dsmc_ctx {
+    dsmc_domain dom;
+    dsmc_cells cells;
+    dsmc_gas gas;
+    std::vector<dsmc_boundary> bcs;
+    dsmc_options opt;
+    std::string err;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int prec = DSMC_FP32, dim = 2, ncells = 0, sms = 0;
+    Cfg hcfg;
+    LaunchShape ls;
+    // allocation state
+    std::vector<DevBuf> bufs;
+    int n_launch = 0;
+    int64_t cap_old = 0, cap_new = 0, gcap = 0, max_big = 0;
+    int64_t total_cells = 0;
+    int n_samples_alloc = 0, steps_alloc = 0, G_alloc = 0;
+    bool debug_alloc = false;
+    uint64_t generation = 0;      // bumps on every reallocation
+    // device pointers
+    Cfg* d_cfg = nullptr;
+    Counters* d_ctr = nullptr;
+    void* X[2][3] = {};
+    void* V[2][3] = {};
+    uint32_t* ID[2] = {};
+    uint32_t *gc = nullptr, *rank = nullptr, *lcr = nullptr, *lcr_dbg = nullptr;
+    uint32_t *count = nullptr, *start = nullptr, *block_sums = nullptr;
+    uint32_t *run_base = nullptr, *next_id = nullptr, *cand = nullptr, *accd = nullptr;
+    uint32_t* big_list = nullptr;
+    double *rem = nullptr, *mom = nullptr, *acc = nullptr, *macro = nullptr;
+    void* smax = nullptr;
+    int32_t* sample_slot = nullptr;
+    int cur = 0;
+    int G = 1;
+    // graphs (batched): one per buffer parity, valid for graph_key
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    uint64_t graph_key = ~0ull;
+    // last run
+    bool have_run = false;
+    int last_runs = 0, last_steps = 0, last_samples = 0;
+    // debug stepping
+    bool dbg = false;
+    std::vector<uint32_t> prev_run_base;
+    dsmc_stats stats;
+    std::vector<cudaEvent_t> events;
+};
+
+static const char* g_static_err = "invalid context";
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+            return DSMC_E_CUDA;                                                           \
+        }                                                                                 \
+    } while (0)
+
+static dsmc_status fail(dsmc_ctx* ctx, dsmc_status s, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// configuration
+
+static dsmc_status build_cfg(dsmc_ctx* ctx, double dt, uint64_t seed)
+{
+    Cfg& c = ctx->hcfg;
+    std::memset(&c, 0, sizeof(c));
+    const dsmc_domain& D = ctx->dom;
+    c.dim = D.dim;
+    for (int a = 0; a < 3; ++a) c.n[a] = (a < D.dim) ? ctx->cells.n[a] : 1;
+    c.ncells = c.n[0] * c.n[1] * c.n[2];
+    for (int a = 0; a < 3; ++a) {
+        c.L[a] = D.extent[a];
+        c.d[a] = c.L[a] / c.n[a];
+    }
+    c.Vc = c.d[0] * c.d[1] * c.d[2];
+    c.dt = dt;
+    c.mass = ctx->gas.mass;
+    c.F_N = ctx->gas.F_N;
+    c.coef = (ctx->gas.F_N * dt) / c.Vc;
+    const double omega = ctx->gas.omega;
+    const double dref = ctx->gas.d_ref;
+    c.hs = (omega == 0.5) ? 1 : 0;
+    c.A_hs = M_PI * (dref * dref);
+    const double mr = ctx->gas.mass / 2.0;
+    c.K_vhs = M_PI * (dref * dref) * std::pow(2.0 * kB * ctx->gas.T_ref / mr, omega - 0.5) /
+              std::tgamma(2.5 - omega);
+    c.one_m_omega = 1.0 - omega;
+    c.seed = seed;
+    c.fill = D.fill;
+    c.fill_lam = D.fill_n * c.Vc / ctx->gas.F_N;
+    c.fill_sd = std::sqrt(kB * D.fill_T / ctx->gas.mass);
+    for (int a = 0; a < 3; ++a) c.fill_U[a] = D.fill_U[a];
+    double T0 = D.fill ? D.fill_T : 0.0;
+    c.n_bc = (int)ctx->bcs.size();
+    int64_t eb = 0;
+    for (int q = 0; q < c.n_bc; ++q) {
+        const dsmc_boundary& b = ctx->bcs[q];
+        BcDev& o = c.bc[q];
+        o.kind = b.kind;
+        o.face = b.face;
+        for (int k = 0; k < 2; ++k) { o.lo[k] = b.lo[k]; o.hi[k] = b.hi[k]; }
+        o.step_from = b.step_from;
+        o.step_to = b.step_to;
+        o.plate_axis = b.plate_axis;
+        o.plate_index = b.plate_index;
+        o.T = b.T;
+        for (int a = 0; a < 3; ++a) o.U[a] = b.U[a];
+        const int axis = b.face < 6 ? b.face / 2 : b.plate_axis;
+        o.axis = axis;
+        o.side = b.face < 6 ? b.face % 2 : 0;
+        o.t0 = axis == 0 ? 1 : 0;
+        o.t1 = axis == 2 ? 1 : 2;
+        o.sd = std::sqrt(kB * b.T / ctx->gas.mass);
+        o.dir = o.side ? -1.0 : 1.0;
+        if ((b.kind == DSMC_BC_INFLOW || b.kind == DSMC_BC_DIFFUSE) && b.T > T0) T0 = b.T;
+        if (b.face == DSMC_FACE_PLATE) {
+            c.plate_idx[c.n_plate++] = q;
+            o.xp = (double)b.plate_index * c.d[axis];
+        }
+        o.elem_base = eb;
+        if (b.kind == DSMC_BC_INFLOW && b.face < 6) {
+            o.elem_w = b.hi[0] - b.lo[0];
+            o.n_elem = (int64_t)(b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]);
+            eb += o.n_elem;
+            o.cmp = std::sqrt(2.0 * kB * b.T / ctx->gas.mass);
+            const double Un = o.dir * b.U[axis];
+            o.s = Un / o.cmp;
+            // drifting-Maxwellian number flux through the face
+            const double flux = b.n * o.cmp / (2.0 * std::sqrt(M_PI)) *
+                                (std::exp(-o.s * o.s) + std::sqrt(M_PI) * o.s * (1.0 + std::erf(o.s)));
+            const double area = c.d[o.t0] * c.d[o.t1];
+            o.lam = flux * area * dt / ctx->gas.F_N;
+            o.xm = (o.s + std::sqrt(o.s * o.s + 2.0)) / 2.0;
+        }
+    }
+    c.n_elem = eb;
+    if (T0 <= 0.0) T0 = ctx->gas.T_ref;
+    // sigma_T(c0) c0 at three most probable speeds of the hottest state
+    const double c0 = 3.0 * std::sqrt(2.0 * kB * T0 / ctx->gas.mass);
+    const double sig0 = M_PI * (dref * dref) *
+                        std::pow(2.0 * kB * ctx->gas.T_ref / (mr * c0 * c0), omega - 0.5) /
+                        std::tgamma(2.5 - omega);
+    c.smax0 = sig0 * c0;
+    return DSMC_OK;
+}
+
+// particles one run may hold, estimated from the fill, the inflow over the
+// whole run and the densest state the run is driven with
+static int64_t estimate_per_run(const dsmc_ctx* ctx, int steps)
+{
+    if (ctx->opt.capacity_per_run > 0) return ctx->opt.capacity_per_run;
+    const Cfg& c = ctx->hcfg;
+    double fill = c.fill ? (c.fill_lam + 1.0) * c.ncells : 0.0;
+    double gen = 0.0, nmax = c.fill ? ctx->dom.fill_n : 0.0;
+    for (int q = 0; q < c.n_bc; ++q) {
+        const BcDev& b = c.bc[q];
+        if (!(b.kind == DSMC_BC_INFLOW && b.face < 6)) continue;
+        const int from = std::max(1, b.step_from);
+        const int to = b.step_to == 0 ? steps : std::min(steps, b.step_to);
+        const int act = std::max(0, to - from + 1);
+        gen += std::ceil(b.lam) * (double)b.n_elem * act;
+        nmax = std::max(nmax, ctx->bcs[q].n);
+    }
+    const double dens = 1.5 * nmax * c.Vc * c.ncells / ctx->gas.F_N;
+    double est = fill + gen;
+    if (dens > fill && est > dens) est = dens;
+    const double factor = ctx->opt.capacity_factor > 0 ? ctx->opt.capacity_factor : 1.25;
+    return (int64_t)(est * factor) + 1024;
+}
+
+static int64_t gen_capacity(const dsmc_ctx* ctx)
+{
+    const Cfg& c = ctx->hcfg;
+    double g = 0.0;
+    for (int q = 0; q < c.n_bc; ++q) {
+        const BcDev& b = c.bc[q];
+        if (b.kind == DSMC_BC_INFLOW && b.face < 6) g += std::ceil(b.lam) * (double)b.n_elem;
+    }
+    return ((int64_t)g + 32 + 31) / 32 * 32;
+}
+
+// ---------------------------------------------------------------------------
+// memory
+
+static void* dev_alloc(dsmc_ctx* ctx, size_t bytes)
+{
+    bytes = (bytes + 255) / 256 * 256;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (ctx->opt.alloc) {
+        p = ctx->opt.alloc(bytes, ctx->opt.alloc_user, (void*)ctx->stream);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) ctx->bufs.push_back({p, bytes});
+    return p;
+}
+
+static void free_all(dsmc_ctx* ctx)
+{
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < 2; ++k)
+        if (ctx->gexec[k]) { cudaGraphExecDestroy(ctx->gexec[k]); ctx->gexec[k] = nullptr; }
+    ctx->graph_key = ~0ull;
+    for (const DevBuf& b : ctx->bufs) {
+        if (ctx->opt.free) ctx->opt.free(b.p, b.bytes, ctx->opt.alloc_user, (void*)ctx->stream);
+        else cudaFree(b.p);
+    }
+    ctx->bufs.clear();
+    ctx->n_launch = 0;
+    ctx->cap_old = 0;
+}
+
+static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, int steps,
+                                int n_samples, int G)
+{
+    const int64_t cap_old = (cap_run * n_launch + 255) / 256 * 256;
+    const int64_t gcap = gen_capacity(ctx);
+    const int64_t cap_new = gcap * n_launch;
+    const int64_t total_cells = (int64_t)ctx->ncells * n_launch;
+    const bool dbg = ctx->opt.debug != 0;
+    if (cap_old + cap_new >= 0xFFFFFFF0ll || total_cells >= 0x7FFFFFF0ll)
+        return fail(ctx, DSMC_E_INVALID, "problem too large for 32-bit particle slots");
+    if (ctx->n_launch == n_launch && ctx->cap_old >= cap_old && ctx->gcap == gcap &&
+        ctx->steps_alloc >= steps + 2 && ctx->n_samples_alloc >= n_samples && ctx->G_alloc == G &&
+        ctx->debug_alloc == dbg)
+        return DSMC_OK;
+    free_all(ctx);
+    const size_t ts = ctx->prec == DSMC_FP64 ? 8 : 4;
+    const int64_t slots = cap_old + cap_new;
+    bool ok = true;
+    auto A = [&](size_t bytes) -> void* {
+        void* p = dev_alloc(ctx, bytes);
+        if (!p) ok = false;
+        return p;
+    };
+    ctx->d_cfg = (Cfg*)A(sizeof(Cfg));
+    ctx->d_ctr = (Counters*)A(sizeof(Counters));
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            ctx->X[b][a] = a < ctx->dim ? A(ts * slots) : nullptr;
+            ctx->V[b][a] = A(ts * slots);
+        }
+        ctx->ID[b] = (uint32_t*)A(4 * slots);
+    }
+    ctx->gc = (uint32_t*)A(4 * slots);
+    ctx->rank = (uint32_t*)A(4 * slots);
+    ctx->lcr = (uint32_t*)A(4 * cap_old);
+    ctx->lcr_dbg = dbg ? (uint32_t*)A(4 * cap_old) : nullptr;
+    ctx->count = (uint32_t*)A(4 * total_cells);
+    ctx->start = (uint32_t*)A(4 * (total_cells + 2));
+    const int scan_blocks = (int)((total_cells + kScanTile - 1) / kScanTile);
+    ctx->block_sums = (uint32_t*)A(4 * scan_blocks);
+    ctx->run_base = (uint32_t*)A(4 * (n_launch + 1));
+    ctx->next_id = (uint32_t*)A(4 * n_launch);
+    ctx->rem = (double*)A(8 * total_cells);
+    ctx->smax = A(ts * total_cells);
+    ctx->mom = (double*)A(8 * DSMC_NMOM * total_cells);
+    ctx->cand = dbg ? (uint32_t*)A(4 * total_cells) : nullptr;
+    ctx->accd = dbg ? (uint32_t*)A(4 * total_cells) : nullptr;
+    const int64_t max_big = cap_old / (kWarpMax + 1) + 1;
+    ctx->big_list = (uint32_t*)A(4 * max_big);
+    ctx->sample_slot = (int32_t*)A(4 * (size_t)(steps + 2));
+    ctx->acc = (double*)A(8 * (size_t)std::max(n_samples, 1) * G * ctx->ncells * DSMC_NMOM);
+    ctx->macro = (double*)A(8 * 10 * (size_t)ctx->ncells);
+    if (!ok) {
+        free_all(ctx);
+        return fail(ctx, DSMC_E_OOM, "device allocation failed");
+    }
+    ctx->n_launch = n_launch;
+    ctx->cap_old = cap_old;
+    ctx->cap_new = cap_new;
+    ctx->gcap = gcap;
+    ctx->max_big = max_big;
+    ctx->total_cells = total_cells;
+    ctx->steps_alloc = steps + 2;
+    ctx->n_samples_alloc = n_samples;
+    ctx->G_alloc = G;
+    ctx->debug_alloc = dbg;
+    ctx->generation++;
+    // the new-region cell keys start dead; every scatter re-kills them
+    CK(cudaMemsetAsync(ctx->gc, 0xFF, 4 * slots, ctx->stream));
+    return DSMC_OK;
+}
+
+template <typename T>
+static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
+{
+    StepArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.cfg = ctx->d_cfg;
+    a.ctr = ctx->d_ctr;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.xi[ax] = (T*)ctx->X[cur][ax];
+        a.vi[ax] = (T*)ctx->V[cur][ax];
+        a.xo[ax] = (T*)ctx->X[1 - cur][ax];
+        a.vo[ax] = (T*)ctx->V[1 - cur][ax];
+    }
+    a.idi = ctx->ID[cur];
+    a.ido = ctx->ID[1 - cur];
+    a.gc = ctx->gc;
+    a.rank = ctx->rank;
+    a.lcr = ctx->lcr;
+    a.lcr_dbg = ctx->lcr_dbg;
+    a.count = ctx->count;
+    a.start = ctx->start;
+    a.block_sums = ctx->block_sums;
+    a.run_base = ctx->run_base;
+    a.next_id = ctx->next_id;
+    a.rem = ctx->rem;
+    a.smax = (T*)ctx->smax;
+    a.mom = ctx->mom;
+    a.cand = ctx->cand;
+    a.accd = ctx->accd;
+    a.big_list = ctx->big_list;
+    a.sample_slot = ctx->sample_slot;
+    a.acc = ctx->acc;
+    a.cap_old = ctx->cap_old;
+    a.cap_new = ctx->cap_new;
+    a.gcap = ctx->gcap;
+    a.max_big = ctx->max_big;
+    a.n_runs = n;
+    a.run0 = run0;
+    a.G = ctx->G;
+    a.total_cells = (int32_t)((int64_t)ctx->ncells * n);
+    a.scan_blocks = (int)((a.total_cells + kScanTile - 1) / kScanTile);
+    return a;
+}
+
+static const void* build_args(const dsmc_ctx* ctx, AnyArgs& u, int cur, int run0, int n)
+{
+    if (ctx->prec == DSMC_FP64) {
+        u.d = args_for<double>(ctx, cur, run0, n);
+        return &u.d;
+    }
+    u.f = args_for<float>(ctx, cur, run0, n);
+    return &u.f;
+}
+
+// ---------------------------------------------------------------------------
+// step sequencing
+
+static cudaEvent_t event_at(dsmc_ctx* ctx, size_t i)
+{
+    while (ctx->events.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->events.push_back(e);
+    }
+    return ctx->events[i];
+}
+
+// One step of every run in the launch described by `args`.  With `ev`
+// non-null an event is recorded after each kernel (profile mode).
+static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev)
+{
+    const int p = ctx->prec;
+    const LaunchShape& ls = ctx->ls;
+    cudaStream_t s = ctx->stream;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(event_at(ctx, (*ev)++), s);
+    };
+    launch_generate(p, args, ls, s); mark();
+    launch_move(p, args, ls, s); mark();
+    launch_scan(p, args, ls, s); mark();
+    launch_scatter(p, args, ls, s); mark();
+    launch_cell(p, args, ls, s); mark();
+    launch_cell_big(p, args, ls, s); mark();
+    launch_reduce(p, args, ls, s); mark();
+    launch_step_end(p, args, s); mark();
+}
+static const int kStepKernels = 8;
+static const int kKindOf[kStepKernels] = {DSMC_K_GENERATE, DSMC_K_MOVE, DSMC_K_SCAN, DSMC_K_SCATTER,
+                                          DSMC_K_CELL, DSMC_K_CELL_BIG, DSMC_K_REDUCE, DSMC_K_OTHER};
+
+static void enqueue_init(dsmc_ctx* ctx, const void* args)
+{
+    launch_init_cells(ctx->prec, args, ctx->ls, ctx->stream);
+    launch_fill(ctx->prec, args, ctx->ls, ctx->stream);
+}
+
+static dsmc_status upload_cfg(dsmc_ctx* ctx)
+{
+    CK(cudaMemcpyAsync(ctx->d_cfg, &ctx->hcfg, sizeof(Cfg), cudaMemcpyHostToDevice, ctx->stream));
+    return DSMC_OK;
+}
+
+static dsmc_status reset_counters(dsmc_ctx* ctx)
+{
+    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    return DSMC_OK;
+}
+
+static dsmc_status read_counters(dsmc_ctx* ctx, Counters* h)
+{
+    CK(cudaMemcpyAsync(h, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DSMC_OK;
+}
+
+static void fill_stats(dsmc_ctx* ctx, const Counters& h)
+{
+    dsmc_stats& s = ctx->stats;
+    s.particle_steps = h.particle_steps;
+    s.generated = h.generated;
+    s.removed = h.removed;
+    s.wall_hits = h.wall_hits;
+    s.candidates = h.candidates;
+    s.collisions = h.collisions;
+    s.clamps = h.clamps;
+    s.bounce_limit = h.bounce_limit;
+    s.reject_limit = h.reject_limit;
+    s.error_word = h.error;
+    s.capacity = ctx->cap_old;
+}
+
+static dsmc_status check_error_word(dsmc_ctx* ctx, uint32_t e)
+{
+    if (!e) return DSMC_OK;
+    char buf[256];
+    std::snprintf(buf, sizeof buf,
+                  "device error word 0x%x (pool=%d gen=%d bigcell=%d biglist=%d); "
+                  "raise capacity_factor / capacity_per_run",
+                  e, !!(e & DSMC_ERR_POOL), !!(e & DSMC_ERR_GEN), !!(e & DSMC_ERR_BIGCELL),
+                  !!(e & DSMC_ERR_BIGLIST));
+    ctx->err = buf;
+    return DSMC_E_CAPACITY;
+}
+
+static dsmc_status validate_run(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                                const int32_t* ss, int n_samples)
+{
+    if (n_runs < 1 || n_runs > (1 << 20)) return fail(ctx, DSMC_E_INVALID, "n_runs out of range");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, DSMC_E_INVALID, "dt must be > 0");
+    if (steps < 0 || steps > (1 << 26)) return fail(ctx, DSMC_E_INVALID, "steps out of range");
+    if (n_samples < 0 || n_samples > kMaxSamples || (n_samples > 0 && !ss))
+        return fail(ctx, DSMC_E_INVALID, "bad sample list");
+    for (int k = 0; k < n_samples; ++k)
+        if (ss[k] < 1 || ss[k] > steps || (k > 0 && ss[k] <= ss[k - 1]))
+            return fail(ctx, DSMC_E_INVALID, "sample_steps must be increasing in [1, steps]");
+    return DSMC_OK;
+}
+
+// set up everything a run needs up to (not including) the step-0 state
+static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, const int32_t* ss,
+                           int n_samples, uint64_t seed, int n_launch)
+{
+    dsmc_status st = build_cfg(ctx, dt, seed);
+    if (st) return st;
+    ctx->G = std::min(n_runs, DSMC_MAX_GROUPS);
+    const int64_t cap_run = estimate_per_run(ctx, steps);
+    st = ensure_alloc(ctx, n_launch, cap_run, steps, n_samples, ctx->G);
+    if (st) return st;
+    st = upload_cfg(ctx);
+    if (st) return st;
+    std::vector<int32_t> slot(steps + 2, -1);
+    for (int k = 0; k < n_samples; ++k) slot[ss[k]] = k;
+    CK(cudaMemcpyAsync(ctx->sample_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    // the upload source is a host vector: finish before it goes away
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemsetAsync(ctx->acc, 0,
+                       8 * (size_t)std::max(n_samples, 1) * ctx->G * ctx->ncells * DSMC_NMOM,
+                       ctx->stream));
+    if (ctx->cand) {
+        CK(cudaMemsetAsync(ctx->cand, 0, 4 * ctx->total_cells, ctx->stream));
+        CK(cudaMemsetAsync(ctx->accd, 0, 4 * ctx->total_cells, ctx->stream));
+    }
+    st = reset_counters(ctx);
+    if (st) return st;
+    CK(prepare_kernels(ctx->prec, ctx->dim));
+    return DSMC_OK;
+}
+
+static dsmc_status build_graphs(dsmc_ctx* ctx, int n_runs)
+{
+    const uint64_t key = (ctx->generation << 24) ^ (uint64_t)n_runs;
+    if (ctx->graph_key == key && ctx->gexec[0] && ctx->gexec[1]) return DSMC_OK;
+    for (int k = 0; k < 2; ++k)
+        if (ctx->gexec[k]) { cudaGraphExecDestroy(ctx->gexec[k]); ctx->gexec[k] = nullptr; }
+    for (int p = 0; p < 2; ++p) {
+        AnyArgs u;
+        const void* args = build_args(ctx, u, p, 0, n_runs);
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(ctx, args, nullptr);
+        CK(cudaStreamEndCapture(ctx->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&ctx->gexec[p], g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    ctx->graph_key = key;
+    return DSMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI (C linkage comes from the declarations in dsmc.h)
+
+dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, const dsmc_gas* gas,
+                        const dsmc_boundary* b, int n_b, const dsmc_options* opt, dsmc_ctx** out)
+{
+    if (!out) return DSMC_E_INVALID;
+    *out = nullptr;
+    if (!domain || !cells || !gas || (n_b > 0 && !b) || n_b < 0 || n_b > DSMC_MAX_BC)
+        return DSMC_E_INVALID;
+    if (domain->struct_size < sizeof(dsmc_domain) || cells->struct_size < sizeof(dsmc_cells) ||
+        gas->struct_size < sizeof(dsmc_gas) || (opt && opt->struct_size < sizeof(dsmc_options)))
+        return DSMC_E_INVALID;
+    if (domain->dim != 2 && domain->dim != 3) return DSMC_E_INVALID;
+    for (int a = 0; a < domain->dim; ++a)
+        if (cells->n[a] < 1 || !(domain->extent[a] > 0.0)) return DSMC_E_INVALID;
+    if (domain->dim == 2 && !(domain->extent[2] > 0.0)) return DSMC_E_INVALID;
+    const int64_t nc = (int64_t)cells->n[0] * cells->n[1] * (domain->dim == 3 ? cells->n[2] : 1);
+    if (nc > (1 << 28)) return DSMC_E_INVALID;
+    if (!(gas->mass > 0.0) || !(gas->d_ref >= 0.0) || !(gas->F_N > 0.0) || !(gas->T_ref > 0.0) ||
+        !(gas->omega >= 0.5 && gas->omega <= 1.0))
+        return DSMC_E_INVALID;
+    if (domain->fill && !(domain->fill_n >= 0.0 && domain->fill_T > 0.0)) return DSMC_E_INVALID;
+    for (int q = 0; q < n_b; ++q) {
+        const dsmc_boundary& s = b[q];
+        if (s.struct_size < sizeof(dsmc_boundary)) return DSMC_E_INVALID;
+        if (s.kind < 0 || s.kind > 3) return DSMC_E_INVALID;
+        if (s.face == DSMC_FACE_PLATE) {
+            if (s.kind != DSMC_BC_SPECULAR && s.kind != DSMC_BC_DIFFUSE) return DSMC_E_INVALID;
+            if (s.plate_axis < 0 || s.plate_axis >= domain->dim) return DSMC_E_INVALID;
+            if (s.plate_index < 0 || s.plate_index > cells->n[s.plate_axis]) return DSMC_E_INVALID;
+        } else if (s.face < 0 || s.face >= 2 * domain->dim) {
+            return DSMC_E_INVALID;
+        }
+        if ((s.kind == DSMC_BC_DIFFUSE || s.kind == DSMC_BC_INFLOW) && !(s.T > 0.0))
+            return DSMC_E_INVALID;
+        if (s.kind == DSMC_BC_INFLOW && !(s.n >= 0.0)) return DSMC_E_INVALID;
+        if (s.lo[0] < 0 || s.hi[0] < s.lo[0] || s.lo[1] < 0 || s.hi[1] < s.lo[1]) return DSMC_E_INVALID;
+        const int ax = s.face == DSMC_FACE_PLATE ? s.plate_axis : s.face / 2;
+        const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
+        const int n0 = cells->n[t0], n1 = t1 < domain->dim ? cells->n[t1] : 1;
+        if (s.hi[0] > n0 || s.hi[1] > n1) return DSMC_E_INVALID;
+        if (s.step_from < 0 || s.step_to < 0) return DSMC_E_INVALID;
+    }
+    dsmc_ctx* ctx = new (std::nothrow) dsmc_ctx();
+    if (!ctx) return DSMC_E_OOM;
+    ctx->dom = *domain;
+    ctx->cells = *cells;
+    if (domain->dim == 2) ctx->cells.n[2] = 1;
+    ctx->gas = *gas;
+    ctx->bcs.assign(b, b + n_b);
+    std::memset(&ctx->opt, 0, sizeof(ctx->opt));
+    ctx->opt.struct_size = sizeof(dsmc_options);
+    ctx->opt.use_graph = 1;
+    if (opt) ctx->opt = *opt;
+    ctx->opt.struct_size = sizeof(dsmc_options);
+    ctx->prec = ctx->opt.precision == DSMC_FP64 ? DSMC_FP64 : DSMC_FP32;
+    ctx->dim = domain->dim;
+    ctx->ncells = (int)nc;
+    ctx->device = ctx->opt.device;
+    std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.struct_size = sizeof(dsmc_stats);
+    if ((ctx->opt.alloc == nullptr) != (ctx->opt.free == nullptr)) {
+        delete ctx;
+        return DSMC_E_INVALID;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return DSMC_E_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return DSMC_E_CUDA;
+    }
+    ctx->sms = prop.multiProcessorCount;
+    if (ctx->opt.stream) {
+        ctx->stream = (cudaStream_t)ctx->opt.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return DSMC_E_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    compute_launch_shape(ctx->prec, ctx->dim, ctx->sms, &ctx->ls);
+    *out = ctx;
+    return DSMC_OK;
+}
+
+void dsmc_destroy(dsmc_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_all(ctx);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* dsmc_last_error(const dsmc_ctx* ctx)
+{
+    if (!ctx) return g_static_err;
+    return ctx->err.c_str();
+}
+
+dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                              const int32_t* sample_steps, int n_samples, uint64_t seed)
+{
+    if (!ctx) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    dsmc_status st = validate_run(ctx, n_runs, dt, steps, sample_steps, n_samples);
+    if (st) return st;
+    ctx->have_run = false;
+    ctx->dbg = false;
+    const bool plain = ctx->opt.mode == DSMC_MODE_PLAIN;
+    const int n_launch = plain ? 1 : n_runs;
+    st = prepare(ctx, n_runs, dt, steps, sample_steps, n_samples, seed, n_launch);
+    if (st) return st;
+    const bool profile = ctx->opt.profile != 0;
+    const bool graph = !plain && !profile && ctx->opt.use_graph;
+    if (graph) {
+        st = build_graphs(ctx, n_runs);
+        if (st) return st;
+    }
+    for (int k = 0; k < 12; ++k) {
+        ctx->stats.ms_kernel[k] = 0.0;
+        ctx->stats.launches_kernel[k] = 0;
+    }
+    cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
+    if (!e0 || !e1) return fail(ctx, DSMC_E_CUDA, "cudaEventCreate failed");
+    size_t evn = 2;
+    float ms_init = 0.f;
+    CK(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < (plain ? n_runs : 1); ++r) {
+        AnyArgs u;
+        const void* a0 = build_args(ctx, u, 0, plain ? r : 0, n_launch);
+        enqueue_init(ctx, a0);
+        ctx->cur = 0;
+        if (r == 0) {
+            // the timed step loop starts after the step-0 state of run 0
+            CK(cudaEventRecord(e1, ctx->stream));
+        }
+        for (int s = 1; s <= steps; ++s) {
+            if (graph) {
+                CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
+            } else {
+                AnyArgs v;
+                const void* a = build_args(ctx, v, ctx->cur, plain ? r : 0, n_launch);
+                enqueue_step(ctx, a, profile ? &evn : nullptr);
+            }
+            ctx->cur ^= 1;
+        }
+    }
+    cudaEvent_t e2 = event_at(ctx, evn);
+    if (!e2) return fail(ctx, DSMC_E_CUDA, "cudaEventCreate failed");
+    CK(cudaEventRecord(e2, ctx->stream));
+    CK(cudaGetLastError());
+    Counters h;
+    st = read_counters(ctx, &h);
+    if (st) return st;
+    CK(cudaEventElapsedTime(&ms_init, e0, e1));
+    float ms_all = 0.f;
+    CK(cudaEventElapsedTime(&ms_all, e1, e2));
+    ctx->stats.ms_steps = ms_all;
+    if (profile) {
+        // events 2.. are recorded after each kernel, in enqueue order
+        size_t i = 2;
+        cudaEvent_t prev = e1;
+        for (int r = 0; r < (plain ? n_runs : 1); ++r) {
+            for (int s = 1; s <= steps; ++s)
+                for (int k = 0; k < kStepKernels; ++k, ++i) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, prev, ctx->events[i]);
+                    ctx->stats.ms_kernel[kKindOf[k]] += ms;
+                    ctx->stats.launches_kernel[kKindOf[k]] += 1;
+                    prev = ctx->events[i];
+                }
+        }
+    }
+    fill_stats(ctx, h);
+    ctx->stats.steps_done = steps;
+    uint32_t total = 0;
+    CK(cudaMemcpy(&total, ctx->run_base + n_launch, 4, cudaMemcpyDeviceToHost));
+    ctx->stats.particles_now = total;
+    st = check_error_word(ctx, h.error);
+    if (st) return st;
+    ctx->have_run = true;
+    ctx->last_runs = n_runs;
+    ctx->last_steps = steps;
+    ctx->last_samples = n_samples;
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_get_samples(dsmc_ctx* ctx, int sample_idx, dsmc_quantity q, double* out,
+                             size_t out_len)
+{
+    if (!ctx) return DSMC_E_INVALID;
+    if (!ctx->have_run) return fail(ctx, DSMC_E_STATE, "no completed run");
+    if (sample_idx < 0 || sample_idx >= ctx->last_samples || !out)
+        return fail(ctx, DSMC_E_INVALID, "bad sample index or output");
+    CK(cudaSetDevice(ctx->device));
+    const size_t nc = (size_t)ctx->ncells;
+    if (q == DSMC_Q_RAW_MOMENTS) {
+        const size_t n = (size_t)ctx->G * nc * DSMC_NMOM;
+        if (out_len < n) return fail(ctx, DSMC_E_INVALID, "out_len too small");
+        CK(cudaMemcpyAsync(out, ctx->acc + (size_t)sample_idx * n, 8 * n, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DSMC_OK;
+    }
+    int off, width;
+    switch (q) {
+    case DSMC_Q_DENSITY: off = 0; width = 1; break;
+    case DSMC_Q_VELOCITY: off = 1; width = 3; break;
+    case DSMC_Q_TEMPERATURE: off = 4; width = 1; break;
+    case DSMC_Q_STDERR_DENSITY: off = 5; width = 1; break;
+    case DSMC_Q_STDERR_VELOCITY: off = 6; width = 3; break;
+    case DSMC_Q_STDERR_TEMPERATURE: off = 9; width = 1; break;
+    default: return fail(ctx, DSMC_E_INVALID, "unknown quantity");
+    }
+    if (out_len < nc * width) return fail(ctx, DSMC_E_INVALID, "out_len too small");
+    AnyArgs u;
+    const void* a = build_args(ctx, u, ctx->cur, 0, ctx->n_launch);
+    launch_macro(ctx->prec, a, sample_idx, ctx->last_runs, ctx->macro, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpy2DAsync(out, 8 * width, ctx->macro + off, 8 * 10, 8 * width, nc,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_get_stats(dsmc_ctx* ctx, dsmc_stats* out)
+{
+    if (!ctx || !out || out->struct_size < sizeof(dsmc_stats)) return DSMC_E_INVALID;
+    *out = ctx->stats;
+    out->struct_size = sizeof(dsmc_stats);
+    return DSMC_OK;
+}
+
+// ---- test hooks -------------------------------------------------------------
+
+dsmc_status dsmc_debug_begin(dsmc_ctx* ctx, int n_runs, double dt, uint64_t seed)
+{
+    if (!ctx) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    dsmc_status st = validate_run(ctx, n_runs, dt, 0, nullptr, 0);
+    if (st) return st;
+    const int steps = 4096;
+    st = prepare(ctx, n_runs, dt, steps, nullptr, 0, seed, n_runs);
+    if (st) return st;
+    AnyArgs u;
+    enqueue_init(ctx, build_args(ctx, u, 0, 0, n_runs));
+    ctx->cur = 0;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->dbg = true;
+    ctx->have_run = false;
+    ctx->last_runs = n_runs;
+    ctx->prev_run_base.assign(n_runs + 1, 0);
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_debug_step(dsmc_ctx* ctx, int n_steps)
+{
+    if (!ctx || n_steps < 0) return DSMC_E_INVALID;
+    if (!ctx->dbg) return fail(ctx, DSMC_E_STATE, "dsmc_debug_begin first");
+    CK(cudaSetDevice(ctx->device));
+    const int n = ctx->n_launch;
+    for (int s = 0; s < n_steps; ++s) {
+        CK(cudaMemcpy(ctx->prev_run_base.data(), ctx->run_base, 4 * (n + 1), cudaMemcpyDeviceToHost));
+        AnyArgs u;
+        enqueue_step(ctx, build_args(ctx, u, ctx->cur, 0, n), nullptr);
+        ctx->cur ^= 1;
+    }
+    CK(cudaGetLastError());
+    Counters h;
+    dsmc_status st = read_counters(ctx, &h);
+    if (st) return st;
+    fill_stats(ctx, h);
+    return check_error_word(ctx, h.error);
+}
+
+template <typename T>
+static dsmc_status get_run_state(dsmc_ctx* ctx, int run, std::vector<double>& x,
+                                 std::vector<double>& v, std::vector<uint32_t>& id)
+{
+    uint32_t rb[2];
+    CK(cudaMemcpy(rb, ctx->run_base + run, 8, cudaMemcpyDeviceToHost));
+    if (rb[1] < rb[0] || (int64_t)rb[1] > ctx->cap_old)
+        return fail(ctx, DSMC_E_CAPACITY, "pool overflowed: state not available");
+    const size_t n = rb[1] - rb[0];
+    x.assign(3 * n, 0.0);
+    v.assign(3 * n, 0.0);
+    id.assign(n, 0);
+    std::vector<T> tmp(n);
+    for (int a = 0; a < 3; ++a) {
+        if (ctx->X[ctx->cur][a]) {
+            CK(cudaMemcpy(tmp.data(), (T*)ctx->X[ctx->cur][a] + rb[0], sizeof(T) * n,
+                          cudaMemcpyDeviceToHost));
+            for (size_t k = 0; k < n; ++k) x[3 * k + a] = (double)tmp[k];
+        }
+        CK(cudaMemcpy(tmp.data(), (T*)ctx->V[ctx->cur][a] + rb[0], sizeof(T) * n,
+                      cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < n; ++k) v[3 * k + a] = (double)tmp[k];
+    }
+    CK(cudaMemcpy(id.data(), ctx->ID[ctx->cur] + rb[0], 4 * n, cudaMemcpyDeviceToHost));
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_debug_get_state(dsmc_ctx* ctx, int run, double* x, double* v, uint32_t* id,
+                                 int64_t cap, int64_t* n_out)
+{
+    if (!ctx || !ctx->n_launch || run < 0 || run >= ctx->n_launch || !n_out) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> hx, hv;
+    std::vector<uint32_t> hid;
+    dsmc_status st = ctx->prec == DSMC_FP64 ? get_run_state<double>(ctx, run, hx, hv, hid)
+                                            : get_run_state<float>(ctx, run, hx, hv, hid);
+    if (st) return st;
+    const int64_t n = (int64_t)hid.size();
+    *n_out = n;
+    const int64_t m = std::min(n, cap);
+    if (x) std::memcpy(x, hx.data(), 8 * 3 * m);
+    if (v) std::memcpy(v, hv.data(), 8 * 3 * m);
+    if (id) std::memcpy(id, hid.data(), 4 * m);
+    return DSMC_OK;
+}
+
+template <typename T>
+static dsmc_status set_run_state(dsmc_ctx* ctx, int run, int64_t n, const double* x, const double* v,
+                                 const uint32_t* id, uint32_t next_id)
+{
+    const int nl = ctx->n_launch;
+    std::vector<uint32_t> rb(nl + 1), nid(nl);
+    CK(cudaMemcpy(rb.data(), ctx->run_base, 4 * (nl + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nid.data(), ctx->next_id, 4 * nl, cudaMemcpyDeviceToHost));
+    if ((int64_t)rb[nl] > ctx->cap_old) return fail(ctx, DSMC_E_CAPACITY, "pool overflowed");
+    const size_t old_total = rb[nl];
+    std::vector<std::vector<T>> X(3), V(3);
+    std::vector<uint32_t> I(old_total);
+    for (int a = 0; a < 3; ++a) {
+        X[a].resize(old_total);
+        V[a].resize(old_total);
+        if (ctx->X[ctx->cur][a])
+            CK(cudaMemcpy(X[a].data(), ctx->X[ctx->cur][a], sizeof(T) * old_total, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(V[a].data(), ctx->V[ctx->cur][a], sizeof(T) * old_total, cudaMemcpyDeviceToHost));
+    }
+    CK(cudaMemcpy(I.data(), ctx->ID[ctx->cur], 4 * old_total, cudaMemcpyDeviceToHost));
+    std::vector<std::vector<T>> NX(3), NV(3);
+    std::vector<uint32_t> NI;
+    std::vector<uint32_t> nrb(nl + 1, 0);
+    for (int r = 0; r < nl; ++r) {
+        nrb[r] = (uint32_t)NI.size();
+        if (r == run) {
+            for (int64_t k = 0; k < n; ++k) {
+                for (int a = 0; a < 3; ++a) {
+                    NX[a].push_back((T)x[3 * k + a]);
+                    NV[a].push_back((T)v[3 * k + a]);
+                }
+                NI.push_back(id[k]);
+            }
+        } else {
+            for (size_t k = rb[r]; k < rb[r + 1]; ++k) {
+                for (int a = 0; a < 3; ++a) {
+                    NX[a].push_back(X[a][k]);
+                    NV[a].push_back(V[a][k]);
+                }
+                NI.push_back(I[k]);
+            }
+        }
+    }
+    nrb[nl] = (uint32_t)NI.size();
+    if ((int64_t)NI.size() > ctx->cap_old) return fail(ctx, DSMC_E_CAPACITY, "state exceeds pool capacity");
+    const size_t tot = NI.size();
+    for (int a = 0; a < 3; ++a) {
+        if (ctx->X[ctx->cur][a] && tot)
+            CK(cudaMemcpy(ctx->X[ctx->cur][a], NX[a].data(), sizeof(T) * tot, cudaMemcpyHostToDevice));
+        if (tot) CK(cudaMemcpy(ctx->V[ctx->cur][a], NV[a].data(), sizeof(T) * tot, cudaMemcpyHostToDevice));
+    }
+    if (tot) CK(cudaMemcpy(ctx->ID[ctx->cur], NI.data(), 4 * tot, cudaMemcpyHostToDevice));
+    nid[run] = next_id;
+    CK(cudaMemcpy(ctx->run_base, nrb.data(), 4 * (nl + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->next_id, nid.data(), 4 * nl, cudaMemcpyHostToDevice));
+    // the next scatter walks the pre-step pool: its size lives at start[total + 1]
+    CK(cudaMemcpy(ctx->start + ctx->total_cells + 1, &nrb[nl], 4, cudaMemcpyHostToDevice));
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_debug_set_state(dsmc_ctx* ctx, int run, int64_t n, const double* x, const double* v,
+                                 const uint32_t* id, uint32_t next_id)
+{
+    if (!ctx || !ctx->dbg || run < 0 || run >= ctx->n_launch || n < 0 || (n > 0 && (!x || !v || !id)))
+        return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ctx->prec == DSMC_FP64 ? set_run_state<double>(ctx, run, n, x, v, id, next_id)
+                                  : set_run_state<float>(ctx, run, n, x, v, id, next_id);
+}
+
+dsmc_status dsmc_debug_get_cells(dsmc_ctx* ctx, int run, int32_t* count, int32_t* cand,
+                                 int32_t* accepted, int64_t* lcr, int64_t cap)
+{
+    if (!ctx || !ctx->dbg || run < 0 || run >= ctx->n_launch) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int nc = ctx->ncells;
+    std::vector<uint32_t> st(nc + 1);
+    CK(cudaMemcpy(st.data(), ctx->start + (size_t)run * nc, 4 * (nc + 1), cudaMemcpyDeviceToHost));
+    if ((int64_t)st[nc] > ctx->cap_old) return fail(ctx, DSMC_E_CAPACITY, "pool overflowed");
+    if (count)
+        for (int c = 0; c < nc; ++c) count[c] = (int32_t)(st[c + 1] - st[c]);
+    if (cand || accepted || lcr) {
+        if (!ctx->cand) return fail(ctx, DSMC_E_STATE, "options.debug was not set");
+        std::vector<uint32_t> tmp(nc);
+        if (cand) {
+            CK(cudaMemcpy(tmp.data(), ctx->cand + (size_t)run * nc, 4 * nc, cudaMemcpyDeviceToHost));
+            for (int c = 0; c < nc; ++c) cand[c] = (int32_t)tmp[c];
+        }
+        if (accepted) {
+            CK(cudaMemcpy(tmp.data(), ctx->accd + (size_t)run * nc, 4 * nc, cudaMemcpyDeviceToHost));
+            for (int c = 0; c < nc; ++c) accepted[c] = (int32_t)tmp[c];
+        }
+        if (lcr) {
+            const size_t n = st[nc] - st[0];
+            std::vector<uint32_t> sl(n);
+            if (n)
+                CK(cudaMemcpy(sl.data(), ctx->lcr_dbg + st[0], 4 * n, cudaMemcpyDeviceToHost));
+            const uint32_t b0 = ctx->prev_run_base[run];
+            const uint32_t n_old = ctx->prev_run_base[run + 1] - b0;
+            const uint64_t gen0 = (uint64_t)ctx->cap_old + (uint64_t)run * ctx->gcap;
+            for (size_t k = 0; k < n && (int64_t)k < cap; ++k) {
+                const uint64_t s = sl[k];
+                lcr[k] = s < (uint64_t)ctx->cap_old ? (int64_t)(s - b0) : (int64_t)(n_old + (s - gen0));
+            }
+        }
+    }
+    return DSMC_OK;
+}
+
+template <typename T>
+static dsmc_status cell_state_io(dsmc_ctx* ctx, int run, double* rem, double* smax, bool get)
+{
+    const size_t nc = ctx->ncells, off = (size_t)run * nc;
+    std::vector<T> tmp(nc);
+    if (get) {
+        if (rem) CK(cudaMemcpy(rem, ctx->rem + off, 8 * nc, cudaMemcpyDeviceToHost));
+        if (smax) {
+            CK(cudaMemcpy(tmp.data(), (T*)ctx->smax + off, sizeof(T) * nc, cudaMemcpyDeviceToHost));
+            for (size_t c = 0; c < nc; ++c) smax[c] = (double)tmp[c];
+        }
+    } else {
+        if (rem) CK(cudaMemcpy(ctx->rem + off, rem, 8 * nc, cudaMemcpyHostToDevice));
+        if (smax) {
+            for (size_t c = 0; c < nc; ++c) tmp[c] = (T)smax[c];
+            CK(cudaMemcpy((T*)ctx->smax + off, tmp.data(), sizeof(T) * nc, cudaMemcpyHostToDevice));
+        }
+    }
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_debug_get_cell_state(dsmc_ctx* ctx, int run, double* rem, double* smax)
+{
+    if (!ctx || !ctx->n_launch || run < 0 || run >= ctx->n_launch) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ctx->prec == DSMC_FP64 ? cell_state_io<double>(ctx, run, rem, smax, true)
+                                  : cell_state_io<float>(ctx, run, rem, smax, true);
+}
+
+dsmc_status dsmc_debug_set_cell_state(dsmc_ctx* ctx, int run, const double* rem, const double* smax)
+{
+    if (!ctx || !ctx->dbg || run < 0 || run >= ctx->n_launch) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ctx->prec == DSMC_FP64
+               ? cell_state_io<double>(ctx, run, const_cast<double*>(rem), const_cast<double*>(smax), false)
+               : cell_state_io<float>(ctx, run, const_cast<double*>(rem), const_cast<double*>(smax), false);
+}
+
+dsmc_status dsmc_debug_sample(dsmc_ctx* ctx, int run, double* mom)
+{
+    if (!ctx || !ctx->dbg || run < 0 || run >= ctx->n_launch || !mom) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    AnyArgs u;
+    launch_sample_now(ctx->prec, build_args(ctx, u, ctx->cur, 0, ctx->n_launch), ctx->stream);
+    CK(cudaGetLastError());
+    const size_t per = (size_t)ctx->ncells * DSMC_NMOM;
+    CK(cudaMemcpyAsync(mom, ctx->mom + (size_t)run * per, 8 * per, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out)
+{
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return DSMC_E_INVALID;
+    if (n == 0) return DSMC_OK;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    if (cudaMalloc(&dc, 16 * n) != cudaSuccess || cudaMalloc(&dk, 8 * n) != cudaSuccess ||
+        cudaMalloc(&dout, 16 * n) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dc); cudaFree(dk); cudaFree(dout);
+        return DSMC_E_OOM;
+    }
+    dsmc_status st = DSMC_OK;
+    if (cudaMemcpy(dc, ctr, 16 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dk, key, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        philox_device(n, dc, dk, dout, 0) != cudaSuccess ||
+        cudaMemcpy(out, dout, 16 * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        st = DSMC_E_CUDA;
+    }
+    cudaFree(dc); cudaFree(dk); cudaFree(dout);
+    return st;
+}
+

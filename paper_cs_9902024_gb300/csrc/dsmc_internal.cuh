@@ -1,0 +1,129 @@
+// dsmc_internal.cuh -- types shared by the host engine and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dsmc.h"
+
+namespace dsmc {
+
+constexpr uint32_t kDead = 0xFFFFFFFFu;   // cell key of a particle that left
+constexpr int kMaxBounce = 16;            // surface events per particle and step
+constexpr int kGenBlocks = 64;            // Philox blocks per generated particle
+constexpr int kWarpMax = 128;             // cells up to this size: one warp each
+constexpr int kCellWarps = 8;             // warps per CTA of the cell kernel
+constexpr int kScanTile = 4096;           // cells per CTA of the scan
+constexpr int kScanThreads = 1024;
+constexpr int kMaxSamples = 4096;
+
+// Philox counter word 1 carries the purpose of a draw in its top 4 bits.
+enum Purpose : uint32_t {
+    kFillCount = 1, kFillPart = 2, kGenCount = 3, kGenPart = 4, kWall = 5, kColl = 6
+};
+
+// One boundary segment with the constants the kernels derive from it (all
+// computed once on the host in double precision).
+struct BcDev {
+    int32_t kind, face, lo[2], hi[2], step_from, step_to, plate_axis, plate_index;
+    int32_t axis, side, t0, t1;      // normal axis, side, tangential axes
+    int32_t elem_w;                  // inflow: elements along the first tangent
+    int32_t pad_;
+    int64_t elem_base;               // inflow: first element number
+    int64_t n_elem;                  // inflow: element count
+    double T, U[3];
+    double lam;    // inflow: expected entrants per element and step
+    double cmp;    // inflow: most probable speed sqrt(2kT/m)
+    double sd;     // sqrt(kT/m): tangential spread (inflow), wall (diffuse)
+    double s;      // inflow: inward normal speed ratio U_n / c_mp
+    double xm;     // inflow: mode of the entrant speed-ratio density
+    double dir;    // +1 on a side-0 face, -1 on a side-1 face
+    double xp;     // plate: plane coordinate
+    double tlo[2], thi[2];   // plate: tangential rectangle
+};
+
+struct Cfg {
+    int32_t dim, n[3], ncells, n_bc, n_plate, hs, fill, pad_;
+    int32_t plate_idx[DSMC_MAX_BC];
+    double L[3], d[3], Vc, dt, mass;
+    double coef;         // F_N dt / Vc
+    double F_N;
+    double A_hs;         // hard sphere: pi d^2 (sigma_T c_r = A_hs c_r)
+    double K_vhs;        // VHS: sigma_T c_r = K_vhs (c_r^2)^(1 - omega)
+    double one_m_omega;
+    double smax0;        // initial (sigma_T c_r)_max
+    double fill_lam, fill_sd, fill_U[3];
+    int64_t n_elem;      // inflow elements over all segments
+    uint64_t seed;
+    BcDev bc[DSMC_MAX_BC];
+};
+
+struct Counters {
+    unsigned long long particle_steps, generated, removed, wall_hits;
+    unsigned long long candidates, collisions, clamps, bounce_limit, reject_limit;
+    uint32_t error, step, n_big, pad_;
+};
+
+// Device pointers of one step (particle pool double-buffered: in -> out).
+template <typename T>
+struct StepArgs {
+    const Cfg* cfg;
+    Counters* ctr;
+    // pool: in/out buffers of positions (dim used), velocities (3), ids
+    T* xi[3]; T* vi[3]; uint32_t* idi;
+    T* xo[3]; T* vo[3]; uint32_t* ido;
+    uint32_t* gc;          // per slot: run-major cell key, or kDead
+    uint32_t* rank;        // per slot: rank within its cell (any order)
+    uint32_t* lcr;         // per pool position: slot (cell-grouped)
+    uint32_t* lcr_dbg;     // optional: slot of each sorted particle
+    uint32_t* count;       // per cell: particles (atomic target)
+    uint32_t* start;       // per cell (+2): exclusive prefix of count; entry
+                           // total_cells + 1 keeps the pre-step pool size
+    uint32_t* block_sums;
+    uint32_t* run_base;    // per run (+1): first pool position of the run
+    uint32_t* next_id;     // per run
+    double* rem;           // per cell: NTC remainder
+    T* smax;               // per cell: (sigma_T c_r)_max
+    double* mom;           // per cell x 7: moments at sample steps
+    uint32_t* cand;        // optional per cell
+    uint32_t* accd;        // optional per cell
+    uint32_t* big_list;
+    const int32_t* sample_slot;   // per step: sample index or -1
+    double* acc;           // [samples][G][ncells][7]
+    int64_t cap_old, cap_new, gcap, max_big;
+    int32_t n_runs;        // runs in this launch
+    int32_t run0;          // global index of the first run of the launch
+    int32_t G;             // sample groups
+    int32_t total_cells;
+    int32_t scan_blocks;
+};
+
+// Launchers (dsmc_kernels.cu).  `prec` is DSMC_FP32 or DSMC_FP64 and selects
+// the instantiation; `args` points to a StepArgs<float> or StepArgs<double>.
+struct LaunchShape {
+    int dim;
+    int sms;
+    int move_blocks, move_threads;
+    int scatter_blocks, cell_blocks, big_blocks;
+};
+
+void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_fill(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_move(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_step_end(int prec, const void* args, cudaStream_t s);
+void launch_macro(int prec, const void* args, int sample, int n_runs, double* out,
+                  cudaStream_t s);
+void launch_sample_now(int prec, const void* args, cudaStream_t s);
+cudaError_t prepare_kernels(int prec, int dim);
+void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls);
+int big_cell_limit(int prec);
+cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t s);
+
+}  // namespace dsmc

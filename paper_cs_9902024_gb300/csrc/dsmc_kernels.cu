@@ -1,0 +1,1231 @@
+// dsmc_kernels.cu -- sm_103a kernels of the ensemble DSMC step.
+//
+// One time step of all runs of the ensemble (Sec. 1.1, Fig. 1: Generation,
+// Motion, Enumeration/Indexing, Interaction, Sampling) as a fixed sequence
+// of launches over the whole batch of runs:
+//
+//   k_generate   one CTA per run: inflow counts, entrants created and moved
+//                for their first fractional step (Generation + Motion)
+//   k_move       grid-stride over the particle pool: free flight, surface
+//                interaction, new cell key and a rank inside the cell from a
+//                warp-aggregated atomic (Motion + Enumeration)
+//   k_scan1/2    exclusive prefix over the run-major cell counts: each
+//                cell's first pool position, each run's first position
+//                (Indexing)
+//   k_scatter    LCR[start[cell] + rank] = slot  (Indexing)
+//   k_cell       one warp per cell: the cell's particles put in particle-id
+//                order, gathered into the next pool, NTC collisions, and the
+//                cell moments at sample steps (Indexing + Interaction +
+//                Sampling)
+//   k_cell_big   one CTA per cell too large for a warp
+//   k_reduce     fixed-order sum of the runs' cell moments into group
+//                accumulators at sample steps (Sampling)
+//
+// Every random number comes from Philox4x32-10 keyed by the seed with
+// (entity, purpose<<28 | draw, step, run) as the counter, so a particle's
+// history does not depend on the launch shape or on the other runs.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dsmc_internal.cuh"
+
+namespace dsmc {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its definition.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw_bits(uint64_t seed, uint32_t run, uint32_t step,
+                                           uint32_t entity, uint32_t purpose, uint32_t sub)
+{
+    return philox(make_uint4(entity, (purpose << 28) | (sub & 0x0FFFFFFFu), step, run),
+                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// (m + 1/2) / 2^23 from the top 23 bits: exact in float and double
+template <typename T>
+__device__ __forceinline__ T u01(uint32_t x)
+{
+    return ((T)(x >> 9) + (T)0.5) * (T)(1.0 / 8388608.0);
+}
+
+__device__ __forceinline__ float dlog(float x) { return logf(x); }
+__device__ __forceinline__ double dlog(double x) { return log(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dpow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double dpow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float dfloor(float x) { return floorf(x); }
+__device__ __forceinline__ double dfloor(double x) { return floor(x); }
+__device__ __forceinline__ void dsincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void dsincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// Box-Muller pair from two uniforms: sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2)
+template <typename T>
+__device__ __forceinline__ void gauss2(T u1, T u2, T& z0, T& z1)
+{
+    const T r = dsqrt((T)-2.0 * dlog(u1));
+    T s, c;
+    dsincospi((T)2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry helpers
+template <typename T>
+__device__ __forceinline__ int cell_1d(const Cfg& c, int a, T x)
+{
+    if (a >= c.dim) return 0;
+    int i = (int)dfloor(x / (T)c.d[a]);
+    return i < 0 ? 0 : (i > c.n[a] - 1 ? c.n[a] - 1 : i);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ int cell_of(const Cfg& c, const T* x)
+{
+    const int i0 = cell_1d<T>(c, 0, x[0]);
+    const int i1 = cell_1d<T>(c, 1, x[1]);
+    const int i2 = DIM == 3 ? cell_1d<T>(c, 2, x[2]) : 0;
+    return i0 + c.n[0] * (i1 + c.n[1] * i2);
+}
+
+__device__ __forceinline__ bool bc_active(const BcDev& b, int step)
+{
+    return step >= b.step_from && (b.step_to == 0 || step <= b.step_to);
+}
+
+// last listed active segment covering face cell (a, b); -1 = open
+__device__ int bc_lookup(const Cfg& c, int face, int a, int b, int step)
+{
+    int win = -1;
+    for (int q = 0; q < c.n_bc; ++q) {
+        const BcDev& s = c.bc[q];
+        if (s.face != face) continue;
+        if (a < s.lo[0] || a >= s.hi[0] || b < s.lo[1] || b >= s.hi[1]) continue;
+        if (!bc_active(s, step)) continue;
+        win = q;
+    }
+    return win;
+}
+
+struct LocalCounters {
+    uint32_t removed = 0, wall_hits = 0, bounce = 0;
+};
+
+// Motion of one particle for time tau: free flight with the surface events
+// taken in time order (ties: x, y, z faces, then plates in list order).
+// Returns false if the particle left through an open face.  vmask collects
+// the velocity components that changed.
+template <typename T, int DIM>
+__device__ bool move_particle(const Cfg& c, T* x, T* v, uint32_t id, uint32_t run,
+                              uint32_t step, T tau, LocalCounters& lc, uint32_t& vmask)
+{
+    for (int bounce = 0;; ++bounce) {
+        int hit = -1;
+        T th = (T)0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            T t;
+            if (v[a] > (T)0) t = ((T)c.L[a] - x[a]) / v[a];
+            else if (v[a] < (T)0) t = ((T)0 - x[a]) / v[a];
+            else continue;
+            if (t < (T)0) t = (T)0;
+            if (t <= tau && (hit < 0 || t < th)) { hit = 2 * a + (v[a] > (T)0 ? 1 : 0); th = t; }
+        }
+        for (int pi = 0; pi < c.n_plate; ++pi) {
+            const int q = c.plate_idx[pi];
+            const BcDev& b = c.bc[q];
+            if (!bc_active(b, step)) continue;
+            const int a = b.plate_axis;
+            const T xp = (T)b.plate_index * (T)c.d[a];
+            if (!((x[a] < xp && v[a] > (T)0) || (x[a] > xp && v[a] < (T)0))) continue;
+            const T t = (xp - x[a]) / v[a];
+            if (!(t <= tau && (hit < 0 || t < th))) continue;
+            bool inside = true;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int ta = k == 0 ? b.t0 : b.t1;
+                if (ta >= DIM) continue;
+                const T y = x[ta] + v[ta] * t;
+                if (!(y >= (T)b.lo[k] * (T)c.d[ta] && y < (T)b.hi[k] * (T)c.d[ta])) inside = false;
+            }
+            if (inside) { hit = 100 + q; th = t; }
+        }
+        if (hit < 0) {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) x[a] = x[a] + v[a] * tau;
+            return true;
+        }
+        if (bounce == kMaxBounce) { lc.bounce++; return true; }
+        int axis, kind, t0, t1;
+        T dir;
+        double Tsd = 0.0;
+        if (hit < 100) {
+            axis = hit >> 1;
+            const int side = hit & 1;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+                x[a] = (a == axis) ? (side ? (T)c.L[a] : (T)0) : x[a] + v[a] * th;
+            t0 = axis == 0 ? 1 : 0;
+            t1 = axis == 2 ? 1 : 2;
+            const int ia = cell_1d<T>(c, t0, x[t0]);
+            const int ib = cell_1d<T>(c, t1, t1 < DIM ? x[t1] : (T)0);
+            const int q = bc_lookup(c, hit, ia, ib, (int)step);
+            kind = q < 0 ? DSMC_BC_OUTFLOW : c.bc[q].kind;
+            if (q >= 0) Tsd = c.bc[q].sd;
+            dir = side ? (T)-1 : (T)1;
+        } else {
+            const BcDev& b = c.bc[hit - 100];
+            axis = b.plate_axis;
+            t0 = b.t0;
+            t1 = b.t1;
+            const T xp = (T)b.plate_index * (T)c.d[axis];
+            dir = v[axis] > (T)0 ? (T)-1 : (T)1;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) x[a] = (a == axis) ? xp : x[a] + v[a] * th;
+            kind = b.kind;
+            Tsd = b.sd;
+        }
+        tau = tau - th;
+        if (kind == DSMC_BC_OUTFLOW || kind == DSMC_BC_INFLOW) { lc.removed++; return false; }
+        lc.wall_hits++;
+        if (kind == DSMC_BC_SPECULAR) {
+            v[axis] = -v[axis];
+            vmask |= 1u << axis;
+        } else {
+            const uint4 r = draw_bits(c.seed, run, step, id, kWall, (uint32_t)bounce);
+            const T sw = (T)Tsd;
+            T z0, z1;
+            gauss2<T>(u01<T>(r.y), u01<T>(r.z), z0, z1);
+            v[axis] = dir * (sw * dsqrt((T)-2.0 * dlog(u01<T>(r.x))));
+            v[t0] = sw * z0;
+            v[t1] = sw * z1;
+            vmask |= 7u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// warp / block helpers
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ void flush_counters(Counters* ctr, const LocalCounters& lc)
+{
+    const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, lc.removed);
+    const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, lc.wall_hits);
+    const uint32_t b = __reduce_add_sync(0xFFFFFFFFu, lc.bounce);
+    if (lane_id() == 0) {
+        if (r) atomicAdd(&ctr->removed, (unsigned long long)r);
+        if (w) atomicAdd(&ctr->wall_hits, (unsigned long long)w);
+        if (b) atomicAdd(&ctr->bounce_limit, (unsigned long long)b);
+    }
+}
+
+// rank of each valid lane among the lanes of its warp with the same key,
+// plus one atomic per distinct key on count[key]
+__device__ __forceinline__ uint32_t warp_rank(uint32_t* count, uint32_t key, bool valid)
+{
+    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, valid);
+    uint32_t rank = 0;
+    if (valid) {
+        const uint32_t peers = __match_any_sync(mask, key);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t lt = (1u << lane_id()) - 1u;
+        uint32_t base = 0;
+        if ((int)lane_id() == leader) base = atomicAdd(&count[key], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        rank = base + (uint32_t)__popc(peers & lt);
+    }
+    return rank;
+}
+
+// exclusive scan of one value per thread over the block (blockDim <= 1024)
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* smem_warp, uint32_t& total)
+{
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nw ? smem_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) smem_warp[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = warp ? smem_warp[warp - 1] : 0u;
+    total = smem_warp[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t run_of_slot(const uint32_t* run_base, int n_runs, uint32_t s)
+{
+    // largest r with run_base[r] <= s
+    int lo = 0, hi = n_runs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(run_base + mid) <= s) lo = mid; else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
+
+// ---------------------------------------------------------------------------
+// Step-0 state
+template <typename T>
+__global__ void k_init_cells(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.total_cells;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        a.rem[i] = 0.0;
+        a.smax[i] = (T)c.smax0;
+        a.count[i] = 0u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctr->step = 1u;
+        a.ctr->n_big = 0u;
+    }
+}
+
+// freestream fill, part 1: Poisson-rounded count per cell
+template <typename T>
+__global__ void k_fill_count(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.total_cells;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t rl = (uint32_t)(i / c.ncells), cell = (uint32_t)(i - (int64_t)rl * c.ncells);
+        const uint4 r = draw_bits(c.seed, a.run0 + rl, 0u, cell, kFillCount, 0u);
+        a.count[i] = c.fill ? (uint32_t)floor(c.fill_lam + u01<double>(r.x)) : 0u;
+    }
+}
+
+// freestream fill, part 2: one warp per cell writes its particles in
+// (cell, k) order; ids count per run in that order
+template <typename T, int DIM>
+__global__ void k_fill_particles(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    const int lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+         i < a.total_cells; i += warps) {
+        const uint32_t rl = (uint32_t)(i / c.ncells), cell = (uint32_t)(i - (int64_t)rl * c.ncells);
+        const uint32_t beg = a.start[i], N = a.start[i + 1] - beg;
+        if ((int64_t)beg + N > a.cap_old) {
+            if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+            continue;
+        }
+        const int ic[3] = {(int)(cell % c.n[0]), (int)((cell / c.n[0]) % c.n[1]),
+                           (int)(cell / (c.n[0] * c.n[1]))};
+        const T sd = (T)c.fill_sd;
+        for (uint32_t k = lane; k < N; k += 32) {
+            const uint4 b0 = draw_bits(c.seed, a.run0 + rl, 0u, cell, kFillPart, 2u * k);
+            const uint4 b1 = draw_bits(c.seed, a.run0 + rl, 0u, cell, kFillPart, 2u * k + 1u);
+            T z[4];
+            gauss2<T>(u01<T>(b0.x), u01<T>(b0.y), z[0], z[1]);
+            gauss2<T>(u01<T>(b0.z), u01<T>(b0.w), z[2], z[3]);
+            const T ub[3] = {u01<T>(b1.x), u01<T>(b1.y), u01<T>(b1.z)};
+            const uint32_t p = beg + k;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) a.xi[ax][p] = ((T)ic[ax] + ub[ax]) * (T)c.d[ax];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) a.vi[ax][p] = (T)c.fill_U[ax] + sd * z[ax];
+            a.idi[p] = (beg - a.run_base[rl]) + k;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_fill_ids(StepArgs<T> a)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n_runs; r += gridDim.x * blockDim.x)
+        a.next_id[r] = a.run_base[r + 1] - a.run_base[r];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.start[a.total_cells + 1] = a.run_base[a.n_runs];
+}
+
+// ---------------------------------------------------------------------------
+// Generation: one CTA per run.  Elements (inflow face cells) are taken in
+// segment-list order; each element's count is floor(lambda + R); entrants
+// are numbered (ids, new-region slots) in (element, k) order, created from
+// their draws and moved for R_f dt.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    __shared__ uint32_t s_off[257];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t rl = blockIdx.x;
+    const uint32_t run = a.run0 + rl;
+    const uint32_t step = a.ctr->step;
+    const uint32_t n_old = min(a.run_base[rl + 1], (uint32_t)a.cap_old) -
+                           min(a.run_base[rl], (uint32_t)a.cap_old);
+    const uint32_t id0 = a.next_id[rl];
+    const int64_t gen_base = a.cap_old + (int64_t)rl * a.gcap;
+    uint32_t running = 0;
+    LocalCounters lc;
+    uint32_t rejects = 0;
+    bool overflow = false;
+    for (int64_t chunk = 0; chunk < c.n_elem; chunk += blockDim.x) {
+        const int64_t e = chunk + threadIdx.x;
+        uint32_t G = 0;
+        if (e < c.n_elem) {
+            int q = 0;
+            while (!(c.bc[q].kind == DSMC_BC_INFLOW && c.bc[q].face < 6 && e >= c.bc[q].elem_base &&
+                     e < c.bc[q].elem_base + c.bc[q].n_elem))
+                ++q;
+            const BcDev& b = c.bc[q];
+            const int64_t loc = e - b.elem_base;
+            const int aa = b.lo[0] + (int)(loc % b.elem_w), bb = b.lo[1] + (int)(loc / b.elem_w);
+            if (bc_active(b, (int)step) && bc_lookup(c, b.face, aa, bb, (int)step) == q) {
+                const uint4 r = draw_bits(c.seed, run, step, (uint32_t)e, kGenCount, 0u);
+                G = (uint32_t)floor(b.lam + u01<double>(r.x));
+            }
+        }
+        uint32_t total;
+        const uint32_t off = block_exclusive_scan(G, s_warp, total);
+        s_off[threadIdx.x] = off;
+        if (threadIdx.x == 0) s_off[blockDim.x] = total;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < total; j += blockDim.x) {
+            // element of entrant j: last t with s_off[t] <= j
+            int lo = 0, hi = (int)blockDim.x - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+            }
+            const int64_t e2 = chunk + lo;
+            const uint32_t k = j - s_off[lo];
+            const uint32_t local = running + j;
+            if ((int64_t)local >= a.gcap) { overflow = true; continue; }
+            int q = 0;
+            while (!(c.bc[q].kind == DSMC_BC_INFLOW && c.bc[q].face < 6 && e2 >= c.bc[q].elem_base &&
+                     e2 < c.bc[q].elem_base + c.bc[q].n_elem))
+                ++q;
+            const BcDev& b = c.bc[q];
+            const int64_t loc = e2 - b.elem_base;
+            const int aa = b.lo[0] + (int)(loc % b.elem_w), bb = b.lo[1] + (int)(loc / b.elem_w);
+            const uint4 b0 = draw_bits(c.seed, run, step, (uint32_t)e2, kGenPart, k * kGenBlocks);
+            const uint4 b1 = draw_bits(c.seed, run, step, (uint32_t)e2, kGenPart, k * kGenBlocks + 1u);
+            T z0, z1;
+            gauss2<T>(u01<T>(b1.x), u01<T>(b1.y), z0, z1);
+            // inward normal speed ratio: normal proposals about the mode xm
+            // (variance 1/2), kept with probability (x/xm) exp(1 - x/xm)
+            const T xm = (T)b.xm;
+            T xi = xm;
+            bool got = false;
+            for (uint32_t blk = 2; blk < (uint32_t)kGenBlocks && !got; ++blk) {
+                const uint4 rb = draw_bits(c.seed, run, step, (uint32_t)e2, kGenPart, k * kGenBlocks + blk);
+                T zz[2];
+                gauss2<T>(u01<T>(rb.x), u01<T>(rb.y), zz[0], zz[1]);
+                const T ua[2] = {u01<T>(rb.z), u01<T>(rb.w)};
+#pragma unroll
+                for (int att = 0; att < 2; ++att) {
+                    if (got) break;
+                    const T xx = xm + zz[att] * (T)0.70710678118654752440;
+                    if (xx > (T)0 && ua[att] < (xx / xm) * dexp((T)1 - xx / xm)) { xi = xx; got = true; }
+                }
+            }
+            if (!got) rejects++;
+            T x[3] = {(T)0, (T)0, (T)0}, v[3];
+            x[b.axis] = b.side ? (T)c.L[b.axis] : (T)0;
+            x[b.t0] = ((T)aa + u01<T>(b0.x)) * (T)c.d[b.t0];
+            if (b.t1 < DIM) x[b.t1] = ((T)bb + u01<T>(b0.y)) * (T)c.d[b.t1];
+            v[b.axis] = (T)b.dir * (T)b.cmp * xi;
+            v[b.t0] = (T)b.U[b.t0] + (T)b.sd * z0;
+            v[b.t1] = (T)b.U[b.t1] + (T)b.sd * z1;
+            const uint32_t id = id0 + local;
+            const T tau = u01<T>(b0.z) * (T)c.dt;
+            uint32_t vmask = 0;
+            const bool alive = move_particle<T, DIM>(c, x, v, id, run, step, tau, lc, vmask);
+            const int64_t slot = gen_base + local;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) a.xi[ax][slot] = x[ax];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) a.vi[ax][slot] = v[ax];
+            a.idi[slot] = id;
+            uint32_t key = kDead, rk = 0;
+            if (alive) {
+                key = rl * (uint32_t)c.ncells + (uint32_t)cell_of<T, DIM>(c, x);
+                rk = atomicAdd(&a.count[key], 1u);
+            }
+            a.gc[slot] = key;
+            a.rank[slot] = rk;
+        }
+        running += total;
+        __syncthreads();
+    }
+    flush_counters(a.ctr, lc);
+    if (rejects) atomicAdd(&a.ctr->reject_limit, (unsigned long long)rejects);
+    if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_GEN);
+    if (threadIdx.x == 0) {
+        const uint32_t made = running < (uint32_t)a.gcap ? running : (uint32_t)a.gcap;
+        a.next_id[rl] = id0 + running;
+        atomicAdd(&a.ctr->generated, (unsigned long long)made);
+        atomicAdd(&a.ctr->particle_steps, (unsigned long long)(n_old + made));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Motion of the pool: grid-stride, warp-uniform trip count.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    // after a pool overflow (reported through the error word) the recorded
+    // size can exceed the buffers: never walk past them
+    const uint32_t n_total = min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
+    const uint32_t step = a.ctr->step;
+    const T dt = (T)c.dt;
+    LocalCounters lc;
+    const uint32_t lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n_total;
+         base += stride) {
+        const uint32_t s = (uint32_t)(base + lane);
+        const bool valid = s < n_total;
+        uint32_t key = kDead;
+        if (valid) {
+            const uint32_t rl = run_of_slot<T>(a.run_base, a.n_runs, s);
+            T x[3], v[3];
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) { x[ax] = a.xi[ax][s]; v[ax] = a.vi[ax][s]; }
+            if (DIM == 2) { x[2] = (T)0; v[2] = (T)0; }
+            uint32_t vmask = 0;
+            bool alive = true;
+            // fast path: the straight flight ends inside the box by a margin
+            // far above rounding, so the full event search would find no
+            // face crossing and give the same x + v dt
+            const T margin = sizeof(T) == 4 ? (T)1e-5 : (T)1e-12;
+            bool inner = c.n_plate == 0;
+            T y[3];
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) {
+                y[ax] = x[ax] + v[ax] * dt;
+                const T L = (T)c.L[ax];
+                inner = inner && (y[ax] > margin * L) && (y[ax] < L - margin * L);
+            }
+            if (inner) {
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) x[ax] = y[ax];
+            } else {
+                alive = move_particle<T, DIM>(c, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
+            }
+            if (alive) {
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) a.xi[ax][s] = x[ax];
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax)
+                    if (vmask & (1u << ax)) a.vi[ax][s] = v[ax];
+                key = rl * (uint32_t)c.ncells + (uint32_t)cell_of<T, DIM>(c, x);
+            }
+        }
+        const bool live = valid && key != kDead;
+        const uint32_t rk = warp_rank(a.count, key, live);
+        if (valid) {
+            a.gc[s] = key;
+            a.rank[s] = rk;
+        }
+    }
+    flush_counters(a.ctr, lc);
+}
+
+// ---------------------------------------------------------------------------
+// Indexing, part 1: exclusive prefix over the run-major cell counts.
+__global__ void __launch_bounds__(kScanThreads) k_scan1(const uint32_t* __restrict__ count,
+                                                        uint32_t* block_sums, int total)
+{
+    __shared__ uint32_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t v = 0;
+    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+        const int64_t i = base + k;
+        if (i < total) v += count[i];
+    }
+    v = __reduce_add_sync(0xFFFFFFFFu, v);
+    if (lane_id() == 0) s_warp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t s = s_warp[threadIdx.x];
+        s = __reduce_add_sync(0xFFFFFFFFu, s);
+        if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
+{
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_red[32];
+    const int total = a.total_cells;
+    const int ncells = a.cfg->ncells;
+    // prefix of the preceding tiles
+    uint32_t p = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) p += a.block_sums[b];
+    p = __reduce_add_sync(0xFFFFFFFFu, p);
+    if (lane_id() == 0) s_red[threadIdx.x >> 5] = p;
+    __syncthreads();
+    uint32_t prefix = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) prefix += s_red[w];
+    __syncthreads();
+    // each thread: 4 consecutive cells
+    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (i0 + k < total) ? a.count[i0 + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t tile_total;
+    uint32_t ex = block_exclusive_scan(sum, s_warp, tile_total) + prefix;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = i0 + k;
+        if (i < total) {
+            a.start[i] = ex;
+            a.count[i] = 0u;
+            if (i % ncells == 0) a.run_base[i / ncells] = ex;
+        }
+        ex += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        a.start[total] = prefix + tile_total;
+        a.run_base[a.n_runs] = prefix + tile_total;
+    }
+}
+
+// Indexing, part 2: LCR[start[cell] + rank] = slot for every live particle
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
+{
+    // the pool holds run_base[n_runs] particles after this step's scan, but
+    // the slots to scatter are those of the pre-step pool: its size is the
+    // start of the new region's scan (kept by the generate kernel)
+    const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
+    const uint64_t n_all = n_old + (uint64_t)a.cap_new;
+    bool overflow = false;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_all;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t slot = t < n_old ? t : (uint64_t)a.cap_old + (t - n_old);
+        const uint32_t key = a.gc[slot];
+        if (key == kDead) continue;
+        if (slot >= (uint64_t)a.cap_old) a.gc[slot] = kDead;
+        const uint64_t pos = (uint64_t)a.start[key] + a.rank[slot];
+        if (pos >= (uint64_t)a.cap_old) { overflow = true; continue; }
+        a.lcr[pos] = (uint32_t)slot;
+    }
+    if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+}
+
+// ---------------------------------------------------------------------------
+// (sigma_T c_r) of a pair with relative speed squared g2 (and speed g)
+template <typename T>
+__device__ __forceinline__ T sigma_cr(const Cfg& c, T g, T g2)
+{
+    if (c.hs) return (T)c.A_hs * g;
+    if (g2 == (T)0) return (T)0;
+    return (T)c.K_vhs * dpow(g2, (T)c.one_m_omega);
+}
+
+// NTC candidate count of a cell with N particles: FP64 with the remainder
+// carried across steps; N < 2 leaves the remainder unchanged.
+__device__ __forceinline__ int64_t ntc_count(const Cfg& c, uint32_t N, double smax, double& rem)
+{
+    if (N < 2) return 0;
+    const double nn = (double)N * (double)(N - 1u);
+    const double x = 0.5 * nn * c.coef * smax + rem;
+    const double M = floor(x);
+    rem = x - M;
+    return (int64_t)M;
+}
+
+// index floor(u * n) of a uniform u = (m + 1/2) / 2^23, computed exactly
+__device__ __forceinline__ uint32_t pick(uint32_t bits, uint32_t n)
+{
+    const uint64_t m2 = 2ull * (uint64_t)(bits >> 9) + 1ull;
+    return (uint32_t)((m2 * (uint64_t)n) >> 24);
+}
+
+// one accepted collision: isotropic scattering of the relative velocity
+template <typename T>
+__device__ __forceinline__ void scatter_pair(T* v1, T* v2, T g, T u3, T ueps)
+{
+    const T cosx = (T)2.0 * u3 - (T)1.0;
+    const T sinx = dsqrt((T)1.0 - cosx * cosx);
+    T se, ce;
+    dsincospi((T)2.0 * ueps, &se, &ce);
+    const T gr[3] = {g * cosx, g * sinx * ce, g * sinx * se};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const T cm = (T)0.5 * (v1[ax] + v2[ax]);
+        v1[ax] = cm + (T)0.5 * gr[ax];
+        v2[ax] = cm - (T)0.5 * gr[ax];
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+// Interaction of one cell whose velocities sit in s_v[3][*] in id order;
+// all lanes of the warp call it; lane 0 does the sequential candidates.
+template <typename T>
+__device__ void collide_cell_warp(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t N, int64_t M,
+                                  T smax, uint32_t cell, uint32_t run, uint32_t step,
+                                  T& seen, uint32_t& nacc, uint32_t& nclamp)
+{
+    const uint32_t lane = lane_id();
+    for (int64_t kb = 0; kb < M; kb += 32) {
+        const int64_t k = kb + lane;
+        uint32_t ci = 0, cj = 0;
+        T u2 = (T)1, u3 = (T)0, ue = (T)0;
+        if (k < M) {
+            const uint4 r = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k));
+            const uint4 r2 = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k + 1));
+            ci = pick(r.x, N);
+            cj = pick(r.y, N - 1u);
+            if (cj >= ci) cj += 1u;
+            u2 = u01<T>(r.z);
+            u3 = u01<T>(r.w);
+            ue = u01<T>(r2.x);
+        }
+        const int cnt = (M - kb) < 32 ? (int)(M - kb) : 32;
+        for (int q = 0; q < cnt; ++q) {
+            const uint32_t i = __shfl_sync(0xFFFFFFFFu, ci, q);
+            const uint32_t j = __shfl_sync(0xFFFFFFFFu, cj, q);
+            const T U2 = __shfl_sync(0xFFFFFFFFu, u2, q);
+            const T U3 = __shfl_sync(0xFFFFFFFFu, u3, q);
+            const T UE = __shfl_sync(0xFFFFFFFFu, ue, q);
+            if (lane == 0) {
+                T v1[3] = {sv0[i], sv1[i], sv2[i]};
+                T v2[3] = {sv0[j], sv1[j], sv2[j]};
+                const T gx = v1[0] - v2[0], gy = v1[1] - v2[1], gz = v1[2] - v2[2];
+                const T g2 = gx * gx + gy * gy + gz * gz;
+                const T g = dsqrt(g2);
+                const T sc = sigma_cr<T>(c, g, g2);
+                if (sc > seen) seen = sc;
+                if (sc > smax) nclamp++;
+                if (U2 < sc / smax) {
+                    scatter_pair<T>(v1, v2, g, U3, UE);
+                    sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
+                    sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
+                    nacc++;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// One warp per cell: gather in id order, collide, sample, write the next pool.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kCellWarps * 32) k_cell(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    __shared__ uint32_t s_slot[kCellWarps][kWarpMax];
+    __shared__ uint32_t s_id[kCellWarps][kWarpMax];
+    __shared__ uint16_t s_perm[kCellWarps][kWarpMax];
+    __shared__ T s_v[kCellWarps][3][kWarpMax];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const uint32_t step = a.ctr->step;
+    const int slot_t = a.sample_slot[step];
+    uint32_t* sl = s_slot[w];
+    uint32_t* sid = s_id[w];
+    uint16_t* sp = s_perm[w];
+    T* sv0 = s_v[w][0];
+    T* sv1 = s_v[w][1];
+    T* sv2 = s_v[w][2];
+    unsigned long long n_cand = 0, n_acc = 0, n_clamp = 0;
+    const int64_t warps = (int64_t)gridDim.x * kCellWarps;
+    for (int64_t gcell = (int64_t)blockIdx.x * kCellWarps + w; gcell < a.total_cells; gcell += warps) {
+        const uint32_t beg = a.start[gcell];
+        const uint32_t N = a.start[gcell + 1] - beg;
+        const uint32_t rl = (uint32_t)(gcell / c.ncells);
+        const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
+        if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
+            if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+            continue;
+        }
+        if (N > (uint32_t)kWarpMax) {
+            if (lane == 0) {
+                const uint32_t idx = atomicAdd(&a.ctr->n_big, 1u);
+                if (idx < a.max_big) a.big_list[idx] = (uint32_t)gcell;
+                else atomicOr(&a.ctr->error, DSMC_ERR_BIGLIST);
+            }
+            continue;
+        }
+        for (uint32_t k = lane; k < N; k += 32) {
+            const uint32_t s = a.lcr[beg + k];
+            sl[k] = s;
+            sid[k] = a.idi[s];
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < N; k += 32) {
+            const uint32_t my = sid[k];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < N; ++j) r += sid[j] < my ? 1u : 0u;
+            sp[r] = (uint16_t)k;
+        }
+        __syncwarp();
+        for (uint32_t r = lane; r < N; r += 32) {
+            const uint32_t k = sp[r];
+            const uint32_t s = sl[k];
+            const uint32_t o = beg + r;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+            a.ido[o] = sid[k];
+            sv0[r] = a.vi[0][s];
+            sv1[r] = a.vi[1][s];
+            sv2[r] = a.vi[2][s];
+            if (a.lcr_dbg) a.lcr_dbg[o] = s;
+        }
+        __syncwarp();
+        double rem = a.rem[gcell];
+        const T smax = a.smax[gcell];
+        const int64_t M = ntc_count(c, N, (double)smax, rem);
+        T seen = (T)0;
+        uint32_t nacc = 0, nclamp = 0;
+        if (M > 0)
+            collide_cell_warp<T>(c, sv0, sv1, sv2, N, M, smax, cell, a.run0 + rl, step, seen, nacc,
+                                 nclamp);
+        if (lane == 0) {
+            a.rem[gcell] = rem;
+            if (seen > smax) a.smax[gcell] = seen;
+            if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
+            n_cand += (unsigned long long)M;
+            n_acc += nacc;
+            n_clamp += nclamp;
+        }
+        __syncwarp();
+        double m[DSMC_NMOM] = {0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t r = lane; r < N; r += 32) {
+            const T v0 = sv0[r], v1 = sv1[r], v2 = sv2[r];
+            const uint32_t o = beg + r;
+            a.vo[0][o] = v0;
+            a.vo[1][o] = v1;
+            a.vo[2][o] = v2;
+            if (slot_t >= 0) {
+                m[0] += 1.0;
+                m[1] += (double)v0; m[2] += (double)v1; m[3] += (double)v2;
+                m[4] += (double)v0 * (double)v0;
+                m[5] += (double)v1 * (double)v1;
+                m[6] += (double)v2 * (double)v2;
+            }
+        }
+        if (slot_t >= 0) {
+#pragma unroll
+            for (int q = 0; q < DSMC_NMOM; ++q) m[q] = warp_sum(m[q]);
+            if (lane < DSMC_NMOM) {
+                double val = m[0];
+#pragma unroll
+                for (int q = 1; q < DSMC_NMOM; ++q) if ((int)lane == q) val = m[q];
+                a.mom[gcell * DSMC_NMOM + lane] = val;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (n_cand) atomicAdd(&a.ctr->candidates, n_cand);
+        if (n_acc) atomicAdd(&a.ctr->collisions, n_acc);
+        if (n_clamp) atomicAdd(&a.ctr->clamps, n_clamp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cells larger than a warp's buffer: one CTA each, (id, slot) keys sorted in
+// shared memory (bitonic), velocities staged in shared memory.
+template <typename T>
+__host__ __device__ constexpr int big_max_of() { return sizeof(T) == 4 ? 8192 : 4096; }
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kMax = big_max_of<T>();
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
+    T* sv0 = reinterpret_cast<T*>(smem_raw + sizeof(unsigned long long) * kMax);
+    T* sv1 = sv0 + kMax;
+    T* sv2 = sv1 + kMax;
+    __shared__ double s_red[8][DSMC_NMOM];
+    const uint32_t step = a.ctr->step;
+    const int slot_t = a.sample_slot[step];
+    const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
+    const uint32_t lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+        const uint32_t gcell = a.big_list[bi];
+        const uint32_t beg = a.start[gcell];
+        const uint32_t N = a.start[gcell + 1] - beg;
+        const uint32_t rl = gcell / (uint32_t)c.ncells;
+        const uint32_t cell = gcell - rl * (uint32_t)c.ncells;
+        if (N > (uint32_t)kMax) {
+            if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_BIGCELL);
+            continue;
+        }
+        uint32_t P = 1;
+        while (P < N) P <<= 1;
+        for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) {
+            if (k < N) {
+                const uint32_t s = a.lcr[beg + k];
+                keys[k] = ((unsigned long long)a.idi[s] << 32) | s;
+            } else {
+                keys[k] = ~0ull;
+            }
+        }
+        __syncthreads();
+        for (uint32_t size = 2; size <= P; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                    const uint32_t i = 2 * t - (t & (stride - 1));
+                    const uint32_t j = i + stride;
+                    const bool up = (i & size) == 0;
+                    const unsigned long long ki = keys[i], kj = keys[j];
+                    if ((ki > kj) == up) { keys[i] = kj; keys[j] = ki; }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
+            const unsigned long long kk = keys[r];
+            const uint32_t s = (uint32_t)kk;
+            const uint32_t o = beg + r;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+            a.ido[o] = (uint32_t)(kk >> 32);
+            sv0[r] = a.vi[0][s];
+            sv1[r] = a.vi[1][s];
+            sv2[r] = a.vi[2][s];
+            if (a.lcr_dbg) a.lcr_dbg[o] = s;
+        }
+        __syncthreads();
+        if (w == 0) {
+            double rem = a.rem[gcell];
+            const T smax = a.smax[gcell];
+            const int64_t M = ntc_count(c, N, (double)smax, rem);
+            T seen = (T)0;
+            uint32_t nacc = 0, nclamp = 0;
+            if (M > 0)
+                collide_cell_warp<T>(c, sv0, sv1, sv2, N, M, smax, cell, a.run0 + rl, step, seen,
+                                     nacc, nclamp);
+            if (lane == 0) {
+                a.rem[gcell] = rem;
+                if (seen > smax) a.smax[gcell] = seen;
+                if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
+                if (M) atomicAdd(&a.ctr->candidates, (unsigned long long)M);
+                if (nacc) atomicAdd(&a.ctr->collisions, (unsigned long long)nacc);
+                if (nclamp) atomicAdd(&a.ctr->clamps, (unsigned long long)nclamp);
+            }
+        }
+        __syncthreads();
+        double m[DSMC_NMOM] = {0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
+            const T v0 = sv0[r], v1 = sv1[r], v2 = sv2[r];
+            const uint32_t o = beg + r;
+            a.vo[0][o] = v0;
+            a.vo[1][o] = v1;
+            a.vo[2][o] = v2;
+            if (slot_t >= 0) {
+                m[0] += 1.0;
+                m[1] += (double)v0; m[2] += (double)v1; m[3] += (double)v2;
+                m[4] += (double)v0 * (double)v0;
+                m[5] += (double)v1 * (double)v1;
+                m[6] += (double)v2 * (double)v2;
+            }
+        }
+        if (slot_t >= 0) {
+#pragma unroll
+            for (int q = 0; q < DSMC_NMOM; ++q) m[q] = warp_sum(m[q]);
+            if (lane == 0)
+                for (int q = 0; q < DSMC_NMOM; ++q) s_red[w][q] = m[q];
+            __syncthreads();
+            if (threadIdx.x < DSMC_NMOM) {
+                double s = 0.0;
+                for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += s_red[ww][threadIdx.x];
+                a.mom[(uint64_t)gcell * DSMC_NMOM + threadIdx.x] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sampling over runs: acc[t][g] += sum of the launch's runs of group g, in
+// increasing run order (the same order in batched and plain modes).
+template <typename T>
+__global__ void k_reduce(StepArgs<T> a)
+{
+    const int slot_t = a.sample_slot[a.ctr->step];
+    if (slot_t < 0) return;
+    const int ncells = a.cfg->ncells;
+    const int64_t per = (int64_t)ncells * DSMC_NMOM;
+    const int64_t n = (int64_t)a.G * per;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i / per);
+        const int64_t ck = i - (int64_t)g * per;
+        double* dst = a.acc + ((int64_t)slot_t * a.G + g) * per + ck;
+        double s = *dst;
+        // first local run r with (run0 + r) mod G == g
+        int r = ((g - a.run0 % a.G) % a.G + a.G) % a.G;
+        for (; r < a.n_runs; r += a.G) s += a.mom[(int64_t)r * per + ck];
+        *dst = s;
+    }
+}
+
+template <typename T>
+__global__ void k_step_end(StepArgs<T> a)
+{
+    a.ctr->step += 1u;
+    a.ctr->n_big = 0u;
+    // remember this step's pool size for the next scatter (the slot range of
+    // the old pool): start[total + 1] = run_base[n_runs]
+    a.start[a.total_cells + 1] = a.run_base[a.n_runs];
+}
+
+// moments of the current pool (test hook), one warp per cell
+template <typename T>
+__global__ void k_sample_now(StepArgs<T> a, const T* v0, const T* v1, const T* v2)
+{
+    const uint32_t lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t gcell = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+         gcell < a.total_cells; gcell += warps) {
+        const uint32_t beg = a.start[gcell];
+        const uint32_t end = min(a.start[gcell + 1], (uint32_t)a.cap_old);
+        const uint32_t N = end > beg ? end - beg : 0u;
+        double m[DSMC_NMOM] = {0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t r = lane; r < N; r += 32) {
+            const double x0 = v0[beg + r], x1 = v1[beg + r], x2 = v2[beg + r];
+            m[0] += 1.0; m[1] += x0; m[2] += x1; m[3] += x2;
+            m[4] += x0 * x0; m[5] += x1 * x1; m[6] += x2 * x2;
+        }
+#pragma unroll
+        for (int q = 0; q < DSMC_NMOM; ++q) m[q] = warp_sum(m[q]);
+        if (lane == 0)
+            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
+    }
+}
+
+// macroscopic quantities of sample t from the group sums; out[cell][10] =
+// n, u, v, w, T, se_n, se_u, se_v, se_w, se_T
+template <typename T>
+__global__ void k_macro(StepArgs<T> a, int t, int n_runs, double* out)
+{
+    const Cfg& c = *a.cfg;
+    const int ncells = c.ncells;
+    const int G = a.G;
+    const double kB = 1.380649e-23;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncells;
+         cell += gridDim.x * blockDim.x) {
+        double pooled[DSMC_NMOM] = {0, 0, 0, 0, 0, 0, 0};
+        double est[DSMC_MAX_GROUPS][5];
+        for (int g = 0; g < G; ++g) {
+            const double* s = a.acc + (((int64_t)t * G + g) * ncells + cell) * DSMC_NMOM;
+            for (int q = 0; q < DSMC_NMOM; ++q) pooled[q] += s[q];
+            const double nr = (double)((n_runs - g + G - 1) / G);
+            const double N = s[0];
+            est[g][0] = N * c.F_N / (nr * c.Vc);
+            const double vx = s[1] / N, vy = s[2] / N, vz = s[3] / N;
+            est[g][1] = vx; est[g][2] = vy; est[g][3] = vz;
+            est[g][4] = c.mass / (3.0 * kB) * ((s[4] + s[5] + s[6]) / N - (vx * vx + vy * vy + vz * vz));
+        }
+        double* o = out + (int64_t)cell * 10;
+        const double N = pooled[0];
+        const double vx = pooled[1] / N, vy = pooled[2] / N, vz = pooled[3] / N;
+        o[0] = N * c.F_N / ((double)n_runs * c.Vc);
+        o[1] = vx; o[2] = vy; o[3] = vz;
+        o[4] = c.mass / (3.0 * kB) * ((pooled[4] + pooled[5] + pooled[6]) / N - (vx * vx + vy * vy + vz * vz));
+        for (int q = 0; q < 5; ++q) {
+            int m = 0;
+            double mean = 0.0;
+            for (int g = 0; g < G; ++g)
+                if (est[g][q] == est[g][q]) { mean += est[g][q]; ++m; }
+            if (m < 2) { o[5 + q] = __longlong_as_double(0x7FF8000000000000ll); continue; }
+            mean /= m;
+            double ss = 0.0;
+            for (int g = 0; g < G; ++g)
+                if (est[g][q] == est[g][q]) ss += (est[g][q] - mean) * (est[g][q] - mean);
+            o[5 + q] = sqrt(ss / (m - 1)) / sqrt((double)G);
+        }
+    }
+}
+
+__global__ void k_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 r = philox(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]),
+                               make_uint2(key[2 * i], key[2 * i + 1]));
+        out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+template <typename T>
+static const StepArgs<T>& A(const void* p) { return *static_cast<const StepArgs<T>*>(p); }
+
+#define DISPATCH_PREC(prec, ...)                                      \
+    do {                                                              \
+        if ((prec) == DSMC_FP64) { using T = double; __VA_ARGS__; }   \
+        else { using T = float; __VA_ARGS__; }                        \
+    } while (0)
+
+#define DISPATCH_DIM(dim, ...)                                        \
+    do {                                                              \
+        if ((dim) == 3) { constexpr int D = 3; __VA_ARGS__; }         \
+        else { constexpr int D = 2; __VA_ARGS__; }                    \
+    } while (0)
+
+void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (k_init_cells<T><<<ls.sms * 4, 256, 0, s>>>(A<T>(args))));
+}
+
+void launch_fill(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, {
+        const StepArgs<T>& a = A<T>(args);
+        k_fill_count<T><<<ls.sms * 4, 256, 0, s>>>(a);
+        launch_scan(prec, args, ls, s);
+        DISPATCH_DIM(ls.dim, (k_fill_particles<T, D><<<ls.sms * 8, 256, 0, s>>>(a)));
+        k_fill_ids<T><<<(a.n_runs + 255) / 256, 256, 0, s>>>(a);
+    });
+}
+
+void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, {
+        const StepArgs<T>& a = A<T>(args);
+        DISPATCH_DIM(ls.dim, (k_generate<T, D><<<a.n_runs, 256, 0, s>>>(a)));
+    });
+}
+
+void launch_move(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim,
+        (k_move<T, D><<<ls.move_blocks, ls.move_threads, 0, s>>>(A<T>(args)))));
+}
+
+void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, {
+        const StepArgs<T>& a = A<T>(args);
+        k_scan1<<<a.scan_blocks, kScanThreads, 0, s>>>(a.count, a.block_sums, a.total_cells);
+        k_scan2<T><<<a.scan_blocks, kScanThreads, 0, s>>>(a);
+    });
+}
+
+void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (k_scatter<T><<<ls.scatter_blocks, 256, 0, s>>>(A<T>(args))));
+}
+
+void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim,
+        (k_cell<T, D><<<ls.cell_blocks, kCellWarps * 32, 0, s>>>(A<T>(args)))));
+}
+
+int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
+
+static size_t big_smem(int prec)
+{
+    return prec == DSMC_FP64 ? (8 + 3 * 8) * (size_t)big_max_of<double>()
+                             : (8 + 3 * 4) * (size_t)big_max_of<float>();
+}
+
+void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim,
+        (k_cell_big<T, D><<<ls.big_blocks, 256, big_smem(prec), s>>>(A<T>(args)))));
+}
+
+void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (k_reduce<T><<<ls.sms * 4, 256, 0, s>>>(A<T>(args))));
+}
+
+void launch_step_end(int prec, const void* args, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (k_step_end<T><<<1, 1, 0, s>>>(A<T>(args))));
+}
+
+void launch_sample_now(int prec, const void* args, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, {
+        const StepArgs<T>& a = A<T>(args);
+        k_sample_now<T><<<128, 256, 0, s>>>(a, a.vi[0], a.vi[1], a.vi[2]);
+    });
+}
+
+void launch_macro(int prec, const void* args, int sample, int n_runs, double* out, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (k_macro<T><<<64, 128, 0, s>>>(A<T>(args), sample, n_runs, out)));
+}
+
+void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
+{
+    ls->dim = dim;
+    ls->sms = sms;
+    int bm = 0, bc = 0;
+    DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_move<T, D>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_cell<T, D>, kCellWarps * 32, 0);
+    }));
+    ls->move_threads = 256;
+    ls->move_blocks = sms * (bm > 0 ? bm : 4);
+    ls->scatter_blocks = sms * 8;
+    ls->cell_blocks = sms * (bc > 0 ? bc : 2);
+    ls->big_blocks = sms;
+}
+
+cudaError_t prepare_kernels(int prec, int dim)
+{
+    cudaError_t e = cudaSuccess;
+    DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
+        e = cudaFuncSetAttribute(k_cell_big<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)big_smem(prec));
+    }));
+    return e;
+}
+
+cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t s)
+{
+    k_philox<<<64, 256, 0, s>>>(n, ctr, key, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dsmc

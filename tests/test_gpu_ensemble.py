@@ -1,0 +1,152 @@
+"""Ensemble-level parity of the CUDA path with the oracle, mode equivalence
+and edge cases (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import Oracle, macro_from_acc, run_ensemble
+from paper_cs_9902024_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    import __graft_entry__ as g
+    g.build()
+    from paper_cs_9902024_gb300 import dsmc
+    return dsmc
+
+
+def _zscores(mg, mo, nmin_mask):
+    out = []
+    for q, se in (("density", "se_density"), ("temperature", "se_temperature")):
+        d = mg[q] - mo[q]
+        s = np.sqrt(mg[se] ** 2 + mo[se] ** 2)
+        z = d[nmin_mask] / s[nmin_mask]
+        out.append(z[np.isfinite(z)])
+    for a in range(3):
+        d = mg["velocity"][..., a] - mo["velocity"][..., a]
+        s = np.sqrt(mg["se_velocity"][..., a] ** 2 + mo["se_velocity"][..., a] ** 2)
+        z = d[nmin_mask] / s[nmin_mask]
+        out.append(z[np.isfinite(z)])
+    return np.concatenate(out)
+
+
+def _gpu_macro(ens, T):
+    ms = [ens.macro(t) for t in range(T)]
+    return {k: np.stack([m[k] for m in ms]) for k in ms[0]}
+
+
+def test_config0_fp32_ensemble_within_3_combined_se(D):
+    """The configuration of the paper-sized small case (64x32 duct, 8 runs,
+    200 steps, samples at 50/100/150/200): FP32 batched device ensemble vs
+    the FP64 oracle; density, velocity and temperature per (sample, cell)
+    within 3 combined standard errors."""
+    w = W.config0()
+    acc_o, st_o = run_ensemble(w, threads=8)
+    mo = macro_from_acc(acc_o, w, w["runs"])
+    ens = D.Ensemble(w)
+    ens.run()
+    T = len(w["sample_steps"])
+    mg = _gpu_macro(ens, T)
+    raw = np.stack([ens.raw(t) for t in range(T)])
+    npool = np.minimum(raw[..., 0].sum(1), acc_o[..., 0].sum(1))
+    mask = npool >= 40
+    z = _zscores(mg, mo, mask)
+    frac = np.mean(np.abs(z) > 3)
+    rel_n = np.nanmedian(np.abs(mg["density"][mask] / mo["density"][mask] - 1))
+    print("config0 fp32: %d comparisons, |z|>3 fraction %.4f, max |z| %.2f, median rel err "
+          "density %.3g" % (z.size, frac, np.abs(z).max(), rel_n))
+    assert z.size > 10000
+    assert frac < 0.01
+    st = ens.stats()
+    # counters agree statistically with the oracle's
+    for k in ("generated", "particle_steps", "collisions"):
+        assert st[k] == pytest.approx(st_o[k], rel=0.02), k
+
+
+def test_config0_fp64_ensemble_matches_oracle_sums(D):
+    """FP64 device state: the group sums of every sample equal the oracle's
+    to rounding (the sampling and the fixed-order reduction over runs)."""
+    w = W.config0()
+    acc_o, st_o = run_ensemble(w, threads=8)
+    ens = D.Ensemble(w, precision="fp64")
+    ens.run()
+    raw = np.stack([ens.raw(t) for t in range(len(w["sample_steps"]))])
+    assert np.array_equal(raw[..., 0], acc_o[..., 0])
+    assert np.allclose(raw, acc_o, rtol=1e-9, atol=1e-6)
+    st = ens.stats()
+    for k in ("generated", "removed", "wall_hits", "candidates", "collisions", "particle_steps"):
+        assert st[k] == st_o[k], k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_plain_equals_batched_bitwise(D, precision):
+    """The plain per-run loop and the batched graph-captured form give
+    bit-identical sums (same draws, same per-cell order, same run order in
+    the reduction): equal sample error by construction."""
+    w = W.config0(runs=19, steps=60, n_samples=3)      # ragged groups (G = 16)
+    a = D.Ensemble(w, precision=precision, mode="batched").run()
+    b = D.Ensemble(w, precision=precision, mode="plain").run()
+    c = D.Ensemble(w, precision=precision, mode="batched", use_graph=False).run()
+    for t in range(3):
+        ra, rb, rc = a.raw(t), b.raw(t), c.raw(t)
+        assert np.array_equal(ra, rb) and np.array_equal(ra, rc)
+    sa, sb = a.stats(), b.stats()
+    for k in ("generated", "removed", "candidates", "collisions", "particle_steps"):
+        assert sa[k] == sb[k]
+
+
+def test_edge_cases(D):
+    # one run, sample at step 1 and at the last step
+    w = W.config0(runs=1, steps=5)
+    ens = D.Ensemble(w).run(sample_steps=[1, 5])
+    assert ens.raw(0)[..., 0].sum() > 0
+    # zero steps, no samples: nothing moves, no error
+    ens.run(steps=0, sample_steps=[])
+    assert ens.stats()["particle_steps"] == 0
+    # an empty closed box: no particles at any time
+    from tests.helpers import box
+    e = D.Ensemble(box(fill=0, runs=3, steps=4)).run()
+    assert e.stats()["particles_now"] == 0
+    assert np.all(e.raw(0) == 0)
+    # invalid sample lists are rejected, the context stays usable
+    with pytest.raises(D.DsmcError) as ex:
+        ens.run(steps=5, sample_steps=[3, 2])
+    assert ex.value.status == D.E_INVALID
+    with pytest.raises(D.DsmcError):
+        ens.run(steps=5, sample_steps=[6])
+    ens.run(steps=5, sample_steps=[5])
+    with pytest.raises(D.DsmcError):
+        ens.raw(1)
+
+
+def test_capacity_overflow_is_reported_not_faulted(D):
+    """A pool far too small overflows on the device; the kernels keep every
+    access in bounds, the run returns DSMC_E_CAPACITY, and the context
+    works again with a proper capacity."""
+    w = W.config0(runs=4, steps=40)
+    ens = D.Ensemble(w, capacity_per_run=300)
+    with pytest.raises(D.DsmcError) as ex:
+        ens.run()
+    assert ex.value.status == D.E_CAPACITY
+    ens.close()
+    ok = D.Ensemble(w).run()
+    assert ok.stats()["error_word"] == 0
+
+
+def test_macro_quantities_match_oracle_formulae(D):
+    """The device's macroscopic quantities equal the oracle's formulae
+    applied to the device's own group sums."""
+    w = W.config0(runs=20, steps=50, n_samples=2)
+    ens = D.Ensemble(w).run()
+    for t in range(2):
+        raw = ens.raw(t)
+        m = ens.macro(t)
+        ref = macro_from_acc(raw[None], w, 20)
+        for k in ("density", "temperature", "se_density", "se_temperature"):
+            a, b = m[k], ref[k][0]
+            fin = np.isfinite(b)
+            assert np.array_equal(np.isfinite(a), fin), k
+            assert np.allclose(a[fin], b[fin], rtol=1e-10, atol=1e-12), k
+        assert np.allclose(m["velocity"], ref["velocity"][0], rtol=1e-10, atol=1e-9, equal_nan=True)
