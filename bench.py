@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: particle-steps/s of the n-run unsteady DSMC ensemble on GB300.
+
+One bench step = one whole ensemble (`dsmc_run_ensemble`): the 512 runs of
+the 64x32 duct (cell = 1 mean free path, dt = 0.2 mean collision time, hard
+spheres, impulsively started inflow) for 400 time steps with 8 sample times
+-- every time step is Generation, Motion, Enumeration/Indexing, Interaction
+and (at sample steps) Sampling of all runs.  The particle pool (~1 GB at
+full fill) is larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank runs its own share of runs (run indices offset by rank)
+and the ensemble's group sums are summed over ranks once per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s over n-run ensemble on 1 GB300, batched vs plain at equal error"
+UNIT = "particle-steps/s"
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--runs", type=int, default=None, help="override runs per GPU")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the plain-mode, profile and CPU-baseline legs")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(runs=None):
+    from paper_cs_9902024_gb300 import workloads as W
+    w = W.config1()
+    if runs:
+        w = W.scaled(w, runs=runs)
+    return w
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in ("paper_cs_9902024_gb300/csrc/dsmc_kernels.cu",
+              "paper_cs_9902024_gb300/csrc/dsmc_internal.cuh"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(w, st, steps, runs):
+    """Algorithmic bytes each kernel must move over one ensemble (FP32 state):
+    one read of every input and one write of every output, no re-reads."""
+    D = w["dim"]
+    t = 4
+    cells = runs * w["ncell"][0] * w["ncell"][1] * (w["ncell"][2] if D == 3 else 1)
+    moved_old = st["particle_steps"] - st["generated"]
+    pool = st["pool_steps"]
+    return {
+        # read x (D) and v (D; the third component only at wall hits), write
+        # x (D), write the cell key and in-cell rank
+        "move": moved_old * (3 * D * t + 8),
+        # read key + rank, write LCR
+        "scatter": pool * 12,
+        # read LCR, id, x, v; write x, id, v; per cell: start, NTC remainder
+        # (read + write) and (sigma c_r)_max
+        "cell": pool * (4 + 2 * (D * t + 3 * t + 4)) + cells * steps * 24,
+        # read counts twice, write starts, clear counts
+        "scan": cells * steps * 16,
+        # write the entrants (x, v, id, key, rank)
+        "generate": st["generated"] * (D * t + 3 * t + 12),
+    }
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import run_ensemble
+    w = workload()
+    cores = min(cpu_cores(), 16)
+    sample_runs = 16
+    wr = dict(w)
+
+    def one():
+        t0 = time.perf_counter()
+        _, st = run_ensemble(wr, runs=sample_runs, threads=cores)
+        return time.perf_counter() - t0, st["particle_steps"]
+
+    for _ in range(args.warmup):
+        one()
+    tot_t, tot_ps = 0.0, 0
+    for _ in range(args.steps):
+        dt, ps = one()
+        tot_t += dt
+        tot_ps += ps
+    value = tot_ps / tot_t
+    sample = "%d of the %d runs x %d steps of %s per step, FP64 oracle, %d threads over runs" % (
+        sample_runs, w["runs"], w["steps"], w["name"], cores)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": w["name"], "runs": w["runs"], "steps_per_run": w["steps"],
+                   "cells": w["ncell"][0] * w["ncell"][1], "sample_times": len(w["sample_steps"])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import numpy as np
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = local
+    torch.cuda.set_device(device)
+    import __graft_entry__ as g
+    g.build()
+    from paper_cs_9902024_gb300.dsmc import Ensemble
+    w = workload(args.runs)
+    runs = w["runs"]
+    steps = w["steps"]
+    n_samples = len(w["sample_steps"])
+    stream = torch.cuda.Stream(device=device)
+    ens = Ensemble(w, device=device, stream=stream, run_offset=rank * runs)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        ens.run()
+    st = ens.stats()
+    ps_per_step = st["particle_steps"]
+    launches_per_step = 6 + steps * 9
+    # -- device-timed region: inputs resident, results stay on the device --
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(device) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ens.run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    ps_total = ps_per_step * args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        p = torch.tensor([ps_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(p)
+        ps_total = float(p.item())
+    value = ps_total / (ms / 1e3)
+    # -- end to end through the C ABI with host buffers --------------------
+    barrier()
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ens.run()
+        raws = [ens.raw(t) for t in range(n_samples)]
+        if ws > 1:
+            r = torch.from_numpy(np.stack(raws)).cuda()
+            torch.distributed.all_reduce(r)
+            raws = r.cpu().numpy()
+        s2 = ens.stats()
+        h2d += s2["h2d_bytes"]
+        d2h += s2["d2h_bytes"]
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ps_total / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"] + " (2-D duct 64x32, HS, 512 runs x 400 steps, "
+                   "8 sample times)", "runs_per_gpu": runs, "steps_per_run": steps,
+                   "cells_per_run": w["ncell"][0] * w["ncell"][1], "sample_times": n_samples,
+                   "mode": "batched, CUDA graph per step", "state": "fp32",
+                   "sampling": "fp64 group sums", "l2": "inputs larger than L2 (pool ~1 GB)",
+                   "parallelism": "runs sharded over %d GPU(s)" % ws},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "particle_steps_per_step": ps_per_step,
+    }
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # -- plain per-run loop on the same workload (a 64-run sample: the
+        #    per-run loop's cost is the same for every run) ---------------
+        plain_runs = 64
+        pe = Ensemble(w, mode="plain", device=device, stream=stream)
+        pe.run(runs=8)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe.run(runs=plain_runs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pst = pe.stats()
+        pms = e0.elapsed_time(e1)
+        # same-seed batched run of the same 64 runs: identical sums
+        be = Ensemble(w, device=device, stream=stream).run(runs=plain_runs)
+        same = all(np.array_equal(pe.raw(t), be.raw(t)) for t in range(n_samples))
+        out["plain"] = {"value": pst["particle_steps"] / (pms / 1e3), "unit": UNIT,
+                        "runs_timed": plain_runs, "ms": pms,
+                        "batched_over_plain": value / (pst["particle_steps"] / (pms / 1e3)),
+                        "sample_error": "equal: plain and batched group sums bit-identical"
+                        if same else "DIFFERENT"}
+        pe.close()
+        be.close()
+        # -- per-kernel device times (profile mode: CUDA events around every
+        #    launch on the library's stream) and the roofline ------------
+        pr = Ensemble(w, profile=True, device=device, stream=stream)
+        pr.run()
+        prs = pr.stats()
+        pr.close()
+        algo = algorithmic_bytes(w, prs, steps, runs)
+        peak, src = measured_peaks()
+        kern = {}
+        total_ms = sum(prs["ms_kernel"].values())
+        for k, msk in prs["ms_kernel"].items():
+            if msk <= 0:
+                continue
+            e = {"ms": msk, "share": msk / total_ms, "launches": prs["launches_kernel"][k]}
+            if k in algo:
+                e["achieved_gbs"] = algo[k] / (msk / 1e3) / 1e9
+                e["frac_of_%s_hbm" % src] = e["achieved_gbs"] / peak
+            kern[k] = e
+        dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["ms"])
+        achieved = kern[dom]["achieved_gbs"]
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            try:
+                tj = json.load(open(tp))
+                ent = tj.get(dom)
+                if ent and ent.get("kernel_hash") == kernel_hash():
+                    per_particle = ent["dram_bytes"] / ent["particles"]
+                    traffic = per_particle * prs["pool_steps"] / prs["launches_kernel"][dom]
+            except Exception:
+                traffic = None
+        out["roofline"] = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved,
+                           "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                           "traffic": traffic, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"
+                           if src == "measured" else src,
+                           "bytes_per_launch": algo[dom] / prs["launches_kernel"][dom]}
+        out["kernels"] = kern
+        out["profile_run_ms"] = prs["ms_steps"]
+        # -- the FP64 oracle on the host cores, bounded sample -------------
+        from oracle import run_ensemble
+        cores = min(cpu_cores(), 16)
+        t0 = time.perf_counter()
+        _, sto = run_ensemble(w, runs=16, threads=cores)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sto["particle_steps"] / dt, "unit": UNIT, "cores": cores,
+                               "kind": "oracle",
+                               "sample": "16 of the 512 runs x 400 steps, FP64, %d threads over "
+                                         "runs, %.1f s" % (cores, dt)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ens.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,9 @@ typedef struct {
     int32_t device;           /* CUDA device ordinal */
     int32_t profile;          /* time every kernel with CUDA events (direct
                                  launches, no graph); see dsmc_stats */
+    int64_t run_offset;       /* global index of run 0 of this context: the
+                                 runs draw as runs run_offset.. (sharding an
+                                 ensemble over processes or GPUs) */
 } dsmc_options;
 
 typedef struct {
@@ -154,6 +157,8 @@ typedef struct {
     uint64_t candidates, collisions, clamps;   /* NTC counters; clamps: pairs
                                                   with sigma c_r > max */
     uint64_t bounce_limit, reject_limit;       /* numerical guards hit */
+    uint64_t pool_steps;      /* sum over steps of the pool size after the
+                                 step (particles written by Indexing) */
     uint32_t error_word;      /* device error bits (DSMC_ERR_*) */
     int32_t steps_done;
     int64_t particles_now;    /* particles in all runs after the last step */
@@ -161,6 +166,9 @@ typedef struct {
     double ms_steps;          /* device time of the last run's step loop */
     double ms_kernel[12];     /* profile mode: device time per kernel kind */
     int64_t launches_kernel[12];
+    uint64_t h2d_bytes;       /* host -> device bytes of the last run */
+    uint64_t d2h_bytes;       /* device -> host bytes since the last run began
+                                 (counters at its end plus dsmc_get_samples) */
 } dsmc_stats;
 
 /* device error bits */

@@ -360,6 +360,7 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.accd = ctx->accd;
     a.big_list = ctx->big_list;
     a.sample_slot = ctx->sample_slot;
+    a.n_slot = ctx->steps_alloc;
     a.acc = ctx->acc;
     a.cap_old = ctx->cap_old;
     a.cap_new = ctx->cap_new;
@@ -428,6 +429,7 @@ static void enqueue_init(dsmc_ctx* ctx, const void* args)
 static dsmc_status upload_cfg(dsmc_ctx* ctx)
 {
     CK(cudaMemcpyAsync(ctx->d_cfg, &ctx->hcfg, sizeof(Cfg), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->stats.h2d_bytes += sizeof(Cfg);
     return DSMC_OK;
 }
 
@@ -440,6 +442,7 @@ static dsmc_status reset_counters(dsmc_ctx* ctx)
 static dsmc_status read_counters(dsmc_ctx* ctx, Counters* h)
 {
     CK(cudaMemcpyAsync(h, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->stats.d2h_bytes += sizeof(Counters);
     CK(cudaStreamSynchronize(ctx->stream));
     return DSMC_OK;
 }
@@ -456,6 +459,7 @@ static void fill_stats(dsmc_ctx* ctx, const Counters& h)
     s.clamps = h.clamps;
     s.bounce_limit = h.bounce_limit;
     s.reject_limit = h.reject_limit;
+    s.pool_steps = h.pool_steps;
     s.error_word = h.error;
     s.capacity = ctx->cap_old;
 }
@@ -476,7 +480,8 @@ static dsmc_status check_error_word(dsmc_ctx* ctx, uint32_t e)
 static dsmc_status validate_run(dsmc_ctx* ctx, int n_runs, double dt, int steps,
                                 const int32_t* ss, int n_samples)
 {
-    if (n_runs < 1 || n_runs > (1 << 20)) return fail(ctx, DSMC_E_INVALID, "n_runs out of range");
+    if (n_runs < 1 || n_runs > (1 << 20) || ctx->opt.run_offset + n_runs > (1ll << 31))
+        return fail(ctx, DSMC_E_INVALID, "n_runs out of range");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, DSMC_E_INVALID, "dt must be > 0");
     if (steps < 0 || steps > (1 << 26)) return fail(ctx, DSMC_E_INVALID, "steps out of range");
     if (n_samples < 0 || n_samples > kMaxSamples || (n_samples > 0 && !ss))
@@ -501,6 +506,7 @@ static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, cons
     if (st) return st;
     std::vector<int32_t> slot(steps + 2, -1);
     for (int k = 0; k < n_samples; ++k) slot[ss[k]] = k;
+    ctx->stats.h2d_bytes += 4 * slot.size();
     CK(cudaMemcpyAsync(ctx->sample_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice,
                        ctx->stream));
     // the upload source is a host vector: finish before it goes away
@@ -526,7 +532,7 @@ static dsmc_status build_graphs(dsmc_ctx* ctx, int n_runs)
         if (ctx->gexec[k]) { cudaGraphExecDestroy(ctx->gexec[k]); ctx->gexec[k] = nullptr; }
     for (int p = 0; p < 2; ++p) {
         AnyArgs u;
-        const void* args = build_args(ctx, u, p, 0, n_runs);
+        const void* args = build_args(ctx, u, p, (int)ctx->opt.run_offset, n_runs);
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         enqueue_step(ctx, args, nullptr);
@@ -601,7 +607,8 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     ctx->device = ctx->opt.device;
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->stats.struct_size = sizeof(dsmc_stats);
-    if ((ctx->opt.alloc == nullptr) != (ctx->opt.free == nullptr)) {
+    if (ctx->opt.run_offset < 0 || ctx->opt.run_offset > (1ll << 30) ||
+        (ctx->opt.alloc == nullptr) != (ctx->opt.free == nullptr)) {
         delete ctx;
         return DSMC_E_INVALID;
     }
@@ -657,6 +664,8 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     if (st) return st;
     ctx->have_run = false;
     ctx->dbg = false;
+    ctx->stats.h2d_bytes = 0;
+    ctx->stats.d2h_bytes = 0;
     const bool plain = ctx->opt.mode == DSMC_MODE_PLAIN;
     const int n_launch = plain ? 1 : n_runs;
     st = prepare(ctx, n_runs, dt, steps, sample_steps, n_samples, seed, n_launch);
@@ -678,7 +687,8 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     CK(cudaEventRecord(e0, ctx->stream));
     for (int r = 0; r < (plain ? n_runs : 1); ++r) {
         AnyArgs u;
-        const void* a0 = build_args(ctx, u, 0, plain ? r : 0, n_launch);
+        const int r0 = (int)ctx->opt.run_offset + (plain ? r : 0);
+        const void* a0 = build_args(ctx, u, 0, r0, n_launch);
         enqueue_init(ctx, a0);
         ctx->cur = 0;
         if (r == 0) {
@@ -690,7 +700,7 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
                 CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
             } else {
                 AnyArgs v;
-                const void* a = build_args(ctx, v, ctx->cur, plain ? r : 0, n_launch);
+                const void* a = build_args(ctx, v, ctx->cur, r0, n_launch);
                 enqueue_step(ctx, a, profile ? &evn : nullptr);
             }
             ctx->cur ^= 1;
@@ -726,6 +736,7 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     ctx->stats.steps_done = steps;
     uint32_t total = 0;
     CK(cudaMemcpy(&total, ctx->run_base + n_launch, 4, cudaMemcpyDeviceToHost));
+    ctx->stats.d2h_bytes += 4;
     ctx->stats.particles_now = total;
     st = check_error_word(ctx, h.error);
     if (st) return st;
@@ -748,6 +759,7 @@ dsmc_status dsmc_get_samples(dsmc_ctx* ctx, int sample_idx, dsmc_quantity q, dou
     if (q == DSMC_Q_RAW_MOMENTS) {
         const size_t n = (size_t)ctx->G * nc * DSMC_NMOM;
         if (out_len < n) return fail(ctx, DSMC_E_INVALID, "out_len too small");
+        ctx->stats.d2h_bytes += 8 * n;
         CK(cudaMemcpyAsync(out, ctx->acc + (size_t)sample_idx * n, 8 * n, cudaMemcpyDeviceToHost,
                            ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -768,6 +780,7 @@ dsmc_status dsmc_get_samples(dsmc_ctx* ctx, int sample_idx, dsmc_quantity q, dou
     const void* a = build_args(ctx, u, ctx->cur, 0, ctx->n_launch);
     launch_macro(ctx->prec, a, sample_idx, ctx->last_runs, ctx->macro, ctx->stream);
     CK(cudaGetLastError());
+    ctx->stats.d2h_bytes += 8 * width * nc;
     CK(cudaMemcpy2DAsync(out, 8 * width, ctx->macro + off, 8 * 10, 8 * width, nc,
                          cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));

@@ -61,6 +61,7 @@ struct Cfg {
 struct Counters {
     unsigned long long particle_steps, generated, removed, wall_hits;
     unsigned long long candidates, collisions, clamps, bounce_limit, reject_limit;
+    unsigned long long pool_steps;
     uint32_t error, step, n_big, pad_;
 };
 
@@ -89,6 +90,7 @@ struct StepArgs {
     uint32_t* accd;        // optional per cell
     uint32_t* big_list;
     const int32_t* sample_slot;   // per step: sample index or -1
+    int32_t n_slot;               // entries of sample_slot
     double* acc;           // [samples][G][ncells][7]
     int64_t cap_old, cap_new, gcap, max_big;
     int32_t n_runs;        // runs in this launch

@@ -369,6 +369,19 @@ __global__ void k_fill_ids(StepArgs<T> a)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.start[a.total_cells + 1] = a.run_base[a.n_runs];
 }
 
+// inflow segment that owns element e (elements are numbered segment by
+// segment in list order); the caller guarantees 0 <= e < n_elem
+__device__ __forceinline__ int inflow_segment_of(const Cfg& c, int64_t e)
+{
+    int q = 0;
+    for (; q < c.n_bc - 1; ++q) {
+        const BcDev& b = c.bc[q];
+        if (b.kind == DSMC_BC_INFLOW && b.face < 6 && e >= b.elem_base && e < b.elem_base + b.n_elem)
+            break;
+    }
+    return q;
+}
+
 // ---------------------------------------------------------------------------
 // Generation: one CTA per run.  Elements (inflow face cells) are taken in
 // segment-list order; each element's count is floor(lambda + R); entrants
@@ -395,10 +408,7 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
         const int64_t e = chunk + threadIdx.x;
         uint32_t G = 0;
         if (e < c.n_elem) {
-            int q = 0;
-            while (!(c.bc[q].kind == DSMC_BC_INFLOW && c.bc[q].face < 6 && e >= c.bc[q].elem_base &&
-                     e < c.bc[q].elem_base + c.bc[q].n_elem))
-                ++q;
+            const int q = inflow_segment_of(c, e);
             const BcDev& b = c.bc[q];
             const int64_t loc = e - b.elem_base;
             const int aa = b.lo[0] + (int)(loc % b.elem_w), bb = b.lo[1] + (int)(loc / b.elem_w);
@@ -423,10 +433,7 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
             const uint32_t k = j - s_off[lo];
             const uint32_t local = running + j;
             if ((int64_t)local >= a.gcap) { overflow = true; continue; }
-            int q = 0;
-            while (!(c.bc[q].kind == DSMC_BC_INFLOW && c.bc[q].face < 6 && e2 >= c.bc[q].elem_base &&
-                     e2 < c.bc[q].elem_base + c.bc[q].n_elem))
-                ++q;
+            const int q = inflow_segment_of(c, e2);
             const BcDev& b = c.bc[q];
             const int64_t loc = e2 - b.elem_base;
             const int aa = b.lo[0] + (int)(loc % b.elem_w), bb = b.lo[1] + (int)(loc / b.elem_w);
@@ -758,7 +765,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cell(StepArgs<T> a)
     const int w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     const uint32_t step = a.ctr->step;
-    const int slot_t = a.sample_slot[step];
+    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     uint32_t* sl = s_slot[w];
     uint32_t* sid = s_id[w];
     uint16_t* sp = s_perm[w];
@@ -879,7 +886,7 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
     T* sv2 = sv1 + kMax;
     __shared__ double s_red[8][DSMC_NMOM];
     const uint32_t step = a.ctr->step;
-    const int slot_t = a.sample_slot[step];
+    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
     const uint32_t lane = lane_id();
     const int w = threadIdx.x >> 5;
@@ -985,7 +992,8 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
 template <typename T>
 __global__ void k_reduce(StepArgs<T> a)
 {
-    const int slot_t = a.sample_slot[a.ctr->step];
+    const uint32_t step = a.ctr->step;
+    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     if (slot_t < 0) return;
     const int ncells = a.cfg->ncells;
     const int64_t per = (int64_t)ncells * DSMC_NMOM;
@@ -1008,6 +1016,7 @@ __global__ void k_step_end(StepArgs<T> a)
 {
     a.ctr->step += 1u;
     a.ctr->n_big = 0u;
+    a.ctr->pool_steps += (unsigned long long)min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
     // remember this step's pool size for the next scatter (the slot range of
     // the old pool): start[total + 1] = run_base[n_runs]
     a.start[a.total_cells + 1] = a.run_base[a.n_runs];

@@ -70,16 +70,16 @@ class Options(C.Structure):
                 ("capacity_factor", C.c_double), ("capacity_per_run", C.c_int64),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("stream", C.c_void_p), ("use_graph", C.c_int32), ("debug", C.c_int32),
-                ("device", C.c_int32), ("profile", C.c_int32)]
+                ("device", C.c_int32), ("profile", C.c_int32), ("run_offset", C.c_int64)]
 
 
 class Stats(C.Structure):
     _fields_ = [("struct_size", C.c_uint32)] + [(k, C.c_uint64) for k in (
         "particle_steps", "generated", "removed", "wall_hits", "candidates", "collisions",
-        "clamps", "bounce_limit", "reject_limit")] + [
+        "clamps", "bounce_limit", "reject_limit", "pool_steps")] + [
         ("error_word", C.c_uint32), ("steps_done", C.c_int32), ("particles_now", C.c_int64),
         ("capacity", C.c_int64), ("ms_steps", C.c_double), ("ms_kernel", C.c_double * 12),
-        ("launches_kernel", C.c_int64 * 12)]
+        ("launches_kernel", C.c_int64 * 12), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
 
 
 _lib = None
@@ -166,7 +166,7 @@ class Ensemble:
 
     def __init__(self, w, mode="batched", precision="fp32", capacity_factor=0.0,
                  capacity_per_run=0, debug=False, profile=False, use_graph=True, device=0,
-                 torch_memory=True, stream=None):
+                 torch_memory=True, stream=None, run_offset=0):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise DsmcError(E_CUDA, "no CUDA device: the DSMC path has no CPU fallback")
@@ -185,6 +185,7 @@ class Ensemble:
         opt.debug = 1 if debug else 0
         opt.profile = 1 if profile else 0
         opt.device = device
+        opt.run_offset = run_offset
         if torch_memory:
             dev = torch.device("cuda", device)
 
