@@ -371,6 +371,7 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.G = ctx->G;
     a.total_cells = (int32_t)((int64_t)ctx->ncells * n);
     a.scan_blocks = (int)((a.total_cells + kScanTile - 1) / kScanTile);
+    a.tile_budget = ctx->ls.tile_budget;
     return a;
 }
 
@@ -520,7 +521,7 @@ static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, cons
     }
     st = reset_counters(ctx);
     if (st) return st;
-    CK(prepare_kernels(ctx->prec, ctx->dim));
+    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
     return DSMC_OK;
 }
 
@@ -634,6 +635,7 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
         }
         ctx->own_stream = true;
     }
+    ctx->ls.tile_budget = 0;
     compute_launch_shape(ctx->prec, ctx->dim, ctx->sms, &ctx->ls);
     *out = ctx;
     return DSMC_OK;

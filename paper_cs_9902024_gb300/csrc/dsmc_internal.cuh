@@ -13,6 +13,8 @@ constexpr int kMaxBounce = 16;            // surface events per particle and ste
 constexpr int kGenBlocks = 64;            // Philox blocks per generated particle
 constexpr int kWarpMax = 128;             // cells up to this size: one warp each
 constexpr int kCellWarps = 8;             // warps per CTA of the cell kernel
+constexpr int kTileCells = 256;           // cells (= threads) per tile CTA
+constexpr int kLaneMax = 512;             // largest cell of the tile path
 constexpr int kScanTile = 4096;           // cells per CTA of the scan
 constexpr int kScanThreads = 1024;
 constexpr int kMaxSamples = 4096;
@@ -98,6 +100,7 @@ struct StepArgs {
     int32_t G;             // sample groups
     int32_t total_cells;
     int32_t scan_blocks;
+    int32_t tile_budget;   // particles a tile CTA stages in shared memory
 };
 
 // Launchers (dsmc_kernels.cu).  `prec` is DSMC_FP32 or DSMC_FP64 and selects
@@ -107,6 +110,7 @@ struct LaunchShape {
     int sms;
     int move_blocks, move_threads;
     int scatter_blocks, cell_blocks, big_blocks;
+    int tile_budget;
 };
 
 void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
@@ -122,7 +126,7 @@ void launch_step_end(int prec, const void* args, cudaStream_t s);
 void launch_macro(int prec, const void* args, int sample, int n_runs, double* out,
                   cudaStream_t s);
 void launch_sample_now(int prec, const void* args, cudaStream_t s);
-cudaError_t prepare_kernels(int prec, int dim);
+cudaError_t prepare_kernels(int prec, int dim, int tile_budget);
 void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls);
 int big_cell_limit(int prec);
 cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,

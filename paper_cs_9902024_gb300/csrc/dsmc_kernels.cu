@@ -703,8 +703,50 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
+// The draws of NTC candidate k of a cell with N particles: the pair (i, j),
+// the acceptance uniform, cos(chi) and the azimuth uniform.
+template <typename T>
+__device__ __forceinline__ void candidate_draws(const Cfg& c, uint32_t run, uint32_t step,
+                                                uint32_t cell, int64_t k, uint32_t N, uint32_t& ci,
+                                                uint32_t& cj, T& u2, T& u3, T& ue)
+{
+    const uint4 r = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k));
+    const uint4 r2 = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k + 1));
+    ci = pick(r.x, N);
+    cj = pick(r.y, N - 1u);
+    if (cj >= ci) cj += 1u;
+    u2 = u01<T>(r.z);
+    u3 = u01<T>(r.w);
+    ue = u01<T>(r2.x);
+}
+
+// One NTC candidate pair (i, j) on velocities in shared memory: accept with
+// probability sigma_T c_r / (sigma_T c_r)_max, then scatter isotropically.
+// Every cell path uses this arithmetic, so results do not depend on the path.
+template <typename T>
+__device__ __forceinline__ void collide_candidate(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t i,
+                                                  uint32_t j, T u2, T u3, T ue, T smax, T& seen,
+                                                  uint32_t& nacc, uint32_t& nclamp)
+{
+    T v1[3] = {sv0[i], sv1[i], sv2[i]};
+    T v2[3] = {sv0[j], sv1[j], sv2[j]};
+    const T gx = v1[0] - v2[0], gy = v1[1] - v2[1], gz = v1[2] - v2[2];
+    const T g2 = gx * gx + gy * gy + gz * gz;
+    const T g = dsqrt(g2);
+    const T sc = sigma_cr<T>(c, g, g2);
+    if (sc > seen) seen = sc;
+    if (sc > smax) nclamp++;
+    if (u2 < sc / smax) {
+        scatter_pair<T>(v1, v2, g, u3, ue);
+        sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
+        sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
+        nacc++;
+    }
+}
+
 // Interaction of one cell whose velocities sit in s_v[3][*] in id order;
-// all lanes of the warp call it; lane 0 does the sequential candidates.
+// all lanes of the warp call it: the lanes draw 32 candidates at a time,
+// lane 0 applies them in order.
 template <typename T>
 __device__ void collide_cell_warp(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t N, int64_t M,
                                   T smax, uint32_t cell, uint32_t run, uint32_t step,
@@ -715,16 +757,7 @@ __device__ void collide_cell_warp(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t
         const int64_t k = kb + lane;
         uint32_t ci = 0, cj = 0;
         T u2 = (T)1, u3 = (T)0, ue = (T)0;
-        if (k < M) {
-            const uint4 r = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k));
-            const uint4 r2 = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k + 1));
-            ci = pick(r.x, N);
-            cj = pick(r.y, N - 1u);
-            if (cj >= ci) cj += 1u;
-            u2 = u01<T>(r.z);
-            u3 = u01<T>(r.w);
-            ue = u01<T>(r2.x);
-        }
+        if (k < M) candidate_draws<T>(c, run, step, cell, k, N, ci, cj, u2, u3, ue);
         const int cnt = (M - kb) < 32 ? (int)(M - kb) : 32;
         for (int q = 0; q < cnt; ++q) {
             const uint32_t i = __shfl_sync(0xFFFFFFFFu, ci, q);
@@ -732,139 +765,245 @@ __device__ void collide_cell_warp(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t
             const T U2 = __shfl_sync(0xFFFFFFFFu, u2, q);
             const T U3 = __shfl_sync(0xFFFFFFFFu, u3, q);
             const T UE = __shfl_sync(0xFFFFFFFFu, ue, q);
-            if (lane == 0) {
-                T v1[3] = {sv0[i], sv1[i], sv2[i]};
-                T v2[3] = {sv0[j], sv1[j], sv2[j]};
-                const T gx = v1[0] - v2[0], gy = v1[1] - v2[1], gz = v1[2] - v2[2];
-                const T g2 = gx * gx + gy * gy + gz * gz;
-                const T g = dsqrt(g2);
-                const T sc = sigma_cr<T>(c, g, g2);
-                if (sc > seen) seen = sc;
-                if (sc > smax) nclamp++;
-                if (U2 < sc / smax) {
-                    scatter_pair<T>(v1, v2, g, U3, UE);
-                    sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
-                    sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
-                    nacc++;
-                }
-            }
+            if (lane == 0) collide_candidate<T>(c, sv0, sv1, sv2, i, j, U2, U3, UE, smax, seen, nacc, nclamp);
             __syncwarp();
         }
     }
 }
 
-// One warp per cell: gather in id order, collide, sample, write the next pool.
+// Sampling of one cell: N, sum v_a, sum v_a^2 in FP64, summed in id order
+// (one fixed order for every path and launch shape).
+template <typename T>
+__device__ __forceinline__ void cell_moments(const T* sv0, const T* sv1, const T* sv2, uint32_t N,
+                                             double* m)
+{
+    for (int q = 0; q < DSMC_NMOM; ++q) m[q] = 0.0;
+    for (uint32_t r = 0; r < N; ++r) {
+        const double v0 = (double)sv0[r], v1 = (double)sv1[r], v2 = (double)sv2[r];
+        m[0] += 1.0;
+        m[1] += v0; m[2] += v1; m[3] += v2;
+        m[4] += v0 * v0; m[5] += v1 * v1; m[6] += v2 * v2;
+    }
+}
+
+struct CellTally {
+    unsigned long long cand = 0, acc = 0, clamp = 0;
+};
+
+// Warp path for one cell of up to kWarpMax particles: id ranks by counting,
+// gather into the next pool, NTC collisions, moments.  Used for tiles that
+// do not fit the tile kernel's shared-memory budget.  `ws` is this warp's
+// scratch: kWarpMax x (2 u32 + u16 + 3 T).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kCellWarps * 32) k_cell(StepArgs<T> a)
+__device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell, uint32_t step,
+                               int slot_t, unsigned char* ws, CellTally& tl)
+{
+    const uint32_t lane = lane_id();
+    uint32_t* sl = reinterpret_cast<uint32_t*>(ws);
+    uint32_t* sid = sl + kWarpMax;
+    T* sv0 = reinterpret_cast<T*>(sid + kWarpMax);
+    T* sv1 = sv0 + kWarpMax;
+    T* sv2 = sv1 + kWarpMax;
+    uint16_t* sp = reinterpret_cast<uint16_t*>(sv2 + kWarpMax);
+    const uint32_t beg = a.start[gcell];
+    const uint32_t N = a.start[gcell + 1] - beg;
+    const uint32_t rl = (uint32_t)(gcell / c.ncells);
+    const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
+    if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
+        if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+        return;
+    }
+    if (N > (uint32_t)kWarpMax) {
+        if (lane == 0) {
+            const uint32_t idx = atomicAdd(&a.ctr->n_big, 1u);
+            if (idx < a.max_big) a.big_list[idx] = (uint32_t)gcell;
+            else atomicOr(&a.ctr->error, DSMC_ERR_BIGLIST);
+        }
+        return;
+    }
+    for (uint32_t k = lane; k < N; k += 32) {
+        const uint32_t s = a.lcr[beg + k];
+        sl[k] = s;
+        sid[k] = a.idi[s];
+    }
+    __syncwarp();
+    for (uint32_t k = lane; k < N; k += 32) {
+        const uint32_t my = sid[k];
+        uint32_t r = 0;
+        for (uint32_t j = 0; j < N; ++j) r += sid[j] < my ? 1u : 0u;
+        sp[r] = (uint16_t)k;
+    }
+    __syncwarp();
+    for (uint32_t r = lane; r < N; r += 32) {
+        const uint32_t k = sp[r];
+        const uint32_t s = sl[k];
+        const uint32_t o = beg + r;
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+        a.ido[o] = sid[k];
+        sv0[r] = a.vi[0][s];
+        sv1[r] = a.vi[1][s];
+        sv2[r] = a.vi[2][s];
+        if (a.lcr_dbg) a.lcr_dbg[o] = s;
+    }
+    __syncwarp();
+    double rem = a.rem[gcell];
+    const T smax = a.smax[gcell];
+    const int64_t M = ntc_count(c, N, (double)smax, rem);
+    T seen = (T)0;
+    uint32_t nacc = 0, nclamp = 0;
+    if (M > 0)
+        collide_cell_warp<T>(c, sv0, sv1, sv2, N, M, smax, cell, a.run0 + rl, step, seen, nacc, nclamp);
+    if (lane == 0) {
+        a.rem[gcell] = rem;
+        if (seen > smax) a.smax[gcell] = seen;
+        if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
+        tl.cand += (unsigned long long)M;
+        tl.acc += nacc;
+        tl.clamp += nclamp;
+        if (slot_t >= 0) {
+            double m[DSMC_NMOM];
+            cell_moments<T>(sv0, sv1, sv2, N, m);
+            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
+        }
+    }
+    __syncwarp();
+    for (uint32_t r = lane; r < N; r += 32) {
+        const uint32_t o = beg + r;
+        a.vo[0][o] = sv0[r];
+        a.vo[1][o] = sv1[r];
+        a.vo[2][o] = sv2[r];
+    }
+    __syncwarp();
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t warp_scratch_bytes()
+{
+    return (size_t)kWarpMax * (2 * sizeof(uint32_t) + 3 * sizeof(T) + sizeof(uint16_t));
+}
+
+// Tile path: one CTA takes kTileCells consecutive (run-major) cells, whose
+// particles occupy one contiguous range of the next pool.  Coalesced
+// thread-per-particle phases: (1) ids through the LCR into shared memory,
+// (2) each particle's rank inside its cell by counting smaller ids, then
+// positions and ids gathered into the next pool at cell start + rank and
+// velocities into shared memory in id order; thread-per-cell phase (3):
+// NTC collisions and moments; (4) velocities written back, coalesced.
+// Tiles whose particles exceed the shared-memory budget go cell by cell
+// through the warp path.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 {
     const Cfg& c = *a.cfg;
-    __shared__ uint32_t s_slot[kCellWarps][kWarpMax];
-    __shared__ uint32_t s_id[kCellWarps][kWarpMax];
-    __shared__ uint16_t s_perm[kCellWarps][kWarpMax];
-    __shared__ T s_v[kCellWarps][3][kWarpMax];
-    const int w = threadIdx.x >> 5;
-    const uint32_t lane = lane_id();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t budget = (uint32_t)a.tile_budget;
+    uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
+    uint32_t* s_id = s_start + (kTileCells + 4);
+    T* s_v0 = reinterpret_cast<T*>(s_id + budget);
+    T* s_v1 = s_v0 + budget;
+    T* s_v2 = s_v1 + budget;
+    __shared__ uint32_t s_red[kTileCells / 32];
+    const int tid = threadIdx.x;
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
-    uint32_t* sl = s_slot[w];
-    uint32_t* sid = s_id[w];
-    uint16_t* sp = s_perm[w];
-    T* sv0 = s_v[w][0];
-    T* sv1 = s_v[w][1];
-    T* sv2 = s_v[w][2];
-    unsigned long long n_cand = 0, n_acc = 0, n_clamp = 0;
-    const int64_t warps = (int64_t)gridDim.x * kCellWarps;
-    for (int64_t gcell = (int64_t)blockIdx.x * kCellWarps + w; gcell < a.total_cells; gcell += warps) {
-        const uint32_t beg = a.start[gcell];
-        const uint32_t N = a.start[gcell + 1] - beg;
-        const uint32_t rl = (uint32_t)(gcell / c.ncells);
-        const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
-        if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
-            if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+    CellTally tl;
+    const int64_t ntiles = ((int64_t)a.total_cells + kTileCells - 1) / kTileCells;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t c0 = tile * kTileCells;
+        const int nct = (int)min((int64_t)kTileCells, (int64_t)a.total_cells - c0);
+        for (int i = tid; i <= kTileCells; i += blockDim.x) s_start[i] = a.start[c0 + min(i, nct)];
+        __syncthreads();
+        const uint32_t B = s_start[0], E = s_start[nct];
+        const uint32_t Tn = E - B;
+        const uint32_t myN = tid < nct ? s_start[tid + 1] - s_start[tid] : 0u;
+        const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, myN);
+        if (lane_id() == 0) s_red[tid >> 5] = wmax;
+        __syncthreads();
+        uint32_t maxN = 0;
+        for (int q = 0; q < kTileCells / 32; ++q) maxN = max(maxN, s_red[q]);
+        const bool fits = Tn <= budget && maxN <= (uint32_t)kLaneMax && (uint64_t)E <= (uint64_t)a.cap_old;
+        if (!fits) {
+            unsigned char* ws = smem_raw + (kTileCells + 4) * sizeof(uint32_t) +
+                                (size_t)(tid >> 5) * warp_scratch_bytes<T>();
+            for (int q = tid >> 5; q < nct; q += kTileCells / 32)
+                cell_warp_path<T, DIM>(a, c, c0 + q, step, slot_t, ws, tl);
+            __syncthreads();
             continue;
         }
-        if (N > (uint32_t)kWarpMax) {
-            if (lane == 0) {
-                const uint32_t idx = atomicAdd(&a.ctr->n_big, 1u);
-                if (idx < a.max_big) a.big_list[idx] = (uint32_t)gcell;
-                else atomicOr(&a.ctr->error, DSMC_ERR_BIGLIST);
+        for (uint32_t k = tid; k < Tn; k += kTileCells) s_id[k] = a.idi[a.lcr[B + k]];
+        __syncthreads();
+        for (uint32_t k = tid; k < Tn; k += kTileCells) {
+            // cell of tile position k: last i with s_start[i] - B <= k
+            int lo = 0, hi = nct - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_start[mid] - B <= k) lo = mid; else hi = mid - 1;
             }
-            continue;
-        }
-        for (uint32_t k = lane; k < N; k += 32) {
-            const uint32_t s = a.lcr[beg + k];
-            sl[k] = s;
-            sid[k] = a.idi[s];
-        }
-        __syncwarp();
-        for (uint32_t k = lane; k < N; k += 32) {
-            const uint32_t my = sid[k];
+            const uint32_t cb = s_start[lo] - B, ce = s_start[lo + 1] - B;
+            const uint32_t my = s_id[k];
             uint32_t r = 0;
-            for (uint32_t j = 0; j < N; ++j) r += sid[j] < my ? 1u : 0u;
-            sp[r] = (uint16_t)k;
-        }
-        __syncwarp();
-        for (uint32_t r = lane; r < N; r += 32) {
-            const uint32_t k = sp[r];
-            const uint32_t s = sl[k];
-            const uint32_t o = beg + r;
+            for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
+            const uint32_t pos = cb + r;
+            const uint32_t s = a.lcr[B + k];
+            const uint32_t o = B + pos;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-            a.ido[o] = sid[k];
-            sv0[r] = a.vi[0][s];
-            sv1[r] = a.vi[1][s];
-            sv2[r] = a.vi[2][s];
+            a.ido[o] = my;
+            s_v0[pos] = a.vi[0][s];
+            s_v1[pos] = a.vi[1][s];
+            s_v2[pos] = a.vi[2][s];
             if (a.lcr_dbg) a.lcr_dbg[o] = s;
         }
-        __syncwarp();
-        double rem = a.rem[gcell];
-        const T smax = a.smax[gcell];
-        const int64_t M = ntc_count(c, N, (double)smax, rem);
-        T seen = (T)0;
-        uint32_t nacc = 0, nclamp = 0;
-        if (M > 0)
-            collide_cell_warp<T>(c, sv0, sv1, sv2, N, M, smax, cell, a.run0 + rl, step, seen, nacc,
-                                 nclamp);
-        if (lane == 0) {
+        __syncthreads();
+        if (tid < nct) {
+            const int64_t gcell = c0 + tid;
+            const uint32_t cb = s_start[tid] - B;
+            const uint32_t N = myN;
+            const uint32_t rl = (uint32_t)(gcell / c.ncells);
+            const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
+            double rem = a.rem[gcell];
+            const T smax = a.smax[gcell];
+            const int64_t M = ntc_count(c, N, (double)smax, rem);
+            T seen = (T)0;
+            uint32_t nacc = 0, nclamp = 0;
+            T* v0 = s_v0 + cb;
+            T* v1 = s_v1 + cb;
+            T* v2 = s_v2 + cb;
+            for (int64_t k = 0; k < M; ++k) {
+                uint32_t i, j;
+                T u2, u3, ue;
+                candidate_draws<T>(c, a.run0 + rl, step, cell, k, N, i, j, u2, u3, ue);
+                collide_candidate<T>(c, v0, v1, v2, i, j, u2, u3, ue, smax, seen, nacc, nclamp);
+            }
             a.rem[gcell] = rem;
             if (seen > smax) a.smax[gcell] = seen;
             if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
-            n_cand += (unsigned long long)M;
-            n_acc += nacc;
-            n_clamp += nclamp;
-        }
-        __syncwarp();
-        double m[DSMC_NMOM] = {0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t r = lane; r < N; r += 32) {
-            const T v0 = sv0[r], v1 = sv1[r], v2 = sv2[r];
-            const uint32_t o = beg + r;
-            a.vo[0][o] = v0;
-            a.vo[1][o] = v1;
-            a.vo[2][o] = v2;
+            tl.cand += (unsigned long long)M;
+            tl.acc += nacc;
+            tl.clamp += nclamp;
             if (slot_t >= 0) {
-                m[0] += 1.0;
-                m[1] += (double)v0; m[2] += (double)v1; m[3] += (double)v2;
-                m[4] += (double)v0 * (double)v0;
-                m[5] += (double)v1 * (double)v1;
-                m[6] += (double)v2 * (double)v2;
+                double m[DSMC_NMOM];
+                cell_moments<T>(v0, v1, v2, N, m);
+                for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
             }
         }
-        if (slot_t >= 0) {
-#pragma unroll
-            for (int q = 0; q < DSMC_NMOM; ++q) m[q] = warp_sum(m[q]);
-            if (lane < DSMC_NMOM) {
-                double val = m[0];
-#pragma unroll
-                for (int q = 1; q < DSMC_NMOM; ++q) if ((int)lane == q) val = m[q];
-                a.mom[gcell * DSMC_NMOM + lane] = val;
-            }
+        __syncthreads();
+        for (uint32_t k = tid; k < Tn; k += kTileCells) {
+            a.vo[0][B + k] = s_v0[k];
+            a.vo[1][B + k] = s_v1[k];
+            a.vo[2][B + k] = s_v2[k];
         }
-        __syncwarp();
+        __syncthreads();
     }
-    if (lane == 0) {
-        if (n_cand) atomicAdd(&a.ctr->candidates, n_cand);
-        if (n_acc) atomicAdd(&a.ctr->collisions, n_acc);
-        if (n_clamp) atomicAdd(&a.ctr->clamps, n_clamp);
+    // counters: one atomic per warp
+    const unsigned long long cs = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.cand);
+    const unsigned long long as = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.acc);
+    const unsigned long long ks = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.clamp);
+    if (lane_id() == 0) {
+        if (cs) atomicAdd(&a.ctr->candidates, cs);
+        if (as) atomicAdd(&a.ctr->collisions, as);
+        if (ks) atomicAdd(&a.ctr->clamps, ks);
     }
 }
 
@@ -884,7 +1023,6 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
     T* sv0 = reinterpret_cast<T*>(smem_raw + sizeof(unsigned long long) * kMax);
     T* sv1 = sv0 + kMax;
     T* sv2 = sv1 + kMax;
-    __shared__ double s_red[8][DSMC_NMOM];
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
@@ -955,32 +1093,16 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
             }
         }
         __syncthreads();
-        double m[DSMC_NMOM] = {0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
-            const T v0 = sv0[r], v1 = sv1[r], v2 = sv2[r];
-            const uint32_t o = beg + r;
-            a.vo[0][o] = v0;
-            a.vo[1][o] = v1;
-            a.vo[2][o] = v2;
-            if (slot_t >= 0) {
-                m[0] += 1.0;
-                m[1] += (double)v0; m[2] += (double)v1; m[3] += (double)v2;
-                m[4] += (double)v0 * (double)v0;
-                m[5] += (double)v1 * (double)v1;
-                m[6] += (double)v2 * (double)v2;
-            }
+        if (slot_t >= 0 && threadIdx.x == 0) {
+            double m[DSMC_NMOM];
+            cell_moments<T>(sv0, sv1, sv2, N, m);
+            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[(uint64_t)gcell * DSMC_NMOM + q] = m[q];
         }
-        if (slot_t >= 0) {
-#pragma unroll
-            for (int q = 0; q < DSMC_NMOM; ++q) m[q] = warp_sum(m[q]);
-            if (lane == 0)
-                for (int q = 0; q < DSMC_NMOM; ++q) s_red[w][q] = m[q];
-            __syncthreads();
-            if (threadIdx.x < DSMC_NMOM) {
-                double s = 0.0;
-                for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += s_red[ww][threadIdx.x];
-                a.mom[(uint64_t)gcell * DSMC_NMOM + threadIdx.x] = s;
-            }
+        for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
+            const uint32_t o = beg + r;
+            a.vo[0][o] = sv0[r];
+            a.vo[1][o] = sv1[r];
+            a.vo[2][o] = sv2[r];
         }
         __syncthreads();
     }
@@ -1161,10 +1283,22 @@ void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStrea
     DISPATCH_PREC(prec, (k_scatter<T><<<ls.scatter_blocks, 256, 0, s>>>(A<T>(args))));
 }
 
+size_t cell_smem_bytes(int prec, int budget)
+{
+    const size_t t = prec == DSMC_FP64 ? 8 : 4;
+    const size_t head = (kTileCells + 4) * sizeof(uint32_t);
+    const size_t tile = (size_t)budget * (4 + 3 * t);
+    const size_t warps = (kTileCells / 32) * (prec == DSMC_FP64 ? warp_scratch_bytes<double>()
+                                                                : warp_scratch_bytes<float>());
+    return head + (tile > warps ? tile : warps);
+}
+
 void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim,
-        (k_cell<T, D><<<ls.cell_blocks, kCellWarps * 32, 0, s>>>(A<T>(args)))));
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
+        const StepArgs<T>& a = A<T>(args);
+        k_cell<T, D><<<ls.cell_blocks, kTileCells, cell_smem_bytes(prec, a.tile_budget), s>>>(a);
+    }));
 }
 
 int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
@@ -1208,10 +1342,18 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
 {
     ls->dim = dim;
     ls->sms = sms;
+    // tile budget: two tile CTAs per SM
+    const int t = prec == DSMC_FP64 ? 8 : 4;
+    int budget = (int)((110 * 1024 - (kTileCells + 4) * 4) / (4 + 3 * t));
+    budget = budget / 256 * 256;
+    if (ls->tile_budget <= 0) ls->tile_budget = budget;
     int bm = 0, bc = 0;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
+        cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cell_smem_bytes(prec, ls->tile_budget));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_move<T, D>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_cell<T, D>, kCellWarps * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_cell<T, D>, kTileCells,
+                                                      cell_smem_bytes(prec, ls->tile_budget));
     }));
     ls->move_threads = 256;
     ls->move_blocks = sms * (bm > 0 ? bm : 4);
@@ -1220,12 +1362,15 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
     ls->big_blocks = sms;
 }
 
-cudaError_t prepare_kernels(int prec, int dim)
+cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
 {
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
         e = cudaFuncSetAttribute(k_cell_big<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)big_smem(prec));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cell_smem_bytes(prec, tile_budget));
     }));
     return e;
 }
