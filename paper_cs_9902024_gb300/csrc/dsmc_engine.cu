@@ -116,6 +116,7 @@ static dsmc_status build_cfg(dsmc_ctx* ctx, double dt, uint64_t seed)
     for (int a = 0; a < 3; ++a) {
         c.L[a] = D.extent[a];
         c.d[a] = c.L[a] / c.n[a];
+        c.inv_d[a] = 1.0 / c.d[a];
     }
     c.Vc = c.d[0] * c.d[1] * c.d[2];
     c.dt = dt;

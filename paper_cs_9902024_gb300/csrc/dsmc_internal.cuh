@@ -47,7 +47,7 @@ struct BcDev {
 struct Cfg {
     int32_t dim, n[3], ncells, n_bc, n_plate, hs, fill, pad_;
     int32_t plate_idx[DSMC_MAX_BC];
-    double L[3], d[3], Vc, dt, mass;
+    double L[3], d[3], inv_d[3], Vc, dt, mass;
     double coef;         // F_N dt / Vc
     double F_N;
     double A_hs;         // hard sphere: pi d^2 (sigma_T c_r = A_hs c_r)

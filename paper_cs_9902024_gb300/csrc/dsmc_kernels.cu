@@ -87,11 +87,16 @@ __device__ __forceinline__ void gauss2(T u1, T u2, T& z0, T& z1)
 
 // ---------------------------------------------------------------------------
 // Geometry helpers
+// position in cell units along axis a: x / dx in double precision; in
+// single precision x times the binary32 reciprocal of dx (one multiply)
+__device__ __forceinline__ double in_cells(const Cfg& c, int a, double x) { return x / c.d[a]; }
+__device__ __forceinline__ float in_cells(const Cfg& c, int a, float x) { return x * (float)c.inv_d[a]; }
+
 template <typename T>
 __device__ __forceinline__ int cell_1d(const Cfg& c, int a, T x)
 {
     if (a >= c.dim) return 0;
-    int i = (int)dfloor(x / (T)c.d[a]);
+    int i = (int)dfloor(in_cells(c, a, x));
     return i < 0 ? 0 : (i > c.n[a] - 1 ? c.n[a] - 1 : i);
 }
 
@@ -282,8 +287,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* smem_warp, uint32
     return before + x - v;
 }
 
-template <typename T>
-__device__ __forceinline__ uint32_t run_of_slot(const uint32_t* run_base, int n_runs, uint32_t s)
+__device__ __forceinline__ uint32_t run_search(const uint32_t* run_base, int n_runs, uint32_t s)
 {
     // largest r with run_base[r] <= s
     int lo = 0, hi = n_runs - 1;
@@ -292,6 +296,17 @@ __device__ __forceinline__ uint32_t run_of_slot(const uint32_t* run_base, int n_
         if (__ldg(run_base + mid) <= s) lo = mid; else hi = mid - 1;
     }
     return (uint32_t)lo;
+}
+
+// run of slot s for a warp whose slots start at s_first: every lane first
+// searches the same target (broadcast loads); lanes past that run's end
+// search their own slot
+__device__ __forceinline__ uint32_t run_of_slot(const uint32_t* run_base, int n_runs,
+                                                uint32_t s_first, uint32_t s)
+{
+    const uint32_t r0 = run_search(run_base, n_runs, s_first);
+    if (s < __ldg(run_base + r0 + 1)) return r0;
+    return run_search(run_base, n_runs, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -518,7 +533,7 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
         const bool valid = s < n_total;
         uint32_t key = kDead;
         if (valid) {
-            const uint32_t rl = run_of_slot<T>(a.run_base, a.n_runs, s);
+            const uint32_t rl = run_of_slot(a.run_base, a.n_runs, (uint32_t)base, s);
             T x[3], v[3];
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) { x[ax] = a.xi[ax][s]; v[ax] = a.vi[ax][s]; }
@@ -884,14 +899,15 @@ __host__ __device__ constexpr size_t warp_scratch_bytes()
 }
 
 // Tile path: one CTA takes kTileCells consecutive (run-major) cells, whose
-// particles occupy one contiguous range of the next pool.  Coalesced
-// thread-per-particle phases: (1) ids through the LCR into shared memory,
-// (2) each particle's rank inside its cell by counting smaller ids, then
-// positions and ids gathered into the next pool at cell start + rank and
-// velocities into shared memory in id order; thread-per-cell phase (3):
-// NTC collisions and moments; (4) velocities written back, coalesced.
-// Tiles whose particles exceed the shared-memory budget go cell by cell
-// through the warp path.
+// particles occupy one contiguous range of the next pool.  Thread-per-
+// particle phases (coalesced through the LCR): (1) ids into shared memory;
+// (2) each particle's rank inside its cell by counting smaller ids, then its
+// position, velocity and id gathered into the next pool at cell start +
+// rank.  Thread-per-cell phase (3): NTC collisions on the cell's velocities
+// in the next pool (just written by this CTA, so cache-resident) and the
+// moments at sample steps.  Only the ids are staged (4 bytes per particle),
+// which keeps many CTAs resident.  Tiles whose particles exceed the budget
+// go cell by cell through the warp path.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 {
@@ -900,9 +916,6 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
     const uint32_t budget = (uint32_t)a.tile_budget;
     uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* s_id = s_start + (kTileCells + 4);
-    T* s_v0 = reinterpret_cast<T*>(s_id + budget);
-    T* s_v1 = s_v0 + budget;
-    T* s_v2 = s_v1 + budget;
     __shared__ uint32_t s_red[kTileCells / 32];
     const int tid = threadIdx.x;
     const uint32_t step = a.ctr->step;
@@ -931,9 +944,12 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             __syncthreads();
             continue;
         }
+#pragma unroll 4
         for (uint32_t k = tid; k < Tn; k += kTileCells) s_id[k] = a.idi[a.lcr[B + k]];
         __syncthreads();
+#pragma unroll 2
         for (uint32_t k = tid; k < Tn; k += kTileCells) {
+            const uint32_t s = a.lcr[B + k];
             // cell of tile position k: last i with s_start[i] - B <= k
             int lo = 0, hi = nct - 1;
             while (lo < hi) {
@@ -944,21 +960,19 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             const uint32_t my = s_id[k];
             uint32_t r = 0;
             for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
-            const uint32_t pos = cb + r;
-            const uint32_t s = a.lcr[B + k];
-            const uint32_t o = B + pos;
+            const uint32_t o = B + cb + r;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
             a.ido[o] = my;
-            s_v0[pos] = a.vi[0][s];
-            s_v1[pos] = a.vi[1][s];
-            s_v2[pos] = a.vi[2][s];
+            a.vo[0][o] = a.vi[0][s];
+            a.vo[1][o] = a.vi[1][s];
+            a.vo[2][o] = a.vi[2][s];
             if (a.lcr_dbg) a.lcr_dbg[o] = s;
         }
         __syncthreads();
         if (tid < nct) {
             const int64_t gcell = c0 + tid;
-            const uint32_t cb = s_start[tid] - B;
+            const uint32_t beg = s_start[tid];
             const uint32_t N = myN;
             const uint32_t rl = (uint32_t)(gcell / c.ncells);
             const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
@@ -967,9 +981,9 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             const int64_t M = ntc_count(c, N, (double)smax, rem);
             T seen = (T)0;
             uint32_t nacc = 0, nclamp = 0;
-            T* v0 = s_v0 + cb;
-            T* v1 = s_v1 + cb;
-            T* v2 = s_v2 + cb;
+            T* v0 = a.vo[0] + beg;
+            T* v1 = a.vo[1] + beg;
+            T* v2 = a.vo[2] + beg;
             for (int64_t k = 0; k < M; ++k) {
                 uint32_t i, j;
                 T u2, u3, ue;
@@ -987,12 +1001,6 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
                 cell_moments<T>(v0, v1, v2, N, m);
                 for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
             }
-        }
-        __syncthreads();
-        for (uint32_t k = tid; k < Tn; k += kTileCells) {
-            a.vo[0][B + k] = s_v0[k];
-            a.vo[1][B + k] = s_v1[k];
-            a.vo[2][B + k] = s_v2[k];
         }
         __syncthreads();
     }
@@ -1285,9 +1293,8 @@ void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStrea
 
 size_t cell_smem_bytes(int prec, int budget)
 {
-    const size_t t = prec == DSMC_FP64 ? 8 : 4;
     const size_t head = (kTileCells + 4) * sizeof(uint32_t);
-    const size_t tile = (size_t)budget * (4 + 3 * t);
+    const size_t tile = (size_t)budget * 4;
     const size_t warps = (kTileCells / 32) * (prec == DSMC_FP64 ? warp_scratch_bytes<double>()
                                                                 : warp_scratch_bytes<float>());
     return head + (tile > warps ? tile : warps);
@@ -1342,10 +1349,9 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
 {
     ls->dim = dim;
     ls->sms = sms;
-    // tile budget: two tile CTAs per SM
-    const int t = prec == DSMC_FP64 ? 8 : 4;
-    int budget = (int)((110 * 1024 - (kTileCells + 4) * 4) / (4 + 3 * t));
-    budget = budget / 256 * 256;
+    // tile budget: up to 8192 staged ids (32 KB), at least the warp path's
+    // scratch; several tile CTAs stay resident per SM
+    int budget = 8192;
     if (ls->tile_budget <= 0) ls->tile_budget = budget;
     int bm = 0, bc = 0;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
