@@ -801,6 +801,27 @@ __device__ __forceinline__ void cell_moments(const T* sv0, const T* sv1, const T
     }
 }
 
+// A slot read back from the LCR; anything outside the pool (possible only
+// after an overflow already flagged in the error word) is replaced by slot 0
+// and flagged, so no access leaves the buffers.
+template <typename T>
+__device__ __forceinline__ uint32_t checked_slot(const StepArgs<T>& a, uint32_t s)
+{
+    if ((int64_t)s >= a.cap_old + a.cap_new) {
+        atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+        return 0u;
+    }
+    return s;
+}
+
+// Particle (idj, j) comes before (idk, k) in a cell: ids are unique within a
+// run, the position only breaks ties in a state already flagged as
+// corrupted, so the ranks always form a permutation.
+__device__ __forceinline__ bool id_before(uint32_t idj, uint32_t j, uint32_t idk, uint32_t k)
+{
+    return idj < idk || (idj == idk && j < k);
+}
+
 struct CellTally {
     unsigned long long cand = 0, acc = 0, clamp = 0;
 };
@@ -837,7 +858,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         return;
     }
     for (uint32_t k = lane; k < N; k += 32) {
-        const uint32_t s = a.lcr[beg + k];
+        const uint32_t s = checked_slot(a, a.lcr[beg + k]);
         sl[k] = s;
         sid[k] = a.idi[s];
     }
@@ -845,7 +866,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
     for (uint32_t k = lane; k < N; k += 32) {
         const uint32_t my = sid[k];
         uint32_t r = 0;
-        for (uint32_t j = 0; j < N; ++j) r += sid[j] < my ? 1u : 0u;
+        for (uint32_t j = 0; j < N; ++j) r += id_before(sid[j], j, my, k) ? 1u : 0u;
         sp[r] = (uint16_t)k;
     }
     __syncwarp();
@@ -945,11 +966,11 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             continue;
         }
 #pragma unroll 4
-        for (uint32_t k = tid; k < Tn; k += kTileCells) s_id[k] = a.idi[a.lcr[B + k]];
+        for (uint32_t k = tid; k < Tn; k += kTileCells) s_id[k] = a.idi[checked_slot(a, a.lcr[B + k])];
         __syncthreads();
 #pragma unroll 2
         for (uint32_t k = tid; k < Tn; k += kTileCells) {
-            const uint32_t s = a.lcr[B + k];
+            const uint32_t s = checked_slot(a, a.lcr[B + k]);
             // cell of tile position k: last i with s_start[i] - B <= k
             int lo = 0, hi = nct - 1;
             while (lo < hi) {
@@ -959,7 +980,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             const uint32_t cb = s_start[lo] - B, ce = s_start[lo + 1] - B;
             const uint32_t my = s_id[k];
             uint32_t r = 0;
-            for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
+            for (uint32_t j = cb; j < ce; ++j) r += id_before(s_id[j], j, my, k) ? 1u : 0u;
             const uint32_t o = B + cb + r;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
@@ -1050,7 +1071,7 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
         while (P < N) P <<= 1;
         for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) {
             if (k < N) {
-                const uint32_t s = a.lcr[beg + k];
+                const uint32_t s = checked_slot(a, a.lcr[beg + k]);
                 keys[k] = ((unsigned long long)a.idi[s] << 32) | s;
             } else {
                 keys[k] = ~0ull;
