@@ -699,7 +699,9 @@ template <typename T>
 __device__ __forceinline__ void scatter_pair(T* v1, T* v2, T g, T u3, T ueps)
 {
     const T cosx = (T)2.0 * u3 - (T)1.0;
-    const T sinx = dsqrt((T)1.0 - cosx * cosx);
+    // sin(chi) = sqrt(1 - cos^2 chi) = 2 sqrt(u3 (1 - u3)): the second form
+    // has no cancellation when cos(chi) is near +-1 (u3 and 1 - u3 are exact)
+    const T sinx = (T)2.0 * dsqrt(u3 * ((T)1.0 - u3));
     T se, ce;
     dsincospi((T)2.0 * ueps, &se, &ce);
     const T gr[3] = {g * cosx, g * sinx * ce, g * sinx * se};
