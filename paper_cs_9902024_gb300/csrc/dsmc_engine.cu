@@ -63,6 +63,7 @@ struct dsmc_ctx {
     void* X[2][3] = {};
     void* V[2][3] = {};
     uint32_t* ID[2] = {};
+    uint32_t* CI[2] = {};            // run-local cell index of each pool particle
     uint32_t *gc = nullptr, *rank = nullptr, *lcr = nullptr, *lcr_dbg = nullptr;
     uint32_t *count = nullptr, *start = nullptr, *block_sums = nullptr;
     uint32_t *run_base = nullptr, *next_id = nullptr, *cand = nullptr, *accd = nullptr;
@@ -289,6 +290,7 @@ static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, in
             ctx->V[b][a] = A(ts * slots);
         }
         ctx->ID[b] = (uint32_t*)A(4 * slots);
+        ctx->CI[b] = (uint32_t*)A(4 * cap_old);
     }
     ctx->gc = (uint32_t*)A(4 * slots);
     ctx->rank = (uint32_t*)A(4 * slots);
@@ -344,6 +346,8 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
         a.vo[ax] = (T*)ctx->V[1 - cur][ax];
     }
     a.idi = ctx->ID[cur];
+    a.ci_i = ctx->CI[cur];
+    a.ci_o = ctx->CI[1 - cur];
     a.ido = ctx->ID[1 - cur];
     a.gc = ctx->gc;
     a.rank = ctx->rank;
@@ -565,7 +569,7 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
         if (cells->n[a] < 1 || !(domain->extent[a] > 0.0)) return DSMC_E_INVALID;
     if (domain->dim == 2 && !(domain->extent[2] > 0.0)) return DSMC_E_INVALID;
     const int64_t nc = (int64_t)cells->n[0] * cells->n[1] * (domain->dim == 3 ? cells->n[2] : 1);
-    if (nc > (1 << 28)) return DSMC_E_INVALID;
+    if (nc > (1 << 24)) return DSMC_E_INVALID;
     if (!(gas->mass > 0.0) || !(gas->d_ref >= 0.0) || !(gas->F_N > 0.0) || !(gas->T_ref > 0.0) ||
         !(gas->omega >= 0.5 && gas->omega <= 1.0))
         return DSMC_E_INVALID;
@@ -577,7 +581,7 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
         if (s.face == DSMC_FACE_PLATE) {
             if (s.kind != DSMC_BC_SPECULAR && s.kind != DSMC_BC_DIFFUSE) return DSMC_E_INVALID;
             if (s.plate_axis < 0 || s.plate_axis >= domain->dim) return DSMC_E_INVALID;
-            if (s.plate_index < 0 || s.plate_index > cells->n[s.plate_axis]) return DSMC_E_INVALID;
+            if (s.plate_index < 1 || s.plate_index > cells->n[s.plate_axis] - 1) return DSMC_E_INVALID;
         } else if (s.face < 0 || s.face >= 2 * domain->dim) {
             return DSMC_E_INVALID;
         }
@@ -841,6 +845,17 @@ dsmc_status dsmc_debug_step(dsmc_ctx* ctx, int n_steps)
     return check_error_word(ctx, h.error);
 }
 
+// run-local cell index <-> per-axis indices
+static void decode_host(const dsmc_ctx* ctx, uint32_t lin, int* ci)
+{
+    const int n0 = ctx->hcfg.n[0], n1 = ctx->hcfg.n[1];
+    ci[0] = (int)(lin % n0);
+    ci[1] = (int)((lin / n0) % n1);
+    ci[2] = (int)(lin / ((uint32_t)n0 * n1));
+}
+
+// the pool holds offsets inside each particle's cell; the test hooks speak
+// absolute positions: x = i * d + f
 template <typename T>
 static dsmc_status get_run_state(dsmc_ctx* ctx, int run, std::vector<double>& x,
                                  std::vector<double>& v, std::vector<uint32_t>& id)
@@ -854,17 +869,23 @@ static dsmc_status get_run_state(dsmc_ctx* ctx, int run, std::vector<double>& x,
     v.assign(3 * n, 0.0);
     id.assign(n, 0);
     std::vector<T> tmp(n);
+    std::vector<uint32_t> cells(n);
+    if (n) CK(cudaMemcpy(cells.data(), ctx->CI[ctx->cur] + rb[0], 4 * n, cudaMemcpyDeviceToHost));
     for (int a = 0; a < 3; ++a) {
-        if (ctx->X[ctx->cur][a]) {
+        if (ctx->X[ctx->cur][a] && n) {
             CK(cudaMemcpy(tmp.data(), (T*)ctx->X[ctx->cur][a] + rb[0], sizeof(T) * n,
                           cudaMemcpyDeviceToHost));
-            for (size_t k = 0; k < n; ++k) x[3 * k + a] = (double)tmp[k];
+            for (size_t k = 0; k < n; ++k) {
+                int ci[3];
+                decode_host(ctx, cells[k], ci);
+                x[3 * k + a] = (double)ci[a] * ctx->hcfg.d[a] + (double)tmp[k];
+            }
         }
-        CK(cudaMemcpy(tmp.data(), (T*)ctx->V[ctx->cur][a] + rb[0], sizeof(T) * n,
-                      cudaMemcpyDeviceToHost));
+        if (n) CK(cudaMemcpy(tmp.data(), (T*)ctx->V[ctx->cur][a] + rb[0], sizeof(T) * n,
+                             cudaMemcpyDeviceToHost));
         for (size_t k = 0; k < n; ++k) v[3 * k + a] = (double)tmp[k];
     }
-    CK(cudaMemcpy(id.data(), ctx->ID[ctx->cur] + rb[0], 4 * n, cudaMemcpyDeviceToHost));
+    if (n) CK(cudaMemcpy(id.data(), ctx->ID[ctx->cur] + rb[0], 4 * n, cudaMemcpyDeviceToHost));
     return DSMC_OK;
 }
 
@@ -899,7 +920,9 @@ static dsmc_status set_run_state(dsmc_ctx* ctx, int run, int64_t n, const double
     if ((int64_t)rb[nl] > ctx->cap_old) return fail(ctx, DSMC_E_CAPACITY, "pool overflowed");
     const size_t old_total = rb[nl];
     std::vector<std::vector<T>> X(3), V(3);
-    std::vector<uint32_t> I(old_total);
+    std::vector<uint32_t> I(old_total), CIh(old_total);
+    if (old_total)
+        CK(cudaMemcpy(CIh.data(), ctx->CI[ctx->cur], 4 * old_total, cudaMemcpyDeviceToHost));
     for (int a = 0; a < 3; ++a) {
         X[a].resize(old_total);
         V[a].resize(old_total);
@@ -909,17 +932,27 @@ static dsmc_status set_run_state(dsmc_ctx* ctx, int run, int64_t n, const double
     }
     CK(cudaMemcpy(I.data(), ctx->ID[ctx->cur], 4 * old_total, cudaMemcpyDeviceToHost));
     std::vector<std::vector<T>> NX(3), NV(3);
-    std::vector<uint32_t> NI;
+    std::vector<uint32_t> NI, NC;
     std::vector<uint32_t> nrb(nl + 1, 0);
     for (int r = 0; r < nl; ++r) {
         nrb[r] = (uint32_t)NI.size();
         if (r == run) {
             for (int64_t k = 0; k < n; ++k) {
+                int ci[3] = {0, 0, 0};
                 for (int a = 0; a < 3; ++a) {
-                    NX[a].push_back((T)x[3 * k + a]);
+                    double f = 0.0;
+                    if (a < ctx->dim) {
+                        const double xa = x[3 * k + a], d = ctx->hcfg.d[a];
+                        int i = (int)std::floor(xa / d);
+                        i = std::max(0, std::min(ctx->hcfg.n[a] - 1, i));
+                        ci[a] = i;
+                        f = xa - (double)i * d;
+                    }
+                    NX[a].push_back((T)f);
                     NV[a].push_back((T)v[3 * k + a]);
                 }
                 NI.push_back(id[k]);
+                NC.push_back((uint32_t)(ci[0] + ctx->hcfg.n[0] * (ci[1] + ctx->hcfg.n[1] * ci[2])));
             }
         } else {
             for (size_t k = rb[r]; k < rb[r + 1]; ++k) {
@@ -928,6 +961,7 @@ static dsmc_status set_run_state(dsmc_ctx* ctx, int run, int64_t n, const double
                     NV[a].push_back(V[a][k]);
                 }
                 NI.push_back(I[k]);
+                NC.push_back(CIh[k]);
             }
         }
     }
@@ -940,6 +974,7 @@ static dsmc_status set_run_state(dsmc_ctx* ctx, int run, int64_t n, const double
         if (tot) CK(cudaMemcpy(ctx->V[ctx->cur][a], NV[a].data(), sizeof(T) * tot, cudaMemcpyHostToDevice));
     }
     if (tot) CK(cudaMemcpy(ctx->ID[ctx->cur], NI.data(), 4 * tot, cudaMemcpyHostToDevice));
+    if (tot) CK(cudaMemcpy(ctx->CI[ctx->cur], NC.data(), 4 * tot, cudaMemcpyHostToDevice));
     nid[run] = next_id;
     CK(cudaMemcpy(ctx->run_base, nrb.data(), 4 * (nl + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->next_id, nid.data(), 4 * nl, cudaMemcpyHostToDevice));

@@ -73,8 +73,10 @@ struct StepArgs {
     const Cfg* cfg;
     Counters* ctr;
     // pool: in/out buffers of positions (dim used), velocities (3), ids
-    T* xi[3]; T* vi[3]; uint32_t* idi;
-    T* xo[3]; T* vo[3]; uint32_t* ido;
+    // positions are offsets inside the particle's cell; ci_* hold the
+    // run-local linear cell index of each particle of the pool
+    T* xi[3]; T* vi[3]; uint32_t* idi; uint32_t* ci_i;
+    T* xo[3]; T* vo[3]; uint32_t* ido; uint32_t* ci_o;
     uint32_t* gc;          // per slot: run-major cell key, or kDead
     uint32_t* rank;        // per slot: rank within its cell (any order)
     uint32_t* lcr;         // per pool position: slot (cell-grouped)

@@ -86,27 +86,59 @@ __device__ __forceinline__ void gauss2(T u1, T u2, T& z0, T& z1)
 }
 
 // ---------------------------------------------------------------------------
-// Geometry helpers
-// position in cell units along axis a: x / dx in double precision; in
-// single precision x times the binary32 reciprocal of dx (one multiply)
-__device__ __forceinline__ double in_cells(const Cfg& c, int a, double x) { return x / c.d[a]; }
-__device__ __forceinline__ float in_cells(const Cfg& c, int a, float x) { return x * (float)c.inv_d[a]; }
+// Geometry.  A particle's position is held as its run-local cell index (one
+// integer per axis while it moves, one linear index in memory) and its
+// offset f in [0, d_a] from that cell's lower corner along each axis.  The
+// distances Motion needs -- to a wall, a plate or a cell face -- are then
+// differences of numbers no larger than a few cells, so binary32 state
+// resolves positions to ~1e-7 of a cell rather than of the domain.
 
+// offset in cell units: f / d in double precision; in single precision f
+// times the binary32 reciprocal of d (one multiply)
+__device__ __forceinline__ double in_cells(const Cfg& c, int a, double f) { return f / c.d[a]; }
+__device__ __forceinline__ float in_cells(const Cfg& c, int a, float f) { return f * (float)c.inv_d[a]; }
+
+// move whole cells so that 0 <= f <= d along axis a (clamped to the grid)
 template <typename T>
-__device__ __forceinline__ int cell_1d(const Cfg& c, int a, T x)
+__device__ __forceinline__ void renorm(const Cfg& c, int a, int& i, T& f)
 {
-    if (a >= c.dim) return 0;
-    int i = (int)dfloor(in_cells(c, a, x));
-    return i < 0 ? 0 : (i > c.n[a] - 1 ? c.n[a] - 1 : i);
+    const int k = (int)dfloor(in_cells(c, a, f));
+    if (k != 0) {
+        int ni = i + k;
+        ni = ni < 0 ? 0 : (ni > c.n[a] - 1 ? c.n[a] - 1 : ni);
+        f = f - (T)(ni - i) * (T)c.d[a];
+        i = ni;
+    }
 }
 
-template <typename T, int DIM>
-__device__ __forceinline__ int cell_of(const Cfg& c, const T* x)
+// x / n for x < 2^24 (float quotient, corrected by one)
+__device__ __forceinline__ uint32_t div_small(uint32_t x, uint32_t n)
 {
-    const int i0 = cell_1d<T>(c, 0, x[0]);
-    const int i1 = cell_1d<T>(c, 1, x[1]);
-    const int i2 = DIM == 3 ? cell_1d<T>(c, 2, x[2]) : 0;
-    return i0 + c.n[0] * (i1 + c.n[1] * i2);
+    uint32_t q = (uint32_t)((float)x * __frcp_rn((float)n));
+    if (q * n > x) --q;
+    else if ((q + 1u) * n <= x) ++q;
+    return q;
+}
+
+template <int DIM>
+__device__ __forceinline__ void decode_cell(const Cfg& c, uint32_t lin, int* ci)
+{
+    const uint32_t q = div_small(lin, (uint32_t)c.n[0]);
+    ci[0] = (int)(lin - q * (uint32_t)c.n[0]);
+    if (DIM == 3) {
+        const uint32_t q2 = div_small(q, (uint32_t)c.n[1]);
+        ci[1] = (int)(q - q2 * (uint32_t)c.n[1]);
+        ci[2] = (int)q2;
+    } else {
+        ci[1] = (int)q;
+        ci[2] = 0;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t encode_cell(const Cfg& c, const int* ci)
+{
+    return (uint32_t)(ci[0] + c.n[0] * (ci[1] + (DIM == 3 ? c.n[1] * ci[2] : 0)));
 }
 
 __device__ __forceinline__ bool bc_active(const BcDev& b, int step)
@@ -132,12 +164,42 @@ struct LocalCounters {
     uint32_t removed = 0, wall_hits = 0, bounce = 0;
 };
 
+// Straight flight for tau that ends strictly inside the box (by a margin far
+// above rounding) and changes no cell along a plate's axis: no surface event
+// can occur, and the result equals move_particle's.  Returns false (state
+// untouched) otherwise.
+template <typename T, int DIM>
+__device__ __forceinline__ bool try_free_flight(const Cfg& c, int* ci, T* f, const T* v, T tau)
+{
+    const T margin = sizeof(T) == 4 ? (T)1e-5 : (T)1e-12;
+    int ni[3];
+    T nf[3];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const T d = (T)c.d[a];
+        nf[a] = f[a] + v[a] * tau;
+        const int k = (int)dfloor(in_cells(c, a, nf[a]));
+        ni[a] = ci[a] + k;
+        if (ni[a] < 0 || ni[a] > c.n[a] - 1) return false;
+        if (k != 0) nf[a] = nf[a] - (T)k * d;
+        if (ni[a] == 0 && !(nf[a] > margin * d)) return false;
+        if (ni[a] == c.n[a] - 1 && !(nf[a] < d - margin * d)) return false;
+    }
+    for (int pi = 0; pi < c.n_plate; ++pi) {
+        const int a = c.bc[c.plate_idx[pi]].plate_axis;
+        if (ni[a] != ci[a]) return false;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { ci[a] = ni[a]; f[a] = nf[a]; }
+    return true;
+}
+
 // Motion of one particle for time tau: free flight with the surface events
 // taken in time order (ties: x, y, z faces, then plates in list order).
 // Returns false if the particle left through an open face.  vmask collects
 // the velocity components that changed.
 template <typename T, int DIM>
-__device__ bool move_particle(const Cfg& c, T* x, T* v, uint32_t id, uint32_t run,
+__device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, uint32_t run,
                               uint32_t step, T tau, LocalCounters& lc, uint32_t& vmask)
 {
     for (int bounce = 0;; ++bounce) {
@@ -145,9 +207,10 @@ __device__ bool move_particle(const Cfg& c, T* x, T* v, uint32_t id, uint32_t ru
         T th = (T)0;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
+            const T d = (T)c.d[a];
             T t;
-            if (v[a] > (T)0) t = ((T)c.L[a] - x[a]) / v[a];
-            else if (v[a] < (T)0) t = ((T)0 - x[a]) / v[a];
+            if (v[a] > (T)0) t = ((T)(c.n[a] - 1 - ci[a]) * d + (d - f[a])) / v[a];
+            else if (v[a] < (T)0) t = ((T)ci[a] * d + f[a]) / (-v[a]);
             else continue;
             if (t < (T)0) t = (T)0;
             if (t <= tau && (hit < 0 || t < th)) { hit = 2 * a + (v[a] > (T)0 ? 1 : 0); th = t; }
@@ -157,23 +220,28 @@ __device__ bool move_particle(const Cfg& c, T* x, T* v, uint32_t id, uint32_t ru
             const BcDev& b = c.bc[q];
             if (!bc_active(b, step)) continue;
             const int a = b.plate_axis;
-            const T xp = (T)b.plate_index * (T)c.d[a];
-            if (!((x[a] < xp && v[a] > (T)0) || (x[a] > xp && v[a] < (T)0))) continue;
-            const T t = (xp - x[a]) / v[a];
+            const T dist = (T)(b.plate_index - ci[a]) * (T)c.d[a] - f[a];   // x_plate - x
+            if (!((dist > (T)0 && v[a] > (T)0) || (dist < (T)0 && v[a] < (T)0))) continue;
+            const T t = dist / v[a];
             if (!(t <= tau && (hit < 0 || t < th))) continue;
             bool inside = true;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int ta = k == 0 ? b.t0 : b.t1;
-                if (ta >= DIM) continue;
-                const T y = x[ta] + v[ta] * t;
-                if (!(y >= (T)b.lo[k] * (T)c.d[ta] && y < (T)b.hi[k] * (T)c.d[ta])) inside = false;
+                const int tb = k == 0 ? b.t0 : b.t1;
+                if (tb >= DIM) continue;
+                int ib = ci[tb];
+                T fb = f[tb] + v[tb] * t;
+                renorm<T>(c, tb, ib, fb);
+                if (!(ib >= b.lo[k] && ib < b.hi[k])) inside = false;
             }
             if (inside) { hit = 100 + q; th = t; }
         }
         if (hit < 0) {
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) x[a] = x[a] + v[a] * tau;
+            for (int a = 0; a < DIM; ++a) {
+                f[a] = f[a] + v[a] * tau;
+                renorm<T>(c, a, ci[a], f[a]);
+            }
             return true;
         }
         if (bounce == kMaxBounce) { lc.bounce++; return true; }
@@ -184,13 +252,18 @@ __device__ bool move_particle(const Cfg& c, T* x, T* v, uint32_t id, uint32_t ru
             axis = hit >> 1;
             const int side = hit & 1;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a)
-                x[a] = (a == axis) ? (side ? (T)c.L[a] : (T)0) : x[a] + v[a] * th;
+            for (int a = 0; a < DIM; ++a) {
+                if (a == axis) {
+                    ci[a] = side ? c.n[a] - 1 : 0;
+                    f[a] = side ? (T)c.d[a] : (T)0;
+                } else {
+                    f[a] = f[a] + v[a] * th;
+                    renorm<T>(c, a, ci[a], f[a]);
+                }
+            }
             t0 = axis == 0 ? 1 : 0;
             t1 = axis == 2 ? 1 : 2;
-            const int ia = cell_1d<T>(c, t0, x[t0]);
-            const int ib = cell_1d<T>(c, t1, t1 < DIM ? x[t1] : (T)0);
-            const int q = bc_lookup(c, hit, ia, ib, (int)step);
+            const int q = bc_lookup(c, hit, ci[t0], t1 < DIM ? ci[t1] : 0, (int)step);
             kind = q < 0 ? DSMC_BC_OUTFLOW : c.bc[q].kind;
             if (q >= 0) Tsd = c.bc[q].sd;
             dir = side ? (T)-1 : (T)1;
@@ -199,10 +272,17 @@ __device__ bool move_particle(const Cfg& c, T* x, T* v, uint32_t id, uint32_t ru
             axis = b.plate_axis;
             t0 = b.t0;
             t1 = b.t1;
-            const T xp = (T)b.plate_index * (T)c.d[axis];
             dir = v[axis] > (T)0 ? (T)-1 : (T)1;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) x[a] = (a == axis) ? xp : x[a] + v[a] * th;
+            for (int a = 0; a < DIM; ++a) {
+                if (a == axis) {
+                    ci[a] = b.plate_index;
+                    f[a] = (T)0;
+                } else {
+                    f[a] = f[a] + v[a] * th;
+                    renorm<T>(c, a, ci[a], f[a]);
+                }
+            }
             kind = b.kind;
             Tsd = b.sd;
         }
@@ -356,8 +436,6 @@ __global__ void k_fill_particles(StepArgs<T> a)
             if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
             continue;
         }
-        const int ic[3] = {(int)(cell % c.n[0]), (int)((cell / c.n[0]) % c.n[1]),
-                           (int)(cell / (c.n[0] * c.n[1]))};
         const T sd = (T)c.fill_sd;
         for (uint32_t k = lane; k < N; k += 32) {
             const uint4 b0 = draw_bits(c.seed, a.run0 + rl, 0u, cell, kFillPart, 2u * k);
@@ -368,10 +446,11 @@ __global__ void k_fill_particles(StepArgs<T> a)
             const T ub[3] = {u01<T>(b1.x), u01<T>(b1.y), u01<T>(b1.z)};
             const uint32_t p = beg + k;
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) a.xi[ax][p] = ((T)ic[ax] + ub[ax]) * (T)c.d[ax];
+            for (int ax = 0; ax < DIM; ++ax) a.xi[ax][p] = ub[ax] * (T)c.d[ax];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) a.vi[ax][p] = (T)c.fill_U[ax] + sd * z[ax];
             a.idi[p] = (beg - a.run_base[rl]) + k;
+            a.ci_i[p] = cell;
         }
     }
 }
@@ -475,16 +554,22 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
             }
             if (!got) rejects++;
             T x[3] = {(T)0, (T)0, (T)0}, v[3];
-            x[b.axis] = b.side ? (T)c.L[b.axis] : (T)0;
-            x[b.t0] = ((T)aa + u01<T>(b0.x)) * (T)c.d[b.t0];
-            if (b.t1 < DIM) x[b.t1] = ((T)bb + u01<T>(b0.y)) * (T)c.d[b.t1];
+            int ci[3] = {0, 0, 0};
+            ci[b.axis] = b.side ? c.n[b.axis] - 1 : 0;
+            x[b.axis] = b.side ? (T)c.d[b.axis] : (T)0;
+            ci[b.t0] = aa;
+            x[b.t0] = u01<T>(b0.x) * (T)c.d[b.t0];
+            if (b.t1 < DIM) {
+                ci[b.t1] = bb;
+                x[b.t1] = u01<T>(b0.y) * (T)c.d[b.t1];
+            }
             v[b.axis] = (T)b.dir * (T)b.cmp * xi;
             v[b.t0] = (T)b.U[b.t0] + (T)b.sd * z0;
             v[b.t1] = (T)b.U[b.t1] + (T)b.sd * z1;
             const uint32_t id = id0 + local;
             const T tau = u01<T>(b0.z) * (T)c.dt;
             uint32_t vmask = 0;
-            const bool alive = move_particle<T, DIM>(c, x, v, id, run, step, tau, lc, vmask);
+            const bool alive = move_particle<T, DIM>(c, ci, x, v, id, run, step, tau, lc, vmask);
             const int64_t slot = gen_base + local;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xi[ax][slot] = x[ax];
@@ -493,7 +578,7 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
             a.idi[slot] = id;
             uint32_t key = kDead, rk = 0;
             if (alive) {
-                key = rl * (uint32_t)c.ncells + (uint32_t)cell_of<T, DIM>(c, x);
+                key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
                 rk = atomicAdd(&a.count[key], 1u);
             }
             a.gc[slot] = key;
@@ -535,36 +620,22 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
         if (valid) {
             const uint32_t rl = run_of_slot(a.run_base, a.n_runs, (uint32_t)base, s);
             T x[3], v[3];
+            int ci[3];
+            decode_cell<DIM>(c, a.ci_i[s], ci);
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) { x[ax] = a.xi[ax][s]; v[ax] = a.vi[ax][s]; }
             if (DIM == 2) { x[2] = (T)0; v[2] = (T)0; }
             uint32_t vmask = 0;
             bool alive = true;
-            // fast path: the straight flight ends inside the box by a margin
-            // far above rounding, so the full event search would find no
-            // face crossing and give the same x + v dt
-            const T margin = sizeof(T) == 4 ? (T)1e-5 : (T)1e-12;
-            bool inner = c.n_plate == 0;
-            T y[3];
-#pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) {
-                y[ax] = x[ax] + v[ax] * dt;
-                const T L = (T)c.L[ax];
-                inner = inner && (y[ax] > margin * L) && (y[ax] < L - margin * L);
-            }
-            if (inner) {
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) x[ax] = y[ax];
-            } else {
-                alive = move_particle<T, DIM>(c, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
-            }
+            if (!try_free_flight<T, DIM>(c, ci, x, v, dt))
+                alive = move_particle<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
             if (alive) {
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) a.xi[ax][s] = x[ax];
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax)
                     if (vmask & (1u << ax)) a.vi[ax][s] = v[ax];
-                key = rl * (uint32_t)c.ncells + (uint32_t)cell_of<T, DIM>(c, x);
+                key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
             }
         }
         const bool live = valid && key != kDead;
@@ -878,6 +949,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         const uint32_t o = beg + r;
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+        a.ci_o[o] = cell;
         a.ido[o] = sid[k];
         sv0[r] = a.vi[0][s];
         sv1[r] = a.vi[1][s];
@@ -940,6 +1012,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
     uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* s_id = s_start + (kTileCells + 4);
     __shared__ uint32_t s_red[kTileCells / 32];
+    __shared__ uint32_t s_lin[kTileCells];
     const int tid = threadIdx.x;
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
@@ -949,6 +1022,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
         const int64_t c0 = tile * kTileCells;
         const int nct = (int)min((int64_t)kTileCells, (int64_t)a.total_cells - c0);
         for (int i = tid; i <= kTileCells; i += blockDim.x) s_start[i] = a.start[c0 + min(i, nct)];
+        if (tid < nct) s_lin[tid] = (uint32_t)((c0 + tid) % c.ncells);
         __syncthreads();
         const uint32_t B = s_start[0], E = s_start[nct];
         const uint32_t Tn = E - B;
@@ -986,6 +1060,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             const uint32_t o = B + cb + r;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+            a.ci_o[o] = s_lin[lo];
             a.ido[o] = my;
             a.vo[0][o] = a.vi[0][s];
             a.vo[1][o] = a.vi[1][s];
@@ -1098,6 +1173,7 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
             const uint32_t o = beg + r;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+            a.ci_o[o] = cell;
             a.ido[o] = (uint32_t)(kk >> 32);
             sv0[r] = a.vi[0][s];
             sv1[r] = a.vi[1][s];
