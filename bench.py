@@ -157,14 +157,15 @@ def algorithmic_bytes(w, st, steps, runs):
     moved_old = st["particle_steps"] - st["generated"]
     pool = st["pool_steps"]
     return {
-        # read x (D) and v (D; the third component only at wall hits), write
-        # x (D), write the cell key and in-cell rank
-        "move": moved_old * (3 * D * t + 8),
+        # read the in-cell offsets (D), v (D; the third component only at
+        # wall hits) and the cell index, write the offsets (D), the cell key
+        # and the in-cell rank
+        "move": moved_old * (3 * D * t + 4 + 8),
         # read key + rank, write LCR
         "scatter": pool * 12,
-        # read LCR, id, x, v; write x, id, v; per cell: start, NTC remainder
-        # (read + write) and (sigma c_r)_max
-        "cell": pool * (4 + 2 * (D * t + 3 * t + 4)) + cells * steps * 24,
+        # read LCR, id, offsets, v; write offsets, cell index, id, v; per
+        # cell: start, NTC remainder (read + write) and (sigma c_r)_max
+        "cell": pool * (4 + 2 * (D * t + 3 * t + 4) + 4) + cells * steps * 24,
         # read counts twice, write starts, clear counts
         "scan": cells * steps * 16,
         # write the entrants (x, v, id, key, rank)

@@ -186,12 +186,35 @@ __device__ __forceinline__ bool try_free_flight(const Cfg& c, int* ci, T* f, con
         if (ni[a] == c.n[a] - 1 && !(nf[a] < d - margin * d)) return false;
     }
     for (int pi = 0; pi < c.n_plate; ++pi) {
-        const int a = c.bc[c.plate_idx[pi]].plate_axis;
-        if (ni[a] != ci[a]) return false;
+        const int pa = c.bc[c.plate_idx[pi]].plate_axis;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            if (a == pa && ni[a] != ci[a]) return false;
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { ci[a] = ni[a]; f[a] = nf[a]; }
     return true;
+}
+
+template <typename T, int DIM>
+__device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, uint32_t run,
+                              uint32_t step, T tau, LocalCounters& lc, uint32_t& vmask);
+
+// move_particle on copies, out of line: its runtime-indexed arrays stay in
+// its own frame and the caller's fast path keeps its state in registers
+template <typename T, int DIM>
+__device__ __noinline__ bool move_particle_slow(const Cfg& c, int* ci, T* f, T* v, uint32_t id,
+                                                uint32_t run, uint32_t step, T tau,
+                                                LocalCounters& lc, uint32_t& vmask)
+{
+    int ci2[3] = {ci[0], ci[1], ci[2]};
+    T f2[3] = {f[0], f[1], f[2]};
+    T v2[3] = {v[0], v[1], v[2]};
+    const bool alive = move_particle<T, DIM>(c, ci2, f2, v2, id, run, step, tau, lc, vmask);
+    ci[0] = ci2[0]; ci[1] = ci2[1]; ci[2] = ci2[2];
+    f[0] = f2[0]; f[1] = f2[1]; f[2] = f2[2];
+    v[0] = v2[0]; v[1] = v2[1]; v[2] = v2[2];
+    return alive;
 }
 
 // Motion of one particle for time tau: free flight with the surface events
@@ -628,7 +651,8 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
             uint32_t vmask = 0;
             bool alive = true;
             if (!try_free_flight<T, DIM>(c, ci, x, v, dt))
-                alive = move_particle<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
+                alive = move_particle_slow<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc,
+                                                   vmask);
             if (alive) {
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) a.xi[ax][s] = x[ax];
@@ -806,6 +830,35 @@ __device__ __forceinline__ void candidate_draws(const Cfg& c, uint32_t run, uint
     u2 = u01<T>(r.z);
     u3 = u01<T>(r.w);
     ue = u01<T>(r2.x);
+}
+
+// the same candidate for a single thread: the azimuth block is drawn only
+// when the pair is accepted
+template <typename T>
+__device__ __forceinline__ void collide_candidate_lazy(const Cfg& c, T* sv0, T* sv1, T* sv2,
+                                                       uint32_t run, uint32_t step, uint32_t cell,
+                                                       int64_t k, uint32_t N, T smax, T& seen,
+                                                       uint32_t& nacc, uint32_t& nclamp)
+{
+    const uint4 r = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k));
+    const uint32_t i = pick(r.x, N);
+    uint32_t j = pick(r.y, N - 1u);
+    if (j >= i) j += 1u;
+    T v1[3] = {sv0[i], sv1[i], sv2[i]};
+    T v2[3] = {sv0[j], sv1[j], sv2[j]};
+    const T gx = v1[0] - v2[0], gy = v1[1] - v2[1], gz = v1[2] - v2[2];
+    const T g2 = gx * gx + gy * gy + gz * gz;
+    const T g = dsqrt(g2);
+    const T sc = sigma_cr<T>(c, g, g2);
+    if (sc > seen) seen = sc;
+    if (sc > smax) nclamp++;
+    if (u01<T>(r.z) < sc / smax) {
+        const uint4 r2 = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k + 1));
+        scatter_pair<T>(v1, v2, g, u01<T>(r.w), u01<T>(r2.x));
+        sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
+        sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
+        nacc++;
+    }
 }
 
 // One NTC candidate pair (i, j) on velocities in shared memory: accept with
@@ -1004,13 +1057,14 @@ __host__ __device__ constexpr size_t warp_scratch_bytes()
 // which keeps many CTAs resident.  Tiles whose particles exceed the budget
 // go cell by cell through the warp path.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
+__global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 {
     const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t budget = (uint32_t)a.tile_budget;
     uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* s_id = s_start + (kTileCells + 4);
+    uint8_t* s_cellof = reinterpret_cast<uint8_t*>(s_id + budget);
     __shared__ uint32_t s_red[kTileCells / 32];
     __shared__ uint32_t s_lin[kTileCells];
     const int tid = threadIdx.x;
@@ -1041,22 +1095,22 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             __syncthreads();
             continue;
         }
+        if (tid < nct)
+            for (uint32_t k = s_start[tid] - B; k < s_start[tid + 1] - B; ++k) s_cellof[k] = (uint8_t)tid;
 #pragma unroll 4
         for (uint32_t k = tid; k < Tn; k += kTileCells) s_id[k] = a.idi[checked_slot(a, a.lcr[B + k])];
         __syncthreads();
 #pragma unroll 2
         for (uint32_t k = tid; k < Tn; k += kTileCells) {
             const uint32_t s = checked_slot(a, a.lcr[B + k]);
-            // cell of tile position k: last i with s_start[i] - B <= k
-            int lo = 0, hi = nct - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_start[mid] - B <= k) lo = mid; else hi = mid - 1;
-            }
+            const int lo = s_cellof[k];
             const uint32_t cb = s_start[lo] - B, ce = s_start[lo + 1] - B;
             const uint32_t my = s_id[k];
+            // ids are unique within a run; a duplicate (possible only in a
+            // state already flagged corrupt) leaves a hole, never an access
+            // outside the cell's range
             uint32_t r = 0;
-            for (uint32_t j = cb; j < ce; ++j) r += id_before(s_id[j], j, my, k) ? 1u : 0u;
+            for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
             const uint32_t o = B + cb + r;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
@@ -1082,12 +1136,9 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             T* v0 = a.vo[0] + beg;
             T* v1 = a.vo[1] + beg;
             T* v2 = a.vo[2] + beg;
-            for (int64_t k = 0; k < M; ++k) {
-                uint32_t i, j;
-                T u2, u3, ue;
-                candidate_draws<T>(c, a.run0 + rl, step, cell, k, N, i, j, u2, u3, ue);
-                collide_candidate<T>(c, v0, v1, v2, i, j, u2, u3, ue, smax, seen, nacc, nclamp);
-            }
+            for (int64_t k = 0; k < M; ++k)
+                collide_candidate_lazy<T>(c, v0, v1, v2, a.run0 + rl, step, cell, k, N, smax, seen,
+                                          nacc, nclamp);
             a.rem[gcell] = rem;
             if (seen > smax) a.smax[gcell] = seen;
             if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
@@ -1393,7 +1444,7 @@ void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStrea
 size_t cell_smem_bytes(int prec, int budget)
 {
     const size_t head = (kTileCells + 4) * sizeof(uint32_t);
-    const size_t tile = (size_t)budget * 4;
+    const size_t tile = (size_t)budget * 5;
     const size_t warps = (kTileCells / 32) * (prec == DSMC_FP64 ? warp_scratch_bytes<double>()
                                                                 : warp_scratch_bytes<float>());
     return head + (tile > warps ? tile : warps);
