@@ -163,9 +163,12 @@ def algorithmic_bytes(w, st, steps, runs):
         "move": moved_old * (3 * D * t + 4 + 8),
         # read key + rank, write LCR
         "scatter": pool * 12,
-        # read LCR, id, offsets, v; write offsets, cell index, id, v; per
-        # cell: start, NTC remainder (read + write) and (sigma c_r)_max
-        "cell": pool * (4 + 2 * (D * t + 3 * t + 4) + 4) + cells * steps * 24,
+        # read LCR, id, offsets, v; write offsets, cell index, id, v
+        "cell": pool * (4 + 2 * (D * t + 3 * t + 4) + 4) + cells * steps * 4,
+        # per cell: start, NTC remainder (read + write), (sigma c_r)_max;
+        # per candidate pair: both velocities read; per collision: written
+        "collide": cells * steps * 24 + st["candidates"] * 2 * 3 * t
+        + st["collisions"] * 2 * 3 * t,
         # read counts twice, write starts, clear counts
         "scan": cells * steps * 16,
         # write the entrants (x, v, id, key, rank)

@@ -179,7 +179,8 @@ typedef struct {
 
 /* kernel kinds of dsmc_stats.ms_kernel */
 enum { DSMC_K_GENERATE = 0, DSMC_K_MOVE = 1, DSMC_K_SCAN = 2, DSMC_K_SCATTER = 3,
-       DSMC_K_CELL = 4, DSMC_K_CELL_BIG = 5, DSMC_K_REDUCE = 6, DSMC_K_OTHER = 7 };
+       DSMC_K_CELL = 4, DSMC_K_CELL_BIG = 5, DSMC_K_REDUCE = 6, DSMC_K_OTHER = 7,
+       DSMC_K_COLLIDE = 8 };
 
 typedef struct dsmc_ctx dsmc_ctx;
 

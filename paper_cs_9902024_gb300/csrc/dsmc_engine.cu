@@ -419,12 +419,14 @@ static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev)
     launch_scatter(p, args, ls, s); mark();
     launch_cell(p, args, ls, s); mark();
     launch_cell_big(p, args, ls, s); mark();
+    launch_collide(p, args, ls, s); mark();
     launch_reduce(p, args, ls, s); mark();
     launch_step_end(p, args, s); mark();
 }
-static const int kStepKernels = 8;
-static const int kKindOf[kStepKernels] = {DSMC_K_GENERATE, DSMC_K_MOVE, DSMC_K_SCAN, DSMC_K_SCATTER,
-                                          DSMC_K_CELL, DSMC_K_CELL_BIG, DSMC_K_REDUCE, DSMC_K_OTHER};
+static const int kStepKernels = 9;
+static const int kKindOf[kStepKernels] = {DSMC_K_GENERATE, DSMC_K_MOVE,     DSMC_K_SCAN,
+                                          DSMC_K_SCATTER,  DSMC_K_CELL,     DSMC_K_CELL_BIG,
+                                          DSMC_K_COLLIDE,  DSMC_K_REDUCE,   DSMC_K_OTHER};
 
 static void enqueue_init(dsmc_ctx* ctx, const void* args)
 {

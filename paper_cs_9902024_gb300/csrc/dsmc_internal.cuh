@@ -111,7 +111,7 @@ struct LaunchShape {
     int dim;
     int sms;
     int move_blocks, move_threads;
-    int scatter_blocks, cell_blocks, big_blocks;
+    int scatter_blocks, cell_blocks, big_blocks, collide_blocks;
     int tile_budget;
 };
 
@@ -123,6 +123,7 @@ void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t
 void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_step_end(int prec, const void* args, cudaStream_t s);
 void launch_macro(int prec, const void* args, int sample, int n_runs, double* out,

@@ -952,21 +952,27 @@ struct CellTally {
     unsigned long long cand = 0, acc = 0, clamp = 0;
 };
 
+// A cell of more than kWarpMax particles is handled whole (sort, gather,
+// collisions, moments) by the one-CTA-per-cell kernel.
+template <typename T>
+__device__ __forceinline__ void push_big(const StepArgs<T>& a, int64_t gcell)
+{
+    const uint32_t idx = atomicAdd(&a.ctr->n_big, 1u);
+    if (idx < a.max_big) a.big_list[idx] = (uint32_t)gcell;
+    else atomicOr(&a.ctr->error, DSMC_ERR_BIGLIST);
+}
+
 // Warp path for one cell of up to kWarpMax particles: id ranks by counting,
-// gather into the next pool, NTC collisions, moments.  Used for tiles that
-// do not fit the tile kernel's shared-memory budget.  `ws` is this warp's
-// scratch: kWarpMax x (2 u32 + u16 + 3 T).
+// then the particles gathered into the next pool in id order.  Used for
+// tiles that do not fit the tile kernel's shared-memory budget.  `ws` is
+// this warp's scratch: kWarpMax x (2 u32 + u16).
 template <typename T, int DIM>
-__device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell, uint32_t step,
-                               int slot_t, unsigned char* ws, CellTally& tl)
+__device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell, unsigned char* ws)
 {
     const uint32_t lane = lane_id();
     uint32_t* sl = reinterpret_cast<uint32_t*>(ws);
     uint32_t* sid = sl + kWarpMax;
-    T* sv0 = reinterpret_cast<T*>(sid + kWarpMax);
-    T* sv1 = sv0 + kWarpMax;
-    T* sv2 = sv1 + kWarpMax;
-    uint16_t* sp = reinterpret_cast<uint16_t*>(sv2 + kWarpMax);
+    uint16_t* sp = reinterpret_cast<uint16_t*>(sid + kWarpMax);
     const uint32_t beg = a.start[gcell];
     const uint32_t N = a.start[gcell + 1] - beg;
     const uint32_t rl = (uint32_t)(gcell / c.ncells);
@@ -976,11 +982,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         return;
     }
     if (N > (uint32_t)kWarpMax) {
-        if (lane == 0) {
-            const uint32_t idx = atomicAdd(&a.ctr->n_big, 1u);
-            if (idx < a.max_big) a.big_list[idx] = (uint32_t)gcell;
-            else atomicOr(&a.ctr->error, DSMC_ERR_BIGLIST);
-        }
+        if (lane == 0) push_big(a, gcell);
         return;
     }
     for (uint32_t k = lane; k < N; k += 32) {
@@ -1004,38 +1006,10 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
         a.ci_o[o] = cell;
         a.ido[o] = sid[k];
-        sv0[r] = a.vi[0][s];
-        sv1[r] = a.vi[1][s];
-        sv2[r] = a.vi[2][s];
+        a.vo[0][o] = a.vi[0][s];
+        a.vo[1][o] = a.vi[1][s];
+        a.vo[2][o] = a.vi[2][s];
         if (a.lcr_dbg) a.lcr_dbg[o] = s;
-    }
-    __syncwarp();
-    double rem = a.rem[gcell];
-    const T smax = a.smax[gcell];
-    const int64_t M = ntc_count(c, N, (double)smax, rem);
-    T seen = (T)0;
-    uint32_t nacc = 0, nclamp = 0;
-    if (M > 0)
-        collide_cell_warp<T>(c, sv0, sv1, sv2, N, M, smax, cell, a.run0 + rl, step, seen, nacc, nclamp);
-    if (lane == 0) {
-        a.rem[gcell] = rem;
-        if (seen > smax) a.smax[gcell] = seen;
-        if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
-        tl.cand += (unsigned long long)M;
-        tl.acc += nacc;
-        tl.clamp += nclamp;
-        if (slot_t >= 0) {
-            double m[DSMC_NMOM];
-            cell_moments<T>(sv0, sv1, sv2, N, m);
-            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
-        }
-    }
-    __syncwarp();
-    for (uint32_t r = lane; r < N; r += 32) {
-        const uint32_t o = beg + r;
-        a.vo[0][o] = sv0[r];
-        a.vo[1][o] = sv1[r];
-        a.vo[2][o] = sv2[r];
     }
     __syncwarp();
 }
@@ -1043,34 +1017,29 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
 template <typename T>
 __host__ __device__ constexpr size_t warp_scratch_bytes()
 {
-    return (size_t)kWarpMax * (2 * sizeof(uint32_t) + 3 * sizeof(T) + sizeof(uint16_t));
+    return (size_t)kWarpMax * (2 * sizeof(uint32_t) + sizeof(uint16_t));
 }
 
-// Tile path: one CTA takes kTileCells consecutive (run-major) cells, whose
-// particles occupy one contiguous range of the next pool.  Thread-per-
-// particle phases (coalesced through the LCR): (1) ids into shared memory;
-// (2) each particle's rank inside its cell by counting smaller ids, then its
-// position, velocity and id gathered into the next pool at cell start +
-// rank.  Thread-per-cell phase (3): NTC collisions on the cell's velocities
-// in the next pool (just written by this CTA, so cache-resident) and the
-// moments at sample steps.  Only the ids are staged (4 bytes per particle),
-// which keeps many CTAs resident.  Tiles whose particles exceed the budget
-// go cell by cell through the warp path.
+// Indexing, part 3 (sort and gather).  One CTA takes kTileCells consecutive
+// (run-major) cells, whose particles occupy one contiguous range of the next
+// pool.  Thread-per-particle phases, coalesced through the LCR: (1) ids into
+// shared memory; (2) each particle's rank inside its cell by counting smaller
+// ids, then its offsets, cell index, velocity and id gathered into the next
+// pool at cell start + rank.  Only the ids are staged (4 bytes per
+// particle), so several CTAs stay resident per SM.  Cells above kWarpMax go
+// to the one-CTA-per-cell kernel; tiles whose particles exceed the budget go
+// cell by cell through the warp path.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
+__global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 {
     const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t budget = (uint32_t)a.tile_budget;
     uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* s_id = s_start + (kTileCells + 4);
-    uint8_t* s_cellof = reinterpret_cast<uint8_t*>(s_id + budget);
-    __shared__ uint32_t s_red[kTileCells / 32];
+    uint16_t* s_cellof = reinterpret_cast<uint16_t*>(s_id + budget);
     __shared__ uint32_t s_lin[kTileCells];
     const int tid = threadIdx.x;
-    const uint32_t step = a.ctr->step;
-    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
-    CellTally tl;
     const int64_t ntiles = ((int64_t)a.total_cells + kTileCells - 1) / kTileCells;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t c0 = tile * kTileCells;
@@ -1080,30 +1049,32 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
         __syncthreads();
         const uint32_t B = s_start[0], E = s_start[nct];
         const uint32_t Tn = E - B;
-        const uint32_t myN = tid < nct ? s_start[tid + 1] - s_start[tid] : 0u;
-        const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, myN);
-        if (lane_id() == 0) s_red[tid >> 5] = wmax;
-        __syncthreads();
-        uint32_t maxN = 0;
-        for (int q = 0; q < kTileCells / 32; ++q) maxN = max(maxN, s_red[q]);
-        const bool fits = Tn <= budget && maxN <= (uint32_t)kLaneMax && (uint64_t)E <= (uint64_t)a.cap_old;
+        const bool fits = Tn <= budget && (uint64_t)E <= (uint64_t)a.cap_old;
         if (!fits) {
             unsigned char* ws = smem_raw + (kTileCells + 4) * sizeof(uint32_t) +
                                 (size_t)(tid >> 5) * warp_scratch_bytes<T>();
             for (int q = tid >> 5; q < nct; q += kTileCells / 32)
-                cell_warp_path<T, DIM>(a, c, c0 + q, step, slot_t, ws, tl);
+                cell_warp_path<T, DIM>(a, c, c0 + q, ws);
             __syncthreads();
             continue;
         }
-        if (tid < nct)
-            for (uint32_t k = s_start[tid] - B; k < s_start[tid + 1] - B; ++k) s_cellof[k] = (uint8_t)tid;
+        if (tid < nct) {
+            const uint32_t cb = s_start[tid] - B, ce = s_start[tid + 1] - B;
+            const bool big = ce - cb > (uint32_t)kWarpMax;
+            if (big) push_big(a, c0 + tid);
+            const uint16_t mark = big ? (uint16_t)0xFFFF : (uint16_t)tid;
+            for (uint32_t k = cb; k < ce; ++k) s_cellof[k] = mark;
+        }
+        __syncthreads();
 #pragma unroll 4
-        for (uint32_t k = tid; k < Tn; k += kTileCells) s_id[k] = a.idi[checked_slot(a, a.lcr[B + k])];
+        for (uint32_t k = tid; k < Tn; k += kTileCells)
+            if (s_cellof[k] != 0xFFFF) s_id[k] = a.idi[checked_slot(a, a.lcr[B + k])];
         __syncthreads();
 #pragma unroll 2
         for (uint32_t k = tid; k < Tn; k += kTileCells) {
-            const uint32_t s = checked_slot(a, a.lcr[B + k]);
             const int lo = s_cellof[k];
+            if (lo == 0xFFFF) continue;
+            const uint32_t s = checked_slot(a, a.lcr[B + k]);
             const uint32_t cb = s_start[lo] - B, ce = s_start[lo + 1] - B;
             const uint32_t my = s_id[k];
             // ids are unique within a run; a duplicate (possible only in a
@@ -1122,38 +1093,50 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
             if (a.lcr_dbg) a.lcr_dbg[o] = s;
         }
         __syncthreads();
-        if (tid < nct) {
-            const int64_t gcell = c0 + tid;
-            const uint32_t beg = s_start[tid];
-            const uint32_t N = myN;
-            const uint32_t rl = (uint32_t)(gcell / c.ncells);
-            const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
-            double rem = a.rem[gcell];
-            const T smax = a.smax[gcell];
-            const int64_t M = ntc_count(c, N, (double)smax, rem);
-            T seen = (T)0;
-            uint32_t nacc = 0, nclamp = 0;
-            T* v0 = a.vo[0] + beg;
-            T* v1 = a.vo[1] + beg;
-            T* v2 = a.vo[2] + beg;
-            for (int64_t k = 0; k < M; ++k)
-                collide_candidate_lazy<T>(c, v0, v1, v2, a.run0 + rl, step, cell, k, N, smax, seen,
-                                          nacc, nclamp);
-            a.rem[gcell] = rem;
-            if (seen > smax) a.smax[gcell] = seen;
-            if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
-            tl.cand += (unsigned long long)M;
-            tl.acc += nacc;
-            tl.clamp += nclamp;
-            if (slot_t >= 0) {
-                double m[DSMC_NMOM];
-                cell_moments<T>(v0, v1, v2, N, m);
-                for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
-            }
-        }
-        __syncthreads();
     }
-    // counters: one atomic per warp
+}
+
+// Interaction and Sampling: one thread per cell of at most kWarpMax
+// particles (larger cells are done by the one-CTA-per-cell kernel), on the
+// cell's velocities in the next pool, now in id order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_collide(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    const uint32_t step = a.ctr->step;
+    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
+    CellTally tl;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t gcell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gcell < a.total_cells;
+         gcell += stride) {
+        const uint32_t beg = a.start[gcell];
+        const uint32_t N = a.start[gcell + 1] - beg;
+        if (N > (uint32_t)kWarpMax || (uint64_t)beg + N > (uint64_t)a.cap_old) continue;
+        const uint32_t rl = (uint32_t)(gcell / c.ncells);
+        const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
+        double rem = a.rem[gcell];
+        const T smax = a.smax[gcell];
+        const int64_t M = ntc_count(c, N, (double)smax, rem);
+        T seen = (T)0;
+        uint32_t nacc = 0, nclamp = 0;
+        T* v0 = a.vo[0] + beg;
+        T* v1 = a.vo[1] + beg;
+        T* v2 = a.vo[2] + beg;
+        for (int64_t k = 0; k < M; ++k)
+            collide_candidate_lazy<T>(c, v0, v1, v2, a.run0 + rl, step, cell, k, N, smax, seen, nacc,
+                                      nclamp);
+        if (N >= 2) a.rem[gcell] = rem;
+        if (seen > smax) a.smax[gcell] = seen;
+        if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
+        tl.cand += (unsigned long long)M;
+        tl.acc += nacc;
+        tl.clamp += nclamp;
+        if (slot_t >= 0) {
+            double m[DSMC_NMOM];
+            cell_moments<T>(v0, v1, v2, N, m);
+            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
+        }
+    }
     const unsigned long long cs = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.cand);
     const unsigned long long as = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.acc);
     const unsigned long long ks = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.clamp);
@@ -1444,7 +1427,7 @@ void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStrea
 size_t cell_smem_bytes(int prec, int budget)
 {
     const size_t head = (kTileCells + 4) * sizeof(uint32_t);
-    const size_t tile = (size_t)budget * 5;
+    const size_t tile = (size_t)budget * 6;
     const size_t warps = (kTileCells / 32) * (prec == DSMC_FP64 ? warp_scratch_bytes<double>()
                                                                 : warp_scratch_bytes<float>());
     return head + (tile > warps ? tile : warps);
@@ -1456,6 +1439,11 @@ void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t
         const StepArgs<T>& a = A<T>(args);
         k_cell<T, D><<<ls.cell_blocks, kTileCells, cell_smem_bytes(prec, a.tile_budget), s>>>(a);
     }));
+}
+
+void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (k_collide<T><<<ls.collide_blocks, 256, 0, s>>>(A<T>(args))));
 }
 
 int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
@@ -1515,6 +1503,9 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
     ls->move_blocks = sms * (bm > 0 ? bm : 4);
     ls->scatter_blocks = sms * 8;
     ls->cell_blocks = sms * (bc > 0 ? bc : 2);
+    int bl = 0;
+    DISPATCH_PREC(prec, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_collide<T>, 256, 0));
+    ls->collide_blocks = sms * (bl > 0 ? bl : 4);
     ls->big_blocks = sms;
 }
 

@@ -23,7 +23,8 @@ FP32, FP64 = 0, 1
 Q_RAW, Q_DENSITY, Q_VELOCITY, Q_TEMPERATURE, Q_SE_DENSITY, Q_SE_VELOCITY, Q_SE_TEMPERATURE = range(7)
 NMOM = 7
 MAX_BC = 32
-KERNEL_KINDS = ["generate", "move", "scan", "scatter", "cell", "cell_big", "reduce", "other"]
+KERNEL_KINDS = ["generate", "move", "scan", "scatter", "cell", "cell_big", "reduce", "other",
+                "collide"]
 
 EXPORTS = [
     "dsmc_create", "dsmc_run_ensemble", "dsmc_get_samples", "dsmc_get_stats", "dsmc_destroy",
