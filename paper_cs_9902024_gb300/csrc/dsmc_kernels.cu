@@ -622,7 +622,29 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// Motion of the pool: grid-stride, warp-uniform trip count.
+// 16-byte vector of four consecutive SoA elements
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* __restrict__ p, uint64_t s, T* out)
+{
+    const typename Vec4<T>::type q = *reinterpret_cast<const typename Vec4<T>::type*>(p + s);
+    out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* __restrict__ p, uint64_t s, const T* in)
+{
+    typename Vec4<T>::type q;
+    q.x = in[0]; q.y = in[1]; q.z = in[2]; q.w = in[3];
+    *reinterpret_cast<typename Vec4<T>::type*>(p + s) = q;
+}
+
+// Motion of the pool.  Each thread takes four consecutive slots per pass,
+// read and written with 16-byte vector accesses of the SoA arrays (the pool
+// buffers are 256-byte aligned); the four rank atomics are independent.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
@@ -633,40 +655,113 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
     const uint32_t step = a.ctr->step;
     const T dt = (T)c.dt;
     LocalCounters lc;
-    const uint32_t lane = lane_id();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n_total;
-         base += stride) {
-        const uint32_t s = (uint32_t)(base + lane);
-        const bool valid = s < n_total;
-        uint32_t key = kDead;
-        if (valid) {
-            const uint32_t rl = run_of_slot(a.run_base, a.n_runs, (uint32_t)base, s);
-            T x[3], v[3];
-            int ci[3];
-            decode_cell<DIM>(c, a.ci_i[s], ci);
+    T* __restrict__ xp0 = a.xi[0];
+    T* __restrict__ xp1 = a.xi[1];
+    T* __restrict__ xp2 = a.xi[2];
+    T* __restrict__ vp0 = a.vi[0];
+    T* __restrict__ vp1 = a.vi[1];
+    T* __restrict__ vp2 = a.vi[2];
+    const uint32_t* __restrict__ cip = a.ci_i;
+    const uint32_t* __restrict__ rbase = a.run_base;
+    uint32_t* __restrict__ count = a.count;
+    uint32_t* __restrict__ gc = a.gc;
+    uint32_t* __restrict__ rank = a.rank;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = ((uint64_t)n_total + 3) / 4;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += nthreads) {
+        const uint64_t s0 = 4 * q;
+        const bool full = s0 + 4 <= n_total;
+        uint32_t cin[4];
+        T x[4][3], v[4][3];
+        if (full) {
+            const uint4 cv = *reinterpret_cast<const uint4*>(cip + s0);
+            cin[0] = cv.x; cin[1] = cv.y; cin[2] = cv.z; cin[3] = cv.w;
+            T t0[4], t1[4], t2[4], t3[4];
+            load4<T>(xp0, s0, t0);
+            load4<T>(xp1, s0, t1);
+            load4<T>(vp0, s0, t2);
+            load4<T>(vp1, s0, t3);
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) { x[ax] = a.xi[ax][s]; v[ax] = a.vi[ax][s]; }
-            if (DIM == 2) { x[2] = (T)0; v[2] = (T)0; }
-            uint32_t vmask = 0;
-            bool alive = true;
-            if (!try_free_flight<T, DIM>(c, ci, x, v, dt))
-                alive = move_particle_slow<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc,
-                                                   vmask);
-            if (alive) {
+            for (int b = 0; b < 4; ++b) {
+                x[b][0] = t0[b]; x[b][1] = t1[b]; v[b][0] = t2[b]; v[b][1] = t3[b];
+                x[b][2] = (T)0; v[b][2] = (T)0;
+            }
+            if (DIM == 3) {
+                load4<T>(xp2, s0, t0);
+                load4<T>(vp2, s0, t1);
 #pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) a.xi[ax][s] = x[ax];
+                for (int b = 0; b < 4; ++b) { x[b][2] = t0[b]; v[b][2] = t1[b]; }
+            }
+        } else {
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax)
-                    if (vmask & (1u << ax)) a.vi[ax][s] = v[ax];
-                key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
+            for (int b = 0; b < 4; ++b) {
+                const uint64_t s = s0 + b;
+                cin[b] = 0;
+                x[b][0] = x[b][1] = x[b][2] = (T)0;
+                v[b][0] = v[b][1] = v[b][2] = (T)0;
+                if (s < n_total) {
+                    cin[b] = cip[s];
+                    x[b][0] = xp0[s]; x[b][1] = xp1[s]; v[b][0] = vp0[s]; v[b][1] = vp1[s];
+                    if (DIM == 3) { x[b][2] = xp2[s]; v[b][2] = vp2[s]; }
+                }
             }
         }
-        const bool live = valid && key != kDead;
-        const uint32_t rk = warp_rank(a.count, key, live);
-        if (valid) {
-            a.gc[s] = key;
-            a.rank[s] = rk;
+        uint32_t key[4];
+        {
+            const uint32_t r0 = run_search(rbase, a.n_runs, (uint32_t)s0);
+            const uint32_t r0_end = __ldg(rbase + r0 + 1);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint64_t s = s0 + b;
+                key[b] = kDead;
+                if (s < n_total) {
+                    const uint32_t rl = s < r0_end ? r0 : run_search(rbase, a.n_runs, (uint32_t)s);
+                    int ci[3];
+                    decode_cell<DIM>(c, cin[b], ci);
+                    T xx[3] = {x[b][0], x[b][1], x[b][2]};
+                    T vv[3] = {v[b][0], v[b][1], v[b][2]};
+                    uint32_t vmask = 0;
+                    bool alive = true;
+                    if (!try_free_flight<T, DIM>(c, ci, xx, vv, dt))
+                        alive = move_particle_slow<T, DIM>(c, ci, xx, vv, a.idi[s], a.run0 + rl, step,
+                                                           dt, lc, vmask);
+                    x[b][0] = xx[0]; x[b][1] = xx[1]; x[b][2] = xx[2];
+                    if (alive) {
+                        if (vmask & 1u) vp0[s] = vv[0];
+                        if (vmask & 2u) vp1[s] = vv[1];
+                        if (vmask & 4u) vp2[s] = vv[2];
+                        key[b] = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
+                    }
+                }
+            }
+        }
+        uint32_t rk[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rk[b] = key[b] != kDead ? atomicAdd(count + key[b], 1u) : 0u;
+        if (full) {
+            T t0[4], t1[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) { t0[b] = x[b][0]; t1[b] = x[b][1]; }
+            store4<T>(xp0, s0, t0);
+            store4<T>(xp1, s0, t1);
+            if (DIM == 3) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) t0[b] = x[b][2];
+                store4<T>(xp2, s0, t0);
+            }
+            *reinterpret_cast<uint4*>(gc + s0) = make_uint4(key[0], key[1], key[2], key[3]);
+            *reinterpret_cast<uint4*>(rank + s0) = make_uint4(rk[0], rk[1], rk[2], rk[3]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint64_t s = s0 + b;
+                if (s < n_total) {
+                    xp0[s] = x[b][0]; xp1[s] = x[b][1];
+                    if (DIM == 3) xp2[s] = x[b][2];
+                    gc[s] = key[b];
+                    rank[s] = rk[b];
+                }
+            }
         }
     }
     flush_counters(a.ctr, lc);
@@ -737,25 +832,57 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
     }
 }
 
-// Indexing, part 2: LCR[start[cell] + rank] = slot for every live particle
+// Indexing, part 2: LCR[start[cell] + rank] = slot for every live particle.
+// Four consecutive slots per thread, keys and ranks read as 16-byte vectors.
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 {
     // the pool holds run_base[n_runs] particles after this step's scan, but
-    // the slots to scatter are those of the pre-step pool: its size is the
-    // start of the new region's scan (kept by the generate kernel)
+    // the slots to scatter are those of the pre-step pool: its size is kept
+    // at start[total + 1] by the previous step
     const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
-    const uint64_t n_all = n_old + (uint64_t)a.cap_new;
+    uint32_t* __restrict__ gc = a.gc;
+    const uint32_t* __restrict__ rank = a.rank;
+    const uint32_t* __restrict__ start = a.start;
+    uint32_t* __restrict__ lcr = a.lcr;
     bool overflow = false;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_all;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t slot = t < n_old ? t : (uint64_t)a.cap_old + (t - n_old);
-        const uint32_t key = a.gc[slot];
-        if (key == kDead) continue;
-        if (slot >= (uint64_t)a.cap_old) a.gc[slot] = kDead;
-        const uint64_t pos = (uint64_t)a.start[key] + a.rank[slot];
-        if (pos >= (uint64_t)a.cap_old) { overflow = true; continue; }
-        a.lcr[pos] = (uint32_t)slot;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    // the old pool [0, n_old) and the entrants' region [cap_old, cap_old +
+    // cap_new) (both start on a multiple of 4 slots), as one index space
+    const uint64_t q_old = (n_old + 3) / 4, q_new = ((uint64_t)a.cap_new + 3) / 4;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_old + q_new; q += nthreads) {
+        const bool in_new = q >= q_old;
+        const uint64_t s0 = in_new ? (uint64_t)a.cap_old + 4 * (q - q_old) : 4 * q;
+        const uint64_t lim = in_new ? (uint64_t)a.cap_old + (uint64_t)a.cap_new : n_old;
+        uint32_t key[4], rk[4];
+        if (s0 + 4 <= lim) {
+            const uint4 kv = *reinterpret_cast<const uint4*>(gc + s0);
+            const uint4 rv = *reinterpret_cast<const uint4*>(rank + s0);
+            key[0] = kv.x; key[1] = kv.y; key[2] = kv.z; key[3] = kv.w;
+            rk[0] = rv.x; rk[1] = rv.y; rk[2] = rv.z; rk[3] = rv.w;
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                key[b] = s0 + b < lim ? gc[s0 + b] : kDead;
+                rk[b] = s0 + b < lim ? rank[s0 + b] : 0u;
+            }
+        }
+        uint32_t st[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) st[b] = key[b] != kDead ? start[key[b]] : 0u;
+        if (in_new && (key[0] != kDead || key[1] != kDead || key[2] != kDead || key[3] != kDead)) {
+            // re-kill the entrants' keys for the next step
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (s0 + b < lim) gc[s0 + b] = kDead;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (key[b] == kDead) continue;
+            const uint64_t pos = (uint64_t)st[b] + rk[b];
+            if (pos >= (uint64_t)a.cap_old) { overflow = true; continue; }
+            lcr[pos] = (uint32_t)(s0 + b);
+        }
     }
     if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
 }
