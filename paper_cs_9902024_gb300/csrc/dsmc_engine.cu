@@ -68,6 +68,7 @@ struct dsmc_ctx {
     uint32_t *count = nullptr, *start = nullptr, *block_sums = nullptr;
     uint32_t *run_base = nullptr, *next_id = nullptr, *cand = nullptr, *accd = nullptr;
     uint32_t* big_list = nullptr;
+    uint32_t* slow_list = nullptr;
     double *rem = nullptr, *mom = nullptr, *acc = nullptr, *macro = nullptr;
     void* smax = nullptr;
     int32_t* sample_slot = nullptr;
@@ -120,6 +121,8 @@ static dsmc_status build_cfg(dsmc_ctx* ctx, double dt, uint64_t seed)
         c.inv_d[a] = 1.0 / c.d[a];
     }
     c.Vc = c.d[0] * c.d[1] * c.d[2];
+    // multiply-high division by ncells: exact for every 32-bit key
+    c.ncells_magic = c.ncells > 1 ? (~0ull) / (uint64_t)c.ncells + 1ull : 0ull;
     c.dt = dt;
     c.mass = ctx->gas.mass;
     c.F_N = ctx->gas.F_N;
@@ -309,6 +312,7 @@ static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, in
     ctx->accd = dbg ? (uint32_t*)A(4 * total_cells) : nullptr;
     const int64_t max_big = cap_old / (kWarpMax + 1) + 1;
     ctx->big_list = (uint32_t*)A(4 * max_big);
+    ctx->slow_list = (uint32_t*)A(4 * cap_old);
     ctx->sample_slot = (int32_t*)A(4 * (size_t)(steps + 2));
     ctx->acc = (double*)A(8 * (size_t)std::max(n_samples, 1) * G * ctx->ncells * DSMC_NMOM);
     ctx->macro = (double*)A(8 * 10 * (size_t)ctx->ncells);
@@ -364,6 +368,7 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.cand = ctx->cand;
     a.accd = ctx->accd;
     a.big_list = ctx->big_list;
+    a.slow_list = ctx->slow_list;
     a.sample_slot = ctx->sample_slot;
     a.n_slot = ctx->steps_alloc;
     a.acc = ctx->acc;
@@ -879,7 +884,7 @@ static dsmc_status get_run_state(dsmc_ctx* ctx, int run, std::vector<double>& x,
                           cudaMemcpyDeviceToHost));
             for (size_t k = 0; k < n; ++k) {
                 int ci[3];
-                decode_host(ctx, cells[k], ci);
+                decode_host(ctx, cells[k] - (uint32_t)run * (uint32_t)ctx->ncells, ci);
                 x[3 * k + a] = (double)ci[a] * ctx->hcfg.d[a] + (double)tmp[k];
             }
         }
@@ -954,7 +959,8 @@ static dsmc_status set_run_state(dsmc_ctx* ctx, int run, int64_t n, const double
                     NV[a].push_back((T)v[3 * k + a]);
                 }
                 NI.push_back(id[k]);
-                NC.push_back((uint32_t)(ci[0] + ctx->hcfg.n[0] * (ci[1] + ctx->hcfg.n[1] * ci[2])));
+                NC.push_back((uint32_t)r * (uint32_t)ctx->ncells +
+                             (uint32_t)(ci[0] + ctx->hcfg.n[0] * (ci[1] + ctx->hcfg.n[1] * ci[2])));
             }
         } else {
             for (size_t k = rb[r]; k < rb[r + 1]; ++k) {

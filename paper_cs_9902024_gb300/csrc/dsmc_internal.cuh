@@ -57,6 +57,7 @@ struct Cfg {
     double fill_lam, fill_sd, fill_U[3];
     int64_t n_elem;      // inflow elements over all segments
     uint64_t seed;
+    uint64_t ncells_magic;   // key / ncells = umul64hi(key, magic); 0 if ncells == 1
     BcDev bc[DSMC_MAX_BC];
 };
 
@@ -64,7 +65,7 @@ struct Counters {
     unsigned long long particle_steps, generated, removed, wall_hits;
     unsigned long long candidates, collisions, clamps, bounce_limit, reject_limit;
     unsigned long long pool_steps;
-    uint32_t error, step, n_big, pad_;
+    uint32_t error, step, n_big, n_slow;
 };
 
 // Device pointers of one step (particle pool double-buffered: in -> out).
@@ -74,7 +75,7 @@ struct StepArgs {
     Counters* ctr;
     // pool: in/out buffers of positions (dim used), velocities (3), ids
     // positions are offsets inside the particle's cell; ci_* hold the
-    // run-local linear cell index of each particle of the pool
+    // run-major cell key (run * ncells + cell) of each particle of the pool
     T* xi[3]; T* vi[3]; uint32_t* idi; uint32_t* ci_i;
     T* xo[3]; T* vo[3]; uint32_t* ido; uint32_t* ci_o;
     uint32_t* gc;          // per slot: run-major cell key, or kDead
@@ -93,6 +94,7 @@ struct StepArgs {
     uint32_t* cand;        // optional per cell
     uint32_t* accd;        // optional per cell
     uint32_t* big_list;
+    uint32_t* slow_list;   // slots whose flight meets a surface this step
     const int32_t* sample_slot;   // per step: sample index or -1
     int32_t n_slot;               // entries of sample_slot
     double* acc;           // [samples][G][ncells][7]

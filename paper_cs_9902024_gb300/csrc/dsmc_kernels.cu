@@ -427,6 +427,7 @@ __global__ void k_init_cells(StepArgs<T> a)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr->step = 1u;
         a.ctr->n_big = 0u;
+        a.ctr->n_slow = 0u;
     }
 }
 
@@ -473,7 +474,7 @@ __global__ void k_fill_particles(StepArgs<T> a)
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) a.vi[ax][p] = (T)c.fill_U[ax] + sd * z[ax];
             a.idi[p] = (beg - a.run_base[rl]) + k;
-            a.ci_i[p] = cell;
+            a.ci_i[p] = (uint32_t)i;
         }
     }
 }
@@ -642,9 +643,18 @@ __device__ __forceinline__ void store4(T* __restrict__ p, uint64_t s, const T* i
     *reinterpret_cast<typename Vec4<T>::type*>(p + s) = q;
 }
 
-// Motion of the pool.  Each thread takes four consecutive slots per pass,
-// read and written with 16-byte vector accesses of the SoA arrays (the pool
-// buffers are 256-byte aligned); the four rank atomics are independent.
+// run of a run-major cell key: key / ncells by a 64-bit multiply-high
+// (exact for every 32-bit key, see the host's magic number)
+__device__ __forceinline__ uint32_t run_of_key(const Cfg& c, uint32_t key)
+{
+    return c.ncells_magic ? (uint32_t)__umul64hi((unsigned long long)key, c.ncells_magic) : key;
+}
+
+// Motion of the pool, straight-flight part: one particle per thread with
+// few registers, so that many warps keep their loads and rank atomics in
+// flight.  Each particle's run and cell come from its stored cell key.  A
+// particle whose flight may meet a surface is appended to the slow list
+// (one atomic per warp) and moved by k_move_slow.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
@@ -652,118 +662,89 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
     // after a pool overflow (reported through the error word) the recorded
     // size can exceed the buffers: never walk past them
     const uint32_t n_total = min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
-    const uint32_t step = a.ctr->step;
     const T dt = (T)c.dt;
-    LocalCounters lc;
     T* __restrict__ xp0 = a.xi[0];
     T* __restrict__ xp1 = a.xi[1];
     T* __restrict__ xp2 = a.xi[2];
-    T* __restrict__ vp0 = a.vi[0];
-    T* __restrict__ vp1 = a.vi[1];
-    T* __restrict__ vp2 = a.vi[2];
+    const T* __restrict__ vp0 = a.vi[0];
+    const T* __restrict__ vp1 = a.vi[1];
+    const T* __restrict__ vp2 = a.vi[2];
     const uint32_t* __restrict__ cip = a.ci_i;
-    const uint32_t* __restrict__ rbase = a.run_base;
     uint32_t* __restrict__ count = a.count;
     uint32_t* __restrict__ gc = a.gc;
     uint32_t* __restrict__ rank = a.rank;
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n4 = ((uint64_t)n_total + 3) / 4;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += nthreads) {
-        const uint64_t s0 = 4 * q;
-        const bool full = s0 + 4 <= n_total;
-        uint32_t cin[4];
-        T x[4][3], v[4][3];
-        if (full) {
-            const uint4 cv = *reinterpret_cast<const uint4*>(cip + s0);
-            cin[0] = cv.x; cin[1] = cv.y; cin[2] = cv.z; cin[3] = cv.w;
-            T t0[4], t1[4], t2[4], t3[4];
-            load4<T>(xp0, s0, t0);
-            load4<T>(xp1, s0, t1);
-            load4<T>(vp0, s0, t2);
-            load4<T>(vp1, s0, t3);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                x[b][0] = t0[b]; x[b][1] = t1[b]; v[b][0] = t2[b]; v[b][1] = t3[b];
-                x[b][2] = (T)0; v[b][2] = (T)0;
-            }
-            if (DIM == 3) {
-                load4<T>(xp2, s0, t0);
-                load4<T>(vp2, s0, t1);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) { x[b][2] = t0[b]; v[b][2] = t1[b]; }
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint64_t s = s0 + b;
-                cin[b] = 0;
-                x[b][0] = x[b][1] = x[b][2] = (T)0;
-                v[b][0] = v[b][1] = v[b][2] = (T)0;
-                if (s < n_total) {
-                    cin[b] = cip[s];
-                    x[b][0] = xp0[s]; x[b][1] = xp1[s]; v[b][0] = vp0[s]; v[b][1] = vp1[s];
-                    if (DIM == 3) { x[b][2] = xp2[s]; v[b][2] = vp2[s]; }
-                }
+    const uint32_t lane = lane_id();
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // warp-uniform trip count (the slow-list append is a warp operation)
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n_total; base += stride) {
+        const uint32_t s = base + lane;
+        bool slow = false;
+        if (s < n_total) {
+            const uint32_t kold = cip[s];
+            T x[3], v[3];
+            x[0] = xp0[s]; x[1] = xp1[s]; v[0] = vp0[s]; v[1] = vp1[s];
+            if (DIM == 3) { x[2] = xp2[s]; v[2] = vp2[s]; } else { x[2] = (T)0; v[2] = (T)0; }
+            const uint32_t rl = run_of_key(c, kold);
+            int ci[3];
+            decode_cell<DIM>(c, kold - rl * (uint32_t)c.ncells, ci);
+            if (try_free_flight<T, DIM>(c, ci, x, v, dt)) {
+                xp0[s] = x[0];
+                xp1[s] = x[1];
+                if (DIM == 3) xp2[s] = x[2];
+                const uint32_t key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
+                gc[s] = key;
+                rank[s] = atomicAdd(count + key, 1u);
+            } else {
+                slow = true;
             }
         }
-        uint32_t key[4];
-        {
-            const uint32_t r0 = run_search(rbase, a.n_runs, (uint32_t)s0);
-            const uint32_t r0_end = __ldg(rbase + r0 + 1);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint64_t s = s0 + b;
-                key[b] = kDead;
-                if (s < n_total) {
-                    const uint32_t rl = s < r0_end ? r0 : run_search(rbase, a.n_runs, (uint32_t)s);
-                    int ci[3];
-                    decode_cell<DIM>(c, cin[b], ci);
-                    T xx[3] = {x[b][0], x[b][1], x[b][2]};
-                    T vv[3] = {v[b][0], v[b][1], v[b][2]};
-                    uint32_t vmask = 0;
-                    bool alive = true;
-                    if (!try_free_flight<T, DIM>(c, ci, xx, vv, dt))
-                        alive = move_particle_slow<T, DIM>(c, ci, xx, vv, a.idi[s], a.run0 + rl, step,
-                                                           dt, lc, vmask);
-                    x[b][0] = xx[0]; x[b][1] = xx[1]; x[b][2] = xx[2];
-                    if (alive) {
-                        if (vmask & 1u) vp0[s] = vv[0];
-                        if (vmask & 2u) vp1[s] = vv[1];
-                        if (vmask & 4u) vp2[s] = vv[2];
-                        key[b] = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
-                    }
-                }
-            }
-        }
-        uint32_t rk[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) rk[b] = key[b] != kDead ? atomicAdd(count + key[b], 1u) : 0u;
-        if (full) {
-            T t0[4], t1[4];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) { t0[b] = x[b][0]; t1[b] = x[b][1]; }
-            store4<T>(xp0, s0, t0);
-            store4<T>(xp1, s0, t1);
-            if (DIM == 3) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) t0[b] = x[b][2];
-                store4<T>(xp2, s0, t0);
-            }
-            *reinterpret_cast<uint4*>(gc + s0) = make_uint4(key[0], key[1], key[2], key[3]);
-            *reinterpret_cast<uint4*>(rank + s0) = make_uint4(rk[0], rk[1], rk[2], rk[3]);
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint64_t s = s0 + b;
-                if (s < n_total) {
-                    xp0[s] = x[b][0]; xp1[s] = x[b][1];
-                    if (DIM == 3) xp2[s] = x[b][2];
-                    gc[s] = key[b];
-                    rank[s] = rk[b];
-                }
-            }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, slow);
+        if (m) {
+            uint32_t base_i = 0;
+            if (lane == 0) base_i = atomicAdd(&a.ctr->n_slow, (uint32_t)__popc(m));
+            base_i = __shfl_sync(0xFFFFFFFFu, base_i, 0);
+            if (slow) a.slow_list[base_i + __popc(m & ((1u << lane) - 1u))] = s;
         }
     }
+}
+
+// Motion with surface events for the particles k_move set aside.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    const uint32_t n = min(a.ctr->n_slow, (uint32_t)a.cap_old);
+    const uint32_t step = a.ctr->step;
+    const T dt = (T)c.dt;
+    LocalCounters lc;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t s = a.slow_list[i];
+        const uint32_t kold = a.ci_i[s];
+        T x[3], v[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            x[ax] = ax < DIM ? a.xi[ax][s] : (T)0;
+            v[ax] = a.vi[ax][s];
+        }
+        const uint32_t rl = run_of_key(c, kold);
+        int ci[3];
+        decode_cell<DIM>(c, kold - rl * (uint32_t)c.ncells, ci);
+        uint32_t vmask = 0;
+        const bool alive = move_particle<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
+        uint32_t key = kDead, rk = 0;
+        if (alive) {
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) a.xi[ax][s] = x[ax];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+                if (vmask & (1u << ax)) a.vi[ax][s] = v[ax];
+            key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
+            rk = atomicAdd(a.count + key, 1u);
+        }
+        a.gc[s] = key;
+        a.rank[s] = rk;
+    }
+    // every thread reaches this point: the warp reductions are full-warp
     flush_counters(a.ctr, lc);
 }
 
@@ -1102,8 +1083,6 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
     uint16_t* sp = reinterpret_cast<uint16_t*>(sid + kWarpMax);
     const uint32_t beg = a.start[gcell];
     const uint32_t N = a.start[gcell + 1] - beg;
-    const uint32_t rl = (uint32_t)(gcell / c.ncells);
-    const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
     if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
         if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
         return;
@@ -1131,7 +1110,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         const uint32_t o = beg + r;
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-        a.ci_o[o] = cell;
+        a.ci_o[o] = (uint32_t)gcell;
         a.ido[o] = sid[k];
         a.vo[0][o] = a.vi[0][s];
         a.vo[1][o] = a.vi[1][s];
@@ -1165,14 +1144,12 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
     uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* s_id = s_start + (kTileCells + 4);
     uint16_t* s_cellof = reinterpret_cast<uint16_t*>(s_id + budget);
-    __shared__ uint32_t s_lin[kTileCells];
     const int tid = threadIdx.x;
     const int64_t ntiles = ((int64_t)a.total_cells + kTileCells - 1) / kTileCells;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t c0 = tile * kTileCells;
         const int nct = (int)min((int64_t)kTileCells, (int64_t)a.total_cells - c0);
         for (int i = tid; i <= kTileCells; i += blockDim.x) s_start[i] = a.start[c0 + min(i, nct)];
-        if (tid < nct) s_lin[tid] = (uint32_t)((c0 + tid) % c.ncells);
         __syncthreads();
         const uint32_t B = s_start[0], E = s_start[nct];
         const uint32_t Tn = E - B;
@@ -1197,27 +1174,45 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
         for (uint32_t k = tid; k < Tn; k += kTileCells)
             if (s_cellof[k] != 0xFFFF) s_id[k] = a.idi[checked_slot(a, a.lcr[B + k])];
         __syncthreads();
-#pragma unroll 2
-        for (uint32_t k = tid; k < Tn; k += kTileCells) {
-            const int lo = s_cellof[k];
-            if (lo == 0xFFFF) continue;
-            const uint32_t s = checked_slot(a, a.lcr[B + k]);
-            const uint32_t cb = s_start[lo] - B, ce = s_start[lo + 1] - B;
-            const uint32_t my = s_id[k];
-            // ids are unique within a run; a duplicate (possible only in a
-            // state already flagged corrupt) leaves a hole, never an access
-            // outside the cell's range
-            uint32_t r = 0;
-            for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
-            const uint32_t o = B + cb + r;
+        for (uint32_t k0 = tid; k0 < Tn; k0 += 2 * kTileCells) {
+            // two particles per pass, every load issued before any store
+            uint32_t kk[2] = {k0, k0 + kTileCells}, sl[2];
+            int lo[2];
+            T px[2][3], pv[2][3];
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-            a.ci_o[o] = s_lin[lo];
-            a.ido[o] = my;
-            a.vo[0][o] = a.vi[0][s];
-            a.vo[1][o] = a.vi[1][s];
-            a.vo[2][o] = a.vi[2][s];
-            if (a.lcr_dbg) a.lcr_dbg[o] = s;
+            for (int b = 0; b < 2; ++b) {
+                lo[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
+                sl[b] = lo[b] != 0xFFFF ? checked_slot(a, a.lcr[B + kk[b]]) : 0u;
+            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                if (lo[b] == 0xFFFF) continue;
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
+                pv[b][0] = a.vi[0][sl[b]];
+                pv[b][1] = a.vi[1][sl[b]];
+                pv[b][2] = a.vi[2][sl[b]];
+            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                if (lo[b] == 0xFFFF) continue;
+                const uint32_t cb = s_start[lo[b]] - B, ce = s_start[lo[b] + 1] - B;
+                const uint32_t my = s_id[kk[b]];
+                // ids are unique within a run; a duplicate (possible only in a
+                // state already flagged corrupt) leaves a hole, never an access
+                // outside the cell's range
+                uint32_t r = 0;
+                for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
+                const uint32_t o = B + cb + r;
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
+                a.ci_o[o] = (uint32_t)(c0 + lo[b]);
+                a.ido[o] = my;
+                a.vo[0][o] = pv[b][0];
+                a.vo[1][o] = pv[b][1];
+                a.vo[2][o] = pv[b][2];
+                if (a.lcr_dbg) a.lcr_dbg[o] = sl[b];
+            }
         }
         __syncthreads();
     }
@@ -1227,7 +1222,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 // particles (larger cells are done by the one-CTA-per-cell kernel), on the
 // cell's velocities in the next pool, now in id order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_collide(StepArgs<T> a)
+__global__ void __launch_bounds__(256, 4) k_collide(StepArgs<T> a)
 {
     const Cfg& c = *a.cfg;
     const uint32_t step = a.ctr->step;
@@ -1334,7 +1329,7 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
             const uint32_t o = beg + r;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-            a.ci_o[o] = cell;
+            a.ci_o[o] = gcell;
             a.ido[o] = (uint32_t)(kk >> 32);
             sv0[r] = a.vi[0][s];
             sv1[r] = a.vi[1][s];
@@ -1406,6 +1401,7 @@ __global__ void k_step_end(StepArgs<T> a)
 {
     a.ctr->step += 1u;
     a.ctr->n_big = 0u;
+    a.ctr->n_slow = 0u;
     a.ctr->pool_steps += (unsigned long long)min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
     // remember this step's pool size for the next scatter (the slot range of
     // the old pool): start[total + 1] = run_base[n_runs]
@@ -1533,8 +1529,10 @@ void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStre
 
 void launch_move(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim,
-        (k_move<T, D><<<ls.move_blocks, ls.move_threads, 0, s>>>(A<T>(args)))));
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
+        k_move<T, D><<<ls.move_blocks, ls.move_threads, 0, s>>>(A<T>(args));
+        k_move_slow<T, D><<<ls.sms * 2, 256, 0, s>>>(A<T>(args));
+    }));
 }
 
 void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
