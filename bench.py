@@ -161,10 +161,11 @@ def algorithmic_bytes(w, st, steps, runs):
         # wall hits) and the cell index, write the offsets (D), the cell key
         # and the in-cell rank
         "move": moved_old * (3 * D * t + 4 + 8),
-        # read key + rank, write LCR
-        "scatter": pool * 12,
-        # read LCR, id, offsets, v; write offsets, cell index, id, v
-        "cell": pool * (4 + 2 * (D * t + 3 * t + 4) + 4) + cells * steps * 4,
+        # read key, rank and id, write the LCR entry (slot, id)
+        "scatter": pool * 20,
+        # read the LCR entry, gather offsets and v; write offsets, cell key,
+        # id, v
+        "cell": pool * (8 + 2 * (D * t + 3 * t) + 8) + cells * steps * 4,
         # per cell: start, NTC remainder (read + write), (sigma c_r)_max;
         # per candidate pair: both velocities read; per collision: written
         "collide": cells * steps * 24 + st["candidates"] * 2 * 3 * t

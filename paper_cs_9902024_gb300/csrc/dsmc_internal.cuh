@@ -80,7 +80,7 @@ struct StepArgs {
     T* xo[3]; T* vo[3]; uint32_t* ido; uint32_t* ci_o;
     uint32_t* gc;          // per slot: run-major cell key, or kDead
     uint32_t* rank;        // per slot: rank within its cell (any order)
-    uint32_t* lcr;         // per pool position: slot (cell-grouped)
+    uint2* lcr;            // per pool position: (slot, id), cell-grouped
     uint32_t* lcr_dbg;     // optional: slot of each sorted particle
     uint32_t* count;       // per cell: particles (atomic target)
     uint32_t* start;       // per cell (+2): exclusive prefix of count; entry

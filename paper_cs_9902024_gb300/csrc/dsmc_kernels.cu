@@ -813,8 +813,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
     }
 }
 
-// Indexing, part 2: LCR[start[cell] + rank] = slot for every live particle.
-// Four consecutive slots per thread, keys and ranks read as 16-byte vectors.
+// Indexing, part 2: LCR[start[cell] + rank] = (slot, id) for every live
+// particle (the id rides along so that the next kernel needs no gather to
+// order a cell).  Four consecutive slots per thread, keys and ranks read as
+// 16-byte vectors.
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 {
@@ -825,7 +827,7 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
     uint32_t* __restrict__ gc = a.gc;
     const uint32_t* __restrict__ rank = a.rank;
     const uint32_t* __restrict__ start = a.start;
-    uint32_t* __restrict__ lcr = a.lcr;
+    uint2* __restrict__ lcr2 = a.lcr;
     bool overflow = false;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     // the old pool [0, n_old) and the entrants' region [cap_old, cap_old +
@@ -848,9 +850,12 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
                 rk[b] = s0 + b < lim ? rank[s0 + b] : 0u;
             }
         }
-        uint32_t st[4];
+        uint32_t st[4], idv[4];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) st[b] = key[b] != kDead ? start[key[b]] : 0u;
+        for (int b = 0; b < 4; ++b) {
+            st[b] = key[b] != kDead ? start[key[b]] : 0u;
+            idv[b] = key[b] != kDead ? a.idi[s0 + b] : 0u;
+        }
         if (in_new && (key[0] != kDead || key[1] != kDead || key[2] != kDead || key[3] != kDead)) {
             // re-kill the entrants' keys for the next step
 #pragma unroll
@@ -862,7 +867,7 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
             if (key[b] == kDead) continue;
             const uint64_t pos = (uint64_t)st[b] + rk[b];
             if (pos >= (uint64_t)a.cap_old) { overflow = true; continue; }
-            lcr[pos] = (uint32_t)(s0 + b);
+            lcr2[pos] = make_uint2((uint32_t)(s0 + b), idv[b]);
         }
     }
     if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
@@ -1092,9 +1097,9 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         return;
     }
     for (uint32_t k = lane; k < N; k += 32) {
-        const uint32_t s = checked_slot(a, a.lcr[beg + k]);
-        sl[k] = s;
-        sid[k] = a.idi[s];
+        const uint2 e = a.lcr[beg + k];
+        sl[k] = checked_slot(a, e.x);
+        sid[k] = e.y;
     }
     __syncwarp();
     for (uint32_t k = lane; k < N; k += 32) {
@@ -1172,7 +1177,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
         __syncthreads();
 #pragma unroll 4
         for (uint32_t k = tid; k < Tn; k += kTileCells)
-            if (s_cellof[k] != 0xFFFF) s_id[k] = a.idi[checked_slot(a, a.lcr[B + k])];
+            if (s_cellof[k] != 0xFFFF) s_id[k] = a.lcr[B + k].y;
         __syncthreads();
         for (uint32_t k0 = tid; k0 < Tn; k0 += 2 * kTileCells) {
             // two particles per pass, every load issued before any store
@@ -1182,7 +1187,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 lo[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
-                sl[b] = lo[b] != 0xFFFF ? checked_slot(a, a.lcr[B + kk[b]]) : 0u;
+                sl[b] = lo[b] != 0xFFFF ? checked_slot(a, a.lcr[B + kk[b]].x) : 0u;
             }
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
@@ -1219,8 +1224,8 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 }
 
 // Interaction and Sampling: one thread per cell of at most kWarpMax
-// particles (larger cells are done by the one-CTA-per-cell kernel), on the
-// cell's velocities in the next pool, now in id order.
+// particles (larger cells are done whole by the one-CTA-per-cell kernel), on
+// the cell's velocities in the next pool, now in id order.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_collide(StepArgs<T> a)
 {
@@ -1234,8 +1239,8 @@ __global__ void __launch_bounds__(256, 4) k_collide(StepArgs<T> a)
         const uint32_t beg = a.start[gcell];
         const uint32_t N = a.start[gcell + 1] - beg;
         if (N > (uint32_t)kWarpMax || (uint64_t)beg + N > (uint64_t)a.cap_old) continue;
-        const uint32_t rl = (uint32_t)(gcell / c.ncells);
-        const uint32_t cell = (uint32_t)(gcell - (int64_t)rl * c.ncells);
+        const uint32_t rl = run_of_key(c, (uint32_t)gcell);
+        const uint32_t cell = (uint32_t)gcell - rl * (uint32_t)c.ncells;
         double rem = a.rem[gcell];
         const T smax = a.smax[gcell];
         const int64_t M = ntc_count(c, N, (double)smax, rem);
@@ -1304,8 +1309,8 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
         while (P < N) P <<= 1;
         for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) {
             if (k < N) {
-                const uint32_t s = checked_slot(a, a.lcr[beg + k]);
-                keys[k] = ((unsigned long long)a.idi[s] << 32) | s;
+                const uint2 e = a.lcr[beg + k];
+                keys[k] = ((unsigned long long)e.y << 32) | checked_slot(a, e.x);
             } else {
                 keys[k] = ~0ull;
             }
@@ -1612,9 +1617,9 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
 {
     ls->dim = dim;
     ls->sms = sms;
-    // tile budget: up to 8192 staged ids (32 KB), at least the warp path's
-    // scratch; several tile CTAs stay resident per SM
-    int budget = 8192;
+    // tile budget: 6144 staged particles (ids and cell tags, 36 KB), at
+    // least the warp path's scratch; several tile CTAs stay resident per SM
+    int budget = 6144;
     if (ls->tile_budget <= 0) ls->tile_budget = budget;
     int bm = 0, bc = 0;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
@@ -1643,6 +1648,7 @@ cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)cell_smem_bytes(prec, tile_budget));
+
     }));
     return e;
 }
