@@ -223,6 +223,37 @@ void dsmc_destroy(dsmc_ctx* ctx);
 /* Message of the last failed call on ctx (static string if ctx is NULL). */
 const char* dsmc_last_error(const dsmc_ctx* ctx);
 
+/* Same result as dsmc_run_ensemble followed by dsmc_get_samples(RAW_MOMENTS)
+ * for every sample, for callers that may not allocate device memory:
+ * a process whose device memory was all handed to another allocator or a
+ * fixed budget at start-up (a cudaMalloc there fails or steals from it),
+ * or a real-time loop that forbids allocator calls (cudaMalloc/cudaFree
+ * can synchronise the device and stall for milliseconds).  No counterpart
+ * in the paper: it is a deployment variant of the batched ensemble run.
+ *  - The whole run lives in one scratch array that is part of the library's
+ *    device image: 48 MiB on every GPU that loads the library, held until
+ *    the process exits.  A problem that needs more is rejected with
+ *    DSMC_E_INVALID and a message giving the bytes it needs (config-0-sized
+ *    ensembles fit; batched-512-run ensembles do not).
+ *  - The call makes no cudaMalloc, cudaFree, event or graph call.  Its first
+ *    call on a device looks up the scratch array's device address; make
+ *    that first call before any stream capture.  (The CUDA driver may also
+ *    reserve local-memory backing for a kernel on its first launch.)
+ *  - raw_out (host memory, raw_len doubles) receives sample k's group sums
+ *    at raw_out[k][G][ncells][7], G = min(n_runs, 16), laid out as
+ *    dsmc_get_samples(RAW_MOMENTS) gives them.  The call blocks until done.
+ *  - Every call on a device shares the one scratch array: calls whose GPU
+ *    work overlaps (several contexts or threads on the same device, or
+ *    streams that run concurrently) race and corrupt each other's results.
+ *    Each call resets what must start from zero; nothing else carries over.
+ *  - ctx must not own device buffers yet (a context that ran
+ *    dsmc_run_ensemble or a debug hook: DSMC_E_STATE); options.debug and
+ *    options.profile are rejected.  Afterwards dsmc_get_samples has no run
+ *    to read (DSMC_E_STATE); dsmc_get_stats reports the call's counters. */
+dsmc_status dsmc_run_ensemble_noalloc(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                                      const int32_t* sample_steps, int n_samples,
+                                      uint64_t seed, double* raw_out, size_t raw_len);
+
 /* ---- test hooks (step-level access for parity tests) ---------------- */
 
 /* Allocate for n_runs and set up the step-0 state (filled or empty) without

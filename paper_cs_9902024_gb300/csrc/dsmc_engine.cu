@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1119,3 +1120,198 @@ dsmc_status dsmc_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* ke
     return st;
 }
 
+
+// ---------------------------------------------------------------------------
+// Ensemble run without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they want a
+// result: processes whose device memory is fully handed to another
+// allocator or a fixed budget up front (a cudaMalloc would fail or take from
+// that budget), or real-time loops that forbid allocator calls on their
+// critical path (cudaMalloc/cudaFree may synchronise the device).  For them, dsmc_run_ensemble_noalloc runs the whole batched step
+// loop inside one fixed scratch array that is part of the library's device
+// image (kNoallocBytes on every GPU that loads the library, held until the
+// process exits).  It calls no cudaMalloc, cudaFree, event or graph creation.
+
+namespace {
+constexpr size_t kNoallocBytes = (size_t)48 << 20;
+constexpr int kNoallocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Builds the per-step sample table in the scratch: -1 everywhere, k at step
+// sample_steps[k] (the steps were copied to `ss` first).
+__global__ void k_noalloc_sample_table(int32_t* slot, int n_slot, const int32_t* ss, int n_samples)
+{
+    for (int i = threadIdx.x; i < n_slot; i += blockDim.x) slot[i] = -1;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_samples; k += blockDim.x) slot[ss[k]] = k;
+}
+
+// Device address of the scratch array on the context's device.  The lookup
+// runs on the first call per device, with that device current.
+static dsmc_status noalloc_base(dsmc_ctx* ctx, unsigned char** out)
+{
+    static unsigned char* base[kNoallocMaxDevices] = {};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (ctx->device < 0 || ctx->device >= kNoallocMaxDevices)
+        return fail(ctx, DSMC_E_INVALID, "device ordinal out of range for the no-allocation path");
+    if (!base[ctx->device]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        base[ctx->device] = static_cast<unsigned char*>(p);
+    }
+    *out = base[ctx->device];
+    return DSMC_OK;
+}
+
+struct ScratchCarver {
+    unsigned char* base;
+    size_t used;
+    void* take(size_t bytes)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        if (bytes == 0) bytes = 256;
+        void* p = base + used;
+        used += bytes;
+        return used <= kNoallocBytes ? p : nullptr;
+    }
+};
+
+// Lays the run's buffers out in the scratch array (the same buffers
+// ensure_alloc would allocate, without the debug ones) and returns the
+// bytes needed; the pointers are valid only if that is <= kNoallocBytes.
+static size_t noalloc_layout(dsmc_ctx* ctx, unsigned char* base, int n_runs, int64_t cap_run,
+                             int steps, int n_samples, int32_t** ss_stage)
+{
+    ScratchCarver sc{base, 0};
+    const int64_t cap_old = (cap_run * n_runs + 255) / 256 * 256;
+    const int64_t gcap = gen_capacity(ctx);
+    const int64_t cap_new = gcap * n_runs;
+    const int64_t total_cells = (int64_t)ctx->ncells * n_runs;
+    const size_t ts = ctx->prec == DSMC_FP64 ? 8 : 4;
+    const int64_t slots = cap_old + cap_new;
+    ctx->d_cfg = (Cfg*)sc.take(sizeof(Cfg));
+    ctx->d_ctr = (Counters*)sc.take(sizeof(Counters));
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            ctx->X[b][a] = a < ctx->dim ? sc.take(ts * slots) : nullptr;
+            ctx->V[b][a] = sc.take(ts * slots);
+        }
+        ctx->ID[b] = (uint32_t*)sc.take(4 * slots);
+        ctx->CI[b] = (uint32_t*)sc.take(4 * cap_old);
+    }
+    ctx->gc = (uint32_t*)sc.take(4 * slots);
+    ctx->rank = (uint32_t*)sc.take(4 * slots);
+    ctx->lcr = (uint2*)sc.take(8 * cap_old);
+    ctx->lcr_dbg = nullptr;
+    ctx->count = (uint32_t*)sc.take(4 * total_cells);
+    ctx->start = (uint32_t*)sc.take(4 * (total_cells + 2));
+    const int scan_blocks = (int)((total_cells + kScanTile - 1) / kScanTile);
+    ctx->block_sums = (uint32_t*)sc.take(4 * scan_blocks);
+    ctx->run_base = (uint32_t*)sc.take(4 * (n_runs + 1));
+    ctx->next_id = (uint32_t*)sc.take(4 * n_runs);
+    ctx->rem = (double*)sc.take(8 * total_cells);
+    ctx->smax = sc.take(ts * total_cells);
+    ctx->mom = (double*)sc.take(8 * DSMC_NMOM * total_cells);
+    ctx->cand = ctx->accd = nullptr;
+    const int64_t max_big = cap_old / (kWarpMax + 1) + 1;
+    ctx->big_list = (uint32_t*)sc.take(4 * max_big);
+    ctx->slow_list = (uint32_t*)sc.take(4 * cap_old);
+    ctx->sample_slot = (int32_t*)sc.take(4 * (size_t)(steps + 2));
+    ctx->acc = (double*)sc.take(8 * (size_t)std::max(n_samples, 1) * ctx->G * ctx->ncells * DSMC_NMOM);
+    ctx->macro = nullptr;
+    *ss_stage = (int32_t*)sc.take(4 * (size_t)std::max(n_samples, 1));
+    ctx->n_launch = n_runs;
+    ctx->cap_old = cap_old;
+    ctx->cap_new = cap_new;
+    ctx->gcap = gcap;
+    ctx->max_big = max_big;
+    ctx->total_cells = total_cells;
+    ctx->steps_alloc = steps + 2;
+    return sc.used;
+}
+
+// forget the scratch layout, so that a later dsmc_run_ensemble allocates its
+// own buffers
+static void noalloc_forget(dsmc_ctx* ctx)
+{
+    ctx->n_launch = 0;
+    ctx->cap_old = 0;
+    ctx->steps_alloc = 0;
+    ctx->generation++;
+    ctx->have_run = false;
+}
+
+dsmc_status dsmc_run_ensemble_noalloc(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                                      const int32_t* sample_steps, int n_samples, uint64_t seed,
+                                      double* raw_out, size_t raw_len)
+{
+    if (!ctx) return DSMC_E_INVALID;
+    CK(cudaSetDevice(ctx->device));
+    dsmc_status st = validate_run(ctx, n_runs, dt, steps, sample_steps, n_samples);
+    if (st) return st;
+    if (!ctx->bufs.empty())
+        return fail(ctx, DSMC_E_STATE,
+                    "context already owns device buffers: use a fresh context for the "
+                    "no-allocation path");
+    if (ctx->opt.debug || ctx->opt.profile)
+        return fail(ctx, DSMC_E_INVALID, "debug and profile options need allocated buffers");
+    const int G = std::min(n_runs, DSMC_MAX_GROUPS);
+    const size_t need = (size_t)n_samples * G * ctx->ncells * DSMC_NMOM;
+    if (n_samples > 0 && (!raw_out || raw_len < need))
+        return fail(ctx, DSMC_E_INVALID, "raw_out missing or smaller than n_samples x G x ncells x 7");
+    unsigned char* base = nullptr;
+    st = noalloc_base(ctx, &base);
+    if (st) return st;
+    st = build_cfg(ctx, dt, seed);
+    if (st) return st;
+    ctx->G = G;
+    const int64_t cap_run = estimate_per_run(ctx, steps);
+    int32_t* ss_dev = nullptr;
+    const size_t bytes = noalloc_layout(ctx, base, n_runs, cap_run, steps, n_samples, &ss_dev);
+    if (bytes > kNoallocBytes || ctx->cap_old + ctx->cap_new >= 0xFFFFFFF0ll) {
+        noalloc_forget(ctx);
+        char msg[200];
+        std::snprintf(msg, sizeof msg,
+                      "problem needs %zu bytes of device scratch; the no-allocation path holds %zu",
+                      bytes, kNoallocBytes);
+        return fail(ctx, DSMC_E_INVALID, msg);
+    }
+    // every buffer that must start from zero (or from the dead key) is set
+    // here: the scratch keeps the previous call's contents
+    CK(cudaMemcpyAsync(ctx->d_cfg, &ctx->hcfg, sizeof(Cfg), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->gc, 0xFF, 4 * (size_t)(ctx->cap_old + ctx->cap_new), ctx->stream));
+    CK(cudaMemsetAsync(ctx->acc, 0, 8 * (size_t)std::max(n_samples, 1) * G * ctx->ncells * DSMC_NMOM,
+                       ctx->stream));
+    if (n_samples > 0)
+        CK(cudaMemcpyAsync(ss_dev, sample_steps, 4 * (size_t)n_samples, cudaMemcpyHostToDevice,
+                           ctx->stream));
+    k_noalloc_sample_table<<<1, 256, 0, ctx->stream>>>(ctx->sample_slot, steps + 2, ss_dev, n_samples);
+    CK(cudaGetLastError());
+    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
+    AnyArgs u;
+    enqueue_init(ctx, build_args(ctx, u, 0, (int)ctx->opt.run_offset, n_runs));
+    ctx->cur = 0;
+    for (int s = 1; s <= steps; ++s) {
+        AnyArgs v;
+        enqueue_step(ctx, build_args(ctx, v, ctx->cur, (int)ctx->opt.run_offset, n_runs), nullptr);
+        ctx->cur ^= 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    Counters h;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && n_samples > 0)
+        e = cudaMemcpyAsync(raw_out, ctx->acc, 8 * need, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    noalloc_forget(ctx);
+    if (e != cudaSuccess) return fail(ctx, DSMC_E_CUDA, std::string("no-allocation run: ") +
+                                                            cudaGetErrorString(e));
+    fill_stats(ctx, h);
+    ctx->stats.steps_done = steps;
+    return check_error_word(ctx, h.error);
+}

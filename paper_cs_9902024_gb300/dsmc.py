@@ -31,6 +31,7 @@ EXPORTS = [
     "dsmc_last_error", "dsmc_debug_begin", "dsmc_debug_step", "dsmc_debug_get_state",
     "dsmc_debug_set_state", "dsmc_debug_get_cells", "dsmc_debug_get_cell_state",
     "dsmc_debug_set_cell_state", "dsmc_debug_sample", "dsmc_debug_philox",
+    "dsmc_run_ensemble_noalloc",
 ]
 
 
@@ -116,6 +117,8 @@ def load_library(path=LIB_PATH):
         lib.dsmc_debug_set_cell_state.argtypes = [P, C.c_int, dp, dp]
         lib.dsmc_debug_sample.argtypes = [P, C.c_int, dp]
         lib.dsmc_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
+        lib.dsmc_run_ensemble_noalloc.argtypes = [P, C.c_int, C.c_double, C.c_int, ip, C.c_int,
+                                                  C.c_uint64, dp, C.c_size_t]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype if name in (
                 "dsmc_destroy", "dsmc_last_error") else C.c_int
@@ -252,6 +255,25 @@ class Ensemble:
         self.runs = runs
         self.n_samples = len(ss)
         return self
+
+    def run_noalloc(self, runs=None, steps=None, sample_steps=None, seed=None, dt=None):
+        """dsmc_run_ensemble_noalloc: the run inside the library's fixed device
+        scratch (no device allocation); returns the group sums of every
+        sample, shape (samples, G, ncells, 7)."""
+        w = self.w
+        runs = w["runs"] if runs is None else runs
+        steps = w["steps"] if steps is None else steps
+        ss = np.ascontiguousarray(w["sample_steps"] if sample_steps is None else sample_steps,
+                                  dtype=np.int32)
+        seed = w["seed"] if seed is None else seed
+        dt = w["dt"] if dt is None else dt
+        G = min(runs, 16)
+        out = np.zeros((max(len(ss), 1), G, self.ncells, NMOM))
+        st = self.lib.dsmc_run_ensemble_noalloc(self.h, runs, dt, steps,
+                                                _ptr(ss, C.c_int32) if len(ss) else None, len(ss),
+                                                seed, _ptr(out, C.c_double), out.size)
+        self._check(st, "dsmc_run_ensemble_noalloc")
+        return out[:len(ss)]
 
     def raw(self, t):
         G = min(self.runs, 16)
