@@ -158,8 +158,8 @@ def algorithmic_bytes(w, st, steps, runs):
     pool = st["pool_steps"]
     return {
         # read the in-cell offsets (D), v (D; the third component only at
-        # wall hits) and the cell index, write the offsets (D), the cell key
-        # and the in-cell rank
+        # wall hits) and the cell key, write the offsets (D), the new key
+        # and the rank inside the cell
         "move": moved_old * (3 * D * t + 4 + 8),
         # read key, rank and id, write the LCR entry (slot, id)
         "scatter": pool * 20,
@@ -167,9 +167,9 @@ def algorithmic_bytes(w, st, steps, runs):
         # id, v
         "cell": pool * (8 + 2 * (D * t + 3 * t) + 8) + cells * steps * 4,
         # per cell: start, NTC remainder (read + write), (sigma c_r)_max;
-        # per candidate pair: both velocities read; per collision: written
-        "collide": cells * steps * 24 + st["candidates"] * 2 * 3 * t
-        + st["collisions"] * 2 * 3 * t,
+        # every particle's velocity read once, both velocities of every
+        # collision written
+        "collide": cells * steps * 24 + pool * 3 * t + st["collisions"] * 2 * 3 * t,
         # read counts twice, write starts, clear counts
         "scan": cells * steps * 16,
         # write the entrants (x, v, id, key, rank)
@@ -185,7 +185,7 @@ def run_reference(args):
     from oracle import run_ensemble
     w = workload()
     cores = min(cpu_cores(), 16)
-    sample_runs = 16
+    sample_runs = 64
     wr = dict(w)
 
     def one():
@@ -247,7 +247,9 @@ def main():
         ens.run()
     st = ens.stats()
     ps_per_step = st["particle_steps"]
-    launches_per_step = 6 + steps * 9
+    # fill: 6 launches; every time step: generate, move, move_slow, scan1,
+    # scan2, scatter, cell, cell_big, collide, reduce, step_end
+    launches_per_step = 6 + steps * 11
     # -- device-timed region: inputs resident, results stay on the device --
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -374,15 +376,21 @@ def main():
         out["kernels"] = kern
         out["profile_run_ms"] = prs["ms_steps"]
         # -- the FP64 oracle on the host cores, bounded sample -------------
+        # (threads over run groups: at most G = 16).  A 16-run probe sizes
+        # the timed sample to about 15 s of host work.
         from oracle import run_ensemble
         cores = min(cpu_cores(), 16)
         t0 = time.perf_counter()
-        _, sto = run_ensemble(w, runs=16, threads=cores)
+        run_ensemble(w, runs=16, threads=cores)
+        probe = time.perf_counter() - t0
+        cpu_runs = int(min(runs, max(16, 16 * round(15.0 / max(probe, 1e-3)))))
+        t0 = time.perf_counter()
+        _, sto = run_ensemble(w, runs=cpu_runs, threads=cores)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": sto["particle_steps"] / dt, "unit": UNIT, "cores": cores,
                                "kind": "oracle",
-                               "sample": "16 of the 512 runs x 400 steps, FP64, %d threads over "
-                                         "runs, %.1f s" % (cores, dt)}
+                               "sample": "%d of the %d runs x %d steps, FP64, %d threads over "
+                                         "run groups, %.1f s" % (cpu_runs, runs, steps, cores, dt)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ens.close()

@@ -50,7 +50,7 @@ typedef enum {
     DSMC_E_CUDA = 3,       /* a CUDA call failed (message in last_error) */
     DSMC_E_CAPACITY = 4,   /* particle pool or a per-cell limit overflowed on
                               the device; the run's results are incomplete */
-    DSMC_E_TIMEOUT = 5,    /* a bounded device wait expired (reserved) */
+    DSMC_E_TIMEOUT = 5,    /* a bounded device wait expired (DSMC_ERR_TIMEOUT) */
     DSMC_E_STATE = 6       /* call out of order (e.g. samples before a run) */
 } dsmc_status;
 
@@ -176,6 +176,7 @@ typedef struct {
 #define DSMC_ERR_GEN       0x2u   /* per-run generation buffer overflow */
 #define DSMC_ERR_BIGCELL   0x4u   /* a cell exceeded the per-cell limit */
 #define DSMC_ERR_BIGLIST   0x8u   /* too many large cells in one step */
+#define DSMC_ERR_TIMEOUT   0x10u  /* a bounded device wait (bulk-copy completion) expired */
 
 /* kernel kinds of dsmc_stats.ms_kernel */
 enum { DSMC_K_GENERATE = 0, DSMC_K_MOVE = 1, DSMC_K_SCAN = 2, DSMC_K_SCATTER = 3,

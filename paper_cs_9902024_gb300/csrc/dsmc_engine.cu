@@ -129,6 +129,7 @@ static dsmc_status build_cfg(dsmc_ctx* ctx, double dt, uint64_t seed)
     c.mass = ctx->gas.mass;
     c.F_N = ctx->gas.F_N;
     c.coef = (ctx->gas.F_N * dt) / c.Vc;
+    c.coef_f = (float)c.coef;
     const double omega = ctx->gas.omega;
     const double dref = ctx->gas.d_ref;
     c.hs = (omega == 0.5) ? 1 : 0;
@@ -344,6 +345,24 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     StepArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.cfg = ctx->d_cfg;
+    const Cfg& c = ctx->hcfg;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.hot.d[ax] = (T)c.d[ax];
+        a.hot.inv_d[ax] = (float)c.inv_d[ax];
+        a.hot.n[ax] = c.n[ax];
+    }
+    a.hot.dt = (T)c.dt;
+    a.hot.ncells = c.ncells;
+    a.hot.plate_axes = 0u;
+    for (int pi = 0; pi < c.n_plate; ++pi) a.hot.plate_axes |= 1u << c.bc[c.plate_idx[pi]].plate_axis;
+    a.hot.hs = c.hs;
+    a.hot.ncells_magic = c.ncells_magic;
+    a.hot.seed = c.seed;
+    a.hot.A_hs = (T)c.A_hs;
+    a.hot.K_vhs = (T)c.K_vhs;
+    a.hot.one_m_omega = (T)c.one_m_omega;
+    a.hot.coef = c.coef;
+    a.hot.coef_f = c.coef_f;
     a.ctr = ctx->d_ctr;
     for (int ax = 0; ax < 3; ++ax) {
         a.xi[ax] = (T*)ctx->X[cur][ax];
@@ -483,6 +502,12 @@ static dsmc_status check_error_word(dsmc_ctx* ctx, uint32_t e)
 {
     if (!e) return DSMC_OK;
     char buf[256];
+    if (e & DSMC_ERR_TIMEOUT) {
+        std::snprintf(buf, sizeof buf,
+                      "device error word 0x%x: a bounded wait for a bulk copy expired", e);
+        ctx->err = buf;
+        return DSMC_E_TIMEOUT;
+    }
     std::snprintf(buf, sizeof buf,
                   "device error word 0x%x (pool=%d gen=%d bigcell=%d biglist=%d); "
                   "raise capacity_factor / capacity_per_run",

@@ -14,6 +14,8 @@ constexpr int kGenBlocks = 64;            // Philox blocks per generated particl
 constexpr int kWarpMax = 128;             // cells up to this size: one warp each
 constexpr int kCellWarps = 8;             // warps per CTA of the cell kernel
 constexpr int kTileCells = 256;           // cells (= threads) per tile CTA
+constexpr int kCollideCells = 128;        // cells (= threads) per CTA of the collision kernel
+constexpr int kCollideStage = 2816;       // particles whose velocities one collision CTA stages
 constexpr int kLaneMax = 512;             // largest cell of the tile path
 constexpr int kScanTile = 4096;           // cells per CTA of the scan
 constexpr int kScanThreads = 1024;
@@ -49,6 +51,7 @@ struct Cfg {
     int32_t plate_idx[DSMC_MAX_BC];
     double L[3], d[3], inv_d[3], Vc, dt, mass;
     double coef;         // F_N dt / Vc
+    float coef_f;        // the same, rounded to binary32
     double F_N;
     double A_hs;         // hard sphere: pi d^2 (sigma_T c_r = A_hs c_r)
     double K_vhs;        // VHS: sigma_T c_r = K_vhs (c_r^2)^(1 - omega)
@@ -68,10 +71,33 @@ struct Counters {
     uint32_t error, step, n_big, n_slow;
 };
 
+// The configuration constants that the streaming kernels use for every
+// particle or NTC candidate, carried by value in the launch parameters
+// (constant bank) rather than read through the configuration pointer.  The
+// field names match Cfg's, so the device helpers accept either; every value
+// is the one the Cfg-based code converts to (the results do not depend on
+// which is used).
+template <typename T>
+struct Hot {
+    T d[3];                  // cell sizes
+    float inv_d[3];          // binary32 reciprocals of d
+    T dt;
+    int32_t n[3];            // cells per axis
+    int32_t ncells;          // cells per run
+    uint32_t plate_axes;     // bit a set: a plate is normal to axis a
+    int32_t hs;
+    uint64_t ncells_magic;
+    uint64_t seed;
+    T A_hs, K_vhs, one_m_omega;
+    double coef;
+    float coef_f;
+};
+
 // Device pointers of one step (particle pool double-buffered: in -> out).
 template <typename T>
 struct StepArgs {
     const Cfg* cfg;
+    Hot<T> hot;
     Counters* ctr;
     // pool: in/out buffers of positions (dim used), velocities (3), ids
     // positions are offsets inside the particle's cell; ci_* hold the

@@ -6,18 +6,21 @@
 //
 //   k_generate   one CTA per run: inflow counts, entrants created and moved
 //                for their first fractional step (Generation + Motion)
-//   k_move       grid-stride over the particle pool: free flight, surface
-//                interaction, new cell key and a rank inside the cell from a
-//                warp-aggregated atomic (Motion + Enumeration)
+//   k_move       grid-stride over the particle pool: free flight (surface
+//                interaction in k_move_slow), new cell key and a rank
+//                inside the cell from an atomic count (Motion + Enumeration)
 //   k_scan1/2    exclusive prefix over the run-major cell counts: each
 //                cell's first pool position, each run's first position
 //                (Indexing)
-//   k_scatter    LCR[start[cell] + rank] = slot  (Indexing)
-//   k_cell       one warp per cell: the cell's particles put in particle-id
-//                order, gathered into the next pool, NTC collisions, and the
-//                cell moments at sample steps (Indexing + Interaction +
-//                Sampling)
-//   k_cell_big   one CTA per cell too large for a warp
+//   k_scatter    LCR[start[cell] + rank] = (slot, id)  (Indexing)
+//   k_cell       one CTA per 256 cells: each cell's particles put in
+//                particle-id order and gathered into the next pool
+//                (Indexing)
+//   k_cell_big   one CTA per cell above 128 particles: ordering,
+//                collisions and moments of that cell
+//   k_collide    one thread per cell, a tile's velocities staged in shared
+//                memory: NTC collisions, and the cell moments at sample
+//                steps (Interaction + Sampling)
 //   k_reduce     fixed-order sum of the runs' cell moments into group
 //                accumulators at sample steps (Sampling)
 //
@@ -97,6 +100,19 @@ __device__ __forceinline__ void gauss2(T u1, T u2, T& z0, T& z1)
 // times the binary32 reciprocal of d (one multiply)
 __device__ __forceinline__ double in_cells(const Cfg& c, int a, double f) { return f / c.d[a]; }
 __device__ __forceinline__ float in_cells(const Cfg& c, int a, float f) { return f * (float)c.inv_d[a]; }
+__device__ __forceinline__ double in_cells(const Hot<double>& c, int a, double f) { return f / c.d[a]; }
+__device__ __forceinline__ float in_cells(const Hot<float>& c, int a, float f) { return f * c.inv_d[a]; }
+
+// a plate normal to axis a exists (a flight that changes cell along it may
+// meet the plate)
+__device__ __forceinline__ bool plate_on_axis(const Cfg& c, int a)
+{
+    for (int pi = 0; pi < c.n_plate; ++pi)
+        if (c.bc[c.plate_idx[pi]].plate_axis == a) return true;
+    return false;
+}
+template <typename T>
+__device__ __forceinline__ bool plate_on_axis(const Hot<T>& c, int a) { return (c.plate_axes >> a) & 1u; }
 
 // move whole cells so that 0 <= f <= d along axis a (clamped to the grid)
 template <typename T>
@@ -120,8 +136,8 @@ __device__ __forceinline__ uint32_t div_small(uint32_t x, uint32_t n)
     return q;
 }
 
-template <int DIM>
-__device__ __forceinline__ void decode_cell(const Cfg& c, uint32_t lin, int* ci)
+template <int DIM, class C>
+__device__ __forceinline__ void decode_cell(const C& c, uint32_t lin, int* ci)
 {
     const uint32_t q = div_small(lin, (uint32_t)c.n[0]);
     ci[0] = (int)(lin - q * (uint32_t)c.n[0]);
@@ -135,8 +151,8 @@ __device__ __forceinline__ void decode_cell(const Cfg& c, uint32_t lin, int* ci)
     }
 }
 
-template <int DIM>
-__device__ __forceinline__ uint32_t encode_cell(const Cfg& c, const int* ci)
+template <int DIM, class C>
+__device__ __forceinline__ uint32_t encode_cell(const C& c, const int* ci)
 {
     return (uint32_t)(ci[0] + c.n[0] * (ci[1] + (DIM == 3 ? c.n[1] * ci[2] : 0)));
 }
@@ -168,8 +184,8 @@ struct LocalCounters {
 // above rounding) and changes no cell along a plate's axis: no surface event
 // can occur, and the result equals move_particle's.  Returns false (state
 // untouched) otherwise.
-template <typename T, int DIM>
-__device__ __forceinline__ bool try_free_flight(const Cfg& c, int* ci, T* f, const T* v, T tau)
+template <typename T, int DIM, class C>
+__device__ __forceinline__ bool try_free_flight(const C& c, int* ci, T* f, const T* v, T tau)
 {
     const T margin = sizeof(T) == 4 ? (T)1e-5 : (T)1e-12;
     int ni[3];
@@ -185,12 +201,9 @@ __device__ __forceinline__ bool try_free_flight(const Cfg& c, int* ci, T* f, con
         if (ni[a] == 0 && !(nf[a] > margin * d)) return false;
         if (ni[a] == c.n[a] - 1 && !(nf[a] < d - margin * d)) return false;
     }
-    for (int pi = 0; pi < c.n_plate; ++pi) {
-        const int pa = c.bc[c.plate_idx[pi]].plate_axis;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a)
-            if (a == pa && ni[a] != ci[a]) return false;
-    }
+    for (int a = 0; a < DIM; ++a)
+        if (ni[a] != ci[a] && plate_on_axis(c, a)) return false;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { ci[a] = ni[a]; f[a] = nf[a]; }
     return true;
@@ -331,6 +344,67 @@ __device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, ui
 // ---------------------------------------------------------------------------
 // warp / block helpers
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, untiled) from global to shared memory,
+// completed on an mbarrier.  Addresses and sizes must be multiples of 16
+// bytes; every wait is bounded.
+constexpr uint32_t kWaitPolls = 1u << 20;   // try_wait polls before a wait is abandoned
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// order this thread's earlier generic-proxy shared-memory accesses before
+// later bulk copies into shared memory
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+// wait for the phase with the given parity to complete; false if it did not
+// within kWaitPolls polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kWaitPolls; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 
 __device__ __forceinline__ void flush_counters(Counters* ctr, const LocalCounters& lc)
 {
@@ -645,7 +719,8 @@ __device__ __forceinline__ void store4(T* __restrict__ p, uint64_t s, const T* i
 
 // run of a run-major cell key: key / ncells by a 64-bit multiply-high
 // (exact for every 32-bit key, see the host's magic number)
-__device__ __forceinline__ uint32_t run_of_key(const Cfg& c, uint32_t key)
+template <class C>
+__device__ __forceinline__ uint32_t run_of_key(const C& c, uint32_t key)
 {
     return c.ncells_magic ? (uint32_t)__umul64hi((unsigned long long)key, c.ncells_magic) : key;
 }
@@ -658,11 +733,11 @@ __device__ __forceinline__ uint32_t run_of_key(const Cfg& c, uint32_t key)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
-    const Cfg& c = *a.cfg;
+    const Hot<T>& c = a.hot;
     // after a pool overflow (reported through the error word) the recorded
     // size can exceed the buffers: never walk past them
     const uint32_t n_total = min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
-    const T dt = (T)c.dt;
+    const T dt = c.dt;
     T* __restrict__ xp0 = a.xi[0];
     T* __restrict__ xp1 = a.xi[1];
     T* __restrict__ xp2 = a.xi[2];
@@ -814,9 +889,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
 }
 
 // Indexing, part 2: LCR[start[cell] + rank] = (slot, id) for every live
-// particle (the id rides along so that the next kernel needs no gather to
-// order a cell).  Four consecutive slots per thread, keys and ranks read as
-// 16-byte vectors.
+// particle (the rank is any order inside a cell: the next kernel orders
+// each cell by id; the id rides along so that it needs no gather to do so).
+// Four consecutive slots per thread, keys and ranks read as 16-byte vectors.
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 {
@@ -875,21 +950,32 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 
 // ---------------------------------------------------------------------------
 // (sigma_T c_r) of a pair with relative speed squared g2 (and speed g)
-template <typename T>
-__device__ __forceinline__ T sigma_cr(const Cfg& c, T g, T g2)
+template <typename T, class C>
+__device__ __forceinline__ T sigma_cr(const C& c, T g, T g2)
 {
     if (c.hs) return (T)c.A_hs * g;
     if (g2 == (T)0) return (T)0;
     return (T)c.K_vhs * dpow(g2, (T)c.one_m_omega);
 }
 
-// NTC candidate count of a cell with N particles: FP64 with the remainder
-// carried across steps; N < 2 leaves the remainder unchanged.
-__device__ __forceinline__ int64_t ntc_count(const Cfg& c, uint32_t N, double smax, double& rem)
+// NTC candidate count of a cell with N particles, M = floor(x) with
+// x = (1/2) N (N-1) F_N dt / V_c (sigma c_r)_max + rem; the fractional
+// remainder rem = x - M is carried across steps in FP64 and N < 2 leaves it
+// unchanged.  With FP32 state the product is formed in binary32 (FP32
+// collision arithmetic) and only the remainder carry is FP64; with FP64
+// state every operation is FP64.
+template <typename T, class C>
+__device__ __forceinline__ int64_t ntc_count(const C& c, uint32_t N, T smax, double& rem)
 {
     if (N < 2) return 0;
-    const double nn = (double)N * (double)(N - 1u);
-    const double x = 0.5 * nn * c.coef * smax + rem;
+    double x;
+    if (sizeof(T) == 4) {
+        const float p = (0.5f * (float)(N * (N - 1u))) * c.coef_f * (float)smax;
+        x = (double)p + rem;
+    } else {
+        const double nn = (double)N * (double)(N - 1u);
+        x = 0.5 * nn * c.coef * (double)smax + rem;
+    }
     const double M = floor(x);
     rem = x - M;
     return (int64_t)M;
@@ -930,8 +1016,8 @@ __device__ __forceinline__ double warp_sum(double x)
 
 // The draws of NTC candidate k of a cell with N particles: the pair (i, j),
 // the acceptance uniform, cos(chi) and the azimuth uniform.
-template <typename T>
-__device__ __forceinline__ void candidate_draws(const Cfg& c, uint32_t run, uint32_t step,
+template <typename T, class C>
+__device__ __forceinline__ void candidate_draws(const C& c, uint32_t run, uint32_t step,
                                                 uint32_t cell, int64_t k, uint32_t N, uint32_t& ci,
                                                 uint32_t& cj, T& u2, T& u3, T& ue)
 {
@@ -947,8 +1033,8 @@ __device__ __forceinline__ void candidate_draws(const Cfg& c, uint32_t run, uint
 
 // the same candidate for a single thread: the azimuth block is drawn only
 // when the pair is accepted
-template <typename T>
-__device__ __forceinline__ void collide_candidate_lazy(const Cfg& c, T* sv0, T* sv1, T* sv2,
+template <typename T, class C>
+__device__ __forceinline__ void collide_candidate_lazy(const C& c, T* sv0, T* sv1, T* sv2,
                                                        uint32_t run, uint32_t step, uint32_t cell,
                                                        int64_t k, uint32_t N, T smax, T& seen,
                                                        uint32_t& nacc, uint32_t& nclamp)
@@ -977,8 +1063,8 @@ __device__ __forceinline__ void collide_candidate_lazy(const Cfg& c, T* sv0, T* 
 // One NTC candidate pair (i, j) on velocities in shared memory: accept with
 // probability sigma_T c_r / (sigma_T c_r)_max, then scatter isotropically.
 // Every cell path uses this arithmetic, so results do not depend on the path.
-template <typename T>
-__device__ __forceinline__ void collide_candidate(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t i,
+template <typename T, class C>
+__device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T* sv2, uint32_t i,
                                                   uint32_t j, T u2, T u3, T ue, T smax, T& seen,
                                                   uint32_t& nacc, uint32_t& nclamp)
 {
@@ -1001,8 +1087,8 @@ __device__ __forceinline__ void collide_candidate(const Cfg& c, T* sv0, T* sv1, 
 // Interaction of one cell whose velocities sit in s_v[3][*] in id order;
 // all lanes of the warp call it: the lanes draw 32 candidates at a time,
 // lane 0 applies them in order.
-template <typename T>
-__device__ void collide_cell_warp(const Cfg& c, T* sv0, T* sv1, T* sv2, uint32_t N, int64_t M,
+template <typename T, class C>
+__device__ void collide_cell_warp(const C& c, T* sv0, T* sv1, T* sv2, uint32_t N, int64_t M,
                                   T smax, uint32_t cell, uint32_t run, uint32_t step,
                                   T& seen, uint32_t& nacc, uint32_t& nclamp)
 {
@@ -1225,44 +1311,186 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 
 // Interaction and Sampling: one thread per cell of at most kWarpMax
 // particles (larger cells are done whole by the one-CTA-per-cell kernel), on
-// the cell's velocities in the next pool, now in id order.
-template <typename T>
-__global__ void __launch_bounds__(256, 4) k_collide(StepArgs<T> a)
+// the cell's velocities in the next pool, now in id order.  A CTA takes
+// kCollideCells consecutive cells.  (1) Thread 0 starts bulk copies (TMA) of
+// the tile's velocities, up to kCollideStage particles, into shared memory;
+// meanwhile every thread forms its cell's NTC candidate count (coalesced
+// remainder and (sigma c_r)_max accesses) and the staged range is cut to
+// whole cells.  (2) The cells are handed to the threads grouped by
+// candidate count (a 32-bin counting sort), so that the cells of one warp
+// run similar numbers of candidates.  (3) Each thread collides its cell --
+// in shared memory if staged, else in place in global memory, with the same
+// arithmetic -- and forms the cell's moments at sample steps.  (4) The
+// staged velocities are stored back with coalesced stores.
+template <typename T, class C>
+__device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2, uint32_t run,
+                                                 uint32_t step, uint32_t cell, uint32_t M, uint32_t N,
+                                                 T smax, T& seen, uint32_t& nacc, uint32_t& nclamp)
 {
-    const Cfg& c = *a.cfg;
+    for (uint32_t k = 0; k < M; ++k)
+        collide_candidate_lazy<T>(c, v0, v1, v2, run, step, cell, k, N, smax, seen, nacc, nclamp);
+}
+
+template <typename T>
+__host__ __device__ constexpr int collide_stage_pitch() { return kCollideStage + 8; }
+
+template <typename T>
+__global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kPitch = collide_stage_pitch<T>();
+    constexpr uint32_t kVec = 16u / sizeof(T);   // elements per 16 bytes
+    T* s0 = reinterpret_cast<T*>(smem_raw);
+    T* s1 = s0 + kPitch;
+    T* s2 = s1 + kPitch;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_b0, s_n, s_nload, s_sh;
+    __shared__ uint32_t s_bin[32];
+    __shared__ uint32_t s_beg[kCollideCells], s_N[kCollideCells], s_M[kCollideCells];
+    __shared__ uint32_t s_ord[kCollideCells];
+    __shared__ T s_smax[kCollideCells];
+    const Hot<T>& c = a.hot;
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
+    const uint32_t tid = threadIdx.x;
+    constexpr uint32_t kOff = 0xFFFFFFFFu;   // s_N of a cell this kernel skips
+    if (tid == 0) mbar_init(&s_bar, 1u);
+    uint32_t phase = 0;
     CellTally tl;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t gcell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gcell < a.total_cells;
-         gcell += stride) {
-        const uint32_t beg = a.start[gcell];
-        const uint32_t N = a.start[gcell + 1] - beg;
-        if (N > (uint32_t)kWarpMax || (uint64_t)beg + N > (uint64_t)a.cap_old) continue;
-        const uint32_t rl = run_of_key(c, (uint32_t)gcell);
-        const uint32_t cell = (uint32_t)gcell - rl * (uint32_t)c.ncells;
-        double rem = a.rem[gcell];
-        const T smax = a.smax[gcell];
-        const int64_t M = ntc_count(c, N, (double)smax, rem);
-        T seen = (T)0;
-        uint32_t nacc = 0, nclamp = 0;
-        T* v0 = a.vo[0] + beg;
-        T* v1 = a.vo[1] + beg;
-        T* v2 = a.vo[2] + beg;
-        for (int64_t k = 0; k < M; ++k)
-            collide_candidate_lazy<T>(c, v0, v1, v2, a.run0 + rl, step, cell, k, N, smax, seen, nacc,
-                                      nclamp);
-        if (N >= 2) a.rem[gcell] = rem;
-        if (seen > smax) a.smax[gcell] = seen;
-        if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
-        tl.cand += (unsigned long long)M;
-        tl.acc += nacc;
-        tl.clamp += nclamp;
-        if (slot_t >= 0) {
-            double m[DSMC_NMOM];
-            cell_moments<T>(v0, v1, v2, N, m);
-            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[gcell * DSMC_NMOM + q] = m[q];
+    const int64_t ntiles = (a.total_cells + kCollideCells - 1) / kCollideCells;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t c0 = tile * kCollideCells;
+        const int64_t rest = a.total_cells - c0;
+        const uint32_t nc = rest < kCollideCells ? (uint32_t)rest : (uint32_t)kCollideCells;
+        const int64_t gcell = c0 + tid;
+        const bool mine = tid < nc;
+        uint32_t beg = 0, N = 0;
+        if (mine) {
+            beg = a.start[gcell];
+            N = a.start[gcell + 1] - beg;
         }
+        if (tid == 0) {
+            // the tile's particles [beg, end), clipped to the stage and the pool
+            const uint32_t end = a.start[c0 + nc];
+            const int64_t room = a.cap_old - (int64_t)beg;
+            int64_t n = end > beg ? (int64_t)(end - beg) : 0;
+            if (n > kCollideStage) n = kCollideStage;
+            if (n > room) n = room > 0 ? room : 0;
+            s_b0 = beg;
+            s_n = (uint32_t)n;
+            s_nload = (uint32_t)n;
+            if (n > 0) {
+                // 16-byte aligned superset [lo, hi) of [beg, beg + n); hi stays
+                // inside the pool, whose capacity is a multiple of 256
+                const uint32_t lo = beg & ~(kVec - 1u);
+                const uint32_t hi = (beg + (uint32_t)n + kVec - 1u) & ~(kVec - 1u);
+                const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(T);
+                s_sh = beg - lo;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s_bar, 3u * bytes);
+                bulk_g2s(s0, a.vo[0] + lo, bytes, &s_bar);
+                bulk_g2s(s1, a.vo[1] + lo, bytes, &s_bar);
+                bulk_g2s(s2, a.vo[2] + lo, bytes, &s_bar);
+            }
+        }
+        if (tid < 32) s_bin[tid] = 0u;
+        __syncthreads();
+        const uint32_t b0 = s_b0;
+        const uint32_t nload = s_nload;
+        // cut the staged range at the first cell that does not fit whole
+        if (mine) {
+            const uint32_t rel = beg - b0;
+            const uint64_t end = (uint64_t)rel + N;
+            if (beg < b0) atomicMin(&s_n, 0u);
+            else if (rel < nload && end > (uint64_t)nload) atomicMin(&s_n, rel);
+        }
+        // NTC candidate count of this thread's cell; the remainder is final
+        const bool act = mine && N <= (uint32_t)kWarpMax && (uint64_t)beg + N <= (uint64_t)a.cap_old;
+        uint32_t M32 = 0;
+        if (act) {
+            double rem = a.rem[gcell];
+            const T smax = a.smax[gcell];
+            const int64_t M = ntc_count<T>(c, N, smax, rem);
+            if (N >= 2) a.rem[gcell] = rem;
+            M32 = M > (int64_t)0x7FFFFFFF ? 0x7FFFFFFFu : (uint32_t)M;
+            s_smax[tid] = smax;
+        }
+        s_beg[tid] = beg;
+        s_N[tid] = act ? N : kOff;
+        s_M[tid] = M32;
+        const uint32_t bin = M32 < 31u ? M32 : 31u;
+        const uint32_t in_bin = atomicAdd(&s_bin[bin], 1u);
+        __syncthreads();
+        const uint32_t n_st = s_n;
+        const uint32_t sh = s_sh;
+        if (tid < 32) {
+            // exclusive prefix over the 32 bins
+            const uint32_t v = s_bin[tid];
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (tid >= (uint32_t)o) x += y;
+            }
+            s_bin[tid] = x - v;
+        }
+        __syncthreads();
+        s_ord[s_bin[bin] + in_bin] = tid;
+        if (nload > 0) {
+            if (!mbar_wait(&s_bar, phase)) {
+                atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
+                mbar_wait(&s_bar, phase);
+            }
+            phase ^= 1u;
+        }
+        __syncthreads();
+        const uint32_t q = s_ord[tid];
+        const uint32_t Nq = s_N[q];
+        if (Nq != kOff) {
+            const int64_t gq = c0 + q;
+            const uint32_t begq = s_beg[q];
+            const uint32_t Mq = s_M[q];
+            const T smax = s_smax[q];
+            const uint32_t rl = run_of_key(c, (uint32_t)gq);
+            const uint32_t cell = (uint32_t)gq - rl * (uint32_t)c.ncells;
+            const bool staged = begq >= b0 && (uint64_t)(begq - b0) + Nq <= (uint64_t)n_st;
+            T seen = (T)0;
+            uint32_t nacc = 0, nclamp = 0;
+            const uint32_t o = sh + (begq - b0);
+            T* v0 = staged ? s0 + o : a.vo[0] + begq;
+            T* v1 = staged ? s1 + o : a.vo[1] + begq;
+            T* v2 = staged ? s2 + o : a.vo[2] + begq;
+            // one call per address space, so that staged cells use
+            // shared-memory loads and stores
+            if (staged)
+                collide_cell_run<T>(c, s0 + o, s1 + o, s2 + o, a.run0 + rl, step, cell, Mq, Nq, smax,
+                                    seen, nacc, nclamp);
+            else
+                collide_cell_run<T>(c, a.vo[0] + begq, a.vo[1] + begq, a.vo[2] + begq, a.run0 + rl,
+                                    step, cell, Mq, Nq, smax, seen, nacc, nclamp);
+            if (seen > smax) a.smax[gq] = seen;
+            if (a.cand) { a.cand[gq] = Mq; a.accd[gq] = nacc; }
+            tl.cand += Mq;
+            tl.acc += nacc;
+            tl.clamp += nclamp;
+            if (slot_t >= 0) {
+                double m[DSMC_NMOM];
+                cell_moments<T>(v0, v1, v2, Nq, m);
+                for (int qq = 0; qq < DSMC_NMOM; ++qq) a.mom[gq * DSMC_NMOM + qq] = m[qq];
+            }
+        }
+        __syncthreads();
+        {
+            T* g0 = a.vo[0] + b0;
+            T* g1 = a.vo[1] + b0;
+            T* g2 = a.vo[2] + b0;
+            for (uint32_t p = tid; p < n_st; p += kCollideCells) {
+                g0[p] = s0[sh + p];
+                g1[p] = s1[sh + p];
+                g2[p] = s2[sh + p];
+            }
+        }
+        __syncthreads();
     }
     const unsigned long long cs = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.cand);
     const unsigned long long as = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.acc);
@@ -1345,7 +1573,7 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
         if (w == 0) {
             double rem = a.rem[gcell];
             const T smax = a.smax[gcell];
-            const int64_t M = ntc_count(c, N, (double)smax, rem);
+            const int64_t M = ntc_count<T>(c, N, smax, rem);
             T seen = (T)0;
             uint32_t nacc = 0, nclamp = 0;
             if (M > 0)
@@ -1571,9 +1799,16 @@ void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t
     }));
 }
 
+static size_t collide_smem(int prec)
+{
+    return prec == DSMC_FP64 ? (size_t)3 * collide_stage_pitch<double>() * 8
+                             : (size_t)3 * collide_stage_pitch<float>() * 4;
+}
+
 void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, (k_collide<T><<<ls.collide_blocks, 256, 0, s>>>(A<T>(args))));
+    DISPATCH_PREC(prec, (k_collide<T><<<ls.collide_blocks, kCollideCells, collide_smem(prec), s>>>(
+                            A<T>(args))));
 }
 
 int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
@@ -1634,8 +1869,13 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
     ls->scatter_blocks = sms * 8;
     ls->cell_blocks = sms * (bc > 0 ? bc : 2);
     int bl = 0;
-    DISPATCH_PREC(prec, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_collide<T>, 256, 0));
-    ls->collide_blocks = sms * (bl > 0 ? bl : 4);
+    DISPATCH_PREC(prec, {
+        cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)collide_smem(prec));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_collide<T>, kCollideCells,
+                                                      collide_smem(prec));
+    });
+    ls->collide_blocks = sms * (bl > 0 ? bl : 3);
     ls->big_blocks = sms;
 }
 
@@ -1648,6 +1888,9 @@ cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)cell_smem_bytes(prec, tile_budget));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)collide_smem(prec));
 
     }));
     return e;

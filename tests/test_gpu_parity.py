@@ -108,7 +108,9 @@ def test_fp32_one_step_from_identical_state(D):
     binary32 on both sides): cell assignments differ only where a particle
     sits within float rounding of a cell face, per-particle relative error
     <= 1e-5, and the integer outputs agree in every cell the mismatches do
-    not touch."""
+    not touch -- except where the oracle's NTC value x = M + rem lies within
+    binary32 rounding of an integer (the device forms the product in FP32
+    and only carries the remainder in FP64)."""
     w = W.config0(runs=2)
     orc = Oracle(w, runs=2)
     for r in range(2):
@@ -134,7 +136,10 @@ def test_fp32_one_step_from_identical_state(D):
             assert res["err_x"] <= 1e-5 and res["err_v"] <= 1e-5, res
             diff = res["cnt"] != res["co"]
             assert diff.sum() <= 2 * res["mismatch"]
-            same = ~diff
+            rem_o, _ = orc.get_cell_state(r)
+            x_o = res["cando"] + rem_o
+            near = (res["co"] >= 2) & (np.minimum(rem_o, 1.0 - rem_o) <= 1e-6 * np.maximum(x_o, 1.0))
+            same = ~diff & ~near
             assert np.array_equal(res["cand"][same], res["cando"][same])
         copy_oracle_state_to_device(orc, ens, range(2), fp32=True)
     assert total_mis <= max(4, 1e-3 * total_n), (total_mis, total_n)
