@@ -1219,23 +1219,26 @@ __host__ __device__ constexpr size_t warp_scratch_bytes()
 
 // Indexing, part 3 (sort and gather).  One CTA takes kTileCells consecutive
 // (run-major) cells, whose particles occupy one contiguous range of the next
-// pool.  Thread-per-particle phases, coalesced through the LCR: (1) ids into
-// shared memory; (2) each particle's rank inside its cell by counting smaller
-// ids, then its offsets, cell index, velocity and id gathered into the next
-// pool at cell start + rank.  Only the ids are staged (4 bytes per
-// particle), so several CTAs stay resident per SM.  Cells above kWarpMax go
-// to the one-CTA-per-cell kernel; tiles whose particles exceed the budget go
-// cell by cell through the warp path.
+// pool and of the LCR.  (1) Thread 0 starts a bulk copy (TMA) of the tile's
+// LCR entries (slot, id) into shared memory while each thread tags its
+// cell's positions.  (2) Thread per position, two per pass: the particle's
+// rank inside its cell by counting smaller ids, and its offsets, velocity
+// and id gathered from the old pool into the next pool at cell start +
+// rank.  Cells above kWarpMax go to the one-CTA-per-cell kernel; tiles whose
+// particles exceed the budget go cell by cell through the warp path.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 {
     const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
     const uint32_t budget = (uint32_t)a.tile_budget;
     uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
-    uint32_t* s_id = s_start + (kTileCells + 4);
-    uint16_t* s_cellof = reinterpret_cast<uint16_t*>(s_id + budget);
+    uint2* s_lcr = reinterpret_cast<uint2*>(smem_raw + (kTileCells + 4) * sizeof(uint32_t));
+    uint16_t* s_cellof = reinterpret_cast<uint16_t*>(s_lcr + budget + 2);
     const int tid = threadIdx.x;
+    if (tid == 0) mbar_init(&s_bar, 1u);
+    uint32_t phase = 0;
     const int64_t ntiles = ((int64_t)a.total_cells + kTileCells - 1) / kTileCells;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t c0 = tile * kTileCells;
@@ -1244,7 +1247,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
         __syncthreads();
         const uint32_t B = s_start[0], E = s_start[nct];
         const uint32_t Tn = E - B;
-        const bool fits = Tn <= budget && (uint64_t)E <= (uint64_t)a.cap_old;
+        const bool fits = E >= B && Tn <= budget && (uint64_t)E <= (uint64_t)a.cap_old;
         if (!fits) {
             unsigned char* ws = smem_raw + (kTileCells + 4) * sizeof(uint32_t) +
                                 (size_t)(tid >> 5) * warp_scratch_bytes<T>();
@@ -1253,6 +1256,17 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             __syncthreads();
             continue;
         }
+        // [lo, hi): the 16-byte aligned superset of [B, E); the LCR holds
+        // cap_old entries, an even number, so hi stays inside it
+        const uint32_t lo = B & ~1u;
+        const uint32_t sh = B - lo;
+        if (tid == 0 && Tn > 0) {
+            const uint32_t hi = (E + 1u) & ~1u;
+            const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint2);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar, bytes);
+            bulk_g2s(s_lcr, a.lcr + lo, bytes, &s_bar);
+        }
         if (tid < nct) {
             const uint32_t cb = s_start[tid] - B, ce = s_start[tid + 1] - B;
             const bool big = ce - cb > (uint32_t)kWarpMax;
@@ -1260,24 +1274,28 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             const uint16_t mark = big ? (uint16_t)0xFFFF : (uint16_t)tid;
             for (uint32_t k = cb; k < ce; ++k) s_cellof[k] = mark;
         }
+        if (Tn > 0) {
+            if (!mbar_wait(&s_bar, phase)) {
+                atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
+                mbar_wait(&s_bar, phase);
+            }
+            phase ^= 1u;
+        }
         __syncthreads();
-#pragma unroll 4
-        for (uint32_t k = tid; k < Tn; k += kTileCells)
-            if (s_cellof[k] != 0xFFFF) s_id[k] = a.lcr[B + k].y;
-        __syncthreads();
+        const uint2* tl = s_lcr + sh;
         for (uint32_t k0 = tid; k0 < Tn; k0 += 2 * kTileCells) {
             // two particles per pass, every load issued before any store
             uint32_t kk[2] = {k0, k0 + kTileCells}, sl[2];
-            int lo[2];
+            int lo2[2];
             T px[2][3], pv[2][3];
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                lo[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
-                sl[b] = lo[b] != 0xFFFF ? checked_slot(a, a.lcr[B + kk[b]].x) : 0u;
+                lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
+                sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
             }
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                if (lo[b] == 0xFFFF) continue;
+                if (lo2[b] == 0xFFFF) continue;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
                 pv[b][0] = a.vi[0][sl[b]];
@@ -1286,18 +1304,18 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             }
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                if (lo[b] == 0xFFFF) continue;
-                const uint32_t cb = s_start[lo[b]] - B, ce = s_start[lo[b] + 1] - B;
-                const uint32_t my = s_id[kk[b]];
+                if (lo2[b] == 0xFFFF) continue;
+                const uint32_t cb = s_start[lo2[b]] - B, ce = s_start[lo2[b] + 1] - B;
+                const uint32_t my = tl[kk[b]].y;
                 // ids are unique within a run; a duplicate (possible only in a
                 // state already flagged corrupt) leaves a hole, never an access
                 // outside the cell's range
                 uint32_t r = 0;
-                for (uint32_t j = cb; j < ce; ++j) r += s_id[j] < my ? 1u : 0u;
+                for (uint32_t j = cb; j < ce; ++j) r += tl[j].y < my ? 1u : 0u;
                 const uint32_t o = B + cb + r;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
-                a.ci_o[o] = (uint32_t)(c0 + lo[b]);
+                a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
                 a.ido[o] = my;
                 a.vo[0][o] = pv[b][0];
                 a.vo[1][o] = pv[b][1];
@@ -1784,8 +1802,9 @@ void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStrea
 
 size_t cell_smem_bytes(int prec, int budget)
 {
+    // start table, LCR entries (two spare for 16-byte alignment), cell tags
     const size_t head = (kTileCells + 4) * sizeof(uint32_t);
-    const size_t tile = (size_t)budget * 6;
+    const size_t tile = ((size_t)budget + 2) * sizeof(uint2) + (size_t)budget * sizeof(uint16_t);
     const size_t warps = (kTileCells / 32) * (prec == DSMC_FP64 ? warp_scratch_bytes<double>()
                                                                 : warp_scratch_bytes<float>());
     return head + (tile > warps ? tile : warps);
@@ -1852,10 +1871,12 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
 {
     ls->dim = dim;
     ls->sms = sms;
-    // tile budget: 6144 staged particles (ids and cell tags, 36 KB), at
-    // least the warp path's scratch; several tile CTAs stay resident per SM
+    // tile budget: 6144 staged particles (LCR entries and cell tags, 61 KB),
+    // at least the warp path's scratch; a multiple of 8 keeps the staged
+    // arrays 16-byte aligned
     int budget = 6144;
     if (ls->tile_budget <= 0) ls->tile_budget = budget;
+    ls->tile_budget = (ls->tile_budget + 7) / 8 * 8;
     int bm = 0, bc = 0;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
         cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
