@@ -345,6 +345,20 @@ __device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, ui
 // warp / block helpers
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
+// atomicAdd returning the old value, with an L2 evict-last policy: the
+// per-cell counters stay cached while the particle streams pass through L2
+__device__ __forceinline__ uint32_t atomic_add_l2_keep(uint32_t* p, uint32_t v)
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    uint32_t old;
+    asm volatile("atom.global.add.L2::cache_hint.u32 %0, [%1], %2, %3;"
+                 : "=r"(old)
+                 : "l"(p), "r"(v), "l"(pol)
+                 : "memory");
+    return old;
+}
+
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (TMA, untiled) from global to shared memory,
 // completed on an mbarrier.  Addresses and sizes must be multiples of 16
@@ -677,7 +691,7 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
             uint32_t key = kDead, rk = 0;
             if (alive) {
                 key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
-                rk = atomicAdd(&a.count[key], 1u);
+                rk = atomic_add_l2_keep(&a.count[key], 1u);
             }
             a.gc[slot] = key;
             a.rank[slot] = rk;
@@ -726,10 +740,13 @@ __device__ __forceinline__ uint32_t run_of_key(const C& c, uint32_t key)
 }
 
 // Motion of the pool, straight-flight part: one particle per thread with
-// few registers, so that many warps keep their loads and rank atomics in
-// flight.  Each particle's run and cell come from its stored cell key.  A
-// particle whose flight may meet a surface is appended to the slow list
-// (one atomic per warp) and moved by k_move_slow.
+// few registers, so that many warps keep their loads in flight.  Each
+// particle's run and cell come from its stored cell key.  The rank inside
+// the new cell comes from one atomic per distinct cell of the warp (the pool
+// is cell-ordered, so a warp's particles share few cells), with an L2
+// evict-last hint on the counters.  A particle whose flight may meet a
+// surface is appended to the slow list (one atomic per warp) and moved by
+// k_move_slow.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
@@ -754,6 +771,7 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
     for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n_total; base += stride) {
         const uint32_t s = base + lane;
         bool slow = false;
+        uint32_t key = kDead;   // no rank needed (past the end, or slow)
         if (s < n_total) {
             const uint32_t kold = cip[s];
             T x[3], v[3];
@@ -766,12 +784,20 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
                 xp0[s] = x[0];
                 xp1[s] = x[1];
                 if (DIM == 3) xp2[s] = x[2];
-                const uint32_t key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
+                key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
                 gc[s] = key;
-                rank[s] = atomicAdd(count + key, 1u);
             } else {
                 slow = true;
             }
+        }
+        const uint32_t act = __ballot_sync(0xFFFFFFFFu, key != kDead);
+        if (key != kDead) {
+            const uint32_t peers = __match_any_sync(act, key);
+            const uint32_t leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if (lane == leader) b = atomic_add_l2_keep(count + key, (uint32_t)__popc(peers));
+            b = __shfl_sync(peers, b, leader);
+            rank[s] = b + __popc(peers & ((1u << lane) - 1u));
         }
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, slow);
         if (m) {
@@ -814,7 +840,7 @@ __global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
             for (int ax = 0; ax < 3; ++ax)
                 if (vmask & (1u << ax)) a.vi[ax][s] = v[ax];
             key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
-            rk = atomicAdd(a.count + key, 1u);
+            rk = atomic_add_l2_keep(a.count + key, 1u);
         }
         a.gc[s] = key;
         a.rank[s] = rk;
