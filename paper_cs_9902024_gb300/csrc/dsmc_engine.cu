@@ -76,8 +76,12 @@ struct dsmc_ctx {
     int32_t* sample_slot = nullptr;
     int cur = 0;
     int G = 1;
-    // graphs (batched): one per buffer parity, valid for graph_key
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // graphs (batched): one per buffer parity and kind of step (without /
+    // with sampling), valid for graph_key; inside a graph Generation runs
+    // on a side stream beside Motion
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t graph_key = ~0ull;
     // last run
     bool have_run = false;
@@ -250,12 +254,21 @@ static void* dev_alloc(dsmc_ctx* ctx, size_t bytes)
     return p;
 }
 
+static void destroy_graphs(dsmc_ctx* ctx)
+{
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 2; ++k)
+            if (ctx->gexec[p][k]) {
+                cudaGraphExecDestroy(ctx->gexec[p][k]);
+                ctx->gexec[p][k] = nullptr;
+            }
+    ctx->graph_key = ~0ull;
+}
+
 static void free_all(dsmc_ctx* ctx)
 {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (int k = 0; k < 2; ++k)
-        if (ctx->gexec[k]) { cudaGraphExecDestroy(ctx->gexec[k]); ctx->gexec[k] = nullptr; }
-    ctx->graph_key = ~0ull;
+    destroy_graphs(ctx);
     for (const DevBuf& b : ctx->bufs) {
         if (ctx->opt.free) ctx->opt.free(b.p, b.bytes, ctx->opt.alloc_user, (void*)ctx->stream);
         else cudaFree(b.p);
@@ -431,7 +444,13 @@ static cudaEvent_t event_at(dsmc_ctx* ctx, size_t i)
 
 // One step of every run in the launch described by `args`.  With `ev`
 // non-null an event is recorded after each kernel (profile mode).
-static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev)
+// One time step.  `ev` (profile mode) records an event after each kernel
+// group.  `fork` (graph capture only) runs Generation on the side stream
+// beside Motion: they touch disjoint slots and only add to the cell counts.
+// `reduce` = false leaves out the reduction over runs, for graphs of steps
+// that take no sample (the kernel would find no sample slot and return).
+static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev, bool fork = false,
+                         bool reduce = true)
 {
     const int p = ctx->prec;
     const LaunchShape& ls = ctx->ls;
@@ -439,14 +458,24 @@ static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev)
     auto mark = [&]() {
         if (ev) cudaEventRecord(event_at(ctx, (*ev)++), s);
     };
-    launch_generate(p, args, ls, s); mark();
-    launch_move(p, args, ls, s); mark();
+    if (fork) {
+        cudaEventRecord(ctx->ev_fork, s);
+        cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+        launch_generate(p, args, ls, ctx->side);
+        cudaEventRecord(ctx->ev_join, ctx->side);
+        launch_move(p, args, ls, s);
+        cudaStreamWaitEvent(s, ctx->ev_join, 0);
+    } else {
+        launch_generate(p, args, ls, s); mark();
+        launch_move(p, args, ls, s); mark();
+    }
     launch_scan(p, args, ls, s); mark();
     launch_scatter(p, args, ls, s); mark();
     launch_cell(p, args, ls, s); mark();
     launch_cell_big(p, args, ls, s); mark();
     launch_collide(p, args, ls, s); mark();
-    launch_reduce(p, args, ls, s); mark();
+    if (reduce) launch_reduce(p, args, ls, s);
+    mark();
     launch_step_end(p, args, s); mark();
 }
 static const int kStepKernels = 9;
@@ -567,20 +596,25 @@ static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, cons
 static dsmc_status build_graphs(dsmc_ctx* ctx, int n_runs)
 {
     const uint64_t key = (ctx->generation << 24) ^ (uint64_t)n_runs;
-    if (ctx->graph_key == key && ctx->gexec[0] && ctx->gexec[1]) return DSMC_OK;
-    for (int k = 0; k < 2; ++k)
-        if (ctx->gexec[k]) { cudaGraphExecDestroy(ctx->gexec[k]); ctx->gexec[k] = nullptr; }
-    for (int p = 0; p < 2; ++p) {
-        AnyArgs u;
-        const void* args = build_args(ctx, u, p, (int)ctx->opt.run_offset, n_runs);
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(ctx, args, nullptr);
-        CK(cudaStreamEndCapture(ctx->stream, &g));
-        cudaError_t e = cudaGraphInstantiate(&ctx->gexec[p], g, 0);
-        cudaGraphDestroy(g);
-        CK(e);
-    }
+    if (ctx->graph_key == key && ctx->gexec[0][0] && ctx->gexec[0][1] && ctx->gexec[1][0] &&
+        ctx->gexec[1][1])
+        return DSMC_OK;
+    destroy_graphs(ctx);
+    if (!ctx->side) CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    for (int p = 0; p < 2; ++p)
+        for (int smp = 0; smp < 2; ++smp) {
+            AnyArgs u;
+            const void* args = build_args(ctx, u, p, (int)ctx->opt.run_offset, n_runs);
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            enqueue_step(ctx, args, nullptr, true, smp != 0);
+            CK(cudaStreamEndCapture(ctx->stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&ctx->gexec[p][smp], g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+        }
     ctx->graph_key = key;
     return DSMC_OK;
 }
@@ -686,6 +720,9 @@ void dsmc_destroy(dsmc_ctx* ctx)
     cudaSetDevice(ctx->device);
     free_all(ctx);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -721,6 +758,8 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
         ctx->stats.ms_kernel[k] = 0.0;
         ctx->stats.launches_kernel[k] = 0;
     }
+    std::vector<char> is_sample(steps + 1, 0);
+    for (int k = 0; k < n_samples; ++k) is_sample[sample_steps[k]] = 1;
     cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
     if (!e0 || !e1) return fail(ctx, DSMC_E_CUDA, "cudaEventCreate failed");
     size_t evn = 2;
@@ -738,7 +777,7 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
         }
         for (int s = 1; s <= steps; ++s) {
             if (graph) {
-                CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
+                CK(cudaGraphLaunch(ctx->gexec[ctx->cur][is_sample[s]], ctx->stream));
             } else {
                 AnyArgs v;
                 const void* a = build_args(ctx, v, ctx->cur, r0, n_launch);

@@ -359,6 +359,17 @@ __device__ __forceinline__ uint32_t atomic_add_l2_keep(uint32_t* p, uint32_t v)
     return old;
 }
 
+// load with an L2 evict-last policy (per-cell tables that later kernels of
+// the step read again)
+__device__ __forceinline__ uint32_t ld_l2_keep(const uint32_t* p)
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    uint32_t v;
+    asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (TMA, untiled) from global to shared memory,
 // completed on an mbarrier.  Addresses and sizes must be multiples of 16
@@ -954,7 +965,7 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
         uint32_t st[4], idv[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            st[b] = key[b] != kDead ? start[key[b]] : 0u;
+            st[b] = key[b] != kDead ? ld_l2_keep(start + key[b]) : 0u;
             idv[b] = key[b] != kDead ? a.idi[s0 + b] : 0u;
         }
         if (in_new && (key[0] != kDead || key[1] != kDead || key[2] != kDead || key[3] != kDead)) {
@@ -1243,15 +1254,18 @@ __host__ __device__ constexpr size_t warp_scratch_bytes()
     return (size_t)kWarpMax * (2 * sizeof(uint32_t) + sizeof(uint16_t));
 }
 
+constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather (measured: 2 and 4 slower)
+
 // Indexing, part 3 (sort and gather).  One CTA takes kTileCells consecutive
 // (run-major) cells, whose particles occupy one contiguous range of the next
 // pool and of the LCR.  (1) Thread 0 starts a bulk copy (TMA) of the tile's
 // LCR entries (slot, id) into shared memory while each thread tags its
-// cell's positions.  (2) Thread per position, two per pass: the particle's
-// rank inside its cell by counting smaller ids, and its offsets, velocity
-// and id gathered from the old pool into the next pool at cell start +
-// rank.  Cells above kWarpMax go to the one-CTA-per-cell kernel; tiles whose
-// particles exceed the budget go cell by cell through the warp path.
+// cell's positions.  (2) Thread per position, kGatherBatch positions per
+// pass: the particle's rank inside its cell by counting smaller ids, and its
+// offsets, velocity and id gathered from the old pool into the next pool at
+// cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
+// kernel; tiles whose particles exceed the budget go cell by cell through
+// the warp path.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 {
@@ -1309,18 +1323,19 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
         }
         __syncthreads();
         const uint2* tl = s_lcr + sh;
-        for (uint32_t k0 = tid; k0 < Tn; k0 += 2 * kTileCells) {
-            // two particles per pass, every load issued before any store
-            uint32_t kk[2] = {k0, k0 + kTileCells}, sl[2];
-            int lo2[2];
-            T px[2][3], pv[2][3];
+        for (uint32_t k0 = tid; k0 < Tn; k0 += kGatherBatch * kTileCells) {
+            // kGatherBatch particles per pass, every load issued before any store
+            uint32_t kk[kGatherBatch], sl[kGatherBatch];
+            int lo2[kGatherBatch];
+            T px[kGatherBatch][3], pv[kGatherBatch][3];
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < kGatherBatch; ++b) {
+                kk[b] = k0 + (uint32_t)b * kTileCells;
                 lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
                 sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
             }
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < kGatherBatch; ++b) {
                 if (lo2[b] == 0xFFFF) continue;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
@@ -1329,7 +1344,7 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
                 pv[b][2] = a.vi[2][sl[b]];
             }
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < kGatherBatch; ++b) {
                 if (lo2[b] == 0xFFFF) continue;
                 const uint32_t cb = s_start[lo2[b]] - B, ce = s_start[lo2[b] + 1] - B;
                 const uint32_t my = tl[kk[b]].y;
