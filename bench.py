@@ -232,12 +232,14 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_cs_9902024_gb300.dsmc import Ensemble
+    from paper_cs_9902024_gb300 import shard
     w = workload(args.runs)
     runs = w["runs"]
+    shard.groups(runs, ws)          # every rank must hold >= 16 runs when sharded
     steps = w["steps"]
     n_samples = len(w["sample_steps"])
     stream = torch.cuda.Stream(device=device)
-    ens = Ensemble(w, device=device, stream=stream, run_offset=rank * runs)
+    ens = Ensemble(w, device=device, stream=stream, run_offset=shard.run_offset(rank, runs))
 
     def barrier():
         if ws > 1:
@@ -267,12 +269,8 @@ def main():
     clocks = clk.summary()
     ps_total = ps_per_step * args.steps
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        p = torch.tensor([ps_total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(p)
-        ps_total = float(p.item())
+        ms = shard.allreduce_max(ms)
+        ps_total = shard.allreduce_sum(ps_total)
     value = ps_total / (ms / 1e3)
     # -- end to end through the C ABI with host buffers --------------------
     barrier()
@@ -281,11 +279,9 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ens.run()
-        raws = [ens.raw(t) for t in range(n_samples)]
+        raws = np.stack([ens.raw(t) for t in range(n_samples)])
         if ws > 1:
-            r = torch.from_numpy(np.stack(raws)).cuda()
-            torch.distributed.all_reduce(r)
-            raws = r.cpu().numpy()
+            raws = shard.allreduce_group_sums(raws)
         s2 = ens.stats()
         h2d += s2["h2d_bytes"]
         d2h += s2["d2h_bytes"]
@@ -293,9 +289,7 @@ def main():
     barrier()
     e2e_s = time.perf_counter() - t0
     if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = shard.allreduce_max(e2e_s)
     e2e = {"value": ps_total / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
     out = {

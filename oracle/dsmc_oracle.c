@@ -186,6 +186,7 @@ typedef struct {
 struct orc_ctx {
     orc_config cfg;
     int n_runs;
+    uint32_t run0;        /* global index of run 0 (Philox counter word 3) */
     double dt;
     uint64_t seed;
     double d[3];          /* cell sizes */
@@ -333,12 +334,12 @@ int orc_init_run(orc_ctx* C, int run)
         int i[3] = { c % g->ncell[0], (c / g->ncell[0]) % g->ncell[1],
                      c / (g->ncell[0] * g->ncell[1]) };
         double u[4];
-        orc_draw(C->seed, run, 0, c, P_FILL_COUNT, 0, u);
+        orc_draw(C->seed, C->run0 + run, 0, c, P_FILL_COUNT, 0, u);
         int64_t N = (int64_t)floor(lam + u[0]);
         for (int64_t k = 0; k < N; ++k) {
             double b0[4], b1[4], z[4];
-            orc_draw(C->seed, run, 0, c, P_FILL_PART, (uint32_t)(2 * k), b0);
-            orc_draw(C->seed, run, 0, c, P_FILL_PART, (uint32_t)(2 * k + 1), b1);
+            orc_draw(C->seed, C->run0 + run, 0, c, P_FILL_PART, (uint32_t)(2 * k), b0);
+            orc_draw(C->seed, C->run0 + run, 0, c, P_FILL_PART, (uint32_t)(2 * k + 1), b1);
             orc_gauss2(b0[0], b0[1], &z[0], &z[1]);
             orc_gauss2(b0[2], b0[3], &z[2], &z[3]);
             orc_particle q;
@@ -376,15 +377,15 @@ static int generation(orc_ctx* C, orc_run* R, int run, int step)
                 uint32_t e = (uint32_t)(C->elem_base[q] + (aa - b->lo[0]) +
                                         (int64_t)w * (bb - b->lo[1]));
                 double u[4];
-                orc_draw(C->seed, run, step, e, P_GEN_COUNT, 0, u);
+                orc_draw(C->seed, C->run0 + run, step, e, P_GEN_COUNT, 0, u);
                 int64_t G = (int64_t)floor(lam + u[0]);
                 if (G >= (1 << 22)) return -3;
                 for (int64_t k = 0; k < G; ++k) {
                     double b0[4], b1[4], z0, z1, xi;
-                    orc_draw(C->seed, run, step, e, P_GEN_PART, (uint32_t)(k * GEN_BLOCKS), b0);
-                    orc_draw(C->seed, run, step, e, P_GEN_PART, (uint32_t)(k * GEN_BLOCKS + 1), b1);
+                    orc_draw(C->seed, C->run0 + run, step, e, P_GEN_PART, (uint32_t)(k * GEN_BLOCKS), b0);
+                    orc_draw(C->seed, C->run0 + run, step, e, P_GEN_PART, (uint32_t)(k * GEN_BLOCKS + 1), b1);
                     orc_gauss2(b1[0], b1[1], &z0, &z1);
-                    if (orc_sample_xi(s, C->seed, run, step, e, (uint32_t)k, &xi) < 0)
+                    if (orc_sample_xi(s, C->seed, C->run0 + run, step, e, (uint32_t)k, &xi) < 0)
                         R->st.reject_limit++;
                     orc_particle p;
                     memset(&p, 0, sizeof(p));
@@ -475,7 +476,7 @@ static int motion(orc_ctx* C, orc_run* R, int run, int step, orc_particle* p)
             p->v[axis] = -p->v[axis];
         } else {
             double u[4], z0, z1;
-            orc_draw(C->seed, run, step, p->id, P_WALL, (uint32_t)bounce, u);
+            orc_draw(C->seed, C->run0 + run, step, p->id, P_WALL, (uint32_t)bounce, u);
             double sw = sqrt(KB * Tw / g->mass);
             orc_gauss2(u[1], u[2], &z0, &z1);
             p->v[axis] = dir * (sw * sqrt(-2.0 * log(u[0])));
@@ -500,7 +501,7 @@ static void interaction_cell(orc_ctx* C, orc_run* R, int run, int step, int c,
     int64_t acc = 0;
     for (int64_t k = 0; k < M; ++k) {
         double u[4];
-        orc_draw(C->seed, run, step, c, P_COLL, (uint32_t)(2 * k), u);
+        orc_draw(C->seed, C->run0 + run, step, c, P_COLL, (uint32_t)(2 * k), u);
         int64_t i = (int64_t)floor(u[0] * (double)N);
         int64_t j = (int64_t)floor(u[1] * (double)(N - 1));
         if (j >= i) j += 1;
@@ -513,7 +514,7 @@ static void interaction_cell(orc_ctx* C, orc_run* R, int run, int step, int c,
         if (sc > R->smax[c]) R->st.clamps++;
         if (u[2] < sc / R->smax[c]) {
             double u2[4];
-            orc_draw(C->seed, run, step, c, P_COLL, (uint32_t)(2 * k + 1), u2);
+            orc_draw(C->seed, C->run0 + run, step, c, P_COLL, (uint32_t)(2 * k + 1), u2);
             orc_scatter(v1, v2, u[3], u2[0]);
             ++acc;
         }
@@ -713,7 +714,9 @@ static void* orc_worker(void* arg)
     double* mom = malloc(per * sizeof(double));
     if (!mom) { J->rc = -2; return NULL; }
     for (int g = J->worker; g < J->G; g += J->n_workers) {
-        for (int r = g; r < C->n_runs; r += J->G) {
+        /* local runs r whose global index run0 + r falls in group g */
+        const int r0 = (int)(((uint32_t)g + (uint32_t)J->G - C->run0 % (uint32_t)J->G) % (uint32_t)J->G);
+        for (int r = r0; r < C->n_runs; r += J->G) {
             orc_stats keep;
             int rc = orc_init_run(C, r);
             int t = 0;
@@ -740,13 +743,22 @@ int orc_run_ensemble(const orc_config* cfg, int n_runs, double dt, int steps,
                      const int32_t* sample_steps, int n_samples, uint64_t seed,
                      int threads, double* acc, orc_stats* stats)
 {
+    return orc_run_ensemble_part(cfg, 0, n_runs, n_runs < NGROUP_MAX ? n_runs : NGROUP_MAX, dt,
+                                 steps, sample_steps, n_samples, seed, threads, acc, stats);
+}
+
+int orc_run_ensemble_part(const orc_config* cfg, uint32_t run0, int n_runs, int G, double dt,
+                          int steps, const int32_t* sample_steps, int n_samples, uint64_t seed,
+                          int threads, double* acc, orc_stats* stats)
+{
     for (int t = 0; t < n_samples; ++t)
         if (sample_steps[t] < 1 || sample_steps[t] > steps ||
             (t > 0 && sample_steps[t] <= sample_steps[t - 1]))
             return -1;
+    if (G < 1 || G > NGROUP_MAX) return -1;
     orc_ctx* C = orc_create(cfg, n_runs, dt, seed);
     if (!C) return -1;
-    int G = n_runs < NGROUP_MAX ? n_runs : NGROUP_MAX;
+    C->run0 = run0;
     memset(acc, 0, (size_t)n_samples * G * C->ncells * ORC_NMOM * sizeof(double));
     if (threads < 1) threads = 1;
     if (threads > G) threads = G;

@@ -119,6 +119,14 @@ int orc_run_ensemble(const orc_config* cfg, int n_runs, double dt, int steps,
                      const int32_t* sample_steps, int n_samples, uint64_t seed,
                      int threads, double* acc, orc_stats* stats);
 
+/* the part of an ensemble with global run indices run0 .. run0 + n_runs - 1
+ * (one rank's share of runs sharded over processes): run r draws with the
+ * global index run0 + r, and its moments go to group (run0 + r) mod G, G
+ * being the whole ensemble's group count */
+int orc_run_ensemble_part(const orc_config* cfg, uint32_t run0, int n_runs, int G, double dt,
+                          int steps, const int32_t* sample_steps, int n_samples, uint64_t seed,
+                          int threads, double* acc, orc_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

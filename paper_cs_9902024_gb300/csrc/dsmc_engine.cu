@@ -71,6 +71,7 @@ struct dsmc_ctx {
     uint32_t *run_base = nullptr, *next_id = nullptr, *cand = nullptr, *accd = nullptr;
     uint32_t* big_list = nullptr;
     uint32_t* slow_list = nullptr;
+    uint32_t *gen_tot = nullptr, *gen_done = nullptr;
     double *rem = nullptr, *mom = nullptr, *acc = nullptr, *macro = nullptr;
     void* smax = nullptr;
     int32_t* sample_slot = nullptr;
@@ -278,6 +279,13 @@ static void free_all(dsmc_ctx* ctx)
     ctx->cap_old = 0;
 }
 
+// Generation CTAs per run: one per kGenElems inflow elements
+static int gen_groups_of(const dsmc_ctx* ctx)
+{
+    const int64_t g = (ctx->hcfg.n_elem + kGenElems - 1) / kGenElems;
+    return g < 1 ? 1 : (int)g;
+}
+
 static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, int steps,
                                 int n_samples, int G)
 {
@@ -329,6 +337,8 @@ static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, in
     const int64_t max_big = cap_old / (kWarpMax + 1) + 1;
     ctx->big_list = (uint32_t*)A(4 * max_big);
     ctx->slow_list = (uint32_t*)A(4 * cap_old);
+    ctx->gen_tot = (uint32_t*)A(4 * (size_t)n_launch * gen_groups_of(ctx));
+    ctx->gen_done = (uint32_t*)A(4 * (size_t)n_launch);
     ctx->sample_slot = (int32_t*)A(4 * (size_t)(steps + 2));
     ctx->acc = (double*)A(8 * (size_t)std::max(n_samples, 1) * G * ctx->ncells * DSMC_NMOM);
     ctx->macro = (double*)A(8 * 10 * (size_t)ctx->ncells);
@@ -368,6 +378,11 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.hot.ncells = c.ncells;
     a.hot.plate_axes = 0u;
     for (int pi = 0; pi < c.n_plate; ++pi) a.hot.plate_axes |= 1u << c.bc[c.plate_idx[pi]].plate_axis;
+    a.hot.n_plate = c.n_plate <= 4 ? c.n_plate : -1;
+    for (int pi = 0; pi < 4; ++pi) {
+        a.hot.plate_ax[pi] = pi < c.n_plate ? c.bc[c.plate_idx[pi]].plate_axis : 0;
+        a.hot.plate_ix[pi] = pi < c.n_plate ? c.bc[c.plate_idx[pi]].plate_index : 0;
+    }
     a.hot.hs = c.hs;
     a.hot.ncells_magic = c.ncells_magic;
     a.hot.seed = c.seed;
@@ -403,6 +418,9 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.accd = ctx->accd;
     a.big_list = ctx->big_list;
     a.slow_list = ctx->slow_list;
+    a.gen_tot = ctx->gen_tot;
+    a.gen_done = ctx->gen_done;
+    a.gen_groups = gen_groups_of(ctx);
     a.sample_slot = ctx->sample_slot;
     a.n_slot = ctx->steps_alloc;
     a.acc = ctx->acc;
@@ -905,7 +923,10 @@ dsmc_status dsmc_debug_step(dsmc_ctx* ctx, int n_steps)
     CK(cudaSetDevice(ctx->device));
     const int n = ctx->n_launch;
     for (int s = 0; s < n_steps; ++s) {
-        CK(cudaMemcpy(ctx->prev_run_base.data(), ctx->run_base, 4 * (n + 1), cudaMemcpyDeviceToHost));
+        // ordered after the previous step's kernels on the context's stream
+        CK(cudaMemcpyAsync(ctx->prev_run_base.data(), ctx->run_base, 4 * (n + 1),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
         AnyArgs u;
         enqueue_step(ctx, build_args(ctx, u, ctx->cur, 0, n), nullptr);
         ctx->cur ^= 1;
@@ -1284,6 +1305,8 @@ static size_t noalloc_layout(dsmc_ctx* ctx, unsigned char* base, int n_runs, int
     const int64_t max_big = cap_old / (kWarpMax + 1) + 1;
     ctx->big_list = (uint32_t*)sc.take(4 * max_big);
     ctx->slow_list = (uint32_t*)sc.take(4 * cap_old);
+    ctx->gen_tot = (uint32_t*)sc.take(4 * (size_t)n_runs * gen_groups_of(ctx));
+    ctx->gen_done = (uint32_t*)sc.take(4 * (size_t)n_runs);
     ctx->sample_slot = (int32_t*)sc.take(4 * (size_t)(steps + 2));
     ctx->acc = (double*)sc.take(8 * (size_t)std::max(n_samples, 1) * ctx->G * ctx->ncells * DSMC_NMOM);
     ctx->macro = nullptr;

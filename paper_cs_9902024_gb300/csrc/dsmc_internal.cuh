@@ -14,6 +14,7 @@ constexpr int kGenBlocks = 64;            // Philox blocks per generated particl
 constexpr int kWarpMax = 128;             // cells up to this size: one warp each
 constexpr int kCellWarps = 8;             // warps per CTA of the cell kernel
 constexpr int kTileCells = 256;           // cells (= threads) per tile CTA
+constexpr int kGenElems = 2048;           // inflow elements per Generation CTA
 constexpr int kCollideCells = 128;        // cells (= threads) per CTA of the collision kernel
 constexpr int kCollideStage = 2816;       // particles whose velocities one collision CTA stages
 constexpr int kLaneMax = 512;             // largest cell of the tile path
@@ -85,6 +86,10 @@ struct Hot {
     int32_t n[3];            // cells per axis
     int32_t ncells;          // cells per run
     uint32_t plate_axes;     // bit a set: a plate is normal to axis a
+    int32_t n_plate;         // plates listed below (-1: more than kHotPlates;
+                             // then any cell change along plate_axes counts)
+    int32_t plate_ax[4], plate_ix[4];   // plate axis and face index (plane
+                                        // between cells plate_ix - 1 and plate_ix)
     int32_t hs;
     uint64_t ncells_magic;
     uint64_t seed;
@@ -121,6 +126,9 @@ struct StepArgs {
     uint32_t* accd;        // optional per cell
     uint32_t* big_list;
     uint32_t* slow_list;   // slots whose flight meets a surface this step
+    uint32_t* gen_tot;     // per run x gen_groups: entrants of each element group
+    uint32_t* gen_done;    // per run: Generation CTAs finished this step
+    int32_t gen_groups;    // Generation CTAs per run (ceil(n_elem / kGenElems))
     const int32_t* sample_slot;   // per step: sample index or -1
     int32_t n_slot;               // entries of sample_slot
     double* acc;           // [samples][G][ncells][7]

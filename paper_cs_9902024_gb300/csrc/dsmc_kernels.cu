@@ -103,16 +103,29 @@ __device__ __forceinline__ float in_cells(const Cfg& c, int a, float f) { return
 __device__ __forceinline__ double in_cells(const Hot<double>& c, int a, double f) { return f / c.d[a]; }
 __device__ __forceinline__ float in_cells(const Hot<float>& c, int a, float f) { return f * c.inv_d[a]; }
 
-// a plate normal to axis a exists (a flight that changes cell along it may
-// meet the plate)
-__device__ __forceinline__ bool plate_on_axis(const Cfg& c, int a)
+// a straight flight from cell i to cell j along axis a passes the plane of
+// a plate normal to a (face index p): min(i, j) < p <= max(i, j).  Every
+// flight that meets a plate passes its plane, so a flight for which this is
+// false for every plate meets none (the plate's extent and activity are not
+// looked at: the test may only send extra flights to the exact path).
+__device__ __forceinline__ bool crosses_plate(const Cfg& c, int a, int i, int j)
 {
-    for (int pi = 0; pi < c.n_plate; ++pi)
-        if (c.bc[c.plate_idx[pi]].plate_axis == a) return true;
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    for (int pi = 0; pi < c.n_plate; ++pi) {
+        const BcDev& b = c.bc[c.plate_idx[pi]];
+        if (b.plate_axis == a && lo < b.plate_index && b.plate_index <= hi) return true;
+    }
     return false;
 }
 template <typename T>
-__device__ __forceinline__ bool plate_on_axis(const Hot<T>& c, int a) { return (c.plate_axes >> a) & 1u; }
+__device__ __forceinline__ bool crosses_plate(const Hot<T>& c, int a, int i, int j)
+{
+    if (c.n_plate < 0) return ((c.plate_axes >> a) & 1u) != 0u;
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    for (int pi = 0; pi < c.n_plate; ++pi)
+        if (c.plate_ax[pi] == a && lo < c.plate_ix[pi] && c.plate_ix[pi] <= hi) return true;
+    return false;
+}
 
 // move whole cells so that 0 <= f <= d along axis a (clamped to the grid)
 template <typename T>
@@ -181,9 +194,9 @@ struct LocalCounters {
 };
 
 // Straight flight for tau that ends strictly inside the box (by a margin far
-// above rounding) and changes no cell along a plate's axis: no surface event
-// can occur, and the result equals move_particle's.  Returns false (state
-// untouched) otherwise.
+// above rounding) and passes no plate's plane: no surface event can occur,
+// and the result equals move_particle's.  Returns false (state untouched)
+// otherwise.
 template <typename T, int DIM, class C>
 __device__ __forceinline__ bool try_free_flight(const C& c, int* ci, T* f, const T* v, T tau)
 {
@@ -203,7 +216,7 @@ __device__ __forceinline__ bool try_free_flight(const C& c, int* ci, T* f, const
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
-        if (ni[a] != ci[a] && plate_on_axis(c, a)) return false;
+        if (ni[a] != ci[a] && crosses_plate(c, a, ci[a], ni[a])) return false;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { ci[a] = ni[a]; f[a] = nf[a]; }
     return true;
@@ -523,6 +536,9 @@ __global__ void k_init_cells(StepArgs<T> a)
         a.smax[i] = (T)c.smax0;
         a.count[i] = 0u;
     }
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n_runs;
+         r += (int64_t)gridDim.x * blockDim.x)
+        a.gen_done[r] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr->step = 1u;
         a.ctr->n_big = 0u;
@@ -599,41 +615,75 @@ __device__ __forceinline__ int inflow_segment_of(const Cfg& c, int64_t e)
     return q;
 }
 
+// Entrants of inflow element e this step: floor(lambda + R) if its segment
+// is active and owns the face cell (the last listed active segment wins),
+// else 0.
+__device__ __forceinline__ uint32_t element_entrants(const Cfg& c, uint32_t run, uint32_t step,
+                                                     int64_t e)
+{
+    const int q = inflow_segment_of(c, e);
+    const BcDev& b = c.bc[q];
+    const int64_t loc = e - b.elem_base;
+    const int aa = b.lo[0] + (int)(loc % b.elem_w), bb = b.lo[1] + (int)(loc / b.elem_w);
+    if (!(bc_active(b, (int)step) && bc_lookup(c, b.face, aa, bb, (int)step) == q)) return 0u;
+    const uint4 r = draw_bits(c.seed, run, step, (uint32_t)e, kGenCount, 0u);
+    return (uint32_t)floor(b.lam + u01<double>(r.x));
+}
+
+// Generation, counting pass (runs with more than kGenElems inflow
+// elements): entrants of every group of kGenElems consecutive elements, one
+// CTA per (run, group), so that the creating pass can number each group's
+// entrants without waiting for the groups before it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    __shared__ uint32_t s_warp[32];
+    const uint32_t G = (uint32_t)a.gen_groups;
+    const uint32_t rl = blockIdx.x / G, grp = blockIdx.x - rl * G;
+    const uint32_t run = a.run0 + rl;
+    const uint32_t step = a.ctr->step;
+    const int64_t e0 = (int64_t)grp * kGenElems;
+    const int64_t e1 = e0 + kGenElems < c.n_elem ? e0 + kGenElems : c.n_elem;
+    uint32_t sum = 0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) sum += element_entrants(c, run, step, e);
+    uint32_t total;
+    block_exclusive_scan(sum, s_warp, total);
+    if (threadIdx.x == 0) a.gen_tot[(int64_t)rl * G + grp] = total;
+}
+
 // ---------------------------------------------------------------------------
-// Generation: one CTA per run.  Elements (inflow face cells) are taken in
-// segment-list order; each element's count is floor(lambda + R); entrants
-// are numbered (ids, new-region slots) in (element, k) order, created from
-// their draws and moved for R_f dt.
+// Generation: one CTA per (run, group of kGenElems inflow elements).
+// Elements are taken in segment-list order; each element's count is
+// floor(lambda + R); a run's entrants are numbered (ids, new-region slots)
+// in (element, k) order -- a group starts after the entrants of the groups
+// before it -- created from their draws and moved for R_f dt.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
 {
     const Cfg& c = *a.cfg;
     __shared__ uint32_t s_off[257];
     __shared__ uint32_t s_warp[32];
-    const uint32_t rl = blockIdx.x;
+    const uint32_t GG = (uint32_t)a.gen_groups;
+    const uint32_t rl = blockIdx.x / GG, grp = blockIdx.x - rl * GG;
     const uint32_t run = a.run0 + rl;
     const uint32_t step = a.ctr->step;
     const uint32_t n_old = min(a.run_base[rl + 1], (uint32_t)a.cap_old) -
                            min(a.run_base[rl], (uint32_t)a.cap_old);
     const uint32_t id0 = a.next_id[rl];
     const int64_t gen_base = a.cap_old + (int64_t)rl * a.gcap;
-    uint32_t running = 0;
+    const int64_t e_begin = (int64_t)grp * kGenElems;
+    const int64_t e_end = GG == 1u ? c.n_elem
+                                   : (e_begin + kGenElems < c.n_elem ? e_begin + kGenElems : c.n_elem);
+    uint32_t prefix = 0;
+    for (uint32_t g = 0; g < grp; ++g) prefix += a.gen_tot[(int64_t)rl * GG + g];
+    uint32_t running = prefix;
     LocalCounters lc;
     uint32_t rejects = 0;
     bool overflow = false;
-    for (int64_t chunk = 0; chunk < c.n_elem; chunk += blockDim.x) {
+    for (int64_t chunk = e_begin; chunk < e_end; chunk += blockDim.x) {
         const int64_t e = chunk + threadIdx.x;
-        uint32_t G = 0;
-        if (e < c.n_elem) {
-            const int q = inflow_segment_of(c, e);
-            const BcDev& b = c.bc[q];
-            const int64_t loc = e - b.elem_base;
-            const int aa = b.lo[0] + (int)(loc % b.elem_w), bb = b.lo[1] + (int)(loc / b.elem_w);
-            if (bc_active(b, (int)step) && bc_lookup(c, b.face, aa, bb, (int)step) == q) {
-                const uint4 r = draw_bits(c.seed, run, step, (uint32_t)e, kGenCount, 0u);
-                G = (uint32_t)floor(b.lam + u01<double>(r.x));
-            }
-        }
+        const uint32_t G = e < e_end ? element_entrants(c, run, step, e) : 0u;
         uint32_t total;
         const uint32_t off = block_exclusive_scan(G, s_warp, total);
         s_off[threadIdx.x] = off;
@@ -714,10 +764,23 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
     if (rejects) atomicAdd(&a.ctr->reject_limit, (unsigned long long)rejects);
     if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_GEN);
     if (threadIdx.x == 0) {
-        const uint32_t made = running < (uint32_t)a.gcap ? running : (uint32_t)a.gcap;
-        a.next_id[rl] = id0 + running;
+        const uint32_t cap = (uint32_t)a.gcap;
+        const uint32_t made = (running < cap ? running : cap) - (prefix < cap ? prefix : cap);
         atomicAdd(&a.ctr->generated, (unsigned long long)made);
-        atomicAdd(&a.ctr->particle_steps, (unsigned long long)(n_old + made));
+        atomicAdd(&a.ctr->particle_steps, (unsigned long long)((grp == 0 ? n_old : 0u) + made));
+        if (GG == 1u) {
+            a.next_id[rl] = id0 + running;
+        } else {
+            // the run's last CTA to finish advances its id counter (every
+            // CTA of the run has read id0 by then)
+            __threadfence();
+            if (atomicAdd(&a.gen_done[rl], 1u) == GG - 1u) {
+                uint32_t all = 0;
+                for (uint32_t g = 0; g < GG; ++g) all += a.gen_tot[(int64_t)rl * GG + g];
+                a.next_id[rl] = id0 + all;
+                a.gen_done[rl] = 0u;
+            }
+        }
     }
 }
 
@@ -783,7 +846,12 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
         const uint32_t s = base + lane;
         bool slow = false;
         uint32_t key = kDead;   // no rank needed (past the end, or slow)
-        if (s < n_total) {
+        if (s < n_total && cip[s] >= (uint32_t)a.total_cells) {
+            // a slot no kernel wrote (possible only after an error already in
+            // the error word): dropped, so no counter outside the table moves
+            atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+            gc[s] = kDead;
+        } else if (s < n_total) {
             const uint32_t kold = cip[s];
             T x[3], v[3];
             x[0] = xp0[s]; x[1] = xp1[s]; v[0] = vp0[s]; v[1] = vp1[s];
@@ -1121,31 +1189,53 @@ __device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T*
     }
 }
 
-// Interaction of one cell whose velocities sit in s_v[3][*] in id order;
-// all lanes of the warp call it: the lanes draw 32 candidates at a time,
-// lane 0 applies them in order.
+// Interaction of one large cell, velocities in id order at sv0..sv2 (shared
+// or global memory); all lanes of the warp call it.  The lanes draw 32
+// candidates at a time; a candidate is applied as soon as no earlier
+// candidate of the batch that shares one of its particles is still pending,
+// so candidates with disjoint pairs are applied side by side, and every
+// particle still sees its collisions in candidate order: the result equals
+// applying the candidates one after another.  On return every lane holds
+// the warp's totals.
 template <typename T, class C>
 __device__ void collide_cell_warp(const C& c, T* sv0, T* sv1, T* sv2, uint32_t N, int64_t M,
                                   T smax, uint32_t cell, uint32_t run, uint32_t step,
                                   T& seen, uint32_t& nacc, uint32_t& nclamp)
 {
     const uint32_t lane = lane_id();
+    T my_seen = (T)0;
+    uint32_t my_acc = 0, my_clamp = 0;
     for (int64_t kb = 0; kb < M; kb += 32) {
         const int64_t k = kb + lane;
-        uint32_t ci = 0, cj = 0;
+        uint32_t ci = 0xFFFFFFFFu, cj = 0xFFFFFFFEu;
         T u2 = (T)1, u3 = (T)0, ue = (T)0;
         if (k < M) candidate_draws<T>(c, run, step, cell, k, N, ci, cj, u2, u3, ue);
-        const int cnt = (M - kb) < 32 ? (int)(M - kb) : 32;
-        for (int q = 0; q < cnt; ++q) {
-            const uint32_t i = __shfl_sync(0xFFFFFFFFu, ci, q);
-            const uint32_t j = __shfl_sync(0xFFFFFFFFu, cj, q);
-            const T U2 = __shfl_sync(0xFFFFFFFFu, u2, q);
-            const T U3 = __shfl_sync(0xFFFFFFFFu, u3, q);
-            const T UE = __shfl_sync(0xFFFFFFFFu, ue, q);
-            if (lane == 0) collide_candidate<T>(c, sv0, sv1, sv2, i, j, U2, U3, UE, smax, seen, nacc, nclamp);
+        uint32_t pending = __ballot_sync(0xFFFFFFFFu, k < M);
+        while (pending) {
+            bool blocked = false;
+#pragma unroll 4
+            for (uint32_t q = 0; q < 31u; ++q) {
+                const uint32_t qi = __shfl_sync(0xFFFFFFFFu, ci, q);
+                const uint32_t qj = __shfl_sync(0xFFFFFFFFu, cj, q);
+                if (q < lane && ((pending >> q) & 1u) &&
+                    (qi == ci || qi == cj || qj == ci || qj == cj))
+                    blocked = true;
+            }
+            const bool go = ((pending >> lane) & 1u) && !blocked;
+            if (go) collide_candidate<T>(c, sv0, sv1, sv2, ci, cj, u2, u3, ue, smax, my_seen, my_acc,
+                                         my_clamp);
             __syncwarp();
+            pending &= ~__ballot_sync(0xFFFFFFFFu, go);
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T other = __shfl_xor_sync(0xFFFFFFFFu, my_seen, o);
+        my_seen = other > my_seen ? other : my_seen;
+    }
+    seen = my_seen;
+    nacc = __reduce_add_sync(0xFFFFFFFFu, my_acc);
+    nclamp = __reduce_add_sync(0xFFFFFFFFu, my_clamp);
 }
 
 // Sampling of one cell: N, sum v_a, sum v_a^2 in FP64, summed in id order
@@ -1565,7 +1655,7 @@ __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
 // Cells larger than a warp's buffer: one CTA each, (id, slot) keys sorted in
 // shared memory (bitonic), velocities staged in shared memory.
 template <typename T>
-__host__ __device__ constexpr int big_max_of() { return sizeof(T) == 4 ? 8192 : 4096; }
+__host__ __device__ constexpr int big_max_of() { return 8192; }
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
@@ -1573,6 +1663,9 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
     const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kMax = big_max_of<T>();
+    // FP32: the cell's velocities are staged in shared memory; FP64: they
+    // stay in the next pool (the keys alone fill 64 KB)
+    constexpr bool kStage = sizeof(T) == 4;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
     T* sv0 = reinterpret_cast<T*>(smem_raw + sizeof(unsigned long long) * kMax);
     T* sv1 = sv0 + kMax;
@@ -1580,7 +1673,6 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
-    const uint32_t lane = lane_id();
     const int w = threadIdx.x >> 5;
     for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
         const uint32_t gcell = a.big_list[bi];
@@ -1588,8 +1680,29 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
         const uint32_t N = a.start[gcell + 1] - beg;
         const uint32_t rl = gcell / (uint32_t)c.ncells;
         const uint32_t cell = gcell - rl * (uint32_t)c.ncells;
+        if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
+            if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+            continue;
+        }
         if (N > (uint32_t)kMax) {
+            // over the per-cell limit: reported, and the particles are still
+            // carried into the next pool (in LCR order, without collisions),
+            // so that the next step reads no unwritten slot
             if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_BIGCELL);
+            for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
+                const uint2 e = a.lcr[beg + r];
+                const uint32_t s = checked_slot(a, e.x);
+                const uint32_t o = beg + r;
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+                a.ci_o[o] = gcell;
+                a.ido[o] = e.y;
+                a.vo[0][o] = a.vi[0][s];
+                a.vo[1][o] = a.vi[1][s];
+                a.vo[2][o] = a.vi[2][s];
+                if (a.lcr_dbg) a.lcr_dbg[o] = s;
+            }
+            __syncthreads();
             continue;
         }
         uint32_t P = 1;
@@ -1623,12 +1736,21 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
             a.ci_o[o] = gcell;
             a.ido[o] = (uint32_t)(kk >> 32);
-            sv0[r] = a.vi[0][s];
-            sv1[r] = a.vi[1][s];
-            sv2[r] = a.vi[2][s];
+            if (kStage) {
+                sv0[r] = a.vi[0][s];
+                sv1[r] = a.vi[1][s];
+                sv2[r] = a.vi[2][s];
+            } else {
+                a.vo[0][o] = a.vi[0][s];
+                a.vo[1][o] = a.vi[1][s];
+                a.vo[2][o] = a.vi[2][s];
+            }
             if (a.lcr_dbg) a.lcr_dbg[o] = s;
         }
         __syncthreads();
+        T* v0 = kStage ? sv0 : a.vo[0] + beg;
+        T* v1 = kStage ? sv1 : a.vo[1] + beg;
+        T* v2 = kStage ? sv2 : a.vo[2] + beg;
         if (w == 0) {
             double rem = a.rem[gcell];
             const T smax = a.smax[gcell];
@@ -1636,9 +1758,9 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
             T seen = (T)0;
             uint32_t nacc = 0, nclamp = 0;
             if (M > 0)
-                collide_cell_warp<T>(c, sv0, sv1, sv2, N, M, smax, cell, a.run0 + rl, step, seen,
-                                     nacc, nclamp);
-            if (lane == 0) {
+                collide_cell_warp<T>(c, v0, v1, v2, N, M, smax, cell, a.run0 + rl, step, seen, nacc,
+                                     nclamp);
+            if (lane_id() == 0) {
                 a.rem[gcell] = rem;
                 if (seen > smax) a.smax[gcell] = seen;
                 if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
@@ -1650,14 +1772,16 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
         __syncthreads();
         if (slot_t >= 0 && threadIdx.x == 0) {
             double m[DSMC_NMOM];
-            cell_moments<T>(sv0, sv1, sv2, N, m);
+            cell_moments<T>(v0, v1, v2, N, m);
             for (int q = 0; q < DSMC_NMOM; ++q) a.mom[(uint64_t)gcell * DSMC_NMOM + q] = m[q];
         }
-        for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
-            const uint32_t o = beg + r;
-            a.vo[0][o] = sv0[r];
-            a.vo[1][o] = sv1[r];
-            a.vo[2][o] = sv2[r];
+        if (kStage) {
+            for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
+                const uint32_t o = beg + r;
+                a.vo[0][o] = sv0[r];
+                a.vo[1][o] = sv1[r];
+                a.vo[2][o] = sv2[r];
+            }
         }
         __syncthreads();
     }
@@ -1815,7 +1939,9 @@ void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStre
 {
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
-        DISPATCH_DIM(ls.dim, (k_generate<T, D><<<a.n_runs, 256, 0, s>>>(a)));
+        const unsigned grid = (unsigned)a.n_runs * (unsigned)a.gen_groups;
+        if (a.gen_groups > 1) k_gen_count<T><<<grid, 256, 0, s>>>(a);
+        DISPATCH_DIM(ls.dim, (k_generate<T, D><<<grid, 256, 0, s>>>(a)));
     });
 }
 
@@ -1875,8 +2001,8 @@ int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() :
 
 static size_t big_smem(int prec)
 {
-    return prec == DSMC_FP64 ? (8 + 3 * 8) * (size_t)big_max_of<double>()
-                             : (8 + 3 * 4) * (size_t)big_max_of<float>();
+    // FP32: keys and staged velocities; FP64: keys only
+    return prec == DSMC_FP64 ? 8 * (size_t)big_max_of<double>() : (8 + 3 * 4) * (size_t)big_max_of<float>();
 }
 
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)

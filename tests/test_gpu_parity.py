@@ -82,6 +82,17 @@ def test_fp64_plate3d_filled(D):
     assert ens.stats()["wall_hits"] > 0
 
 
+def test_fp64_plate3d_grouped_generation(D):
+    """Five inflow faces with 5184 elements: Generation runs as three CTAs
+    per run after a counting pass, and each run's entrants must still be
+    numbered in (element, k) order."""
+    w = W.plate3d(nx=48, ny=24, nz=24, plate=8, plate_x=16, ppc=2, runs=2, steps=6,
+                  n_samples=2)
+    ens, orc, res = _lockstep(D, w, runs=2, steps=6)
+    _assert_exact(res)
+    assert ens.stats()["generated"] > 10000
+
+
 def test_fp64_jet_big_cells_and_pulse(D):
     """VHS jet through an orifice that closes after 5 steps, with a particle
     weight low enough that cells near the orifice hold hundreds of particles
