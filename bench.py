@@ -250,9 +250,9 @@ def main():
     st = ens.stats()
     ps_per_step = st["particle_steps"]
     # fill: 6 launches; every time step: generate, move, move_slow, scan1,
-    # scan2, scatter, cell, cell_big, collide, step_end, and reduce at the
-    # sample steps only
-    launches_per_step = 6 + steps * 10 + n_samples
+    # scan2, scatter, cell, cell_big, collide_big, collide, step_end, and
+    # reduce at the sample steps only
+    launches_per_step = 6 + steps * 11 + n_samples
     # -- device-timed region: inputs resident, results stay on the device --
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)

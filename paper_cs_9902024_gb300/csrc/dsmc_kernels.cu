@@ -16,8 +16,10 @@
 //   k_cell       one CTA per 256 cells: each cell's particles put in
 //                particle-id order and gathered into the next pool
 //                (Indexing)
-//   k_cell_big   one CTA per cell above 128 particles: ordering,
-//                collisions and moments of that cell
+//   k_cell_big   one CTA per cell above 128 particles: the cell ordered by
+//                id (bitonic sort) and gathered into the next pool
+//   k_collide_big one warp per such cell: NTC collisions (disjoint pairs
+//                side by side) and moments
 //   k_collide    one thread per cell, a tile's velocities staged in shared
 //                memory: NTC collisions, and the cell moments at sample
 //                steps (Interaction + Sampling)
@@ -1652,42 +1654,33 @@ __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// Cells larger than a warp's buffer: one CTA each, (id, slot) keys sorted in
-// shared memory (bitonic), velocities staged in shared memory.
+// Cells above kWarpMax particles, part 1: one CTA of kBigThreads per cell,
+// (id, slot) keys sorted in shared memory (bitonic), the cell's particles
+// gathered into the next pool in id order.
+constexpr int kBigThreads = 1024;
+
 template <typename T>
 __host__ __device__ constexpr int big_max_of() { return 8192; }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
+__global__ void __launch_bounds__(kBigThreads) k_cell_big(StepArgs<T> a)
 {
-    const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kMax = big_max_of<T>();
-    // FP32: the cell's velocities are staged in shared memory; FP64: they
-    // stay in the next pool (the keys alone fill 64 KB)
-    constexpr bool kStage = sizeof(T) == 4;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
-    T* sv0 = reinterpret_cast<T*>(smem_raw + sizeof(unsigned long long) * kMax);
-    T* sv1 = sv0 + kMax;
-    T* sv2 = sv1 + kMax;
-    const uint32_t step = a.ctr->step;
-    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
-    const int w = threadIdx.x >> 5;
     for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
         const uint32_t gcell = a.big_list[bi];
         const uint32_t beg = a.start[gcell];
         const uint32_t N = a.start[gcell + 1] - beg;
-        const uint32_t rl = gcell / (uint32_t)c.ncells;
-        const uint32_t cell = gcell - rl * (uint32_t)c.ncells;
         if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
             if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
             continue;
         }
         if (N > (uint32_t)kMax) {
             // over the per-cell limit: reported, and the particles are still
-            // carried into the next pool (in LCR order, without collisions),
-            // so that the next step reads no unwritten slot
+            // carried into the next pool (in LCR order), so that the next
+            // step reads no unwritten slot
             if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_BIGCELL);
             for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
                 const uint2 e = a.lcr[beg + r];
@@ -1736,54 +1729,61 @@ __global__ void __launch_bounds__(256) k_cell_big(StepArgs<T> a)
             for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
             a.ci_o[o] = gcell;
             a.ido[o] = (uint32_t)(kk >> 32);
-            if (kStage) {
-                sv0[r] = a.vi[0][s];
-                sv1[r] = a.vi[1][s];
-                sv2[r] = a.vi[2][s];
-            } else {
-                a.vo[0][o] = a.vi[0][s];
-                a.vo[1][o] = a.vi[1][s];
-                a.vo[2][o] = a.vi[2][s];
-            }
+            a.vo[0][o] = a.vi[0][s];
+            a.vo[1][o] = a.vi[1][s];
+            a.vo[2][o] = a.vi[2][s];
             if (a.lcr_dbg) a.lcr_dbg[o] = s;
         }
         __syncthreads();
-        T* v0 = kStage ? sv0 : a.vo[0] + beg;
-        T* v1 = kStage ? sv1 : a.vo[1] + beg;
-        T* v2 = kStage ? sv2 : a.vo[2] + beg;
-        if (w == 0) {
-            double rem = a.rem[gcell];
-            const T smax = a.smax[gcell];
-            const int64_t M = ntc_count<T>(c, N, smax, rem);
-            T seen = (T)0;
-            uint32_t nacc = 0, nclamp = 0;
-            if (M > 0)
-                collide_cell_warp<T>(c, v0, v1, v2, N, M, smax, cell, a.run0 + rl, step, seen, nacc,
-                                     nclamp);
-            if (lane_id() == 0) {
-                a.rem[gcell] = rem;
-                if (seen > smax) a.smax[gcell] = seen;
-                if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
-                if (M) atomicAdd(&a.ctr->candidates, (unsigned long long)M);
-                if (nacc) atomicAdd(&a.ctr->collisions, (unsigned long long)nacc);
-                if (nclamp) atomicAdd(&a.ctr->clamps, (unsigned long long)nclamp);
-            }
+    }
+}
+
+// Cells above kWarpMax particles, part 2: one warp per cell, on the cell's
+// velocities in the next pool (id order): NTC count, candidates applied by
+// collide_cell_warp (disjoint pairs side by side, in-order result), and the
+// cell's moments at sample steps.  Many large cells proceed at once.
+template <typename T>
+__global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
+{
+    const Cfg& c = *a.cfg;
+    constexpr int kMax = big_max_of<T>();
+    const uint32_t step = a.ctr->step;
+    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
+    const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
+    const uint32_t lane = lane_id();
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < nb; bi += warps) {
+        const uint32_t gcell = a.big_list[bi];
+        const uint32_t beg = a.start[gcell];
+        const uint32_t N = a.start[gcell + 1] - beg;
+        if ((uint64_t)beg + N > (uint64_t)a.cap_old || N > (uint32_t)kMax) continue;   // flagged
+        const uint32_t rl = gcell / (uint32_t)c.ncells;
+        const uint32_t cell = gcell - rl * (uint32_t)c.ncells;
+        double rem = a.rem[gcell];
+        const T smax = a.smax[gcell];
+        const int64_t M = ntc_count<T>(c, N, smax, rem);
+        T* v0 = a.vo[0] + beg;
+        T* v1 = a.vo[1] + beg;
+        T* v2 = a.vo[2] + beg;
+        T seen = (T)0;
+        uint32_t nacc = 0, nclamp = 0;
+        if (M > 0)
+            collide_cell_warp<T>(c, v0, v1, v2, N, M, smax, cell, a.run0 + rl, step, seen, nacc,
+                                 nclamp);
+        if (lane == 0) {
+            a.rem[gcell] = rem;
+            if (seen > smax) a.smax[gcell] = seen;
+            if (a.cand) { a.cand[gcell] = (uint32_t)M; a.accd[gcell] = nacc; }
+            if (M) atomicAdd(&a.ctr->candidates, (unsigned long long)M);
+            if (nacc) atomicAdd(&a.ctr->collisions, (unsigned long long)nacc);
+            if (nclamp) atomicAdd(&a.ctr->clamps, (unsigned long long)nclamp);
         }
-        __syncthreads();
-        if (slot_t >= 0 && threadIdx.x == 0) {
+        __syncwarp();
+        if (slot_t >= 0 && lane == 0) {
             double m[DSMC_NMOM];
             cell_moments<T>(v0, v1, v2, N, m);
             for (int q = 0; q < DSMC_NMOM; ++q) a.mom[(uint64_t)gcell * DSMC_NMOM + q] = m[q];
         }
-        if (kStage) {
-            for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
-                const uint32_t o = beg + r;
-                a.vo[0][o] = sv0[r];
-                a.vo[1][o] = sv1[r];
-                a.vo[2][o] = sv2[r];
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -1999,16 +1999,15 @@ void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStrea
 
 int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
 
-static size_t big_smem(int prec)
-{
-    // FP32: keys and staged velocities; FP64: keys only
-    return prec == DSMC_FP64 ? 8 * (size_t)big_max_of<double>() : (8 + 3 * 4) * (size_t)big_max_of<float>();
-}
+static size_t big_smem(int) { return 8 * (size_t)big_max_of<float>(); }
 
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim,
-        (k_cell_big<T, D><<<ls.big_blocks, 256, big_smem(prec), s>>>(A<T>(args)))));
+    DISPATCH_PREC(prec, {
+        DISPATCH_DIM(ls.dim, (k_cell_big<T, D><<<ls.big_blocks, kBigThreads, big_smem(prec), s>>>(
+                                 A<T>(args))));
+        k_collide_big<T><<<ls.sms * 8, 256, 0, s>>>(A<T>(args));
+    });
 }
 
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
@@ -2064,7 +2063,7 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
                                                       collide_smem(prec));
     });
     ls->collide_blocks = sms * (bl > 0 ? bl : 3);
-    ls->big_blocks = sms;
+    ls->big_blocks = sms * 2;
 }
 
 cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
