@@ -239,7 +239,8 @@ def main():
     steps = w["steps"]
     n_samples = len(w["sample_steps"])
     stream = torch.cuda.Stream(device=device)
-    ens = Ensemble(w, device=device, stream=stream, run_offset=shard.run_offset(rank, runs))
+    ens = Ensemble(w, device=device, stream=stream, run_offset=shard.run_offset(rank, runs),
+                   autotune=True)
 
     def barrier():
         if ws > 1:
@@ -305,6 +306,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
+        "launch_shape": dict(st["shape"], autotuned=bool(st["tuned"])),
         "particle_steps_per_step": ps_per_step,
     }
     if rank == 0 and ws == 1 and not args.no_extras:
@@ -334,7 +336,7 @@ def main():
         be.close()
         # -- per-kernel device times (profile mode: CUDA events around every
         #    launch on the library's stream) and the roofline ------------
-        pr = Ensemble(w, profile=True, device=device, stream=stream)
+        pr = Ensemble(w, profile=True, device=device, stream=stream, autotune=True)
         pr.run()
         prs = pr.stats()
         pr.close()

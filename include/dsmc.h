@@ -148,6 +148,15 @@ typedef struct {
     int64_t run_offset;       /* global index of run 0 of this context: the
                                  runs draw as runs run_offset.. (sharding an
                                  ensemble over processes or GPUs) */
+    int32_t autotune;         /* batched mode: 1 = on the first run of a
+                                 problem size, advance a trial ensemble to
+                                 mid-run and time candidate launch shapes
+                                 (sort/gather tile budget, grid sizes of the
+                                 Motion, scatter and collision kernels) over
+                                 short windows, keeping the fastest per kernel
+                                 time per particle; the real run then starts
+                                 from t = 0.  Results do not depend on the
+                                 shapes.  0 = fixed shapes (default) */
 } dsmc_options;
 
 typedef struct {
@@ -169,6 +178,10 @@ typedef struct {
     uint64_t h2d_bytes;       /* host -> device bytes of the last run */
     uint64_t d2h_bytes;       /* device -> host bytes since the last run began
                                  (counters at its end plus dsmc_get_samples) */
+    int32_t shape[4];         /* launch shape in use: Motion CTAs, scatter
+                                 CTAs, sort/gather tile budget (particles),
+                                 collision CTAs */
+    int32_t tuned;            /* 1 if the shape came from options.autotune */
 } dsmc_stats;
 
 /* device error bits */

@@ -84,6 +84,7 @@ struct dsmc_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t graph_key = ~0ull;
+    uint64_t tuned_key = 0;          // (runs << 1) | 1 once options.autotune ran
     // last run
     bool have_run = false;
     int last_runs = 0, last_steps = 0, last_samples = 0;
@@ -460,8 +461,6 @@ static cudaEvent_t event_at(dsmc_ctx* ctx, size_t i)
     return ctx->events[i];
 }
 
-// One step of every run in the launch described by `args`.  With `ev`
-// non-null an event is recorded after each kernel (profile mode).
 // One time step.  `ev` (profile mode) records an event after each kernel
 // group.  `fork` (graph capture only) runs Generation on the side stream
 // beside Motion: they touch disjoint slots and only add to the cell counts.
@@ -543,6 +542,11 @@ static void fill_stats(dsmc_ctx* ctx, const Counters& h)
     s.pool_steps = h.pool_steps;
     s.error_word = h.error;
     s.capacity = ctx->cap_old;
+    s.shape[0] = ctx->ls.move_blocks;
+    s.shape[1] = ctx->ls.scatter_blocks;
+    s.shape[2] = ctx->ls.tile_budget;
+    s.shape[3] = ctx->ls.collide_blocks;
+    s.tuned = ctx->tuned_key != 0 ? 1 : 0;
 }
 
 static dsmc_status check_error_word(dsmc_ctx* ctx, uint32_t e)
@@ -751,6 +755,99 @@ const char* dsmc_last_error(const dsmc_ctx* ctx)
     return ctx->err.c_str();
 }
 
+// ---------------------------------------------------------------------------
+// Launch-shape search (options.autotune).  A trial ensemble of the same size
+// is advanced with the current shapes to mid-run (the pool near its typical
+// size), then each tunable is set to each candidate in turn for a window of
+// kTuneWindow steps timed with events around every kernel group; the cost
+// of a candidate is its kernel group's time per particle-step of the window
+// (the pool still grows slowly between windows).  Tunables are searched
+// one after another, each keeping its best value.  The caller re-prepares
+// the buffers afterwards: the trial leaves the pool, counters and sample
+// sums dirty.
+static const int kTuneWindow = 6;
+
+static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
+{
+    const int r0 = (int)ctx->opt.run_offset;
+    AnyArgs u;
+    enqueue_init(ctx, build_args(ctx, u, 0, r0, n_runs));
+    ctx->cur = 0;
+    // 10 windows follow the warm-up; the whole trial stays within `steps`
+    const int warm = std::max(1, std::min(std::min(steps / 2, 200), steps - 10 * kTuneWindow));
+    for (int s = 0; s < warm; ++s) {
+        AnyArgs v;
+        enqueue_step(ctx, build_args(ctx, v, ctx->cur, r0, n_runs), nullptr);
+        ctx->cur ^= 1;
+    }
+    // kernel-group cost of the current shapes over one window
+    auto window = [&](int group, double* cost) -> dsmc_status {
+        Counters h0, h1;
+        dsmc_status st = read_counters(ctx, &h0);
+        if (st) return st;
+        cudaEvent_t e0 = event_at(ctx, 0);
+        if (!e0) return fail(ctx, DSMC_E_CUDA, "cudaEventCreate failed");
+        CK(cudaEventRecord(e0, ctx->stream));
+        size_t evn = 1;
+        for (int s = 0; s < kTuneWindow; ++s) {
+            AnyArgs v;
+            enqueue_step(ctx, build_args(ctx, v, ctx->cur, r0, n_runs), &evn);
+            ctx->cur ^= 1;
+        }
+        st = read_counters(ctx, &h1);
+        if (st) return st;
+        double ms = 0.0;
+        for (int s = 0; s < kTuneWindow; ++s) {
+            float m = 0.f;
+            const size_t i = 1 + (size_t)s * kStepKernels + (size_t)group;
+            CK(cudaEventElapsedTime(&m, ctx->events[i - 1], ctx->events[i]));
+            ms += m;
+        }
+        const double units = (double)(h1.pool_steps - h0.pool_steps);
+        *cost = ms / (units > 0.0 ? units : 1.0);
+        return DSMC_OK;
+    };
+    LaunchShape& ls = ctx->ls;
+    const int sms = ctx->sms;
+    dsmc_status st = DSMC_OK;
+    // sort/gather tile budget (sets the tile kernel's grid from occupancy;
+    // the other grids go back to their defaults and are searched next)
+    {
+        const int cand[3] = {4608, 6144, 7680};
+        int best = ls.tile_budget;
+        double best_cost = 1e300;
+        for (int k = 0; k < 3; ++k) {
+            ls.tile_budget = cand[k];
+            compute_launch_shape(ctx->prec, ctx->dim, sms, &ls);
+            CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget));
+            double cst = 0.0;
+            if ((st = window(4, &cst))) return st;
+            if (cst < best_cost) { best_cost = cst; best = cand[k]; }
+        }
+        ls.tile_budget = best;
+        compute_launch_shape(ctx->prec, ctx->dim, sms, &ls);
+        CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget));
+    }
+    struct Knob { int* v; int group; int cand[3]; };
+    const int mb = ls.move_blocks, cb = ls.collide_blocks;
+    Knob knobs[3] = {{&ls.move_blocks, 1, {mb, 2 * mb, 0}},
+                     {&ls.scatter_blocks, 3, {4 * sms, 8 * sms, 16 * sms}},
+                     {&ls.collide_blocks, 6, {cb, 2 * cb, 0}}};
+    for (Knob& kn : knobs) {
+        int best = *kn.v;
+        double best_cost = 1e300;
+        for (int k = 0; k < 3 && kn.cand[k] > 0; ++k) {
+            *kn.v = kn.cand[k];
+            double cst = 0.0;
+            if ((st = window(kn.group, &cst))) return st;
+            if (cst < best_cost) { best_cost = cst; best = kn.cand[k]; }
+        }
+        *kn.v = best;
+    }
+    ctx->tuned_key = ((uint64_t)n_runs << 1) | 1u;
+    return DSMC_OK;
+}
+
 dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
                               const int32_t* sample_steps, int n_samples, uint64_t seed)
 {
@@ -766,6 +863,16 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     const int n_launch = plain ? 1 : n_runs;
     st = prepare(ctx, n_runs, dt, steps, sample_steps, n_samples, seed, n_launch);
     if (st) return st;
+    // (runs shorter than 100 steps keep the default shapes: the trial needs
+    // room to reach mid-run)
+    if (ctx->opt.autotune && !plain && steps >= 100 &&
+        ctx->tuned_key != (((uint64_t)n_runs << 1) | 1u)) {
+        st = autotune(ctx, n_runs, steps);
+        if (st) return st;
+        destroy_graphs(ctx);
+        st = prepare(ctx, n_runs, dt, steps, sample_steps, n_samples, seed, n_launch);
+        if (st) return st;
+    }
     const bool profile = ctx->opt.profile != 0;
     const bool graph = !plain && !profile && ctx->opt.use_graph;
     if (graph) {

@@ -2006,7 +2006,7 @@ void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStre
     DISPATCH_PREC(prec, {
         DISPATCH_DIM(ls.dim, (k_cell_big<T, D><<<ls.big_blocks, kBigThreads, big_smem(prec), s>>>(
                                  A<T>(args))));
-        k_collide_big<T><<<ls.sms * 8, 256, 0, s>>>(A<T>(args));
+        k_collide_big<T><<<ls.sms * 2, 256, 0, s>>>(A<T>(args));
     });
 }
 

@@ -72,7 +72,8 @@ class Options(C.Structure):
                 ("capacity_factor", C.c_double), ("capacity_per_run", C.c_int64),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("stream", C.c_void_p), ("use_graph", C.c_int32), ("debug", C.c_int32),
-                ("device", C.c_int32), ("profile", C.c_int32), ("run_offset", C.c_int64)]
+                ("device", C.c_int32), ("profile", C.c_int32), ("run_offset", C.c_int64),
+                ("autotune", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -81,7 +82,8 @@ class Stats(C.Structure):
         "clamps", "bounce_limit", "reject_limit", "pool_steps")] + [
         ("error_word", C.c_uint32), ("steps_done", C.c_int32), ("particles_now", C.c_int64),
         ("capacity", C.c_int64), ("ms_steps", C.c_double), ("ms_kernel", C.c_double * 12),
-        ("launches_kernel", C.c_int64 * 12), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
+        ("launches_kernel", C.c_int64 * 12), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+        ("shape", C.c_int32 * 4), ("tuned", C.c_int32)]
 
 
 _lib = None
@@ -170,7 +172,7 @@ class Ensemble:
 
     def __init__(self, w, mode="batched", precision="fp32", capacity_factor=0.0,
                  capacity_per_run=0, debug=False, profile=False, use_graph=True, device=0,
-                 torch_memory=True, stream=None, run_offset=0):
+                 torch_memory=True, stream=None, run_offset=0, autotune=False):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise DsmcError(E_CUDA, "no CUDA device: the DSMC path has no CPU fallback")
@@ -190,6 +192,7 @@ class Ensemble:
         opt.profile = 1 if profile else 0
         opt.device = device
         opt.run_offset = run_offset
+        opt.autotune = 1 if autotune else 0
         if torch_memory:
             dev = torch.device("cuda", device)
 
@@ -299,7 +302,10 @@ class Ensemble:
     def stats(self):
         s = Stats(struct_size=C.sizeof(Stats))
         self._check(self.lib.dsmc_get_stats(self.h, C.byref(s)), "dsmc_get_stats")
-        d = {k: getattr(s, k) for k, _ in Stats._fields_ if k not in ("ms_kernel", "launches_kernel")}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_
+             if k not in ("ms_kernel", "launches_kernel", "shape")}
+        d["shape"] = {"move_blocks": s.shape[0], "scatter_blocks": s.shape[1],
+                      "tile_budget": s.shape[2], "collide_blocks": s.shape[3]}
         d["ms_kernel"] = {KERNEL_KINDS[i]: s.ms_kernel[i] for i in range(len(KERNEL_KINDS))}
         d["launches_kernel"] = {KERNEL_KINDS[i]: int(s.launches_kernel[i])
                                 for i in range(len(KERNEL_KINDS))}

@@ -150,3 +150,19 @@ def test_macro_quantities_match_oracle_formulae(D):
             assert np.array_equal(np.isfinite(a), fin), k
             assert np.allclose(a[fin], b[fin], rtol=1e-10, atol=1e-12), k
         assert np.allclose(m["velocity"], ref["velocity"][0], rtol=1e-10, atol=1e-9, equal_nan=True)
+
+
+def test_autotune_keeps_results(D):
+    """options.autotune searches launch shapes on a trial ensemble; the real
+    run's group sums are bit-identical to the fixed-shape run."""
+    w = W.config0(runs=32, steps=120, n_samples=3)
+    a = D.Ensemble(w, autotune=True).run()
+    b = D.Ensemble(w).run()
+    for t in range(3):
+        assert np.array_equal(a.raw(t), b.raw(t))
+    sa, sb = a.stats(), b.stats()
+    assert sa["tuned"] == 1 and sb["tuned"] == 0
+    assert sa["shape"]["tile_budget"] in (4608, 6144, 7680)
+    for k in ("generated", "removed", "candidates", "collisions", "particle_steps"):
+        assert sa[k] == sb[k], k
+    print("autotuned shape:", sa["shape"], "default:", sb["shape"])
