@@ -470,7 +470,8 @@ static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev, bool fork 
                          bool reduce = true)
 {
     const int p = ctx->prec;
-    const LaunchShape& ls = ctx->ls;
+    LaunchShape ls = ctx->ls;
+    ls.pdl = fork ? 0 : 1;
     cudaStream_t s = ctx->stream;
     auto mark = [&]() {
         if (ev) cudaEventRecord(event_at(ctx, (*ev)++), s);
@@ -493,7 +494,7 @@ static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev, bool fork 
     launch_collide(p, args, ls, s); mark();
     if (reduce) launch_reduce(p, args, ls, s);
     mark();
-    launch_step_end(p, args, s); mark();
+    launch_step_end(p, args, ls, s); mark();
 }
 static const int kStepKernels = 9;
 static const int kKindOf[kStepKernels] = {DSMC_K_GENERATE, DSMC_K_MOVE,     DSMC_K_SCAN,

@@ -149,6 +149,8 @@ struct LaunchShape {
     int move_blocks, move_threads;
     int scatter_blocks, cell_blocks, big_blocks, collide_blocks;
     int tile_budget;
+    int pdl;   // direct launches overlap with the previous kernel (programmatic
+               // dependent launch); 0 while a step is captured into a graph
 };
 
 void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
@@ -161,7 +163,7 @@ void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_step_end(int prec, const void* args, cudaStream_t s);
+void launch_step_end(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_macro(int prec, const void* args, int sample, int n_runs, double* out,
                   cudaStream_t s);
 void launch_sample_now(int prec, const void* args, cudaStream_t s);

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "dsmc_internal.cuh"
 
@@ -360,6 +361,17 @@ __device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, ui
 // warp / block helpers
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
+// Programmatic dependent launch: the step kernels are launched so that each
+// may be scheduled while the kernel before it in the stream is finishing.
+// Every step kernel calls this first: it lets the next kernel begin its
+// launch, then waits until the previous kernel has completed and its memory
+// is visible (a no-op for a kernel launched without the attribute).
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // atomicAdd returning the old value, with an L2 evict-last policy: the
 // per-cell counters stay cached while the particle streams pass through L2
 __device__ __forceinline__ uint32_t atomic_add_l2_keep(uint32_t* p, uint32_t v)
@@ -639,6 +651,7 @@ __device__ __forceinline__ uint32_t element_entrants(const Cfg& c, uint32_t run,
 template <typename T>
 __global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
 {
+    pdl_enter();
     const Cfg& c = *a.cfg;
     __shared__ uint32_t s_warp[32];
     const uint32_t G = (uint32_t)a.gen_groups;
@@ -663,6 +676,7 @@ __global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
 {
+    pdl_enter();
     const Cfg& c = *a.cfg;
     __shared__ uint32_t s_off[257];
     __shared__ uint32_t s_warp[32];
@@ -826,6 +840,7 @@ __device__ __forceinline__ uint32_t run_of_key(const C& c, uint32_t key)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
+    pdl_enter();
     const Hot<T>& c = a.hot;
     // after a pool overflow (reported through the error word) the recorded
     // size can exceed the buffers: never walk past them
@@ -894,6 +909,7 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
 {
+    pdl_enter();
     const Cfg& c = *a.cfg;
     const uint32_t n = min(a.ctr->n_slow, (uint32_t)a.cap_old);
     const uint32_t step = a.ctr->step;
@@ -935,6 +951,7 @@ __global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
 __global__ void __launch_bounds__(kScanThreads) k_scan1(const uint32_t* __restrict__ count,
                                                         uint32_t* block_sums, int total)
 {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint32_t v = 0;
@@ -955,6 +972,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan1(const uint32_t* __restri
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
 {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_red[32];
     const int total = a.total_cells;
@@ -1002,6 +1020,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 {
+    pdl_enter();
     // the pool holds run_base[n_runs] particles after this step's scan, but
     // the slots to scatter are those of the pre-step pool: its size is kept
     // at start[total + 1] by the previous step
@@ -1361,6 +1380,7 @@ constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
 {
+    pdl_enter();
     const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
@@ -1488,6 +1508,7 @@ __host__ __device__ constexpr int collide_stage_pitch() { return kCollideStage +
 template <typename T>
 __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kPitch = collide_stage_pitch<T>();
     constexpr uint32_t kVec = 16u / sizeof(T);   // elements per 16 bytes
@@ -1665,6 +1686,7 @@ __host__ __device__ constexpr int big_max_of() { return 8192; }
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBigThreads) k_cell_big(StepArgs<T> a)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kMax = big_max_of<T>();
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -1745,6 +1767,7 @@ __global__ void __launch_bounds__(kBigThreads) k_cell_big(StepArgs<T> a)
 template <typename T>
 __global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
 {
+    pdl_enter();
     const Cfg& c = *a.cfg;
     constexpr int kMax = big_max_of<T>();
     const uint32_t step = a.ctr->step;
@@ -1793,6 +1816,7 @@ __global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
 template <typename T>
 __global__ void k_reduce(StepArgs<T> a)
 {
+    pdl_enter();
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     if (slot_t < 0) return;
@@ -1815,6 +1839,7 @@ __global__ void k_reduce(StepArgs<T> a)
 template <typename T>
 __global__ void k_step_end(StepArgs<T> a)
 {
+    pdl_enter();
     a.ctr->step += 1u;
     a.ctr->n_big = 0u;
     a.ctr->n_slow = 0u;
@@ -1919,6 +1944,36 @@ static const StepArgs<T>& A(const void* p) { return *static_cast<const StepArgs<
         else { constexpr int D = 2; __VA_ARGS__; }                    \
     } while (0)
 
+// launch a step kernel with programmatic stream serialisation (see
+// pdl_enter) when ls.pdl is set: its launch overlaps the end of the
+// previous kernel.  Graph replays are not helped by it (measured slower),
+// so captured steps use plain launches.
+template <typename... P, typename... Args>
+static void launch_pdl(const LaunchShape& ls, void (*kernel)(P...), unsigned grid, unsigned block,
+                       size_t smem, cudaStream_t s, const Args&... args)
+{
+    if (!ls.pdl) {
+        kernel<<<grid, block, smem, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // a launch the attribute makes fail is retried as a plain launch, which
+    // reports any error of its own through cudaGetLastError
+    if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
+        (void)cudaGetLastError();
+        kernel<<<grid, block, smem, s>>>(args...);
+    }
+}
+
 void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
     DISPATCH_PREC(prec, (k_init_cells<T><<<ls.sms * 4, 256, 0, s>>>(A<T>(args))));
@@ -1940,16 +1995,16 @@ void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStre
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
         const unsigned grid = (unsigned)a.n_runs * (unsigned)a.gen_groups;
-        if (a.gen_groups > 1) k_gen_count<T><<<grid, 256, 0, s>>>(a);
-        DISPATCH_DIM(ls.dim, (k_generate<T, D><<<grid, 256, 0, s>>>(a)));
+        if (a.gen_groups > 1) launch_pdl(ls, k_gen_count<T>, grid, 256, 0, s, a);
+        DISPATCH_DIM(ls.dim, launch_pdl(ls, k_generate<T, D>, grid, 256, 0, s, a));
     });
 }
 
 void launch_move(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
-        k_move<T, D><<<ls.move_blocks, ls.move_threads, 0, s>>>(A<T>(args));
-        k_move_slow<T, D><<<ls.sms * 2, 256, 0, s>>>(A<T>(args));
+        launch_pdl(ls, k_move<T, D>, ls.move_blocks, ls.move_threads, 0, s, A<T>(args));
+        launch_pdl(ls, k_move_slow<T, D>, ls.sms * 2, 256, 0, s, A<T>(args));
     }));
 }
 
@@ -1957,14 +2012,15 @@ void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t
 {
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
-        k_scan1<<<a.scan_blocks, kScanThreads, 0, s>>>(a.count, a.block_sums, a.total_cells);
-        k_scan2<T><<<a.scan_blocks, kScanThreads, 0, s>>>(a);
+        launch_pdl(ls, k_scan1, a.scan_blocks, kScanThreads, 0, s, (const uint32_t*)a.count, a.block_sums,
+                   a.total_cells);
+        launch_pdl(ls, k_scan2<T>, a.scan_blocks, kScanThreads, 0, s, a);
     });
 }
 
 void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, (k_scatter<T><<<ls.scatter_blocks, 256, 0, s>>>(A<T>(args))));
+    DISPATCH_PREC(prec, launch_pdl(ls, k_scatter<T>, ls.scatter_blocks, 256, 0, s, A<T>(args)));
 }
 
 size_t cell_smem_bytes(int prec, int budget)
@@ -1981,7 +2037,7 @@ void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t
 {
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
         const StepArgs<T>& a = A<T>(args);
-        k_cell<T, D><<<ls.cell_blocks, kTileCells, cell_smem_bytes(prec, a.tile_budget), s>>>(a);
+        launch_pdl(ls, k_cell<T, D>, ls.cell_blocks, kTileCells, cell_smem_bytes(prec, a.tile_budget), s, a);
     }));
 }
 
@@ -1993,8 +2049,8 @@ static size_t collide_smem(int prec)
 
 void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, (k_collide<T><<<ls.collide_blocks, kCollideCells, collide_smem(prec), s>>>(
-                            A<T>(args))));
+    DISPATCH_PREC(prec, launch_pdl(ls, k_collide<T>, ls.collide_blocks, kCollideCells, collide_smem(prec),
+                                   s, A<T>(args)));
 }
 
 int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
@@ -2004,20 +2060,20 @@ static size_t big_smem(int) { return 8 * (size_t)big_max_of<float>(); }
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
     DISPATCH_PREC(prec, {
-        DISPATCH_DIM(ls.dim, (k_cell_big<T, D><<<ls.big_blocks, kBigThreads, big_smem(prec), s>>>(
-                                 A<T>(args))));
-        k_collide_big<T><<<ls.sms * 2, 256, 0, s>>>(A<T>(args));
+        DISPATCH_DIM(ls.dim, launch_pdl(ls, k_cell_big<T, D>, ls.big_blocks, kBigThreads, big_smem(prec), s,
+                                        A<T>(args)));
+        launch_pdl(ls, k_collide_big<T>, ls.sms * 2, 256, 0, s, A<T>(args));
     });
 }
 
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, (k_reduce<T><<<ls.sms * 4, 256, 0, s>>>(A<T>(args))));
+    DISPATCH_PREC(prec, launch_pdl(ls, k_reduce<T>, ls.sms * 4, 256, 0, s, A<T>(args)));
 }
 
-void launch_step_end(int prec, const void* args, cudaStream_t s)
+void launch_step_end(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, (k_step_end<T><<<1, 1, 0, s>>>(A<T>(args))));
+    DISPATCH_PREC(prec, launch_pdl(ls, k_step_end<T>, 1, 1, 0, s, A<T>(args)));
 }
 
 void launch_sample_now(int prec, const void* args, cudaStream_t s)
