@@ -389,3 +389,46 @@ def philox_gpu(ctr, key):
     if st != OK:
         raise DsmcError(st, "dsmc_debug_philox failed")
     return out
+
+
+class MixedEnsemble:
+    """A mixed-size ensemble (workloads.mixed): the runs that share a grid
+    form one batched context (their global run indices through
+    run_offset), and all contexts advance at once, one host thread and one
+    CUDA stream each, the GPU's block scheduler sharing the SMs among their
+    kernels.  Each group keeps its own samples (group sums over its runs)."""
+
+    def __init__(self, m, precision="fp32", device=0, **kw):
+        import torch
+        self.m = m
+        self.parts = []
+        for w in m["groups"]:
+            stream = torch.cuda.Stream(device=device)
+            self.parts.append(Ensemble(w, precision=precision, device=device, stream=stream,
+                                       run_offset=w["run0"], **kw))
+
+    def run(self):
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=len(self.parts)) as ex:
+            for f in [ex.submit(e.run) for e in self.parts]:
+                f.result()
+        return self
+
+    def raw(self, group, t):
+        return self.parts[group].raw(t)
+
+    def stats(self):
+        per = [e.stats() for e in self.parts]
+        keys = ("particle_steps", "generated", "removed", "wall_hits", "candidates", "collisions",
+                "particles_now")
+        out = {k: sum(int(s[k]) for s in per) for k in keys}
+        out["error_word"] = 0
+        for s in per:
+            out["error_word"] |= int(s["error_word"])
+        out["groups"] = per
+        return out
+
+    def close(self):
+        for e in self.parts:
+            e.close()
+        self.parts = []

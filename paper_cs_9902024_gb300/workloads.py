@@ -208,9 +208,45 @@ def config3(**kw):
     return plate3d(**args)
 
 
+def mixed(n_runs=1024, cells_lo=32 * 16, cells_hi=512 * 256, steps=300, n_samples=4, seed=1,
+          draw_seed=12345, name="duct_mixed"):
+    """Mixed-size ensemble: n_runs runs of the duct, each on its own grid,
+    the cell count drawn log-uniformly in [cells_lo, cells_hi] (so the
+    particles a run holds at full fill, ~20 per cell, are log-uniform from
+    ~10k to ~2.6M) with aspect 2:1 and nx a multiple of 16.  Runs that drew
+    the same grid form one group (one batched context); run r keeps global
+    index r, so its draws do not depend on the grouping.  Returns
+    dict(name, runs, steps, groups): each group is a duct workload with
+    `runs` its run count and `run0` the global index of its first run
+    (global indices are handed out grid by grid, so each group's runs are
+    one consecutive range)."""
+    import numpy as np
+    rng = np.random.default_rng(draw_seed)
+    cells = np.exp(rng.uniform(np.log(cells_lo), np.log(cells_hi), size=n_runs))
+    nx = np.clip(np.round(np.sqrt(2.0 * cells) / 16.0) * 16, 32, 512).astype(int)
+    order = np.argsort(nx, kind="stable")
+    groups = []
+    # global run indices are assigned in grid order, so that every group is
+    # one consecutive range of runs (one run_offset per context)
+    start = 0
+    for g in sorted(set(nx.tolist())):
+        cnt = int((nx == g).sum())
+        w = duct(nx=g, ny=g // 2, runs=cnt, steps=steps, n_samples=n_samples, seed=seed,
+                 name="%s_%dx%d" % (name, g, g // 2))
+        w["run0"] = start
+        groups.append(w)
+        start += cnt
+    assert start == n_runs and len(order) == n_runs
+    return dict(name=name, runs=n_runs, steps=steps, groups=groups)
+
+
+def config4(**kw):
+    return mixed(**kw)
+
+
 def by_name(name, **kw):
     table = {"config0": config0, "config1": config1, "config2": config2,
-             "config3": config3}
+             "config3": config3, "config4": config4}
     return table[name](**kw)
 
 
