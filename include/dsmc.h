@@ -298,6 +298,14 @@ dsmc_status dsmc_debug_sample(dsmc_ctx* ctx, int run, double* mom);
 dsmc_status dsmc_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* key,
                               uint32_t* out);
 
+/* Test hook for the bounded device waits (no counterpart in the paper):
+ * runs one kernel whose bulk-copy barrier is never completed, so its wait
+ * gives up after `polls` polls (1 .. 2^20) and sets DSMC_ERR_TIMEOUT, as the
+ * step kernels' waits would; nothing stays in flight on the device.  Needs
+ * dsmc_debug_begin.  Returns DSMC_E_TIMEOUT; the run's state and counters
+ * are untouched and the context stays usable. */
+dsmc_status dsmc_debug_timeout_probe(dsmc_ctx* ctx, uint32_t polls);
+
 #ifdef __cplusplus
 }
 #endif

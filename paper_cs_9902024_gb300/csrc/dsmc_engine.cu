@@ -1197,6 +1197,22 @@ dsmc_status dsmc_debug_set_state(dsmc_ctx* ctx, int run, int64_t n, const double
                                   : set_run_state<float>(ctx, run, n, x, v, id, next_id);
 }
 
+dsmc_status dsmc_debug_timeout_probe(dsmc_ctx* ctx, uint32_t polls)
+{
+    if (!ctx || polls < 1 || polls > (1u << 20)) return DSMC_E_INVALID;
+    if (!ctx->dbg) return fail(ctx, DSMC_E_STATE, "dsmc_debug_begin first");
+    CK(cudaSetDevice(ctx->device));
+    CK(timeout_probe(ctx->d_ctr, polls, ctx->stream));
+    Counters h;
+    dsmc_status st = read_counters(ctx, &h);
+    if (st) return st;
+    CK(cudaMemsetAsync(&ctx->d_ctr->probe, 0, sizeof(uint32_t), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h.probe & DSMC_ERR_TIMEOUT)
+        return fail(ctx, DSMC_E_TIMEOUT, "probe: a bounded wait for a bulk copy expired");
+    return DSMC_OK;
+}
+
 dsmc_status dsmc_debug_get_cells(dsmc_ctx* ctx, int run, int32_t* count, int32_t* cand,
                                  int32_t* accepted, int64_t* lcr, int64_t cap)
 {

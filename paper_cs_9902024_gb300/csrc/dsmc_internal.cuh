@@ -70,6 +70,7 @@ struct Counters {
     unsigned long long candidates, collisions, clamps, bounce_limit, reject_limit;
     unsigned long long pool_steps;
     uint32_t error, step, n_big, n_slow;
+    uint32_t probe;        // error bits of the timeout test hook only
 };
 
 // The configuration constants that the streaming kernels use for every
@@ -168,6 +169,7 @@ void launch_macro(int prec, const void* args, int sample, int n_runs, double* ou
                   cudaStream_t s);
 void launch_sample_now(int prec, const void* args, cudaStream_t s);
 cudaError_t prepare_kernels(int prec, int dim, int tile_budget);
+cudaError_t timeout_probe(Counters* ctr, uint32_t polls, cudaStream_t s);
 void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls);
 int big_cell_limit(int prec);
 cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,

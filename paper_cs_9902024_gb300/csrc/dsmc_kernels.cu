@@ -2139,6 +2139,29 @@ cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
     return e;
 }
 
+// Test hook for the bounded waits: an mbarrier expects 16 bytes that no
+// copy will deliver, so its wait gives up after `polls` polls and sets
+// DSMC_ERR_TIMEOUT (in the hook's own word, not the run's error word), as a
+// bulk-copy wait of the step kernels would.  No asynchronous operation is
+// left in flight.
+__global__ void k_timeout_probe(Counters* ctr, uint32_t polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1u);
+        mbar_arrive_expect_tx(&bar, 16u);
+        bool done = false;
+        for (uint32_t it = 0; it < polls && !done; ++it) done = mbar_try_wait(&bar, 0u);
+        if (!done) atomicOr(&ctr->probe, DSMC_ERR_TIMEOUT);
+    }
+}
+
+cudaError_t timeout_probe(Counters* ctr, uint32_t polls, cudaStream_t s)
+{
+    k_timeout_probe<<<1, 32, 0, s>>>(ctr, polls);
+    return cudaGetLastError();
+}
+
 cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s)
 {

@@ -31,7 +31,7 @@ EXPORTS = [
     "dsmc_last_error", "dsmc_debug_begin", "dsmc_debug_step", "dsmc_debug_get_state",
     "dsmc_debug_set_state", "dsmc_debug_get_cells", "dsmc_debug_get_cell_state",
     "dsmc_debug_set_cell_state", "dsmc_debug_sample", "dsmc_debug_philox",
-    "dsmc_run_ensemble_noalloc",
+    "dsmc_run_ensemble_noalloc", "dsmc_debug_timeout_probe",
 ]
 
 
@@ -119,6 +119,7 @@ def load_library(path=LIB_PATH):
         lib.dsmc_debug_set_cell_state.argtypes = [P, C.c_int, dp, dp]
         lib.dsmc_debug_sample.argtypes = [P, C.c_int, dp]
         lib.dsmc_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
+        lib.dsmc_debug_timeout_probe.argtypes = [P, C.c_uint32]
         lib.dsmc_run_ensemble_noalloc.argtypes = [P, C.c_int, C.c_double, C.c_int, ip, C.c_int,
                                                   C.c_uint64, dp, C.c_size_t]
         for name in EXPORTS:
@@ -319,6 +320,10 @@ class Ensemble:
                                               w["seed"] if seed is None else seed),
                     "dsmc_debug_begin")
         self.runs = runs
+
+    def debug_timeout_probe(self, polls=64):
+        """dsmc_debug_timeout_probe: returns the status (E_TIMEOUT expected)."""
+        return self.lib.dsmc_debug_timeout_probe(self.h, polls)
 
     def debug_step(self, n=1):
         self._check(self.lib.dsmc_debug_step(self.h, n), "dsmc_debug_step")
