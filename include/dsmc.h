@@ -220,11 +220,25 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
                               const int32_t* sample_steps, int n_samples,
                               uint64_t seed);
 
+/* dsmc_run_ensemble with time-averaged samples: sample k sums the moments
+ * after Interaction of every step first[k] .. last[k] (inclusive) of every
+ * run -- the averaging interval dt_av of the unsteady-flow method (Sec. 1.1:
+ * macroparameters averaged over an interval short against the flow's time
+ * scale and over the n runs); first = last gives dsmc_run_ensemble.  Windows
+ * lie in [1, steps], increasing and disjoint (at most 4096).  Each run's
+ * sums over a window are formed in step order, then added to the group
+ * sums in increasing run order (the same in batched and plain modes).
+ * Errors as dsmc_run_ensemble. */
+dsmc_status dsmc_run_ensemble_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                                      const int32_t* first, const int32_t* last, int n_windows,
+                                      uint64_t seed);
+
 /* Copy sample `sample_idx` of the last run into out[0 .. out_len).  The
  * runs are split into G = min(n_runs, 16) groups (run r in group r mod G);
  * RAW_MOMENTS gives the group sums [G][ncells][7] of N, sum v_a and
  * sum v_a^2; the macroscopic quantities pool all groups:
- *   n = sum N F_N / (n_runs V_c),  u = sum v / sum N,
+ *   n = sum N F_N / (n_runs L V_c),  u = sum v / sum N  (L: the sample's
+ *   window length in steps, 1 for dsmc_run_ensemble),
  *   T = m / (3 k) (sum |v|^2 / sum N - |u|^2)  (NaN where sum N = 0);
  * STDERR_* are the standard deviations over the G group estimates divided
  * by sqrt(G).  Errors: DSMC_E_INVALID (index or out_len too small),

@@ -701,7 +701,8 @@ int orc_get_stats(const orc_ctx* C, int run, orc_stats* s)
 typedef struct {
     orc_ctx* C;
     int worker, n_workers, G, steps, n_samples;
-    const int32_t* sample_steps;
+    const int32_t* first;   /* sample k averages steps first[k] .. last[k] */
+    const int32_t* last;
     double* acc;
     int rc;
 } orc_job;
@@ -712,7 +713,8 @@ static void* orc_worker(void* arg)
     orc_ctx* C = J->C;
     size_t per = (size_t)C->ncells * ORC_NMOM;
     double* mom = malloc(per * sizeof(double));
-    if (!mom) { J->rc = -2; return NULL; }
+    double* win = malloc(per * sizeof(double));   /* the run's sums over the current window */
+    if (!mom || !win) { J->rc = -2; free(mom); free(win); return NULL; }
     for (int g = J->worker; g < J->G; g += J->n_workers) {
         /* local runs r whose global index run0 + r falls in group g */
         const int r0 = (int)(((uint32_t)g + (uint32_t)J->G - C->run0 % (uint32_t)J->G) % (uint32_t)J->G);
@@ -722,20 +724,29 @@ static void* orc_worker(void* arg)
             int t = 0;
             for (int s = 1; rc == 0 && s <= J->steps; ++s) {
                 rc = orc_step(C, r, s);
-                if (rc == 0 && t < J->n_samples && J->sample_steps[t] == s) {
+                if (rc == 0 && t < J->n_samples && J->first[t] <= s && s <= J->last[t]) {
                     orc_sample(C, r, mom);
-                    double* dst = J->acc + ((size_t)t * J->G + g) * per;
-                    for (size_t i = 0; i < per; ++i) dst[i] += mom[i];
-                    ++t;
+                    /* the window's sums in step order, then added to the group
+                     * at the window's last step */
+                    if (s == J->first[t])
+                        for (size_t i = 0; i < per; ++i) win[i] = mom[i];
+                    else
+                        for (size_t i = 0; i < per; ++i) win[i] += mom[i];
+                    if (s == J->last[t]) {
+                        double* dst = J->acc + ((size_t)t * J->G + g) * per;
+                        for (size_t i = 0; i < per; ++i) dst[i] += win[i];
+                        ++t;
+                    }
                 }
             }
-            if (rc) { J->rc = rc; free(mom); return NULL; }
+            if (rc) { J->rc = rc; free(mom); free(win); return NULL; }
             keep = C->runs[r].st;
             run_free(&C->runs[r]);
             C->runs[r].st = keep;
         }
     }
     free(mom);
+    free(win);
     return NULL;
 }
 
@@ -751,9 +762,17 @@ int orc_run_ensemble_part(const orc_config* cfg, uint32_t run0, int n_runs, int 
                           int steps, const int32_t* sample_steps, int n_samples, uint64_t seed,
                           int threads, double* acc, orc_stats* stats)
 {
+    return orc_run_ensemble_windows(cfg, run0, n_runs, G, dt, steps, sample_steps, sample_steps,
+                                    n_samples, seed, threads, acc, stats);
+}
+
+int orc_run_ensemble_windows(const orc_config* cfg, uint32_t run0, int n_runs, int G, double dt,
+                             int steps, const int32_t* first, const int32_t* last, int n_samples,
+                             uint64_t seed, int threads, double* acc, orc_stats* stats)
+{
     for (int t = 0; t < n_samples; ++t)
-        if (sample_steps[t] < 1 || sample_steps[t] > steps ||
-            (t > 0 && sample_steps[t] <= sample_steps[t - 1]))
+        if (first[t] < 1 || last[t] > steps || first[t] > last[t] ||
+            (t > 0 && first[t] <= last[t - 1]))
             return -1;
     if (G < 1 || G > NGROUP_MAX) return -1;
     orc_ctx* C = orc_create(cfg, n_runs, dt, seed);
@@ -767,7 +786,7 @@ int orc_run_ensemble_part(const orc_config* cfg, uint32_t run0, int n_runs, int 
     int rc = 0;
     if (!jobs || !th) rc = -2;
     for (int w = 0; rc == 0 && w < threads; ++w) {
-        jobs[w] = (orc_job){ C, w, threads, G, steps, n_samples, sample_steps, acc, 0 };
+        jobs[w] = (orc_job){ C, w, threads, G, steps, n_samples, first, last, acc, 0 };
         if (threads == 1) orc_worker(&jobs[w]);
         else if (pthread_create(&th[w], NULL, orc_worker, &jobs[w])) rc = -2;
     }

@@ -127,6 +127,15 @@ int orc_run_ensemble_part(const orc_config* cfg, uint32_t run0, int n_runs, int 
                           int steps, const int32_t* sample_steps, int n_samples, uint64_t seed,
                           int threads, double* acc, orc_stats* stats);
 
+/* the same with time-averaged samples: sample t sums the moments after
+ * Interaction of steps first[t] .. last[t] (inclusive) of every run (the
+ * averaging interval of Sec. 1.1); each run's window sums are formed in step
+ * order and added to its group at the window's last step.  Windows lie in
+ * [1, steps], increasing and disjoint. */
+int orc_run_ensemble_windows(const orc_config* cfg, uint32_t run0, int n_runs, int G, double dt,
+                             int steps, const int32_t* first, const int32_t* last, int n_samples,
+                             uint64_t seed, int threads, double* acc, orc_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

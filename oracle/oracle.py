@@ -107,6 +107,10 @@ def oracle_lib():
             lib.orc_run_ensemble_part.argtypes = [C.POINTER(Config), C.c_uint32, C.c_int, C.c_int,
                                                   C.c_double, C.c_int, ip, C.c_int, C.c_uint64,
                                                   C.c_int, dp, C.POINTER(Stats)]
+            lib.orc_run_ensemble_windows.argtypes = [C.POINTER(Config), C.c_uint32, C.c_int,
+                                                     C.c_int, C.c_double, C.c_int, ip, ip,
+                                                     C.c_int, C.c_uint64, C.c_int, dp,
+                                                     C.POINTER(Stats)]
             _lib = lib
     return _lib
 
@@ -290,11 +294,12 @@ class Oracle:
 
 
 def run_ensemble(w, runs=None, steps=None, sample_steps=None, seed=None,
-                 threads=1, dt=None, gas_override=None, run0=0, groups=None):
+                 threads=1, dt=None, gas_override=None, run0=0, groups=None, windows=None):
     """Whole ensemble through the oracle.  Returns (acc, stats) with
     acc[t, g, cell, k] the group sums (g = run mod G, G = min(runs, 16)).
     With run0 / groups: the runs with global indices run0 .. run0 + runs - 1
-    of a larger ensemble whose group count is `groups`."""
+    of a larger ensemble whose group count is `groups`.  With windows =
+    [(first, last), ...]: time-averaged samples over those step ranges."""
     lib = oracle_lib()
     cfg = make_config(w, gas_override)
     runs = runs if runs is not None else w["runs"]
@@ -304,11 +309,17 @@ def run_ensemble(w, runs=None, steps=None, sample_steps=None, seed=None,
     seed = seed if seed is not None else w["seed"]
     dt = dt if dt is not None else w["dt"]
     G = min(runs, 16) if groups is None else groups
+    if windows is not None:
+        fi = np.ascontiguousarray([a for a, _ in windows], dtype=np.int32)
+        la = np.ascontiguousarray([b for _, b in windows], dtype=np.int32)
+    else:
+        fi = la = ss
     nc = ncells_of(w)
-    acc = np.zeros((len(ss), G, nc, NMOM))
+    acc = np.zeros((len(fi), G, nc, NMOM))
     st = Stats()
-    rc = lib.orc_run_ensemble_part(C.byref(cfg), run0, runs, G, dt, steps, _ptr(ss, C.c_int32),
-                                   len(ss), seed, threads, _ptr(acc, C.c_double), C.byref(st))
+    rc = lib.orc_run_ensemble_windows(C.byref(cfg), run0, runs, G, dt, steps,
+                                      _ptr(fi, C.c_int32), _ptr(la, C.c_int32), len(fi), seed,
+                                      threads, _ptr(acc, C.c_double), C.byref(st))
     if rc != 0:
         raise RuntimeError("orc_run_ensemble failed (%d)" % rc)
     return acc, st.as_dict()

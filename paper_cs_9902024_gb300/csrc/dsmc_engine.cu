@@ -88,6 +88,7 @@ struct dsmc_ctx {
     // last run
     bool have_run = false;
     int last_runs = 0, last_steps = 0, last_samples = 0;
+    std::vector<int> win_len;        // steps of each sample window of the last run
     // debug stepping
     bool dbg = false;
     std::vector<uint32_t> prev_run_base;
@@ -569,24 +570,28 @@ static dsmc_status check_error_word(dsmc_ctx* ctx, uint32_t e)
     return DSMC_E_CAPACITY;
 }
 
+// sample windows: [first[k], last[k]] inside [1, steps], increasing and
+// disjoint (a plain sample list is first = last)
 static dsmc_status validate_run(dsmc_ctx* ctx, int n_runs, double dt, int steps,
-                                const int32_t* ss, int n_samples)
+                                const int32_t* first, const int32_t* last, int n_samples)
 {
     if (n_runs < 1 || n_runs > (1 << 20) || ctx->opt.run_offset + n_runs > (1ll << 31))
         return fail(ctx, DSMC_E_INVALID, "n_runs out of range");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, DSMC_E_INVALID, "dt must be > 0");
     if (steps < 0 || steps > (1 << 26)) return fail(ctx, DSMC_E_INVALID, "steps out of range");
-    if (n_samples < 0 || n_samples > kMaxSamples || (n_samples > 0 && !ss))
+    if (n_samples < 0 || n_samples > kMaxSamples || (n_samples > 0 && (!first || !last)))
         return fail(ctx, DSMC_E_INVALID, "bad sample list");
     for (int k = 0; k < n_samples; ++k)
-        if (ss[k] < 1 || ss[k] > steps || (k > 0 && ss[k] <= ss[k - 1]))
-            return fail(ctx, DSMC_E_INVALID, "sample_steps must be increasing in [1, steps]");
+        if (first[k] < 1 || last[k] > steps || first[k] > last[k] ||
+            (k > 0 && first[k] <= last[k - 1]))
+            return fail(ctx, DSMC_E_INVALID,
+                        "sample steps (windows) must be increasing and disjoint in [1, steps]");
     return DSMC_OK;
 }
 
 // set up everything a run needs up to (not including) the step-0 state
-static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, const int32_t* ss,
-                           int n_samples, uint64_t seed, int n_launch)
+static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, const int32_t* first,
+                           const int32_t* last, int n_samples, uint64_t seed, int n_launch)
 {
     dsmc_status st = build_cfg(ctx, dt, seed);
     if (st) return st;
@@ -597,7 +602,9 @@ static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, cons
     st = upload_cfg(ctx);
     if (st) return st;
     std::vector<int32_t> slot(steps + 2, -1);
-    for (int k = 0; k < n_samples; ++k) slot[ss[k]] = k;
+    for (int k = 0; k < n_samples; ++k)
+        for (int s = first[k]; s <= last[k]; ++s)
+            slot[s] = k | (s == first[k] ? kSlotFirst : 0) | (s == last[k] ? kSlotLast : 0);
     ctx->stats.h2d_bytes += 4 * slot.size();
     CK(cudaMemcpyAsync(ctx->sample_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -849,12 +856,13 @@ static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
     return DSMC_OK;
 }
 
-dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
-                              const int32_t* sample_steps, int n_samples, uint64_t seed)
+static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                               const int32_t* first, const int32_t* last, int n_samples,
+                               uint64_t seed)
 {
     if (!ctx) return DSMC_E_INVALID;
     CK(cudaSetDevice(ctx->device));
-    dsmc_status st = validate_run(ctx, n_runs, dt, steps, sample_steps, n_samples);
+    dsmc_status st = validate_run(ctx, n_runs, dt, steps, first, last, n_samples);
     if (st) return st;
     ctx->have_run = false;
     ctx->dbg = false;
@@ -862,7 +870,7 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     ctx->stats.d2h_bytes = 0;
     const bool plain = ctx->opt.mode == DSMC_MODE_PLAIN;
     const int n_launch = plain ? 1 : n_runs;
-    st = prepare(ctx, n_runs, dt, steps, sample_steps, n_samples, seed, n_launch);
+    st = prepare(ctx, n_runs, dt, steps, first, last, n_samples, seed, n_launch);
     if (st) return st;
     // (runs shorter than 100 steps keep the default shapes: the trial needs
     // room to reach mid-run)
@@ -871,7 +879,7 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
         st = autotune(ctx, n_runs, steps);
         if (st) return st;
         destroy_graphs(ctx);
-        st = prepare(ctx, n_runs, dt, steps, sample_steps, n_samples, seed, n_launch);
+        st = prepare(ctx, n_runs, dt, steps, first, last, n_samples, seed, n_launch);
         if (st) return st;
     }
     const bool profile = ctx->opt.profile != 0;
@@ -884,8 +892,9 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
         ctx->stats.ms_kernel[k] = 0.0;
         ctx->stats.launches_kernel[k] = 0;
     }
+    // graphs with the reduction over runs at the windows' last steps
     std::vector<char> is_sample(steps + 1, 0);
-    for (int k = 0; k < n_samples; ++k) is_sample[sample_steps[k]] = 1;
+    for (int k = 0; k < n_samples; ++k) is_sample[last[k]] = 1;
     cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
     if (!e0 || !e1) return fail(ctx, DSMC_E_CUDA, "cudaEventCreate failed");
     size_t evn = 2;
@@ -950,7 +959,22 @@ dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     ctx->last_runs = n_runs;
     ctx->last_steps = steps;
     ctx->last_samples = n_samples;
+    ctx->win_len.assign(n_samples, 1);
+    for (int k = 0; k < n_samples; ++k) ctx->win_len[k] = last[k] - first[k] + 1;
     return DSMC_OK;
+}
+
+dsmc_status dsmc_run_ensemble(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                              const int32_t* sample_steps, int n_samples, uint64_t seed)
+{
+    return run_windows(ctx, n_runs, dt, steps, sample_steps, sample_steps, n_samples, seed);
+}
+
+dsmc_status dsmc_run_ensemble_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
+                                      const int32_t* first, const int32_t* last, int n_windows,
+                                      uint64_t seed)
+{
+    return run_windows(ctx, n_runs, dt, steps, first, last, n_windows, seed);
 }
 
 dsmc_status dsmc_get_samples(dsmc_ctx* ctx, int sample_idx, dsmc_quantity q, double* out,
@@ -984,7 +1008,9 @@ dsmc_status dsmc_get_samples(dsmc_ctx* ctx, int sample_idx, dsmc_quantity q, dou
     if (out_len < nc * width) return fail(ctx, DSMC_E_INVALID, "out_len too small");
     AnyArgs u;
     const void* a = build_args(ctx, u, ctx->cur, 0, ctx->n_launch);
-    launch_macro(ctx->prec, a, sample_idx, ctx->last_runs, ctx->macro, ctx->stream);
+    launch_macro(ctx->prec, a, sample_idx, ctx->last_runs,
+                 sample_idx < (int)ctx->win_len.size() ? ctx->win_len[sample_idx] : 1, ctx->macro,
+                 ctx->stream);
     CK(cudaGetLastError());
     ctx->stats.d2h_bytes += 8 * width * nc;
     CK(cudaMemcpy2DAsync(out, 8 * width, ctx->macro + off, 8 * 10, 8 * width, nc,
@@ -1007,10 +1033,10 @@ dsmc_status dsmc_debug_begin(dsmc_ctx* ctx, int n_runs, double dt, uint64_t seed
 {
     if (!ctx) return DSMC_E_INVALID;
     CK(cudaSetDevice(ctx->device));
-    dsmc_status st = validate_run(ctx, n_runs, dt, 0, nullptr, 0);
+    dsmc_status st = validate_run(ctx, n_runs, dt, 0, nullptr, nullptr, 0);
     if (st) return st;
     const int steps = 4096;
-    st = prepare(ctx, n_runs, dt, steps, nullptr, 0, seed, n_runs);
+    st = prepare(ctx, n_runs, dt, steps, nullptr, nullptr, 0, seed, n_runs);
     if (st) return st;
     AnyArgs u;
     enqueue_init(ctx, build_args(ctx, u, 0, 0, n_runs));
@@ -1349,13 +1375,14 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-// Builds the per-step sample table in the scratch: -1 everywhere, k at step
-// sample_steps[k] (the steps were copied to `ss` first).
+// Builds the per-step sample table in the scratch: -1 everywhere, sample k
+// (a one-step window) at step sample_steps[k] (the steps were copied to
+// `ss` first).
 __global__ void k_noalloc_sample_table(int32_t* slot, int n_slot, const int32_t* ss, int n_samples)
 {
     for (int i = threadIdx.x; i < n_slot; i += blockDim.x) slot[i] = -1;
     __syncthreads();
-    for (int k = threadIdx.x; k < n_samples; k += blockDim.x) slot[ss[k]] = k;
+    for (int k = threadIdx.x; k < n_samples; k += blockDim.x) slot[ss[k]] = k | kSlotFirst | kSlotLast;
 }
 
 // Device address of the scratch array on the context's device.  The lookup
@@ -1462,7 +1489,7 @@ dsmc_status dsmc_run_ensemble_noalloc(dsmc_ctx* ctx, int n_runs, double dt, int 
 {
     if (!ctx) return DSMC_E_INVALID;
     CK(cudaSetDevice(ctx->device));
-    dsmc_status st = validate_run(ctx, n_runs, dt, steps, sample_steps, n_samples);
+    dsmc_status st = validate_run(ctx, n_runs, dt, steps, sample_steps, sample_steps, n_samples);
     if (st) return st;
     if (!ctx->bufs.empty())
         return fail(ctx, DSMC_E_STATE,

@@ -21,6 +21,10 @@ constexpr int kLaneMax = 512;             // largest cell of the tile path
 constexpr int kScanTile = 4096;           // cells per CTA of the scan
 constexpr int kScanThreads = 1024;
 constexpr int kMaxSamples = 4096;
+// sample_slot[step]: -1, or the sample index k of the window the step belongs
+// to, with a flag on the window's first step (the per-run sums restart) and
+// on its last step (the runs' sums are added into the group sums)
+constexpr int32_t kSlotIndex = 0x000FFFFF, kSlotFirst = 0x00100000, kSlotLast = 0x00200000;
 
 // Philox counter word 1 carries the purpose of a draw in its top 4 bits.
 enum Purpose : uint32_t {
@@ -165,7 +169,7 @@ void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStre
 void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_step_end(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_macro(int prec, const void* args, int sample, int n_runs, double* out,
+void launch_macro(int prec, const void* args, int sample, int n_runs, int window, double* out,
                   cudaStream_t s);
 void launch_sample_now(int prec, const void* args, cudaStream_t s);
 cudaError_t prepare_kernels(int prec, int dim, int tile_budget);

@@ -1648,7 +1648,11 @@ __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
             if (slot_t >= 0) {
                 double m[DSMC_NMOM];
                 cell_moments<T>(v0, v1, v2, Nq, m);
-                for (int qq = 0; qq < DSMC_NMOM; ++qq) a.mom[gq * DSMC_NMOM + qq] = m[qq];
+                double* mo = a.mom + gq * DSMC_NMOM;
+                if (slot_t & kSlotFirst)
+                    for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] = m[qq];
+                else
+                    for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] += m[qq];
             }
         }
         __syncthreads();
@@ -1805,21 +1809,28 @@ __global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
         if (slot_t >= 0 && lane == 0) {
             double m[DSMC_NMOM];
             cell_moments<T>(v0, v1, v2, N, m);
-            for (int q = 0; q < DSMC_NMOM; ++q) a.mom[(uint64_t)gcell * DSMC_NMOM + q] = m[q];
+            double* mo = a.mom + (uint64_t)gcell * DSMC_NMOM;
+            if (slot_t & kSlotFirst)
+                for (int q = 0; q < DSMC_NMOM; ++q) mo[q] = m[q];
+            else
+                for (int q = 0; q < DSMC_NMOM; ++q) mo[q] += m[q];
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Sampling over runs: acc[t][g] += sum of the launch's runs of group g, in
-// increasing run order (the same order in batched and plain modes).
+// Sampling over runs, at the last step of a sample window: acc[k][g] +=
+// sum of the launch's runs of group g (each run's sums over the window's
+// steps), in increasing run order (the same order in batched and plain
+// modes).
 template <typename T>
 __global__ void k_reduce(StepArgs<T> a)
 {
     pdl_enter();
     const uint32_t step = a.ctr->step;
-    const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
-    if (slot_t < 0) return;
+    const int slot_v = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
+    if (slot_v < 0 || !(slot_v & kSlotLast)) return;
+    const int slot_t = slot_v & kSlotIndex;
     const int ncells = a.cfg->ncells;
     const int64_t per = (int64_t)ncells * DSMC_NMOM;
     const int64_t n = (int64_t)a.G * per;
@@ -1876,7 +1887,7 @@ __global__ void k_sample_now(StepArgs<T> a, const T* v0, const T* v1, const T* v
 // macroscopic quantities of sample t from the group sums; out[cell][10] =
 // n, u, v, w, T, se_n, se_u, se_v, se_w, se_T
 template <typename T>
-__global__ void k_macro(StepArgs<T> a, int t, int n_runs, double* out)
+__global__ void k_macro(StepArgs<T> a, int t, int n_runs, int window, double* out)
 {
     const Cfg& c = *a.cfg;
     const int ncells = c.ncells;
@@ -1889,7 +1900,8 @@ __global__ void k_macro(StepArgs<T> a, int t, int n_runs, double* out)
         for (int g = 0; g < G; ++g) {
             const double* s = a.acc + (((int64_t)t * G + g) * ncells + cell) * DSMC_NMOM;
             for (int q = 0; q < DSMC_NMOM; ++q) pooled[q] += s[q];
-            const double nr = (double)((n_runs - g + G - 1) / G);
+            // (run, step) pairs of group g: its runs times the window's steps
+            const double nr = (double)((n_runs - g + G - 1) / G) * (double)window;
             const double N = s[0];
             est[g][0] = N * c.F_N / (nr * c.Vc);
             const double vx = s[1] / N, vy = s[2] / N, vz = s[3] / N;
@@ -1899,7 +1911,7 @@ __global__ void k_macro(StepArgs<T> a, int t, int n_runs, double* out)
         double* o = out + (int64_t)cell * 10;
         const double N = pooled[0];
         const double vx = pooled[1] / N, vy = pooled[2] / N, vz = pooled[3] / N;
-        o[0] = N * c.F_N / ((double)n_runs * c.Vc);
+        o[0] = N * c.F_N / ((double)n_runs * (double)window * c.Vc);
         o[1] = vx; o[2] = vy; o[3] = vz;
         o[4] = c.mass / (3.0 * kB) * ((pooled[4] + pooled[5] + pooled[6]) / N - (vx * vx + vy * vy + vz * vz));
         for (int q = 0; q < 5; ++q) {
@@ -2084,9 +2096,10 @@ void launch_sample_now(int prec, const void* args, cudaStream_t s)
     });
 }
 
-void launch_macro(int prec, const void* args, int sample, int n_runs, double* out, cudaStream_t s)
+void launch_macro(int prec, const void* args, int sample, int n_runs, int window, double* out,
+                  cudaStream_t s)
 {
-    DISPATCH_PREC(prec, (k_macro<T><<<64, 128, 0, s>>>(A<T>(args), sample, n_runs, out)));
+    DISPATCH_PREC(prec, (k_macro<T><<<64, 128, 0, s>>>(A<T>(args), sample, n_runs, window, out)));
 }
 
 void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)

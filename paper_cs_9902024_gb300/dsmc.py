@@ -31,7 +31,7 @@ EXPORTS = [
     "dsmc_last_error", "dsmc_debug_begin", "dsmc_debug_step", "dsmc_debug_get_state",
     "dsmc_debug_set_state", "dsmc_debug_get_cells", "dsmc_debug_get_cell_state",
     "dsmc_debug_set_cell_state", "dsmc_debug_sample", "dsmc_debug_philox",
-    "dsmc_run_ensemble_noalloc", "dsmc_debug_timeout_probe",
+    "dsmc_run_ensemble_noalloc", "dsmc_debug_timeout_probe", "dsmc_run_ensemble_windows",
 ]
 
 
@@ -120,6 +120,8 @@ def load_library(path=LIB_PATH):
         lib.dsmc_debug_sample.argtypes = [P, C.c_int, dp]
         lib.dsmc_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
         lib.dsmc_debug_timeout_probe.argtypes = [P, C.c_uint32]
+        lib.dsmc_run_ensemble_windows.argtypes = [P, C.c_int, C.c_double, C.c_int, ip, ip, C.c_int,
+                                                  C.c_uint64]
         lib.dsmc_run_ensemble_noalloc.argtypes = [P, C.c_int, C.c_double, C.c_int, ip, C.c_int,
                                                   C.c_uint64, dp, C.c_size_t]
         for name in EXPORTS:
@@ -245,19 +247,31 @@ class Ensemble:
             pass
 
     # -- main entry points -------------------------------------------------
-    def run(self, runs=None, steps=None, sample_steps=None, seed=None, dt=None):
+    def run(self, runs=None, steps=None, sample_steps=None, seed=None, dt=None, windows=None):
+        """dsmc_run_ensemble, or with windows=[(first, last), ...]
+        dsmc_run_ensemble_windows (time-averaged samples)."""
         w = self.w
         runs = w["runs"] if runs is None else runs
         steps = w["steps"] if steps is None else steps
-        ss = np.ascontiguousarray(w["sample_steps"] if sample_steps is None else sample_steps,
-                                  dtype=np.int32)
         seed = w["seed"] if seed is None else seed
         dt = w["dt"] if dt is None else dt
-        st = self.lib.dsmc_run_ensemble(self.h, runs, dt, steps,
-                                        _ptr(ss, C.c_int32) if len(ss) else None, len(ss), seed)
-        self._check(st, "dsmc_run_ensemble")
+        if windows is not None:
+            fi = np.ascontiguousarray([a for a, _ in windows], dtype=np.int32)
+            la = np.ascontiguousarray([b for _, b in windows], dtype=np.int32)
+            n = len(fi)
+            st = self.lib.dsmc_run_ensemble_windows(
+                self.h, runs, dt, steps, _ptr(fi, C.c_int32) if n else None,
+                _ptr(la, C.c_int32) if n else None, n, seed)
+            self._check(st, "dsmc_run_ensemble_windows")
+        else:
+            ss = np.ascontiguousarray(w["sample_steps"] if sample_steps is None else sample_steps,
+                                      dtype=np.int32)
+            n = len(ss)
+            st = self.lib.dsmc_run_ensemble(self.h, runs, dt, steps,
+                                            _ptr(ss, C.c_int32) if n else None, n, seed)
+            self._check(st, "dsmc_run_ensemble")
         self.runs = runs
-        self.n_samples = len(ss)
+        self.n_samples = n
         return self
 
     def run_noalloc(self, runs=None, steps=None, sample_steps=None, seed=None, dt=None):

@@ -166,3 +166,27 @@ def test_autotune_keeps_results(D):
     for k in ("generated", "removed", "candidates", "collisions", "particle_steps"):
         assert sa[k] == sb[k], k
     print("autotuned shape:", sa["shape"], "default:", sb["shape"])
+
+
+def test_sample_windows_match_oracle_and_modes(D):
+    """Time-averaged samples: FP64 device sums equal the oracle's (counts
+    exactly), plain == batched bit for bit, and the device density divides
+    by runs x window length."""
+    w = W.config0(runs=5, steps=60, n_samples=2)
+    win = [(10, 19), (40, 60)]
+    acc_o, _ = run_ensemble(w, windows=win)
+    e64 = D.Ensemble(w, precision="fp64").run(windows=win)
+    for t in range(2):
+        raw = e64.raw(t)
+        assert np.array_equal(raw[..., 0], acc_o[t][..., 0])
+        assert np.allclose(raw, acc_o[t], rtol=1e-9, atol=1e-6)
+    a = D.Ensemble(w).run(windows=win)
+    b = D.Ensemble(w, mode="plain").run(windows=win)
+    for t in range(2):
+        assert np.array_equal(a.raw(t), b.raw(t))
+    raw = a.raw(1)
+    m = a.macro(1)
+    d = [w["L"][k] / w["ncell"][k] for k in range(3)]
+    Vc = d[0] * d[1] * w["L"][2]
+    n_expect = raw[..., 0].sum(axis=0) * w["gas"]["F_N"] / (5 * 21 * Vc)
+    assert np.allclose(m["density"], n_expect, rtol=1e-12)

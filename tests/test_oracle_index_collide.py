@@ -196,3 +196,19 @@ def test_ensemble_groups_are_sums_of_runs():
                 ref[t, r % G] += o.sample(r)
                 t += 1
     assert np.array_equal(ref, acc1)
+
+
+def test_sample_windows_sum_single_step_samples():
+    """Time-averaged samples (Sec. 1.1's averaging interval): a window's
+    group sums are the sums of the one-step samples of its steps, and a
+    one-step window is the plain sample."""
+    from oracle import run_ensemble
+    from paper_cs_9902024_gb300 import workloads as W
+    w = W.config0(runs=3, steps=40, n_samples=2)
+    single, _ = run_ensemble(w, sample_steps=list(range(21, 31)))
+    win, _ = run_ensemble(w, windows=[(21, 30)])
+    assert np.array_equal(win[0][..., 0], single[..., 0].sum(axis=0))
+    assert np.allclose(win[0], single.sum(axis=0), rtol=1e-12, atol=1e-9)
+    one, _ = run_ensemble(w, windows=[(20, 20), (40, 40)])
+    plain, _ = run_ensemble(w, sample_steps=[20, 40])
+    assert np.array_equal(one, plain)
