@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <nvtx3/nvToolsExt.h>
 #include <new>
 #include <string>
 #include <vector>
@@ -256,6 +257,13 @@ static void* dev_alloc(dsmc_ctx* ctx, size_t bytes)
     if (p) ctx->bufs.push_back({p, bytes});
     return p;
 }
+
+// NVTX range for the profilers' timelines (header-only NVTX3; a no-op
+// when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 static void destroy_graphs(dsmc_ctx* ctx)
 {
@@ -625,6 +633,7 @@ static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, cons
 
 static dsmc_status build_graphs(dsmc_ctx* ctx, int n_runs)
 {
+    NvtxRange range("dsmc graph capture");
     const uint64_t key = (ctx->generation << 24) ^ (uint64_t)n_runs;
     if (ctx->graph_key == key && ctx->gexec[0][0] && ctx->gexec[0][1] && ctx->gexec[1][0] &&
         ctx->gexec[1][1])
@@ -777,6 +786,7 @@ static const int kTuneWindow = 6;
 
 static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
 {
+    NvtxRange range("dsmc autotune");
     const int r0 = (int)ctx->opt.run_offset;
     AnyArgs u;
     enqueue_init(ctx, build_args(ctx, u, 0, r0, n_runs));
@@ -860,6 +870,7 @@ static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
                                const int32_t* first, const int32_t* last, int n_samples,
                                uint64_t seed)
 {
+    NvtxRange range("dsmc_run_ensemble");
     if (!ctx) return DSMC_E_INVALID;
     CK(cudaSetDevice(ctx->device));
     dsmc_status st = validate_run(ctx, n_runs, dt, steps, first, last, n_samples);

@@ -98,3 +98,18 @@ def test_bounded_wait_timeout_reported(D):
     ens.close()
     ok = D.Ensemble(w).run()
     assert ok.stats()["error_word"] == 0
+
+
+def test_cell_over_the_limit_reported_not_faulted(D):
+    """Cells of ~9000 particles (above the 8192 per-cell limit) in FP32 and
+    FP64: the run returns DSMC_E_CAPACITY (BIGCELL), every particle is still
+    carried into the next pool, and nothing faults."""
+    for prec in ("fp32", "fp64"):
+        w = box(dim=2, ncell=(2, 2, 1), ppc=9000, dt=1e-6, runs=1, steps=2)
+        ens = D.Ensemble(w, precision=prec)
+        with pytest.raises(D.DsmcError) as ex:
+            ens.run()
+        assert ex.value.status == D.E_CAPACITY
+        assert ens.stats()["error_word"] & 0x4
+        assert ens.stats()["particles_now"] > 30000
+        ens.close()

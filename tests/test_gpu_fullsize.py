@@ -45,7 +45,7 @@ def _zfrac(mg, mo, mask):
 
 def test_bench_ensemble_full_size_within_3_combined_se(D):
     w = W.config1()
-    ens = D.Ensemble(w).run()
+    ens = D.Ensemble(w, autotune=True).run()     # as bench.py launches it
     T = len(w["sample_steps"])
     ms = [ens.macro(t) for t in range(T)]
     mg = {k: np.stack([m[k] for m in ms]) for k in ms[0]}
