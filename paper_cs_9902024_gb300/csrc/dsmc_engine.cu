@@ -2,10 +2,13 @@
 //
 // The engine owns the device buffers of one problem, sizes them from the
 // workload, and drives the step kernels either for all runs at once
-// (batched: one launch per kernel per step, one CUDA graph per step and
-// buffer parity) or one run after another (plain).  Everything a step
-// computes happens in the kernels of dsmc_kernels.cu; the host only derives
-// constants, allocates, launches and copies results out.
+// (batched: one launch per kernel per step, replayed from one of four CUDA
+// graphs -- buffer parity x whether the step closes a sample window --
+// with Generation forked beside Motion) or one run after another (plain,
+// direct launches with programmatic dependent launch).  It also holds the
+// launch-shape autotuner, the test hooks and the no-allocation entry point.
+// Everything a step computes happens in the kernels of dsmc_kernels.cu; the
+// host only derives constants, allocates, launches and copies results out.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -11,13 +11,11 @@ namespace dsmc {
 constexpr uint32_t kDead = 0xFFFFFFFFu;   // cell key of a particle that left
 constexpr int kMaxBounce = 16;            // surface events per particle and step
 constexpr int kGenBlocks = 64;            // Philox blocks per generated particle
-constexpr int kWarpMax = 128;             // cells up to this size: one warp each
-constexpr int kCellWarps = 8;             // warps per CTA of the cell kernel
-constexpr int kTileCells = 256;           // cells (= threads) per tile CTA
+constexpr int kWarpMax = 128;             // larger cells go to the one-CTA-per-cell kernels
+constexpr int kTileCells = 256;           // cells (= threads) per CTA of the sort/gather kernel
 constexpr int kGenElems = 2048;           // inflow elements per Generation CTA
 constexpr int kCollideCells = 128;        // cells (= threads) per CTA of the collision kernel
 constexpr int kCollideStage = 2816;       // particles whose velocities one collision CTA stages
-constexpr int kLaneMax = 512;             // largest cell of the tile path
 constexpr int kScanTile = 4096;           // cells per CTA of the scan
 constexpr int kScanThreads = 1024;
 constexpr int kMaxSamples = 4096;
