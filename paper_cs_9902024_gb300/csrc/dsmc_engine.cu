@@ -404,6 +404,10 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.hot.one_m_omega = (T)c.one_m_omega;
     a.hot.coef = c.coef;
     a.hot.coef_f = c.coef_f;
+    for (int r = 0; r < 10; ++r) {
+        a.hot.rk[2 * r] = (uint32_t)c.seed + (uint32_t)r * 0x9E3779B9u;
+        a.hot.rk[2 * r + 1] = (uint32_t)(c.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
     a.ctr = ctx->d_ctr;
     for (int ax = 0; ax < 3; ++ax) {
         a.xi[ax] = (T*)ctx->X[cur][ax];

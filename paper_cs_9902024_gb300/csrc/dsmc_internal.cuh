@@ -99,6 +99,7 @@ struct Hot {
     T A_hs, K_vhs, one_m_omega;
     double coef;
     float coef_f;
+    uint32_t rk[20];         // Philox4x32-10 round keys of the seed (rounds 0..9)
 };
 
 // Device pointers of one step (particle pool double-buffered: in -> out).

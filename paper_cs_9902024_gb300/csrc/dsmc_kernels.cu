@@ -60,6 +60,19 @@ __device__ __forceinline__ uint4 draw_bits(uint64_t seed, uint32_t run, uint32_t
                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
+// the same rounds with the key schedule precomputed (rk[2r], rk[2r + 1] =
+// the round-r key words), read from the launch parameters
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t* rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 // (m + 1/2) / 2^23 from the top 23 bits: exact in float and double
 template <typename T>
 __device__ __forceinline__ T u01(uint32_t x)
@@ -1075,6 +1088,20 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
+// a Philox draw through the configuration the caller holds: the Cfg
+// computes the key schedule, the launch-parameter constants carry it
+__device__ __forceinline__ uint4 draw_c(const Cfg& c, uint32_t run, uint32_t step, uint32_t entity,
+                                        uint32_t purpose, uint32_t sub)
+{
+    return draw_bits(c.seed, run, step, entity, purpose, sub);
+}
+template <typename T>
+__device__ __forceinline__ uint4 draw_c(const Hot<T>& c, uint32_t run, uint32_t step,
+                                        uint32_t entity, uint32_t purpose, uint32_t sub)
+{
+    return philox_rk(make_uint4(entity, (purpose << 28) | (sub & 0x0FFFFFFFu), step, run), c.rk);
+}
+
 // (sigma_T c_r) of a pair with relative speed squared g2 (and speed g)
 template <typename T, class C>
 __device__ __forceinline__ T sigma_cr(const C& c, T g, T g2)
@@ -1114,6 +1141,28 @@ __device__ __forceinline__ uint32_t pick(uint32_t bits, uint32_t n)
     return (uint32_t)((m2 * (uint64_t)n) >> 24);
 }
 
+// NTC acceptance u < sigma c_r / (sigma c_r)_max: FP64 state divides, as the
+// oracle does; FP32 state compares u (sigma c_r)_max < sigma c_r (no
+// division; FP32 collision arithmetic)
+template <typename T>
+__device__ __forceinline__ bool ntc_accept(T u, T sc, T smax) { return u < sc / smax; }
+template <>
+__device__ __forceinline__ bool ntc_accept<float>(float u, float sc, float smax) { return u * smax < sc; }
+
+// (cos eps, sin eps) of the azimuth eps = 2 pi u: FP64 by sincospi; FP32 by
+// the fast intrinsic on theta = pi (2u - 1) in [-pi, pi) (its accurate
+// range, absolute error ~4e-7), eps = theta + pi
+template <typename T>
+__device__ __forceinline__ void azimuth(T u, T* s, T* c) { dsincospi((T)2.0 * u, s, c); }
+template <>
+__device__ __forceinline__ void azimuth<float>(float u, float* s, float* c)
+{
+    float st, ct;
+    __sincosf(3.14159265358979f * (2.0f * u - 1.0f), &st, &ct);
+    *s = -st;
+    *c = -ct;
+}
+
 // one accepted collision: isotropic scattering of the relative velocity
 template <typename T>
 __device__ __forceinline__ void scatter_pair(T* v1, T* v2, T g, T u3, T ueps)
@@ -1123,7 +1172,7 @@ __device__ __forceinline__ void scatter_pair(T* v1, T* v2, T g, T u3, T ueps)
     // has no cancellation when cos(chi) is near +-1 (u3 and 1 - u3 are exact)
     const T sinx = (T)2.0 * dsqrt(u3 * ((T)1.0 - u3));
     T se, ce;
-    dsincospi((T)2.0 * ueps, &se, &ce);
+    azimuth<T>(ueps, &se, &ce);
     const T gr[3] = {g * cosx, g * sinx * ce, g * sinx * se};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
@@ -1147,8 +1196,8 @@ __device__ __forceinline__ void candidate_draws(const C& c, uint32_t run, uint32
                                                 uint32_t cell, int64_t k, uint32_t N, uint32_t& ci,
                                                 uint32_t& cj, T& u2, T& u3, T& ue)
 {
-    const uint4 r = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k));
-    const uint4 r2 = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k + 1));
+    const uint4 r = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k));
+    const uint4 r2 = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k + 1));
     ci = pick(r.x, N);
     cj = pick(r.y, N - 1u);
     if (cj >= ci) cj += 1u;
@@ -1165,7 +1214,7 @@ __device__ __forceinline__ void collide_candidate_lazy(const C& c, T* sv0, T* sv
                                                        int64_t k, uint32_t N, T smax, T& seen,
                                                        uint32_t& nacc, uint32_t& nclamp)
 {
-    const uint4 r = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k));
+    const uint4 r = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k));
     const uint32_t i = pick(r.x, N);
     uint32_t j = pick(r.y, N - 1u);
     if (j >= i) j += 1u;
@@ -1177,8 +1226,8 @@ __device__ __forceinline__ void collide_candidate_lazy(const C& c, T* sv0, T* sv
     const T sc = sigma_cr<T>(c, g, g2);
     if (sc > seen) seen = sc;
     if (sc > smax) nclamp++;
-    if (u01<T>(r.z) < sc / smax) {
-        const uint4 r2 = draw_bits(c.seed, run, step, cell, kColl, (uint32_t)(2 * k + 1));
+    if (ntc_accept<T>(u01<T>(r.z), sc, smax)) {
+        const uint4 r2 = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k + 1));
         scatter_pair<T>(v1, v2, g, u01<T>(r.w), u01<T>(r2.x));
         sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
         sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
@@ -1202,7 +1251,7 @@ __device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T*
     const T sc = sigma_cr<T>(c, g, g2);
     if (sc > seen) seen = sc;
     if (sc > smax) nclamp++;
-    if (u2 < sc / smax) {
+    if (ntc_accept<T>(u2, sc, smax)) {
         scatter_pair<T>(v1, v2, g, u3, ue);
         sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
         sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
