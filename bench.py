@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--runs", type=int, default=None, help="override runs per GPU")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the plain-mode, profile and CPU-baseline legs")
+    p.add_argument("--workload", default="config1",
+                   choices=["config0", "config1", "config2", "config3"],
+                   help="workload (default: the 512-run duct the metric is quoted on; the others "
+                        "are the parity workloads, measured the same way)")
     return p.parse_args()
 
 
@@ -54,12 +58,49 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(runs=None):
+WORKLOAD_TEXT = {
+    "config0": "2-D duct 64x32, HS, 8 runs x 200 steps, 4 sample times",
+    "config1": "2-D duct 64x32, HS, 512 runs x 400 steps, 8 sample times",
+    "config2": "2-D pulsed VHS jet 256x128, 64 runs x 1000 steps, 20 sample times",
+    "config3": "3-D plate box 128x64x64, HS, 16 runs x 600 steps, 12 sample times",
+}
+
+
+def workload(runs=None, name="config1"):
     from paper_cs_9902024_gb300 import workloads as W
-    w = W.config1()
+    w = W.by_name(name)
     if runs:
         w = W.scaled(w, runs=runs)
     return w
+
+
+# oracle sample: whole runs for the duct workloads; the first steps of up to
+# 16 runs for the large ones (a whole run of those takes minutes on a core)
+ORACLE_PROBE_STEPS = {"config0": None, "config1": None, "config2": 20, "config3": 4}
+
+
+def oracle_rate(w, threads, probe_steps, target_s):
+    """Particle-steps/s of the FP64 oracle (threads over run groups) on a
+    bounded sample of workload w sized to about target_s seconds: a probe of
+    up to 16 runs sizes the sample (more whole runs, or more steps)."""
+    from oracle import run_ensemble
+    runs, steps = w["runs"], w["steps"]
+    r0 = min(runs, 16)
+    s0 = steps if probe_steps is None else min(steps, probe_steps)
+    t0 = time.perf_counter()
+    run_ensemble(w, runs=r0, steps=s0, sample_steps=[], threads=threads)
+    tp = max(time.perf_counter() - t0, 1e-3)
+    if s0 == steps:
+        rs, ss = int(min(runs, max(r0, r0 * round(target_s / tp)))), steps
+    else:
+        # later steps can hold more particles than the probe's: at most 5x
+        rs, ss = r0, int(min(steps, 5 * s0, max(s0, s0 * target_s / tp)))
+    t0 = time.perf_counter()
+    _, st = run_ensemble(w, runs=rs, steps=ss, sample_steps=[], threads=threads)
+    dt = time.perf_counter() - t0
+    text = "%d of the %d runs x %d of the %d steps, FP64, %d thread(s) over run groups, %.1f s" % (
+        rs, runs, ss, steps, threads, dt)
+    return st["particle_steps"] / dt, text, dt
 
 
 def cpu_cores():
@@ -183,14 +224,17 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import run_ensemble
-    w = workload()
+    w = workload(name=args.workload)
     cores = min(cpu_cores(), 16)
-    sample_runs = 64
+    sample_runs = min(64, w["runs"])
+    probe = ORACLE_PROBE_STEPS[args.workload]
+    sample_steps = w["steps"] if probe is None else min(w["steps"], 5 * probe)
     wr = dict(w)
 
     def one():
         t0 = time.perf_counter()
-        _, st = run_ensemble(wr, runs=sample_runs, threads=cores)
+        _, st = run_ensemble(wr, runs=sample_runs, steps=sample_steps, sample_steps=[],
+                             threads=cores)
         return time.perf_counter() - t0, st["particle_steps"]
 
     for _ in range(args.warmup):
@@ -201,8 +245,8 @@ def run_reference(args):
         tot_t += dt
         tot_ps += ps
     value = tot_ps / tot_t
-    sample = "%d of the %d runs x %d steps of %s per step, FP64 oracle, %d threads over runs" % (
-        sample_runs, w["runs"], w["steps"], w["name"], cores)
+    sample = "%d of the %d runs x %d of the %d steps of %s per step, FP64 oracle, %d threads over runs" % (
+        sample_runs, w["runs"], sample_steps, w["steps"], w["name"], cores)
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
@@ -233,7 +277,7 @@ def main():
     g.build()
     from paper_cs_9902024_gb300.dsmc import Ensemble
     from paper_cs_9902024_gb300 import shard
-    w = workload(args.runs)
+    w = workload(args.runs, args.workload)
     runs = w["runs"]
     shard.groups(runs, ws)          # every rank must hold >= 16 runs when sharded
     steps = w["steps"]
@@ -297,9 +341,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["name"] + " (2-D duct 64x32, HS, 512 runs x 400 steps, "
-                   "8 sample times)", "runs_per_gpu": runs, "steps_per_run": steps,
-                   "cells_per_run": w["ncell"][0] * w["ncell"][1], "sample_times": n_samples,
+        "config": {"workload": w["name"] + " (" + WORKLOAD_TEXT[args.workload] + ")",
+                   "runs_per_gpu": runs, "steps_per_run": steps,
+                   "cells_per_run": int(np.prod([w["ncell"][a] for a in range(w["dim"])])),
+                   "sample_times": n_samples,
                    "mode": "batched, CUDA graph per step", "state": "fp32",
                    "sampling": "fp64 group sums", "l2": "inputs larger than L2 (pool ~1 GB)",
                    "parallelism": "runs sharded over %d GPU(s)" % ws},
@@ -310,11 +355,11 @@ def main():
         "particle_steps_per_step": ps_per_step,
     }
     if rank == 0 and ws == 1 and not args.no_extras:
-        # -- plain per-run loop on the same workload (a 64-run sample: the
-        #    per-run loop's cost is the same for every run) ---------------
-        plain_runs = 64
+        # -- plain per-run loop on the same workload (a sample of the runs:
+        #    the per-run loop's cost is the same for every run) ------------
+        plain_runs = max(2, min(64, runs // 8))
         pe = Ensemble(w, mode="plain", device=device, stream=stream)
-        pe.run(runs=8)
+        pe.run(runs=min(8, plain_runs))
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -372,22 +417,16 @@ def main():
                            "bytes_per_launch": algo[dom] / prs["launches_kernel"][dom]}
         out["kernels"] = kern
         out["profile_run_ms"] = prs["ms_steps"]
-        # -- the FP64 oracle on the host cores, bounded sample -------------
-        # (threads over run groups: at most G = 16).  A 16-run probe sizes
-        # the timed sample to about 15 s of host work.
-        from oracle import run_ensemble
+        # -- the FP64 oracle on the host cores, bounded samples (threads over
+        #    run groups: at most G = 16), and on one core ------------------
         cores = min(cpu_cores(), 16)
-        t0 = time.perf_counter()
-        run_ensemble(w, runs=16, threads=cores)
-        probe = time.perf_counter() - t0
-        cpu_runs = int(min(runs, max(16, 16 * round(15.0 / max(probe, 1e-3)))))
-        t0 = time.perf_counter()
-        _, sto = run_ensemble(w, runs=cpu_runs, threads=cores)
-        dt = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": sto["particle_steps"] / dt, "unit": UNIT, "cores": cores,
-                               "kind": "oracle",
-                               "sample": "%d of the %d runs x %d steps, FP64, %d threads over "
-                                         "run groups, %.1f s" % (cpu_runs, runs, steps, cores, dt)}
+        probe = ORACLE_PROBE_STEPS[args.workload]
+        rate, text, _ = oracle_rate(w, cores, probe, 15.0)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": text}
+        rate1, text1, _ = oracle_rate(w, 1, probe if probe is not None else 40, 8.0)
+        out["cpu_baseline_1core"] = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                     "sample": text1}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ens.close()
