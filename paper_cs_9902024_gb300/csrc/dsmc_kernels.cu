@@ -1729,8 +1729,9 @@ __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
 
 // ---------------------------------------------------------------------------
 // Cells above kWarpMax particles, part 1: one CTA of kBigThreads per cell,
-// (id, slot) keys sorted in shared memory (bitonic), the cell's particles
-// gathered into the next pool in id order.
+// the (id, slot) keys ranked in shared memory -- by counting smaller keys for
+// cells of up to kBigThreads particles, by a bitonic sort above -- and the
+// cell's particles gathered into the next pool in id order.
 constexpr int kBigThreads = 1024;
 
 template <typename T>
@@ -1765,6 +1766,34 @@ __global__ void __launch_bounds__(kBigThreads) k_cell_big(StepArgs<T> a)
                 for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
                 a.ci_o[o] = gcell;
                 a.ido[o] = e.y;
+                a.vo[0][o] = a.vi[0][s];
+                a.vo[1][o] = a.vi[1][s];
+                a.vo[2][o] = a.vi[2][s];
+                if (a.lcr_dbg) a.lcr_dbg[o] = s;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (N <= (uint32_t)kBigThreads) {
+            // up to one particle per thread: its rank is the number of
+            // smaller (id, slot) keys of the cell (broadcast reads, no
+            // barriers); the keys are unique, so the ranks are a permutation
+            const uint32_t k = threadIdx.x;
+            if (k < N) {
+                const uint2 e = a.lcr[beg + k];
+                keys[k] = ((unsigned long long)e.y << 32) | checked_slot(a, e.x);
+            }
+            __syncthreads();
+            if (k < N) {
+                const unsigned long long my = keys[k];
+                uint32_t r = 0;
+                for (uint32_t j = 0; j < N; ++j) r += keys[j] < my ? 1u : 0u;
+                const uint32_t s = (uint32_t)my;
+                const uint32_t o = beg + r;
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+                a.ci_o[o] = gcell;
+                a.ido[o] = (uint32_t)(my >> 32);
                 a.vo[0][o] = a.vi[0][s];
                 a.vo[1][o] = a.vi[1][s];
                 a.vo[2][o] = a.vi[2][s];
