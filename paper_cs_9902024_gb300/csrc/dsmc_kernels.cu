@@ -242,23 +242,6 @@ template <typename T, int DIM>
 __device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, uint32_t run,
                               uint32_t step, T tau, LocalCounters& lc, uint32_t& vmask);
 
-// move_particle on copies, out of line: its runtime-indexed arrays stay in
-// its own frame and the caller's fast path keeps its state in registers
-template <typename T, int DIM>
-__device__ __noinline__ bool move_particle_slow(const Cfg& c, int* ci, T* f, T* v, uint32_t id,
-                                                uint32_t run, uint32_t step, T tau,
-                                                LocalCounters& lc, uint32_t& vmask)
-{
-    int ci2[3] = {ci[0], ci[1], ci[2]};
-    T f2[3] = {f[0], f[1], f[2]};
-    T v2[3] = {v[0], v[1], v[2]};
-    const bool alive = move_particle<T, DIM>(c, ci2, f2, v2, id, run, step, tau, lc, vmask);
-    ci[0] = ci2[0]; ci[1] = ci2[1]; ci[2] = ci2[2];
-    f[0] = f2[0]; f[1] = f2[1]; f[2] = f2[2];
-    v[0] = v2[0]; v[1] = v2[1]; v[2] = v2[2];
-    return alive;
-}
-
 // Motion of one particle for time tau: free flight with the surface events
 // taken in time order (ties: x, y, z faces, then plates in list order).
 // Returns false if the particle left through an open face.  vmask collects
@@ -483,24 +466,6 @@ __device__ __forceinline__ void flush_counters(Counters* ctr, const LocalCounter
     }
 }
 
-// rank of each valid lane among the lanes of its warp with the same key,
-// plus one atomic per distinct key on count[key]
-__device__ __forceinline__ uint32_t warp_rank(uint32_t* count, uint32_t key, bool valid)
-{
-    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, valid);
-    uint32_t rank = 0;
-    if (valid) {
-        const uint32_t peers = __match_any_sync(mask, key);
-        const int leader = __ffs(peers) - 1;
-        const uint32_t lt = (1u << lane_id()) - 1u;
-        uint32_t base = 0;
-        if ((int)lane_id() == leader) base = atomicAdd(&count[key], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        rank = base + (uint32_t)__popc(peers & lt);
-    }
-    return rank;
-}
-
 // exclusive scan of one value per thread over the block (blockDim <= 1024)
 __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* smem_warp, uint32_t& total)
 {
@@ -527,28 +492,6 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* smem_warp, uint32
     total = smem_warp[nw - 1];
     __syncthreads();
     return before + x - v;
-}
-
-__device__ __forceinline__ uint32_t run_search(const uint32_t* run_base, int n_runs, uint32_t s)
-{
-    // largest r with run_base[r] <= s
-    int lo = 0, hi = n_runs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(run_base + mid) <= s) lo = mid; else hi = mid - 1;
-    }
-    return (uint32_t)lo;
-}
-
-// run of slot s for a warp whose slots start at s_first: every lane first
-// searches the same target (broadcast loads); lanes past that run's end
-// search their own slot
-__device__ __forceinline__ uint32_t run_of_slot(const uint32_t* run_base, int n_runs,
-                                                uint32_t s_first, uint32_t s)
-{
-    const uint32_t r0 = run_search(run_base, n_runs, s_first);
-    if (s < __ldg(run_base + r0 + 1)) return r0;
-    return run_search(run_base, n_runs, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -814,26 +757,6 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// 16-byte vector of four consecutive SoA elements
-template <typename T> struct Vec4;
-template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4_32a; };
-
-template <typename T>
-__device__ __forceinline__ void load4(const T* __restrict__ p, uint64_t s, T* out)
-{
-    const typename Vec4<T>::type q = *reinterpret_cast<const typename Vec4<T>::type*>(p + s);
-    out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
-}
-
-template <typename T>
-__device__ __forceinline__ void store4(T* __restrict__ p, uint64_t s, const T* in)
-{
-    typename Vec4<T>::type q;
-    q.x = in[0]; q.y = in[1]; q.z = in[2]; q.w = in[3];
-    *reinterpret_cast<typename Vec4<T>::type*>(p + s) = q;
-}
-
 // run of a run-major cell key: key / ncells by a 64-bit multiply-high
 // (exact for every 32-bit key, see the host's magic number)
 template <class C>
