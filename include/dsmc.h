@@ -157,6 +157,16 @@ typedef struct {
                                  time per particle; the real run then starts
                                  from t = 0.  Results do not depend on the
                                  shapes.  0 = fixed shapes (default) */
+    int32_t shape[4];         /* batched mode: entries > 0 replace the default
+                                 launch shape (as dsmc_stats.shape: Motion
+                                 CTAs, scatter CTAs, sort/gather tile budget
+                                 in particles, collision CTAs), e.g. a shape
+                                 an earlier autotune found; 0 keeps the
+                                 default.  CTA counts lie in [1, 2^20], the
+                                 tile budget in [256, 16384] (rounded up to a
+                                 multiple of 8); else DSMC_E_INVALID.  With
+                                 autotune the tuned shape replaces it.
+                                 Results do not depend on the shape. */
 } dsmc_options;
 
 typedef struct {

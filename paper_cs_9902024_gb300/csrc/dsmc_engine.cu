@@ -709,6 +709,14 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
         if (s.hi[0] > n0 || s.hi[1] > n1) return DSMC_E_INVALID;
         if (s.step_from < 0 || s.step_to < 0) return DSMC_E_INVALID;
     }
+    if (opt) {
+        for (int i = 0; i < 4; ++i) {
+            const int32_t v = opt->shape[i];
+            const bool ok = v == 0 || (i == 2 ? v >= 256 && v <= kMaxTileBudget
+                                              : v >= 1 && v <= (1 << 20));
+            if (!ok) return DSMC_E_INVALID;
+        }
+    }
     dsmc_ctx* ctx = new (std::nothrow) dsmc_ctx();
     if (!ctx) return DSMC_E_OOM;
     ctx->dom = *domain;
@@ -754,8 +762,13 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
         }
         ctx->own_stream = true;
     }
-    ctx->ls.tile_budget = 0;
+    // default shape (the occupancy of the tile kernel follows the budget),
+    // then the caller's entries
+    ctx->ls.tile_budget = ctx->opt.shape[2];
     compute_launch_shape(ctx->prec, ctx->dim, ctx->sms, &ctx->ls);
+    if (ctx->opt.shape[0] > 0) ctx->ls.move_blocks = ctx->opt.shape[0];
+    if (ctx->opt.shape[1] > 0) ctx->ls.scatter_blocks = ctx->opt.shape[1];
+    if (ctx->opt.shape[3] > 0) ctx->ls.collide_blocks = ctx->opt.shape[3];
     *out = ctx;
     return DSMC_OK;
 }

@@ -13,6 +13,7 @@ constexpr int kMaxBounce = 16;            // surface events per particle and ste
 constexpr int kGenBlocks = 64;            // Philox blocks per generated particle
 constexpr int kWarpMax = 128;             // larger cells go to the one-CTA-per-cell kernels
 constexpr int kTileCells = 256;           // cells (= threads) per CTA of the sort/gather kernel
+constexpr int kMaxTileBudget = 16384;     // largest particle budget of a sort/gather tile
 constexpr int kGenElems = 2048;           // inflow elements per Generation CTA
 constexpr int kCollideCells = 128;        // cells (= threads) per CTA of the collision kernel
 constexpr int kCollideStage = 2816;       // particles whose velocities one collision CTA stages

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <utility>
 
 #include "dsmc_internal.cuh"
@@ -2103,6 +2104,26 @@ void launch_macro(int prec, const void* args, int sample, int n_runs, int window
     DISPATCH_PREC(prec, (k_macro<T><<<64, 128, 0, s>>>(A<T>(args), sample, n_runs, window, out)));
 }
 
+// The tile kernel's dynamic shared-memory limit is a property of the
+// function, shared by every context of the process: it only ever rises, so
+// that a context whose tile budget is larger than a later context's keeps
+// launching.
+static cudaError_t raise_cell_smem_limit(int prec, int dim, size_t bytes)
+{
+    static std::mutex mu;
+    static size_t set[2][2] = {{0, 0}, {0, 0}};
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[prec == DSMC_FP64 ? 1 : 0][dim == 3 ? 1 : 0];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
+        e = cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+    }));
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
 {
     ls->dim = dim;
@@ -2114,9 +2135,8 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
     if (ls->tile_budget <= 0) ls->tile_budget = budget;
     ls->tile_budget = (ls->tile_budget + 7) / 8 * 8;
     int bm = 0, bc = 0;
+    raise_cell_smem_limit(prec, dim, cell_smem_bytes(prec, ls->tile_budget));
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
-        cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cell_smem_bytes(prec, ls->tile_budget));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_move<T, D>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_cell<T, D>, kTileCells,
                                                       cell_smem_bytes(prec, ls->tile_budget));
@@ -2143,13 +2163,10 @@ cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
         e = cudaFuncSetAttribute(k_cell_big<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)big_smem(prec));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)cell_smem_bytes(prec, tile_budget));
-        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)collide_smem(prec));
-
     }));
+    if (e == cudaSuccess) e = raise_cell_smem_limit(prec, dim, cell_smem_bytes(prec, tile_budget));
     return e;
 }
 

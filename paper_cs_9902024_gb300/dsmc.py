@@ -63,6 +63,9 @@ class Boundary(C.Structure):
                 ("n", C.c_double), ("T", C.c_double), ("U", C.c_double * 3)]
 
 
+# entries of dsmc_options.shape / dsmc_stats.shape
+SHAPE_KEYS = ("move_blocks", "scatter_blocks", "tile_budget", "collide_blocks")
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -73,7 +76,7 @@ class Options(C.Structure):
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("stream", C.c_void_p), ("use_graph", C.c_int32), ("debug", C.c_int32),
                 ("device", C.c_int32), ("profile", C.c_int32), ("run_offset", C.c_int64),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("shape", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -171,11 +174,15 @@ class Ensemble:
     """One problem (geometry, gas, boundaries) on one GPU.
 
     `mode`: "batched" (all runs per launch, CUDA graphs) or "plain" (one run
-    after another); `precision`: "fp32" or "fp64" particle state."""
+    after another); `precision`: "fp32" or "fp64" particle state;
+    `autotune`: search the launch shape on the first run of a size;
+    `shape`: a dict with any of SHAPE_KEYS replacing the default launch
+    shape (e.g. stats()["shape"] of a tuned ensemble)."""
 
     def __init__(self, w, mode="batched", precision="fp32", capacity_factor=0.0,
                  capacity_per_run=0, debug=False, profile=False, use_graph=True, device=0,
-                 torch_memory=True, stream=None, run_offset=0, autotune=False):
+                 torch_memory=True, stream=None, run_offset=0, autotune=False,
+                 shape=None):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise DsmcError(E_CUDA, "no CUDA device: the DSMC path has no CPU fallback")
@@ -196,6 +203,9 @@ class Ensemble:
         opt.device = device
         opt.run_offset = run_offset
         opt.autotune = 1 if autotune else 0
+        if shape:
+            for i, k in enumerate(SHAPE_KEYS):
+                opt.shape[i] = int(shape.get(k, 0))
         if torch_memory:
             dev = torch.device("cuda", device)
 
@@ -319,8 +329,7 @@ class Ensemble:
         self._check(self.lib.dsmc_get_stats(self.h, C.byref(s)), "dsmc_get_stats")
         d = {k: getattr(s, k) for k, _ in Stats._fields_
              if k not in ("ms_kernel", "launches_kernel", "shape")}
-        d["shape"] = {"move_blocks": s.shape[0], "scatter_blocks": s.shape[1],
-                      "tile_budget": s.shape[2], "collide_blocks": s.shape[3]}
+        d["shape"] = {k: s.shape[i] for i, k in enumerate(SHAPE_KEYS)}
         d["ms_kernel"] = {KERNEL_KINDS[i]: s.ms_kernel[i] for i in range(len(KERNEL_KINDS))}
         d["launches_kernel"] = {KERNEL_KINDS[i]: int(s.launches_kernel[i])
                                 for i in range(len(KERNEL_KINDS))}

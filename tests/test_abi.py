@@ -49,9 +49,11 @@ def test_ctypes_layout_matches_header():
     int main(void) {
       printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dsmc_domain), sizeof(dsmc_cells),
              sizeof(dsmc_gas), sizeof(dsmc_boundary), sizeof(dsmc_options), sizeof(dsmc_stats));
-      printf("%zu %zu %zu %zu %zu\n", offsetof(dsmc_boundary, n), offsetof(dsmc_options, stream),
-             offsetof(dsmc_options, profile), offsetof(dsmc_stats, ms_steps),
-             offsetof(dsmc_stats, launches_kernel));
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsmc_boundary, n),
+             offsetof(dsmc_options, stream), offsetof(dsmc_options, profile),
+             offsetof(dsmc_options, autotune), offsetof(dsmc_options, shape),
+             offsetof(dsmc_stats, ms_steps), offsetof(dsmc_stats, launches_kernel),
+             offsetof(dsmc_stats, shape));
       return 0;
     }
     """
@@ -66,7 +68,8 @@ def test_ctypes_layout_matches_header():
                      C.sizeof(D.Boundary), C.sizeof(D.Options), C.sizeof(D.Stats)]
     offs = [int(x) for x in lines[1].split()]
     assert offs == [D.Boundary.n.offset, D.Options.stream.offset, D.Options.profile.offset,
-                    D.Stats.ms_steps.offset, D.Stats.launches_kernel.offset]
+                    D.Options.autotune.offset, D.Options.shape.offset,
+                    D.Stats.ms_steps.offset, D.Stats.launches_kernel.offset, D.Stats.shape.offset]
 
 
 def _args():
@@ -105,6 +108,12 @@ def test_invalid_arguments_rejected_without_gpu(lib):
                            C.byref(h)) == D.E_INVALID
     assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(gas), arr, 33, C.byref(opt),
                            C.byref(h)) == D.E_INVALID
+    # launch-shape entries out of range
+    for i, v in ((0, -1), (1, 1 << 21), (2, 255), (2, 16385), (3, -5)):
+        bo = D.Options.from_buffer_copy(opt)
+        bo.shape[i] = v
+        assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(gas), arr, nb, C.byref(bo),
+                               C.byref(h)) == D.E_INVALID
     assert not h.value
     # calls on a null context fail cleanly
     assert lib.dsmc_run_ensemble(None, 1, 1e-6, 1, None, 0, 1) == D.E_INVALID

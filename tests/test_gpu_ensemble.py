@@ -166,6 +166,36 @@ def test_autotune_keeps_results(D):
     for k in ("generated", "removed", "candidates", "collisions", "particle_steps"):
         assert sa[k] == sb[k], k
     print("autotuned shape:", sa["shape"], "default:", sb["shape"])
+    # the tuned shape given explicitly to a new context: same shape, same sums
+    c = D.Ensemble(w, shape=sa["shape"]).run()
+    assert c.stats()["shape"] == sa["shape"] and c.stats()["tuned"] == 0
+    for t in range(3):
+        assert np.array_equal(a.raw(t), c.raw(t))
+
+
+def test_explicit_launch_shape(D):
+    """options.shape replaces the default launch shape entry by entry; the
+    group sums do not change, including a small tile budget (most tiles on
+    the per-cell path) created after a context with a large budget (the tile
+    kernel's shared-memory limit must not drop under the larger context).
+    Out-of-range entries are refused."""
+    w = W.config0(runs=16, steps=40, n_samples=2)
+    big = D.Ensemble(w, shape={"tile_budget": 16384, "move_blocks": 152})
+    ref = D.Ensemble(w).run()
+    small = D.Ensemble(w, shape={"tile_budget": 256, "scatter_blocks": 7,
+                                 "collide_blocks": 3}).run()
+    big.run()
+    assert big.stats()["shape"]["tile_budget"] == 16384
+    assert big.stats()["shape"]["move_blocks"] == 152
+    s = small.stats()["shape"]
+    assert (s["tile_budget"], s["scatter_blocks"], s["collide_blocks"]) == (256, 7, 3)
+    for t in range(2):
+        assert np.array_equal(ref.raw(t), small.raw(t))
+        assert np.array_equal(ref.raw(t), big.raw(t))
+    for bad in ({"tile_budget": 100}, {"tile_budget": 20000}, {"move_blocks": -1},
+                {"collide_blocks": 1 << 21}):
+        with pytest.raises(D.DsmcError):
+            D.Ensemble(w, shape=bad)
 
 
 def test_sample_windows_match_oracle_and_modes(D):
