@@ -181,11 +181,15 @@ def measured_peaks():
 
 
 def kernel_hash():
+    # the device code: the kernel source up to its host launchers, and the
+    # shared header
     h = hashlib.sha256()
     for p in ("paper_cs_9902024_gb300/csrc/dsmc_kernels.cu",
               "paper_cs_9902024_gb300/csrc/dsmc_internal.cuh"):
         with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+            text = f.read()
+        cut = text.find(b"\n// Host launchers\n")
+        h.update(text if cut < 0 else text[:cut])
     return h.hexdigest()[:16]
 
 
@@ -197,6 +201,9 @@ def algorithmic_bytes(w, st, steps, runs):
     cells = runs * w["ncell"][0] * w["ncell"][1] * (w["ncell"][2] if D == 3 else 1)
     moved_old = st["particle_steps"] - st["generated"]
     pool = st["pool_steps"]
+    big = st.get("big_pool_steps", 0)
+    # read the LCR entry, gather offsets and v; write offsets, cell key, id, v
+    gather = 8 + 2 * (D * t + 3 * t) + 8
     return {
         # read the in-cell offsets (D), v (D; the third component only at
         # wall hits) and the cell key, write the offsets (D), the new key
@@ -204,9 +211,10 @@ def algorithmic_bytes(w, st, steps, runs):
         "move": moved_old * (3 * D * t + 4 + 8),
         # read key, rank and id, write the LCR entry (slot, id)
         "scatter": pool * 20,
-        # read the LCR entry, gather offsets and v; write offsets, cell key,
-        # id, v
-        "cell": pool * (8 + 2 * (D * t + 3 * t) + 8) + cells * steps * 4,
+        # the tile kernel: particles of cells up to 128 (+ the start table);
+        # cells above 128 particles: one CTA per cell, the same bytes
+        "cell": (pool - big) * gather + cells * steps * 4,
+        "cell_big": big * gather,
         # per cell: start, NTC remainder (read + write), (sigma c_r)_max;
         # every particle's velocity read once, both velocities of every
         # collision written
@@ -416,7 +424,10 @@ def main():
                 ent = tj.get(dom)
                 if ent and ent.get("kernel_hash") == kernel_hash():
                     per_particle = ent["dram_bytes"] / ent["particles"]
-                    traffic = per_particle * prs["pool_steps"] / prs["launches_kernel"][dom]
+                    units = prs["pool_steps"]
+                    if dom == "cell":
+                        units -= prs["big_pool_steps"]
+                    traffic = per_particle * units / prs["launches_kernel"][dom]
             except Exception:
                 traffic = None
         out["roofline"] = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved,

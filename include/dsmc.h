@@ -192,6 +192,9 @@ typedef struct {
                                  CTAs, sort/gather tile budget (particles),
                                  collision CTAs */
     int32_t tuned;            /* 1 if the shape came from options.autotune */
+    uint64_t big_pool_steps;  /* the part of pool_steps in cells above 128
+                                 particles (ordered and gathered one cell per
+                                 CTA) */
 } dsmc_stats;
 
 /* device error bits */
@@ -204,7 +207,7 @@ typedef struct {
 /* kernel kinds of dsmc_stats.ms_kernel */
 enum { DSMC_K_GENERATE = 0, DSMC_K_MOVE = 1, DSMC_K_SCAN = 2, DSMC_K_SCATTER = 3,
        DSMC_K_CELL = 4, DSMC_K_CELL_BIG = 5, DSMC_K_REDUCE = 6, DSMC_K_OTHER = 7,
-       DSMC_K_COLLIDE = 8 };
+       DSMC_K_COLLIDE = 8, DSMC_K_COLLIDE_BIG = 9 };
 
 typedef struct dsmc_ctx dsmc_ctx;
 

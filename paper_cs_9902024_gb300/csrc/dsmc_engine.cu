@@ -507,15 +507,19 @@ static void enqueue_step(dsmc_ctx* ctx, const void* args, size_t* ev, bool fork 
     launch_scatter(p, args, ls, s); mark();
     launch_cell(p, args, ls, s); mark();
     launch_cell_big(p, args, ls, s); mark();
+    launch_collide_big(p, args, ls, s); mark();
     launch_collide(p, args, ls, s); mark();
     if (reduce) launch_reduce(p, args, ls, s);
     mark();
     launch_step_end(p, args, ls, s); mark();
 }
-static const int kStepKernels = 9;
-static const int kKindOf[kStepKernels] = {DSMC_K_GENERATE, DSMC_K_MOVE,     DSMC_K_SCAN,
-                                          DSMC_K_SCATTER,  DSMC_K_CELL,     DSMC_K_CELL_BIG,
-                                          DSMC_K_COLLIDE,  DSMC_K_REDUCE,   DSMC_K_OTHER};
+static const int kStepKernels = 10;
+static const int kKindOf[kStepKernels] = {DSMC_K_GENERATE,  DSMC_K_MOVE,        DSMC_K_SCAN,
+                                          DSMC_K_SCATTER,   DSMC_K_CELL,        DSMC_K_CELL_BIG,
+                                          DSMC_K_COLLIDE_BIG, DSMC_K_COLLIDE,   DSMC_K_REDUCE,
+                                          DSMC_K_OTHER};
+// position of each tuned kernel group in enqueue_step's order
+static const int kGroupMove = 1, kGroupScatter = 3, kGroupCell = 4, kGroupCollide = 7;
 
 static void enqueue_init(dsmc_ctx* ctx, const void* args)
 {
@@ -557,6 +561,7 @@ static void fill_stats(dsmc_ctx* ctx, const Counters& h)
     s.bounce_limit = h.bounce_limit;
     s.reject_limit = h.reject_limit;
     s.pool_steps = h.pool_steps;
+    s.big_pool_steps = h.big_pool_steps;
     s.error_word = h.error;
     s.capacity = ctx->cap_old;
     s.shape[0] = ctx->ls.move_blocks;
@@ -859,7 +864,7 @@ static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
             compute_launch_shape(ctx->prec, ctx->dim, sms, &ls);
             CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget));
             double cst = 0.0;
-            if ((st = window(4, &cst))) return st;
+            if ((st = window(kGroupCell, &cst))) return st;
             if (cst < best_cost) { best_cost = cst; best = cand[k]; }
         }
         ls.tile_budget = best;
@@ -868,9 +873,9 @@ static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
     }
     struct Knob { int* v; int group; int cand[3]; };
     const int mb = ls.move_blocks, cb = ls.collide_blocks;
-    Knob knobs[3] = {{&ls.move_blocks, 1, {mb, 2 * mb, 0}},
-                     {&ls.scatter_blocks, 3, {4 * sms, 8 * sms, 16 * sms}},
-                     {&ls.collide_blocks, 6, {cb, 2 * cb, 0}}};
+    Knob knobs[3] = {{&ls.move_blocks, kGroupMove, {mb, 2 * mb, 0}},
+                     {&ls.scatter_blocks, kGroupScatter, {4 * sms, 8 * sms, 16 * sms}},
+                     {&ls.collide_blocks, kGroupCollide, {cb, 2 * cb, 0}}};
     for (Knob& kn : knobs) {
         int best = *kn.v;
         double best_cost = 1e300;

@@ -72,6 +72,7 @@ struct Counters {
     unsigned long long particle_steps, generated, removed, wall_hits;
     unsigned long long candidates, collisions, clamps, bounce_limit, reject_limit;
     unsigned long long pool_steps;
+    unsigned long long big_pool_steps;   // particles ordered by the one-CTA-per-cell kernel
     uint32_t error, step, n_big, n_slow;
     uint32_t probe;        // error bits of the timeout test hook only
 };
@@ -166,6 +167,7 @@ void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t
 void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
+void launch_collide_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
 void launch_step_end(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);

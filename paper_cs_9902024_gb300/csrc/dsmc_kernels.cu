@@ -16,8 +16,9 @@
 //   k_cell       one CTA per 256 cells: each cell's particles put in
 //                particle-id order and gathered into the next pool
 //                (Indexing)
-//   k_cell_big   one CTA per cell above 128 particles: the cell ordered by
-//                id (bitonic sort) and gathered into the next pool
+//   k_cell_big   cells above 128 particles (a CTA, or a quarter CTA, per
+//                cell): the cell ordered by id (LSD radix sort of the ids)
+//                and gathered into the next pool
 //   k_collide_big one warp per such cell: NTC collisions (disjoint pairs
 //                side by side) and moments
 //   k_collide    one thread per cell, a tile's velocities staged in shared
@@ -1652,117 +1653,248 @@ __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// Cells above kWarpMax particles, part 1: one CTA of kBigThreads per cell,
-// the (id, slot) keys ranked in shared memory -- by counting smaller keys for
-// cells of up to kBigThreads particles, by a bitonic sort above -- and the
-// cell's particles gathered into the next pool in id order.
+// Cells above kWarpMax particles, part 1: each cell's particles put in id
+// order and gathered into the next pool.  The order comes from an LSD radix
+// sort of the ids relative to the cell's smallest id, 8 bits a pass (as many
+// passes as the ids' span needs, at most 4), on 16-bit positions into the
+// cell's keys staged in shared memory.  Each pass is a stable counting sort:
+// warp w ranks the chunks of its contiguous range in order (match_any
+// groups equal digits; the group's first lane advances the warp's count of
+// that digit), an exclusive scan of the counts in (digit, warp) order gives
+// each (digit, warp) its first destination, and every position moves there
+// plus its rank.  Stable passes make every result a permutation.  A CTA of
+// kBigThreads takes the cells above kBigThreads particles one at a time,
+// then splits into groups of kMidThreads (named barriers) that take the
+// smaller ones, a cell per group.
 constexpr int kBigThreads = 1024;
+constexpr int kMidThreads = 256;
+constexpr int kMidGroups = kBigThreads / kMidThreads;
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
 
 template <typename T>
 __host__ __device__ constexpr int big_max_of() { return 8192; }
 
+// shared memory of order_cell for THREADS threads and cells up to KMAX
+// particles: ids (u32), slots (u32), two position buffers (u16), the
+// (digit, warp) counts (u16; one 16-byte word per thread)
+template <int THREADS, int KMAX>
+__host__ __device__ constexpr size_t order_smem()
+{
+    return (size_t)KMAX * (4 + 4 + 2 + 2) + (size_t)kRadixBins * (THREADS / 32) * sizeof(uint16_t);
+}
+
+__host__ __device__ constexpr size_t big_smem_bytes()
+{
+    return order_smem<kBigThreads, big_max_of<float>()>() >
+                   kMidGroups * order_smem<kMidThreads, kBigThreads>()
+               ? order_smem<kBigThreads, big_max_of<float>()>()
+               : kMidGroups * order_smem<kMidThreads, kBigThreads>();
+}
+
+// barrier of the THREADS threads that order one cell: the whole CTA, or a
+// named barrier of one group
+template <int THREADS>
+__device__ __forceinline__ void order_sync(uint32_t bar)
+{
+    if (THREADS == kBigThreads) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(THREADS) : "memory");
+}
+
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBigThreads) k_cell_big(StepArgs<T> a)
+__device__ __forceinline__ void big_put(const StepArgs<T>& a, uint32_t o, uint32_t s, uint32_t id,
+                                        uint32_t gcell)
+{
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
+    a.ci_o[o] = gcell;
+    a.ido[o] = id;
+    a.vo[0][o] = a.vi[0][s];
+    a.vo[1][o] = a.vi[1][s];
+    a.vo[2][o] = a.vi[2][s];
+    if (a.lcr_dbg) a.lcr_dbg[o] = s;
+}
+
+// One cell of N particles (KMAX / 8 < N <= KMAX) ordered by id and gathered
+// by THREADS threads (t = 0 .. THREADS - 1, barrier `bar`) on `sm`
+// (order_smem bytes, 16-byte aligned) and `red` (2 x THREADS / 32 words).
+// Every thread of the group calls it with the same cell.
+template <int THREADS, int KMAX, typename T, int DIM>
+__device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell, uint32_t beg,
+                                           uint32_t N, unsigned char* sm, uint32_t* red, uint32_t t,
+                                           uint32_t bar)
+{
+    constexpr uint32_t W = THREADS / 32;
+    static_assert(KMAX <= 8 * THREADS, "at most 8 chunks of 32 per warp (8-bit ranks)");
+    static_assert(kRadixBins * W * sizeof(uint16_t) == THREADS * 16,
+                  "one 16-byte word of counts per thread");
+    uint32_t* s_id = reinterpret_cast<uint32_t*>(sm);
+    uint32_t* s_slot = s_id + KMAX;
+    uint16_t* pa = reinterpret_cast<uint16_t*>(s_slot + KMAX);
+    uint16_t* pb = pa + KMAX;
+    uint16_t* cnt = pb + KMAX;   // [digit][warp]
+    const uint32_t lane = t & 31u, w = t >> 5;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (uint32_t k = t; k < N; k += THREADS) {
+        const uint2 e = a.lcr[beg + k];
+        s_id[k] = e.y;
+        s_slot[k] = checked_slot(a, e.x);
+        pa[k] = (uint16_t)k;
+        lo = min(lo, e.y);
+        hi = max(hi, e.y);
+    }
+    lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+    hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+    if (lane == 0) { red[w] = lo; red[W + w] = hi; }
+    order_sync<THREADS>(bar);
+    lo = __reduce_min_sync(0xFFFFFFFFu, lane < W ? red[lane] : 0xFFFFFFFFu);
+    hi = __reduce_max_sync(0xFFFFFFFFu, lane < W ? red[W + lane] : 0u);
+    const uint32_t span = hi - lo;
+    const int passes = span == 0u ? 0 : (32 - __clz(span) + kRadixBits - 1) / kRadixBits;
+    // warp w owns positions [w * C * 32, (w + 1) * C * 32), C <= 8
+    const uint32_t C = (N + THREADS - 1) / THREADS;
+    const uint32_t wbase = w * C * 32u;
+    const uint32_t below = (1u << lane) - 1u;
+    for (int p = 0; p < passes; ++p) {
+        const int sh = p * kRadixBits;
+        order_sync<THREADS>(bar);   // the previous pass's reads of cnt, pa and red done
+        reinterpret_cast<uint4*>(cnt)[t] = make_uint4(0u, 0u, 0u, 0u);
+        order_sync<THREADS>(bar);
+        // (1) rank of each position among the equal digits of its warp range
+        uint32_t rk0 = 0u, rk1 = 0u;
+#pragma unroll
+        for (uint32_t c = 0; c < 8u; ++c) {
+            if (c < C) {
+                const uint32_t e = wbase + c * 32u + lane;
+                const bool ok = e < N;
+                const uint32_t d = ok ? ((s_id[pa[e]] - lo) >> sh) & (kRadixBins - 1u)
+                                      : (uint32_t)kRadixBins;
+                const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+                const uint32_t before = ok ? (uint32_t)cnt[d * W + w] : 0u;
+                const uint32_t r = before + __popc(peers & below);
+                __syncwarp();
+                if (ok && (peers & below) == 0u) cnt[d * W + w] = (uint16_t)(before + __popc(peers));
+                __syncwarp();
+                if (c < 4u) rk0 |= r << (8u * c);
+                else rk1 |= r << (8u * (c - 4u));
+            }
+        }
+        order_sync<THREADS>(bar);
+        // (2) exclusive scan of the counts in (digit, warp) order: eight
+        // consecutive counts per thread, then across the threads
+        uint4 q = reinterpret_cast<const uint4*>(cnt)[t];
+        uint32_t v[8] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16,
+                         q.z & 0xFFFFu, q.z >> 16, q.w & 0xFFFFu, q.w >> 16};
+        uint32_t tot = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tot += v[i];
+        uint32_t x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31u) red[w] = x;
+        order_sync<THREADS>(bar);
+        if (w == 0) {
+            const uint32_t ws = lane < W ? red[lane] : 0u;
+            uint32_t z = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+                if (lane >= (uint32_t)o) z += y;
+            }
+            if (lane < W) red[W + lane] = z - ws;
+        }
+        order_sync<THREADS>(bar);
+        uint32_t run = red[W + w] + x - tot;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t u = v[i];
+            v[i] = run;
+            run += u;
+        }
+        q.x = v[0] | (v[1] << 16);
+        q.y = v[2] | (v[3] << 16);
+        q.z = v[4] | (v[5] << 16);
+        q.w = v[6] | (v[7] << 16);
+        reinterpret_cast<uint4*>(cnt)[t] = q;
+        order_sync<THREADS>(bar);
+        // (3) every position to its (digit, warp) start plus its rank
+#pragma unroll
+        for (uint32_t c = 0; c < 8u; ++c) {
+            if (c < C) {
+                const uint32_t e = wbase + c * 32u + lane;
+                if (e < N) {
+                    const uint32_t pe = pa[e];
+                    const uint32_t d = ((s_id[pe] - lo) >> sh) & (kRadixBins - 1u);
+                    const uint32_t r = (c < 4u ? rk0 >> (8u * c) : rk1 >> (8u * (c - 4u))) & 0xFFu;
+                    pb[cnt[d * W + w] + r] = (uint16_t)pe;
+                }
+            }
+        }
+        uint16_t* sw = pa;
+        pa = pb;
+        pb = sw;
+    }
+    order_sync<THREADS>(bar);
+    for (uint32_t r = t; r < N; r += THREADS) {
+        const uint32_t pe = pa[r];
+        big_put<T, DIM>(a, beg + r, s_slot[pe], s_id[pe], gcell);
+    }
+    order_sync<THREADS>(bar);   // buffers free for the group's next cell
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_red[2 * (kBigThreads / 32)];
     constexpr int kMax = big_max_of<T>();
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
+    const uint32_t tid = threadIdx.x;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
+    // (1) cells above kBigThreads particles: the whole CTA per cell
     for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
         const uint32_t gcell = a.big_list[bi];
         const uint32_t beg = a.start[gcell];
         const uint32_t N = a.start[gcell + 1] - beg;
+        if (N <= (uint32_t)kBigThreads) continue;
         if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
-            if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+            if (tid == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
             continue;
         }
+        if (tid == 0) atomicAdd(&a.ctr->big_pool_steps, (unsigned long long)N);
         if (N > (uint32_t)kMax) {
             // over the per-cell limit: reported, and the particles are still
             // carried into the next pool (in LCR order), so that the next
             // step reads no unwritten slot
-            if (threadIdx.x == 0) atomicOr(&a.ctr->error, DSMC_ERR_BIGCELL);
-            for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
+            if (tid == 0) atomicOr(&a.ctr->error, DSMC_ERR_BIGCELL);
+            for (uint32_t r = tid; r < N; r += blockDim.x) {
                 const uint2 e = a.lcr[beg + r];
-                const uint32_t s = checked_slot(a, e.x);
-                const uint32_t o = beg + r;
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-                a.ci_o[o] = gcell;
-                a.ido[o] = e.y;
-                a.vo[0][o] = a.vi[0][s];
-                a.vo[1][o] = a.vi[1][s];
-                a.vo[2][o] = a.vi[2][s];
-                if (a.lcr_dbg) a.lcr_dbg[o] = s;
+                big_put<T, DIM>(a, beg + r, checked_slot(a, e.x), e.y, gcell);
             }
-            __syncthreads();
             continue;
         }
-        if (N <= (uint32_t)kBigThreads) {
-            // up to one particle per thread: its rank is the number of
-            // smaller (id, slot) keys of the cell (broadcast reads, no
-            // barriers); the keys are unique, so the ranks are a permutation
-            const uint32_t k = threadIdx.x;
-            if (k < N) {
-                const uint2 e = a.lcr[beg + k];
-                keys[k] = ((unsigned long long)e.y << 32) | checked_slot(a, e.x);
-            }
-            __syncthreads();
-            if (k < N) {
-                const unsigned long long my = keys[k];
-                uint32_t r = 0;
-                for (uint32_t j = 0; j < N; ++j) r += keys[j] < my ? 1u : 0u;
-                const uint32_t s = (uint32_t)my;
-                const uint32_t o = beg + r;
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-                a.ci_o[o] = gcell;
-                a.ido[o] = (uint32_t)(my >> 32);
-                a.vo[0][o] = a.vi[0][s];
-                a.vo[1][o] = a.vi[1][s];
-                a.vo[2][o] = a.vi[2][s];
-                if (a.lcr_dbg) a.lcr_dbg[o] = s;
-            }
-            __syncthreads();
+        order_cell<kBigThreads, kMax, T, DIM>(a, gcell, beg, N, smem_raw, s_red, tid, 0u);
+    }
+    __syncthreads();
+    // (2) cells of kWarpMax + 1 .. kBigThreads particles: a group of
+    // kMidThreads per cell, kMidGroups groups side by side
+    const uint32_t g = tid / kMidThreads, tg = tid % kMidThreads;
+    unsigned char* sm = smem_raw + (size_t)g * order_smem<kMidThreads, kBigThreads>();
+    uint32_t* red = s_red + g * 2 * (kMidThreads / 32);
+    for (uint32_t bi = blockIdx.x * kMidGroups + g; bi < nb; bi += gridDim.x * kMidGroups) {
+        const uint32_t gcell = a.big_list[bi];
+        const uint32_t beg = a.start[gcell];
+        const uint32_t N = a.start[gcell + 1] - beg;
+        if (N > (uint32_t)kBigThreads) continue;
+        if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
+            if (tg == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
             continue;
         }
-        uint32_t P = 1;
-        while (P < N) P <<= 1;
-        for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) {
-            if (k < N) {
-                const uint2 e = a.lcr[beg + k];
-                keys[k] = ((unsigned long long)e.y << 32) | checked_slot(a, e.x);
-            } else {
-                keys[k] = ~0ull;
-            }
-        }
-        __syncthreads();
-        for (uint32_t size = 2; size <= P; size <<= 1) {
-            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-                for (uint32_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                    const uint32_t i = 2 * t - (t & (stride - 1));
-                    const uint32_t j = i + stride;
-                    const bool up = (i & size) == 0;
-                    const unsigned long long ki = keys[i], kj = keys[j];
-                    if ((ki > kj) == up) { keys[i] = kj; keys[j] = ki; }
-                }
-                __syncthreads();
-            }
-        }
-        for (uint32_t r = threadIdx.x; r < N; r += blockDim.x) {
-            const unsigned long long kk = keys[r];
-            const uint32_t s = (uint32_t)kk;
-            const uint32_t o = beg + r;
-#pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
-            a.ci_o[o] = gcell;
-            a.ido[o] = (uint32_t)(kk >> 32);
-            a.vo[0][o] = a.vi[0][s];
-            a.vo[1][o] = a.vi[1][s];
-            a.vo[2][o] = a.vi[2][s];
-            if (a.lcr_dbg) a.lcr_dbg[o] = s;
-        }
-        __syncthreads();
+        if (tg == 0) atomicAdd(&a.ctr->big_pool_steps, (unsigned long long)N);
+        order_cell<kMidThreads, kBigThreads, T, DIM>(a, gcell, beg, N, sm, red, tg, 1u + g);
     }
 }
 
@@ -2069,15 +2201,17 @@ void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStrea
 
 int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
 
-static size_t big_smem(int) { return 8 * (size_t)big_max_of<float>(); }
+static size_t big_smem(int) { return big_smem_bytes(); }
 
 void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
 {
-    DISPATCH_PREC(prec, {
-        DISPATCH_DIM(ls.dim, launch_pdl(ls, k_cell_big<T, D>, ls.big_blocks, kBigThreads, big_smem(prec), s,
-                                        A<T>(args)));
-        launch_pdl(ls, k_collide_big<T>, ls.sms * 2, 256, 0, s, A<T>(args));
-    });
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, launch_pdl(ls, k_cell_big<T, D>, ls.big_blocks, kBigThreads,
+                                                        big_smem(prec), s, A<T>(args))));
+}
+
+void launch_collide_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, launch_pdl(ls, k_collide_big<T>, ls.sms * 2, 256, 0, s, A<T>(args)));
 }
 
 void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)

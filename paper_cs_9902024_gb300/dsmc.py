@@ -24,7 +24,7 @@ Q_RAW, Q_DENSITY, Q_VELOCITY, Q_TEMPERATURE, Q_SE_DENSITY, Q_SE_VELOCITY, Q_SE_T
 NMOM = 7
 MAX_BC = 32
 KERNEL_KINDS = ["generate", "move", "scan", "scatter", "cell", "cell_big", "reduce", "other",
-                "collide"]
+                "collide", "collide_big"]
 
 EXPORTS = [
     "dsmc_create", "dsmc_run_ensemble", "dsmc_get_samples", "dsmc_get_stats", "dsmc_destroy",
@@ -86,7 +86,7 @@ class Stats(C.Structure):
         ("error_word", C.c_uint32), ("steps_done", C.c_int32), ("particles_now", C.c_int64),
         ("capacity", C.c_int64), ("ms_steps", C.c_double), ("ms_kernel", C.c_double * 12),
         ("launches_kernel", C.c_int64 * 12), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-        ("shape", C.c_int32 * 4), ("tuned", C.c_int32)]
+        ("shape", C.c_int32 * 4), ("tuned", C.c_int32), ("big_pool_steps", C.c_uint64)]
 
 
 _lib = None

@@ -109,7 +109,7 @@ def test_pulsed_jet_full_grid_fp64_exact(D):
     w = W.config2(runs=1)
     ens, orc = _lockstep_one_run(D, w, 12)
     cnt = _exact_one_run(ens, orc, w)
-    assert cnt.max() > 128          # cells of the one-CTA-per-cell path
+    assert cnt.max() > 1024         # cells of the radix-sorted one-CTA-per-cell path
     st = ens.stats()
     so = orc.stats(0)
     for k in ("generated", "removed", "wall_hits", "candidates", "collisions"):

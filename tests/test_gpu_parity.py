@@ -106,6 +106,63 @@ def test_fp64_jet_big_cells_and_pulse(D):
     assert ens.stats()["collisions"] > 0
 
 
+def test_fp64_big_cells_wide_id_spans(D):
+    """Cells of 129 to 8000 particles (the radix-sorted paths: a quarter CTA
+    per cell up to 1024 particles, a whole CTA above) whose ids span 2, 3
+    and 4 radix digits -- up to the whole u32 range -- placed in shuffled
+    pool order on both sides: after one step every cell's particles are in
+    id order (LCR), and counts, NTC counts and the state agree exactly with
+    the oracle."""
+    from tests.helpers import box
+    w = box(dim=2, ncell=(6, 4, 1), ppc=50, dt=1e-7, runs=1, steps=1, fill=0)
+    rng = np.random.default_rng(11)
+    # (cell x, cell y, particles, lowest id, id range)
+    cells = [(5, 0, 600, 100, 600), (1, 1, 1500, 1_000_000, 4000),
+             (3, 1, 3000, 20_000_000, 5_000_000), (1, 2, 5000, 0, (1 << 32) - 1),
+             (4, 2, 8000, 0, (1 << 32) - 1), (2, 3, 129, 0, (1 << 32) - 1),
+             (5, 3, 1024, 5_000_000, 70_000), (0, 0, 1025, 3_000_000_000, 1_000_000)]
+    dx = [w["L"][a] / w["ncell"][a] for a in range(2)]
+    xs, ids, used = [], [], set()
+    for cx, cy, n, lo, span in cells:
+        got = []
+        while len(got) < n:
+            for i in rng.integers(lo, lo + span, 2 * n, dtype=np.uint64).tolist():
+                if i not in used and len(got) < n:
+                    used.add(i)
+                    got.append(i)
+        ids.append(np.array(got, dtype=np.uint32))
+        x = np.zeros((n, 3))
+        x[:, 0] = (cx + rng.uniform(0.05, 0.95, n)) * dx[0]
+        x[:, 1] = (cy + rng.uniform(0.05, 0.95, n)) * dx[1]
+        xs.append(x)
+    x = np.concatenate(xs)
+    ids = np.concatenate(ids)
+    v = rng.normal(0.0, 250.0, (len(ids), 3))
+    order = rng.permutation(len(ids))
+    x, v, ids = x[order], v[order], ids[order]
+    nid = int(ids.max()) + 1
+    ens = D.Ensemble(w, precision="fp64", debug=True, capacity_per_run=32768)
+    ens.debug_begin(runs=1)
+    orc = Oracle(w, runs=1)
+    orc.init_run(0)
+    orc.set_state(0, x, v, ids, nid)
+    ens.set_state(0, x, v, ids, nid)
+    ens.debug_step(1)
+    orc.step(0, 1)
+    res = compare_run(ens, orc, 0, w, 0, 0)
+    _assert_exact([[res]])
+    cnt = ens.get_cells(0)[0]
+    assert sorted(cnt[cnt > 128].tolist()) == [129, 600, 1024, 1025, 1500, 3000, 5000, 8000]
+    _, _, ids_after = ens.get_state(0)
+    st = ens.stats()
+    assert st["collisions"] > 0 and st["error_word"] == 0
+    # within each cell the ids ascend (the pool is in LCR order)
+    starts = np.concatenate([[0], np.cumsum(cnt)])
+    for c in np.nonzero(cnt > 128)[0]:
+        seg = ids_after[starts[c]:starts[c + 1]].astype(np.int64)
+        assert np.all(np.diff(seg) > 0)
+
+
 def test_fp64_specular_and_tiny_cells(D):
     """Closed specular box, one particle per few cells, ragged grid."""
     from tests.helpers import box
