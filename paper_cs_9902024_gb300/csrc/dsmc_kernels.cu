@@ -1285,8 +1285,8 @@ __device__ __forceinline__ void push_big(const StepArgs<T>& a, int64_t gcell)
 
 // Warp path for one cell of up to kWarpMax particles: id ranks by counting,
 // then the particles gathered into the next pool in id order.  Used for
-// tiles that do not fit the tile kernel's shared-memory budget.  `ws` is
-// this warp's scratch: kWarpMax x (2 u32 + u16).
+// tiles whose start table is inconsistent (a corrupt state): it checks
+// every cell.  `ws` is this warp's scratch: kWarpMax x (2 u32 + u16).
 template <typename T, int DIM>
 __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell, unsigned char* ws)
 {
@@ -1349,10 +1349,10 @@ constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather
 // pass: the particle's rank inside its cell by counting smaller ids, and its
 // offsets, velocity and id gathered from the old pool into the next pool at
 // cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
-// kernel; tiles whose particles exceed the budget go cell by cell through
-// the warp path.
+// kernel; a tile whose particles exceed the budget is taken in consecutive
+// cell ranges that fit it.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
+__global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 {
     pdl_enter();
     const Cfg& c = *a.cfg;
@@ -1372,9 +1372,9 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
         for (int i = tid; i <= kTileCells; i += blockDim.x) s_start[i] = a.start[c0 + min(i, nct)];
         __syncthreads();
         const uint32_t B = s_start[0], E = s_start[nct];
-        const uint32_t Tn = E - B;
-        const bool fits = E >= B && Tn <= budget && (uint64_t)E <= (uint64_t)a.cap_old;
-        if (!fits) {
+        if (E < B || (uint64_t)E > (uint64_t)a.cap_old) {
+            // an inconsistent start table (a state already flagged corrupt):
+            // cell by cell through the warp path, which checks every cell
             unsigned char* ws = smem_raw + (kTileCells + 4) * sizeof(uint32_t) +
                                 (size_t)(tid >> 5) * warp_scratch_bytes<T>();
             for (int q = tid >> 5; q < nct; q += kTileCells / 32)
@@ -1382,75 +1382,101 @@ __global__ void __launch_bounds__(kTileCells) k_cell(StepArgs<T> a)
             __syncthreads();
             continue;
         }
-        // [lo, hi): the 16-byte aligned superset of [B, E); the LCR holds
-        // cap_old entries, an even number, so hi stays inside it
-        const uint32_t lo = B & ~1u;
-        const uint32_t sh = B - lo;
-        if (tid == 0 && Tn > 0) {
-            const uint32_t hi = (E + 1u) & ~1u;
-            const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint2);
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&s_bar, bytes);
-            bulk_g2s(s_lcr, a.lcr + lo, bytes, &s_bar);
-        }
-        if (tid < nct) {
-            const uint32_t cb = s_start[tid] - B, ce = s_start[tid + 1] - B;
-            const bool big = ce - cb > (uint32_t)kWarpMax;
-            if (big) push_big(a, c0 + tid);
-            const uint16_t mark = big ? (uint16_t)0xFFFF : (uint16_t)tid;
-            for (uint32_t k = cb; k < ce; ++k) s_cellof[k] = mark;
-        }
-        if (Tn > 0) {
-            if (!mbar_wait(&s_bar, phase)) {
-                atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
-                mbar_wait(&s_bar, phase);
+        // the tile's cells in consecutive ranges [q0, q1) of at most `budget`
+        // particles, one range when the whole tile fits; a range of one cell
+        // above the budget (a cell above kWarpMax) is only listed for the
+        // one-CTA-per-cell kernel
+        int q0 = 0;
+        while (q0 < nct) {
+            const uint32_t Bq = s_start[q0];
+            int q1 = nct;
+            if (E - Bq > budget) {
+                q1 = q0 + __syncthreads_count(tid >= q0 && tid < nct && s_start[tid + 1] - Bq <= budget);
+                if (q1 == q0) {
+                    if (tid == q0) push_big(a, c0 + q0);
+                    q0 += 1;
+                    continue;
+                }
             }
-            phase ^= 1u;
+            const uint32_t Eq = s_start[q1];
+            const uint32_t Tn = Eq - Bq;
+            if (Eq < Bq || Tn > budget) {
+                // not a nondecreasing start table: flagged, the rest skipped
+                if (tid == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+                __syncthreads();   // every thread has read the table
+                break;
+            }
+            // [lo, hi): the 16-byte aligned superset of [Bq, Eq); the LCR
+            // holds cap_old entries, an even number, so hi stays inside it
+            const uint32_t lo = Bq & ~1u;
+            const uint32_t sh = Bq - lo;
+            if (tid == 0 && Tn > 0) {
+                const uint32_t hi = (Eq + 1u) & ~1u;
+                const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint2);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s_bar, bytes);
+                bulk_g2s(s_lcr, a.lcr + lo, bytes, &s_bar);
+            }
+            if (tid >= q0 && tid < q1) {
+                const uint32_t cb = s_start[tid] - Bq, ce = s_start[tid + 1] - Bq;
+                const bool big = ce - cb > (uint32_t)kWarpMax;
+                if (big) push_big(a, c0 + tid);
+                const uint16_t mark = big ? (uint16_t)0xFFFF : (uint16_t)tid;
+                for (uint32_t k = cb; k < ce; ++k) s_cellof[k] = mark;
+            }
+            if (Tn > 0) {
+                if (!mbar_wait(&s_bar, phase)) {
+                    atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
+                    mbar_wait(&s_bar, phase);
+                }
+                phase ^= 1u;
+            }
+            __syncthreads();
+            const uint2* tl = s_lcr + sh;
+            for (uint32_t k0 = tid; k0 < Tn; k0 += kGatherBatch * kTileCells) {
+                // kGatherBatch particles per pass, every load issued before any store
+                uint32_t kk[kGatherBatch], sl[kGatherBatch];
+                int lo2[kGatherBatch];
+                T px[kGatherBatch][3], pv[kGatherBatch][3];
+#pragma unroll
+                for (int b = 0; b < kGatherBatch; ++b) {
+                    kk[b] = k0 + (uint32_t)b * kTileCells;
+                    lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
+                    sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
+                }
+#pragma unroll
+                for (int b = 0; b < kGatherBatch; ++b) {
+                    if (lo2[b] == 0xFFFF) continue;
+#pragma unroll
+                    for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
+                    pv[b][0] = a.vi[0][sl[b]];
+                    pv[b][1] = a.vi[1][sl[b]];
+                    pv[b][2] = a.vi[2][sl[b]];
+                }
+#pragma unroll
+                for (int b = 0; b < kGatherBatch; ++b) {
+                    if (lo2[b] == 0xFFFF) continue;
+                    const uint32_t cb = s_start[lo2[b]] - Bq, ce = s_start[lo2[b] + 1] - Bq;
+                    const uint32_t my = tl[kk[b]].y;
+                    // ids are unique within a run; a duplicate (possible only in a
+                    // state already flagged corrupt) leaves a hole, never an access
+                    // outside the cell's range
+                    uint32_t r = 0;
+                    for (uint32_t j = cb; j < ce; ++j) r += tl[j].y < my ? 1u : 0u;
+                    const uint32_t o = Bq + cb + r;
+#pragma unroll
+                    for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
+                    a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
+                    a.ido[o] = my;
+                    a.vo[0][o] = pv[b][0];
+                    a.vo[1][o] = pv[b][1];
+                    a.vo[2][o] = pv[b][2];
+                    if (a.lcr_dbg) a.lcr_dbg[o] = sl[b];
+                }
+            }
+            __syncthreads();
+            q0 = q1;
         }
-        __syncthreads();
-        const uint2* tl = s_lcr + sh;
-        for (uint32_t k0 = tid; k0 < Tn; k0 += kGatherBatch * kTileCells) {
-            // kGatherBatch particles per pass, every load issued before any store
-            uint32_t kk[kGatherBatch], sl[kGatherBatch];
-            int lo2[kGatherBatch];
-            T px[kGatherBatch][3], pv[kGatherBatch][3];
-#pragma unroll
-            for (int b = 0; b < kGatherBatch; ++b) {
-                kk[b] = k0 + (uint32_t)b * kTileCells;
-                lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
-                sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
-            }
-#pragma unroll
-            for (int b = 0; b < kGatherBatch; ++b) {
-                if (lo2[b] == 0xFFFF) continue;
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
-                pv[b][0] = a.vi[0][sl[b]];
-                pv[b][1] = a.vi[1][sl[b]];
-                pv[b][2] = a.vi[2][sl[b]];
-            }
-#pragma unroll
-            for (int b = 0; b < kGatherBatch; ++b) {
-                if (lo2[b] == 0xFFFF) continue;
-                const uint32_t cb = s_start[lo2[b]] - B, ce = s_start[lo2[b] + 1] - B;
-                const uint32_t my = tl[kk[b]].y;
-                // ids are unique within a run; a duplicate (possible only in a
-                // state already flagged corrupt) leaves a hole, never an access
-                // outside the cell's range
-                uint32_t r = 0;
-                for (uint32_t j = cb; j < ce; ++j) r += tl[j].y < my ? 1u : 0u;
-                const uint32_t o = B + cb + r;
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
-                a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
-                a.ido[o] = my;
-                a.vo[0][o] = pv[b][0];
-                a.vo[1][o] = pv[b][1];
-                a.vo[2][o] = pv[b][2];
-                if (a.lcr_dbg) a.lcr_dbg[o] = sl[b];
-            }
-        }
-        __syncthreads();
     }
 }
 

@@ -163,6 +163,26 @@ def test_fp64_big_cells_wide_id_spans(D):
         assert np.all(np.diff(seg) > 0)
 
 
+def test_fp64_tiles_above_the_budget(D):
+    """A 256-particle tile budget: nearly every tile of 256 cells holds more
+    particles and is ordered in consecutive cell ranges that fit; LCR,
+    counts, NTC counts and states still equal the oracle's every step."""
+    w = W.config0(runs=2)
+    ens = D.Ensemble(w, precision="fp64", debug=True, shape={"tile_budget": 256})
+    ens.debug_begin(runs=2)
+    orc = Oracle(w, runs=2)
+    for r in range(2):
+        orc.init_run(r)
+    for s in range(1, 41):
+        ens.debug_step(1)
+        for r in range(2):
+            orc.step(r, s)
+        if s % 10 == 0:
+            _assert_exact([[compare_run(ens, orc, r, w, 0, 0) for r in range(2)]])
+    assert ens.stats()["shape"]["tile_budget"] == 256
+    assert compare_run(ens, orc, 0, w, 0, 0)["n"] > 2000
+
+
 def test_fp64_specular_and_tiny_cells(D):
     """Closed specular box, one particle per few cells, ragged grid."""
     from tests.helpers import box
