@@ -44,8 +44,9 @@ def parse():
     p.add_argument("--runs", type=int, default=None, help="override runs per GPU")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the plain-mode, profile and CPU-baseline legs")
-    p.add_argument("--workload", default="config1",
-                   choices=["config0", "config1", "config2", "config3"],
+    p.add_argument("--workload", default="duct64x32_n512",
+                   choices=["duct64x32_n8", "duct64x32_n512", "jet256x128_n64",
+                            "plate128x64x64_n16"],
                    help="workload (default: the 512-run duct the metric is quoted on; the others "
                         "are the parity workloads, measured the same way)")
     return p.parse_args()
@@ -59,14 +60,14 @@ def dist_env():
 
 
 WORKLOAD_TEXT = {
-    "config0": "2-D duct 64x32, HS, 8 runs x 200 steps, 4 sample times",
-    "config1": "2-D duct 64x32, HS, 512 runs x 400 steps, 8 sample times",
-    "config2": "2-D pulsed VHS jet 256x128, 64 runs x 1000 steps, 20 sample times",
-    "config3": "3-D plate box 128x64x64, HS, 16 runs x 600 steps, 12 sample times",
+    "duct64x32_n8": "2-D duct 64x32, HS, 8 runs x 200 steps, 4 sample times",
+    "duct64x32_n512": "2-D duct 64x32, HS, 512 runs x 400 steps, 8 sample times",
+    "jet256x128_n64": "2-D pulsed VHS jet 256x128, 64 runs x 1000 steps, 20 sample times",
+    "plate128x64x64_n16": "3-D plate box 128x64x64, HS, 16 runs x 600 steps, 12 sample times",
 }
 
 
-def workload(runs=None, name="config1"):
+def workload(runs=None, name="duct64x32_n512"):
     from paper_cs_9902024_gb300 import workloads as W
     w = W.by_name(name)
     if runs:
@@ -76,7 +77,8 @@ def workload(runs=None, name="config1"):
 
 # oracle sample: whole runs for the duct workloads; the first steps of up to
 # 16 runs for the large ones (a whole run of those takes minutes on a core)
-ORACLE_PROBE_STEPS = {"config0": None, "config1": None, "config2": 20, "config3": 4}
+ORACLE_PROBE_STEPS = {"duct64x32_n8": None, "duct64x32_n512": None, "jet256x128_n64": 20,
+                      "plate128x64x64_n16": 4}
 
 
 def oracle_rate(w, threads, probe_steps, target_s):

@@ -108,7 +108,7 @@ def duct(nx=64, ny=32, runs=8, steps=200, n_samples=4, seed=1, ppc=20.0,
     return _clip_ranges(w)
 
 
-def config0(**kw):
+def duct64x32_n8(**kw):
     """Plain method, tiny: 64x32 duct, 200 steps, n = 8 runs, samples at
     steps 50/100/150/200, Philox seed 1."""
     args = dict(nx=64, ny=32, runs=8, steps=200, n_samples=4, seed=1,
@@ -117,7 +117,7 @@ def config0(**kw):
     return duct(**args)
 
 
-def config1(**kw):
+def duct64x32_n512(**kw):
     """Batched ensemble of the 64x32 duct: n = 512 runs, 400 steps, 8 sample
     times."""
     args = dict(nx=64, ny=32, runs=512, steps=400, n_samples=8, seed=1,
@@ -161,7 +161,7 @@ def pulsed_jet(nx=256, ny=128, runs=64, steps=1000, n_samples=20, seed=1,
     return _clip_ranges(w)
 
 
-def config2(**kw):
+def jet256x128_n64(**kw):
     args = dict(name="jet256x128_n64_s1000")
     args.update(kw)
     return pulsed_jet(**args)
@@ -202,7 +202,7 @@ def plate3d(nx=128, ny=64, nz=64, runs=16, steps=600, n_samples=12, seed=1,
     return _clip_ranges(w)
 
 
-def config3(**kw):
+def plate128x64x64_n16(**kw):
     args = dict(name="plate128x64x64_n16_s600")
     args.update(kw)
     return plate3d(**args)
@@ -240,13 +240,14 @@ def mixed(n_runs=1024, cells_lo=32 * 16, cells_hi=512 * 256, steps=300, n_sample
     return dict(name=name, runs=n_runs, steps=steps, groups=groups)
 
 
-def config4(**kw):
+def mixed_n1024(**kw):
     return mixed(**kw)
 
 
 def by_name(name, **kw):
-    table = {"config0": config0, "config1": config1, "config2": config2,
-             "config3": config3, "config4": config4}
+    table = {"duct64x32_n8": duct64x32_n8, "duct64x32_n512": duct64x32_n512,
+             "jet256x128_n64": jet256x128_n64, "plate128x64x64_n16": plate128x64x64_n16,
+             "mixed_n1024": mixed_n1024}
     return table[name](**kw)
 
 

@@ -29,7 +29,7 @@ def main():
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(a.port)
     dist.init_process_group("gloo", rank=a.rank, world_size=a.world)
-    w = W.config0(steps=40, n_samples=2)
+    w = W.duct64x32_n8(steps=40, n_samples=2)
     G = shard.groups(a.per, a.world)
     acc, st = run_ensemble(w, runs=a.per, run0=shard.run_offset(a.rank, a.per), groups=G)
     tot = shard.allreduce_group_sums(acc)

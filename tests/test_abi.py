@@ -74,7 +74,7 @@ def test_ctypes_layout_matches_header():
 
 def _args():
     from paper_cs_9902024_gb300 import workloads as W
-    return D._structs(W.config0())
+    return D._structs(W.duct64x32_n8())
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):
@@ -140,4 +140,4 @@ def test_binding_refuses_to_run_without_gpu():
         pytest.skip("a GPU is present")
     from paper_cs_9902024_gb300 import workloads as W
     with pytest.raises(D.DsmcError):
-        D.Ensemble(W.config0())
+        D.Ensemble(W.duct64x32_n8())

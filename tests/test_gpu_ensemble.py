@@ -37,12 +37,12 @@ def _gpu_macro(ens, T):
     return {k: np.stack([m[k] for m in ms]) for k in ms[0]}
 
 
-def test_config0_fp32_ensemble_within_3_combined_se(D):
+def test_duct_ensemble_fp32_within_3_combined_se(D):
     """The configuration of the paper-sized small case (64x32 duct, 8 runs,
     200 steps, samples at 50/100/150/200): FP32 batched device ensemble vs
     the FP64 oracle; density, velocity and temperature per (sample, cell)
     within 3 combined standard errors."""
-    w = W.config0()
+    w = W.duct64x32_n8()
     acc_o, st_o = run_ensemble(w, threads=8)
     mo = macro_from_acc(acc_o, w, w["runs"])
     ens = D.Ensemble(w)
@@ -55,7 +55,7 @@ def test_config0_fp32_ensemble_within_3_combined_se(D):
     z = _zscores(mg, mo, mask)
     frac = np.mean(np.abs(z) > 3)
     rel_n = np.nanmedian(np.abs(mg["density"][mask] / mo["density"][mask] - 1))
-    print("config0 fp32: %d comparisons, |z|>3 fraction %.4f, max |z| %.2f, median rel err "
+    print("duct64x32_n8 fp32: %d comparisons, |z|>3 fraction %.4f, max |z| %.2f, median rel err "
           "density %.3g" % (z.size, frac, np.abs(z).max(), rel_n))
     assert z.size > 10000
     assert frac < 0.01
@@ -65,10 +65,10 @@ def test_config0_fp32_ensemble_within_3_combined_se(D):
         assert st[k] == pytest.approx(st_o[k], rel=0.02), k
 
 
-def test_config0_fp64_ensemble_matches_oracle_sums(D):
+def test_duct_ensemble_fp64_matches_oracle_sums(D):
     """FP64 device state: the group sums of every sample equal the oracle's
     to rounding (the sampling and the fixed-order reduction over runs)."""
-    w = W.config0()
+    w = W.duct64x32_n8()
     acc_o, st_o = run_ensemble(w, threads=8)
     ens = D.Ensemble(w, precision="fp64")
     ens.run()
@@ -85,7 +85,7 @@ def test_plain_equals_batched_bitwise(D, precision):
     """The plain per-run loop and the batched graph-captured form give
     bit-identical sums (same draws, same per-cell order, same run order in
     the reduction): equal sample error by construction."""
-    w = W.config0(runs=19, steps=60, n_samples=3)      # ragged groups (G = 16)
+    w = W.duct64x32_n8(runs=19, steps=60, n_samples=3)      # ragged groups (G = 16)
     a = D.Ensemble(w, precision=precision, mode="batched").run()
     b = D.Ensemble(w, precision=precision, mode="plain").run()
     c = D.Ensemble(w, precision=precision, mode="batched", use_graph=False).run()
@@ -99,7 +99,7 @@ def test_plain_equals_batched_bitwise(D, precision):
 
 def test_edge_cases(D):
     # one run, sample at step 1 and at the last step
-    w = W.config0(runs=1, steps=5)
+    w = W.duct64x32_n8(runs=1, steps=5)
     ens = D.Ensemble(w).run(sample_steps=[1, 5])
     assert ens.raw(0)[..., 0].sum() > 0
     # zero steps, no samples: nothing moves, no error
@@ -125,7 +125,7 @@ def test_capacity_overflow_is_reported_not_faulted(D):
     """A pool far too small overflows on the device; the kernels keep every
     access in bounds, the run returns DSMC_E_CAPACITY, and the context
     works again with a proper capacity."""
-    w = W.config0(runs=4, steps=40)
+    w = W.duct64x32_n8(runs=4, steps=40)
     ens = D.Ensemble(w, capacity_per_run=300)
     with pytest.raises(D.DsmcError) as ex:
         ens.run()
@@ -138,7 +138,7 @@ def test_capacity_overflow_is_reported_not_faulted(D):
 def test_macro_quantities_match_oracle_formulae(D):
     """The device's macroscopic quantities equal the oracle's formulae
     applied to the device's own group sums."""
-    w = W.config0(runs=20, steps=50, n_samples=2)
+    w = W.duct64x32_n8(runs=20, steps=50, n_samples=2)
     ens = D.Ensemble(w).run()
     for t in range(2):
         raw = ens.raw(t)
@@ -155,7 +155,7 @@ def test_macro_quantities_match_oracle_formulae(D):
 def test_autotune_keeps_results(D):
     """options.autotune searches launch shapes on a trial ensemble; the real
     run's group sums are bit-identical to the fixed-shape run."""
-    w = W.config0(runs=32, steps=120, n_samples=3)
+    w = W.duct64x32_n8(runs=32, steps=120, n_samples=3)
     a = D.Ensemble(w, autotune=True).run()
     b = D.Ensemble(w).run()
     for t in range(3):
@@ -179,7 +179,7 @@ def test_explicit_launch_shape(D):
     the per-cell path) created after a context with a large budget (the tile
     kernel's shared-memory limit must not drop under the larger context).
     Out-of-range entries are refused."""
-    w = W.config0(runs=16, steps=40, n_samples=2)
+    w = W.duct64x32_n8(runs=16, steps=40, n_samples=2)
     big = D.Ensemble(w, shape={"tile_budget": 16384, "move_blocks": 152})
     ref = D.Ensemble(w).run()
     small = D.Ensemble(w, shape={"tile_budget": 256, "scatter_blocks": 7,
@@ -202,7 +202,7 @@ def test_sample_windows_match_oracle_and_modes(D):
     """Time-averaged samples: FP64 device sums equal the oracle's (counts
     exactly), plain == batched bit for bit, and the device density divides
     by runs x window length."""
-    w = W.config0(runs=5, steps=60, n_samples=2)
+    w = W.duct64x32_n8(runs=5, steps=60, n_samples=2)
     win = [(10, 19), (40, 60)]
     acc_o, _ = run_ensemble(w, windows=win)
     e64 = D.Ensemble(w, precision="fp64").run(windows=win)

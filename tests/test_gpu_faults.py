@@ -28,7 +28,7 @@ def test_allocator_refusal_reports_oom(D):
     allocator that works."""
     import torch
     lib = D.load_library()
-    w = W.config0(runs=2, steps=10, n_samples=1)
+    w = W.duct64x32_n8(runs=2, steps=10, n_samples=1)
     dom, cells, gas, arr, nb = D._structs(w)
     held = {}
     state = {"refuse": True}
@@ -89,7 +89,7 @@ def test_surface_event_limit_counted_like_the_oracle(D):
 def test_bounded_wait_timeout_reported(D):
     """A bulk-copy barrier that nothing completes: the wait gives up after
     its poll limit, DSMC_E_TIMEOUT comes back, and the context still runs."""
-    w = W.config0(runs=2, steps=5, n_samples=1)
+    w = W.duct64x32_n8(runs=2, steps=5, n_samples=1)
     ens = D.Ensemble(w, debug=True)
     ens.debug_begin(runs=2)
     assert ens.debug_timeout_probe(256) == D.E_TIMEOUT

@@ -44,7 +44,7 @@ def _zfrac(mg, mo, mask):
 
 
 def test_bench_ensemble_full_size_within_3_combined_se(D):
-    w = W.config1()
+    w = W.duct64x32_n512()
     ens = D.Ensemble(w, autotune=True).run()     # as bench.py launches it
     T = len(w["sample_steps"])
     ms = [ens.macro(t) for t in range(T)]
@@ -95,7 +95,7 @@ def _lockstep_one_run(D, w, steps):
 
 
 def test_plate_box_full_grid_fp64_exact(D):
-    w = W.config3(runs=1)
+    w = W.plate128x64x64_n16(runs=1)
     ens, orc = _lockstep_one_run(D, w, 2)
     cnt = _exact_one_run(ens, orc, w)
     assert cnt.sum() > 7_000_000
@@ -106,7 +106,7 @@ def test_plate_box_full_grid_fp64_exact(D):
 
 
 def test_pulsed_jet_full_grid_fp64_exact(D):
-    w = W.config2(runs=1)
+    w = W.jet256x128_n64(runs=1)
     ens, orc = _lockstep_one_run(D, w, 12)
     cnt = _exact_one_run(ens, orc, w)
     assert cnt.max() > 1024         # cells of the radix-sorted one-CTA-per-cell path
@@ -116,7 +116,7 @@ def test_pulsed_jet_full_grid_fp64_exact(D):
         assert st[k] == so[k], k
 
 
-@pytest.mark.parametrize("name", ["config2", "config3"])
+@pytest.mark.parametrize("name", ["jet256x128_n64", "plate128x64x64_n16"])
 def test_full_ensembles_conserve_particles(D, name):
     w = getattr(W, name)()
     ens = D.Ensemble(w).run()

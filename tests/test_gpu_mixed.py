@@ -45,7 +45,7 @@ def test_mixed_full_size_fp32_conserves_particles(D):
     """The 1024-run mixed ensemble (grids 32x16 .. 512x256, 300 steps) in
     FP32: no device error, and in every group the particles left equal the
     entrants minus the leavers (the duct starts empty)."""
-    m = W.config4()
+    m = W.mixed_n1024()
     me = D.MixedEnsemble(m).run()
     st = me.stats()
     assert st["error_word"] == 0

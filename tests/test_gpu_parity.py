@@ -61,7 +61,7 @@ def _assert_exact(results, tol_x=1e-12, tol_v=1e-10):
 def test_fp64_duct_every_step(D):
     """Empty duct filling from the inflow face: generation, diffuse walls,
     outflow, warp-path cells; 4 runs, 40 steps, every step compared."""
-    w = W.config0(runs=4)
+    w = W.duct64x32_n8(runs=4)
     ens, orc, res = _lockstep(D, w, runs=4, steps=40)
     _assert_exact(res)
     assert res[-1][0]["n"] > 4000
@@ -167,7 +167,7 @@ def test_fp64_tiles_above_the_budget(D):
     """A 256-particle tile budget: nearly every tile of 256 cells holds more
     particles and is ordered in consecutive cell ranges that fit; LCR,
     counts, NTC counts and states still equal the oracle's every step."""
-    w = W.config0(runs=2)
+    w = W.duct64x32_n8(runs=2)
     ens = D.Ensemble(w, precision="fp64", debug=True, shape={"tile_budget": 256})
     ens.debug_begin(runs=2)
     orc = Oracle(w, runs=2)
@@ -199,7 +199,7 @@ def test_fp32_one_step_from_identical_state(D):
     not touch -- except where the oracle's NTC value x = M + rem lies within
     binary32 rounding of an integer (the device forms the product in FP32
     and only carries the remainder in FP64)."""
-    w = W.config0(runs=2)
+    w = W.duct64x32_n8(runs=2)
     orc = Oracle(w, runs=2)
     for r in range(2):
         orc.init_run(r)
@@ -238,7 +238,7 @@ def test_fp32_short_horizon(D):
     change of a cell assignment matches the oracle exactly in its integer
     outputs and to 1e-5 in positions and velocities; the horizon is
     reported."""
-    w = W.config0(runs=8)
+    w = W.duct64x32_n8(runs=8)
     ens = D.Ensemble(w, precision="fp32", debug=True)
     ens.debug_begin(runs=8)
     orc = Oracle(w, runs=8)

@@ -67,7 +67,7 @@ def test_generation_count_and_velocities():
     """Duct inflow: entrants per element per step average to
     flux * A * dt / F_N; their normal velocity has the closed-form mean and
     their tangential components are N(U_t, kT/m)."""
-    w = W.config0(runs=1)
+    w = W.duct64x32_n8(runs=1)
     w["gas"]["d_ref"] = 0.0          # no collisions: velocities stay as drawn
     for b in w["bcs"]:               # specular side walls only flip v_y, whose
         if b["face"] in (W.YMIN, W.YMAX):   # law is symmetric about 0

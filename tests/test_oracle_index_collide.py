@@ -17,7 +17,7 @@ def test_lcr_is_sort_by_cell_then_id():
     """After a step P is ordered by (cell, id): the readdressing array equals
     a plain sort of the survivors, counts equal a bincount, and LCR is a
     permutation of the surviving pre-step slots."""
-    w = W.config0(runs=1, steps=40)
+    w = W.duct64x32_n8(runs=1, steps=40)
     o = Oracle(w, runs=1)
     o.init_run(0)
     for s in range(1, 41):
@@ -62,7 +62,7 @@ def test_scatter_conserves_momentum_and_energy():
 
 
 def test_hard_sphere_cross_section():
-    w = W.config0()
+    w = W.duct64x32_n8()
     for g in (1.0, 400.0, 2500.0):
         assert sigma_cr(w, g) == pytest.approx(math.pi * W.D_HS ** 2 * g, rel=1e-15)
 
@@ -74,7 +74,7 @@ def test_vhs_reference_diameter_property(omega):
     equilibrium relative-speed law at T_ref (reduced mass m/2) and compare
     with pi d_ref^2 <c_r>, <c_r> = 4 sqrt(kT/(pi m))."""
     T = 273.0
-    w = W.config2()
+    w = W.jet256x128_n64()
     over = dict(omega=omega, T_ref=T)
     mr = M / 2
     a = mr / (2 * KB * T)
@@ -161,7 +161,7 @@ def test_maxwell_molecule_relaxation():
 
 
 def test_sampling_is_brute_force_sum():
-    w = W.config0(runs=1)
+    w = W.duct64x32_n8(runs=1)
     o = Oracle(w, runs=1)
     o.init_run(0)
     for s in range(1, 31):
@@ -180,7 +180,7 @@ def test_ensemble_groups_are_sums_of_runs():
     """run_ensemble's group accumulators equal the per-run samples of the
     step-level API summed per group (g = run mod G) -- independently of the
     number of worker threads."""
-    w = W.config0(runs=5, steps=12, n_samples=2)
+    w = W.duct64x32_n8(runs=5, steps=12, n_samples=2)
     acc1, st1 = run_ensemble(w, threads=1)
     acc3, st3 = run_ensemble(w, threads=3)
     assert np.array_equal(acc1, acc3) and st1 == st3
@@ -204,7 +204,7 @@ def test_sample_windows_sum_single_step_samples():
     one-step window is the plain sample."""
     from oracle import run_ensemble
     from paper_cs_9902024_gb300 import workloads as W
-    w = W.config0(runs=3, steps=40, n_samples=2)
+    w = W.duct64x32_n8(runs=3, steps=40, n_samples=2)
     single, _ = run_ensemble(w, sample_steps=list(range(21, 31)))
     win, _ = run_ensemble(w, windows=[(21, 30)])
     assert np.array_equal(win[0][..., 0], single[..., 0].sum(axis=0))

@@ -31,7 +31,7 @@ def test_two_ranks_equal_one_process(tmp_path):
     for p in procs:
         assert p.wait(timeout=300) == 0
     got = np.load(out)
-    w = W.config0(steps=40, n_samples=2)
+    w = W.duct64x32_n8(steps=40, n_samples=2)
     ref, st = run_ensemble(w, runs=32, threads=4)
     # group g holds global runs g and g + 16 on both sides: the same two
     # addends, so the sums agree bit for bit

@@ -26,7 +26,7 @@ def D():
 
 
 def test_noalloc_matches_allocating_run_twice(D):
-    w = W.config0(runs=6, steps=80, n_samples=4)
+    w = W.duct64x32_n8(runs=6, steps=80, n_samples=4)
     ref_ens = D.Ensemble(w).run()
     ref = np.stack([ref_ens.raw(t) for t in range(len(w["sample_steps"]))])
     ref_stats = ref_ens.stats()
@@ -44,14 +44,14 @@ def test_noalloc_matches_allocating_run_twice(D):
 
 
 def test_noalloc_rejects_oversized_problem_and_used_context(D):
-    big = W.config1()
+    big = W.duct64x32_n512()
     ens = D.Ensemble(big, torch_memory=False)
     with pytest.raises(D.DsmcError) as ex:
         ens.run_noalloc()
     assert ex.value.status == D.E_INVALID
     assert "bytes of device scratch" in str(ex.value)
     ens.close()
-    w = W.config0(runs=2, steps=10, n_samples=1)
+    w = W.duct64x32_n8(runs=2, steps=10, n_samples=1)
     used = D.Ensemble(w, torch_memory=False).run()
     with pytest.raises(D.DsmcError) as ex:
         used.run_noalloc()
