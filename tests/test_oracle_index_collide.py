@@ -3,7 +3,7 @@ import math
 
 import numpy as np
 import pytest
-from scipy import integrate, special
+from scipy import integrate, special, stats
 
 from oracle import Oracle, run_ensemble, scatter, sigma_cr
 from paper_cs_9902024_gb300 import workloads as W
@@ -212,3 +212,47 @@ def test_sample_windows_sum_single_step_samples():
     one, _ = run_ensemble(w, windows=[(20, 20), (40, 40)])
     plain, _ = run_ensemble(w, sample_steps=[20, 40])
     assert np.array_equal(one, plain)
+
+
+def test_hard_sphere_relaxation_to_maxwellian():
+    """Homogeneous hard-sphere gas started on a speed shell (every particle
+    at the same speed, isotropic directions: each velocity component has
+    kurtosis 9/5) relaxes to the Maxwellian at the same energy: after ~19
+    collisions per particle every component has kurtosis 3 and passes a
+    Kolmogorov-Smirnov test against N(0, kT/m); energy and the momentum
+    along the wall-free axis are conserved to rounding throughout."""
+    n = 1e20
+    N = 2000
+    w = box(dim=2, ncell=(1, 1, 1), L=[0.05, 0.05, 1.0], fill=0, ppc=N, omega=0.5,
+            T_ref=300.0, dt=2e-5, fill_n=n)
+    rng = np.random.default_rng(5)
+    c0 = math.sqrt(3 * KB * 300.0 / M)
+    kurt0, kurt1, pks = [], [], []
+    for rep in range(3):
+        x = np.zeros((N, 3))
+        x[:, 0] = rng.uniform(0, 0.05, N)
+        x[:, 1] = rng.uniform(0, 0.05, N)
+        dirs = rng.normal(size=(N, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        v = c0 * dirs
+        v -= v.mean(0)                       # zero net momentum
+        E0 = (v ** 2).sum()
+        kurt0.append(((v ** 4).mean(0) / (v ** 2).mean(0) ** 2).mean())
+        o = Oracle(w, runs=1, seed=70 + rep)
+        o.init_run(0)
+        o.set_state(0, x, v, np.arange(N, dtype=np.uint32), N)
+        for s in range(1, 41):
+            o.step(0, s)
+        vv = o.get_state(0)[1]
+        assert abs((vv ** 2).sum() / E0 - 1) < 1e-12
+        # specular walls reverse x and y; the z momentum only collisions change
+        assert abs(vv[:, 2].sum()) < 1e-9 * c0 * N
+        assert o.stats(0)["collisions"] > 8 * N       # > 16 collisions per particle
+        kurt1.append(((vv ** 4).mean(0) / (vv ** 2).mean(0) ** 2).mean())
+        T = M * (vv ** 2).sum() / (3 * N * KB)
+        sd = math.sqrt(KB * T / M)
+        for a in range(3):
+            pks.append(stats.kstest(vv[:, a] / sd, "norm").pvalue)
+    assert abs(np.mean(kurt0) - 1.8) < 0.05
+    assert abs(np.mean(kurt1) - 3.0) < 0.2
+    assert min(pks) > 1e-4

@@ -164,3 +164,35 @@ def test_plate_reflects_inside_and_passes_outside(kind):
         assert np.allclose(x1[inside, 0], 2 * xp - free[inside], atol=1e-12 * L)
         assert np.array_equal(v1[inside, 0], -v[inside, 0])
     assert o.stats(0)["wall_hits"] == inside.sum()
+
+
+@pytest.mark.parametrize("order", ["x_outflow_y_diffuse", "x_diffuse_y_outflow"])
+def test_simultaneous_corner_hit_takes_x_face_first(order):
+    """A flight that reaches two faces at exactly the same time (a corner)
+    meets the x face first.  Outflow on x: the particle leaves without a
+    wall hit.  Diffuse on x, outflow on y: it is re-emitted by the x wall
+    (one wall hit) from the corner, where the y face still removes it
+    unless its new velocity points into the domain."""
+    if order == "x_outflow_y_diffuse":
+        kinds = {W.XMIN: W.OUTFLOW, W.YMIN: W.DIFFUSE}
+    else:
+        kinds = {W.XMIN: W.DIFFUSE, W.YMIN: W.OUTFLOW}
+    w = box(dim=2, ncell=(4, 4, 1), kinds=kinds, fill=0, dt=1e-5)
+    d = w["L"][0] / 4
+    assert d == w["L"][1] / 4
+    x = np.array([[0.5 * d, 0.5 * d, 0.0]])          # equal distances to both faces
+    v = np.array([[-1000.0, -1000.0, 0.0]])          # equal speeds: exactly equal times
+    o = Oracle(w, runs=1)
+    o.init_run(0)
+    o.set_state(0, x, v, np.array([0], dtype=np.uint32), 1)
+    o.step(0, 1)
+    st = o.stats(0)
+    if order == "x_outflow_y_diffuse":
+        assert st["removed"] == 1 and st["wall_hits"] == 0
+    else:
+        assert st["wall_hits"] >= 1
+        n_left = o.count(0)
+        assert st["removed"] + n_left == 1
+        if n_left:
+            xs, vs, _ = o.get_state(0)
+            assert xs[0, 0] >= 0.0 and xs[0, 1] >= 0.0
