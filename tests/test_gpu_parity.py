@@ -183,6 +183,35 @@ def test_fp64_tiles_above_the_budget(D):
     assert compare_run(ens, orc, 0, w, 0, 0)["n"] > 2000
 
 
+@pytest.mark.parametrize("kinds", [(0, 3), (3, 0)])
+def test_fp64_exact_corner_tie(D, kinds):
+    """A flight reaching an x face and a y face at exactly the same time
+    meets the x face first on the device as in the oracle (outflow x with
+    diffuse y: removed, no wall hit; diffuse x with outflow y: re-emitted)."""
+    from tests.helpers import box
+    w = box(dim=2, ncell=(4, 4, 1), kinds={W.XMIN: kinds[0], W.YMIN: kinds[1]}, fill=0, dt=1e-5)
+    d = w["L"][0] / 4
+    x = np.array([[0.5 * d, 0.5 * d, 0.0]])
+    v = np.array([[-1000.0, -1000.0, 0.0]])
+    ids = np.array([0], dtype=np.uint32)
+    ens = D.Ensemble(w, precision="fp64", debug=True, capacity_per_run=1024)
+    ens.debug_begin(runs=1)
+    orc = Oracle(w, runs=1)
+    orc.init_run(0)
+    orc.set_state(0, x, v, ids, 1)
+    ens.set_state(0, x, v, ids, 1)
+    ens.debug_step(1)
+    orc.step(0, 1)
+    st, so = ens.stats(), orc.stats(0)
+    for k in ("removed", "wall_hits"):
+        assert st[k] == so[k], k
+    if kinds[0] == W.OUTFLOW:
+        assert st["removed"] == 1 and st["wall_hits"] == 0
+    else:
+        assert st["wall_hits"] >= 1
+    _assert_exact([[compare_run(ens, orc, 0, w, 0, 0)]])
+
+
 def test_fp64_specular_and_tiny_cells(D):
     """Closed specular box, one particle per few cells, ragged grid."""
     from tests.helpers import box
