@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -184,14 +185,17 @@ def measured_peaks():
 
 def kernel_hash():
     # the device code: the kernel source up to its host launchers, and the
-    # shared header
+    # shared header, without comments and blank space
     h = hashlib.sha256()
     for p in ("paper_cs_9902024_gb300/csrc/dsmc_kernels.cu",
               "paper_cs_9902024_gb300/csrc/dsmc_internal.cuh"):
-        with open(os.path.join(ROOT, p), "rb") as f:
+        with open(os.path.join(ROOT, p)) as f:
             text = f.read()
-        cut = text.find(b"\n// Host launchers\n")
-        h.update(text if cut < 0 else text[:cut])
+        cut = text.find("\n// Host launchers\n")
+        text = text if cut < 0 else text[:cut]
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

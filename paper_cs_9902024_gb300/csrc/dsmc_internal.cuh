@@ -11,7 +11,7 @@ namespace dsmc {
 constexpr uint32_t kDead = 0xFFFFFFFFu;   // cell key of a particle that left
 constexpr int kMaxBounce = 16;            // surface events per particle and step
 constexpr int kGenBlocks = 64;            // Philox blocks per generated particle
-constexpr int kWarpMax = 128;             // larger cells go to the one-CTA-per-cell kernels
+constexpr int kWarpMax = 128;             // larger cells go to the big-cell kernels
 constexpr int kTileCells = 256;           // cells (= threads) per CTA of the sort/gather kernel
 constexpr int kMaxTileBudget = 16384;     // largest particle budget of a sort/gather tile
 constexpr int kGenElems = 2048;           // inflow elements per Generation CTA
@@ -72,7 +72,7 @@ struct Counters {
     unsigned long long particle_steps, generated, removed, wall_hits;
     unsigned long long candidates, collisions, clamps, bounce_limit, reject_limit;
     unsigned long long pool_steps;
-    unsigned long long big_pool_steps;   // particles ordered by the one-CTA-per-cell kernel
+    unsigned long long big_pool_steps;   // particles ordered by the big-cell kernel
     uint32_t error, step, n_big, n_slow;
     uint32_t probe;        // error bits of the timeout test hook only
 };

@@ -1274,7 +1274,7 @@ struct CellTally {
 };
 
 // A cell of more than kWarpMax particles is handled whole (sort, gather,
-// collisions, moments) by the one-CTA-per-cell kernel.
+// collisions, moments) by the big-cell kernel.
 template <typename T>
 __device__ __forceinline__ void push_big(const StepArgs<T>& a, int64_t gcell)
 {
@@ -1385,7 +1385,7 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
         // the tile's cells in consecutive ranges [q0, q1) of at most `budget`
         // particles, one range when the whole tile fits; a range of one cell
         // above the budget (a cell above kWarpMax) is only listed for the
-        // one-CTA-per-cell kernel
+        // big-cell kernel
         int q0 = 0;
         while (q0 < nct) {
             const uint32_t Bq = s_start[q0];
@@ -1481,7 +1481,7 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 }
 
 // Interaction and Sampling: one thread per cell of at most kWarpMax
-// particles (larger cells are done whole by the one-CTA-per-cell kernel), on
+// particles (larger cells are done whole by the big-cell kernel), on
 // the cell's velocities in the next pool, now in id order.  A CTA takes
 // kCollideCells consecutive cells.  (1) Thread 0 starts bulk copies (TMA) of
 // the tile's velocities, up to kCollideStage particles, into shared memory;
