@@ -199,24 +199,60 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+# Algorithmic bytes per particle-step of the method's steps (FP32 SoA
+# state; 2-D, 3-D): Motion reads x and the two (three) in-plane velocity
+# components and writes x and the cell index; Indexing reads the cell index
+# twice (histogram and scatter), writes the LCR and permutes the state
+# (x, v, id read once and written once); Interaction reads the cell's
+# velocities and writes the collided ones (with the cell data, ~16 B).
+def _method_bytes(D):
+    t = 4
+    return {"motion": (2 * D + D) * t + 4 if D == 2 else 40,
+            "scatter": 12,
+            "permute": 2 * (D * t + 3 * t + 4),
+            "interaction": 16}
+
+
+METHOD_ROWS = {"motion": ("move",), "indexing": ("scan", "scatter", "cell", "cell_big"),
+               "interaction": ("collide", "collide_big")}
+
+
 def algorithmic_bytes(w, st, steps, runs):
-    """Algorithmic bytes each kernel must move over one ensemble (FP32 state):
-    one read of every input and one write of every output, no re-reads."""
+    """Bytes each kernel group moves over one ensemble (FP32 state).
+
+    "method": the algorithmic bytes of the method's step that the kernel
+    carries out (28 B per moved particle for Motion in 2-D, 40 in 3-D; 12
+    for the LCR scatter and 48 [56] for the permute of Indexing, 60 [68] in
+    all; 16 for Interaction), times the particles it processes.
+    "layout": the bytes of this build's data layout (one read of every
+    input, one write of every output, no re-reads): the cell-relative
+    offsets and stored cell keys, the (slot, id) LCR entries, the staged
+    velocities."""
     D = w["dim"]
     t = 4
     cells = runs * w["ncell"][0] * w["ncell"][1] * (w["ncell"][2] if D == 3 else 1)
     moved_old = st["particle_steps"] - st["generated"]
     pool = st["pool_steps"]
     big = st.get("big_pool_steps", 0)
+    mb = _method_bytes(D)
     # read the LCR entry, gather offsets and v; write offsets, cell key, id, v
     gather = 8 + 2 * (D * t + 3 * t) + 8
-    return {
+    method = {
+        "move": moved_old * mb["motion"],
+        "scatter": pool * mb["scatter"],
+        "cell": (pool - big) * mb["permute"],
+        "cell_big": big * mb["permute"],
+        "collide": (pool - big) * mb["interaction"],
+        "collide_big": big * mb["interaction"],
+        "scan": 0,
+    }
+    layout = {
         # read the in-cell offsets (D), v (D; the third component only at
-        # wall hits) and the cell key, write the offsets (D), the new key
-        # and the rank inside the cell
-        "move": moved_old * (3 * D * t + 4 + 8),
-        # read key, rank and id, write the LCR entry (slot, id)
-        "scatter": pool * 20,
+        # wall hits) and the cell key, write the offsets (D) and the new key;
+        # the count atomics stay in L2
+        "move": moved_old * (2 * D * t + D * t + 8),
+        # read key and id, write the LCR entry (slot, id)
+        "scatter": pool * 16,
         # the tile kernel: particles of cells up to 128 (+ the start table);
         # cells above 128 particles: one CTA per cell, the same bytes
         "cell": (pool - big) * gather + cells * steps * 4,
@@ -225,11 +261,27 @@ def algorithmic_bytes(w, st, steps, runs):
         # every particle's velocity read once, both velocities of every
         # collision written
         "collide": cells * steps * 24 + pool * 3 * t + st["collisions"] * 2 * 3 * t,
-        # read counts twice, write starts, clear counts
-        "scan": cells * steps * 16,
-        # write the entrants (x, v, id, key, rank)
-        "generate": st["generated"] * (D * t + 3 * t + 12),
+        "collide_big": big * 3 * t,
+        # read counts, write starts
+        "scan": cells * steps * 8,
+        # write the entrants (x, v, id, key)
+        "generate": st["generated"] * (D * t + 3 * t + 8),
     }
+    return method, layout
+
+
+def method_rows(method, kern_ms, peak):
+    """Achieved bandwidth of each of the method's steps on its algorithmic
+    bytes: the bytes of the step's kernels over their summed time."""
+    rows = {}
+    for row, ks in METHOD_ROWS.items():
+        ms = sum(kern_ms.get(k, 0.0) for k in ks)
+        by = sum(method.get(k, 0) for k in ks)
+        if ms > 0 and by > 0:
+            gbs = by / (ms / 1e3) / 1e9
+            rows[row] = {"kernels": list(ks), "ms": ms, "bytes": by, "achieved_gbs": gbs,
+                         "frac": gbs / peak}
+    return rows
 
 
 # ---------------------------------------------------------------------------
@@ -408,7 +460,7 @@ def main():
         for key in ("ms_kernel", "launches_kernel"):
             prs[key] = {k: sum(p[key][k] for p in passes) / len(passes) for k in passes[-1][key]}
         prs["ms_steps"] = sum(p["ms_steps"] for p in passes) / len(passes)
-        algo = algorithmic_bytes(w, prs, steps, runs)
+        algo, layout = algorithmic_bytes(w, prs, steps, runs)
         peak, src = measured_peaks()
         kern = {}
         total_ms = sum(prs["ms_kernel"].values())
@@ -416,11 +468,14 @@ def main():
             if msk <= 0:
                 continue
             e = {"ms": msk, "share": msk / total_ms, "launches": prs["launches_kernel"][k]}
-            if k in algo:
+            if algo.get(k):
                 e["achieved_gbs"] = algo[k] / (msk / 1e3) / 1e9
                 e["frac_of_%s_hbm" % src] = e["achieved_gbs"] / peak
+            if layout.get(k):
+                e["layout_gbs"] = layout[k] / (msk / 1e3) / 1e9
+                e["layout_frac_of_%s_hbm" % src] = e["layout_gbs"] / peak
             kern[k] = e
-        dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["ms"])
+        dom = max((k for k in kern if algo.get(k)), key=lambda k: kern[k]["ms"])
         achieved = kern[dom]["achieved_gbs"]
         traffic = None
         tp = os.path.join(ROOT, "profiles", "traffic.json")
@@ -440,7 +495,11 @@ def main():
                            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                            "traffic": traffic, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"
                            if src == "measured" else src,
-                           "bytes_per_launch": algo[dom] / prs["launches_kernel"][dom]}
+                           "bytes_per_launch": algo[dom] / prs["launches_kernel"][dom],
+                           "bytes": "the method's algorithmic bytes of the kernel's step",
+                           "layout_achieved": kern[dom].get("layout_gbs"),
+                           "layout_frac": (kern[dom].get("layout_gbs") or 0.0) / peak}
+        out["method_steps"] = method_rows(algo, prs["ms_kernel"], peak)
         out["kernels"] = kern
         out["profile_run_ms"] = prs["ms_steps"]
         out["profile_shape"] = passes[-1]["shape"]

@@ -295,6 +295,55 @@ dsmc_status dsmc_run_ensemble_noalloc(dsmc_ctx* ctx, int n_runs, double dt, int 
                                       const int32_t* sample_steps, int n_samples,
                                       uint64_t seed, double* raw_out, size_t raw_len);
 
+/* ---- mixed-size ensembles ------------------------------------------- */
+
+/* Several problems advanced together: a mixed-size ensemble whose runs sit
+ * on grids of different sizes (one context per grid, its runs one batch).
+ * Every time step is one launch per kernel kind over the runs of all
+ * parts.  The CTAs of the tile-shaped kernels -- Motion, LCR scatter,
+ * sort/gather, collisions -- claim their work items, (part, tile) or
+ * (part, chunk of particles), from device counters as they finish earlier
+ * ones, so that processors that are done with their share move to runs
+ * with work left: the dynamic reallocation of processors between runs of
+ * the two-level scheme with dynamic load balancing (Sec. 3, the "heap" of
+ * processors handed to parallel sections by their load), with CTAs as the
+ * processors.
+ *
+ * dsmc_mixed_create takes n_parts (1 .. 64) contexts of one device,
+ * precision and dimension.  Each keeps its own grid, boundaries, options
+ * (capacity, allocator) and run_offset; the mixed ensemble launches on
+ * parts[0]'s stream, from its own graphs.  The contexts stay owned by the
+ * caller and must outlive the mixed ensemble; they must not be used
+ * elsewhere while it runs.  flags: DSMC_MIXED_PROFILE times every kernel
+ * kind with CUDA events (direct launches, no graph; dsmc_mixed_get_stats);
+ * DSMC_MIXED_NO_GRAPH launches directly.  The launch shape is the default
+ * one (no autotune).  Errors: DSMC_E_INVALID (count, NULL part, parts on
+ * different devices or with different precision or dimension),
+ * DSMC_E_OOM, DSMC_E_CUDA. */
+typedef struct dsmc_mixed dsmc_mixed;
+#define DSMC_MIXED_PROFILE 1
+#define DSMC_MIXED_NO_GRAPH 2
+dsmc_status dsmc_mixed_create(dsmc_ctx* const* parts, int n_parts, int flags, dsmc_mixed** out);
+
+/* Run n_runs[i] runs of part i (host array of n_parts entries), every part
+ * for the same `steps` steps of length dt with the same sample steps and
+ * seed -- what dsmc_run_ensemble(parts[i], n_runs[i], ...) computes for each
+ * part alone, bit for bit (a run's draws depend only on its global index
+ * run_offset + r and the seed; every sum is formed in the same order).
+ * Afterwards dsmc_get_samples and dsmc_get_stats on each part read its
+ * samples and counters.  Blocks until the device is done.  Errors: as
+ * dsmc_run_ensemble (the failing part's message is copied to
+ * dsmc_mixed_last_error). */
+dsmc_status dsmc_mixed_run(dsmc_mixed* m, const int32_t* n_runs, double dt, int steps,
+                           const int32_t* sample_steps, int n_samples, uint64_t seed);
+
+/* Totals over the parts of the last dsmc_mixed_run: counters summed,
+ * ms_steps the device time of its step loop, per-kernel-kind times with
+ * DSMC_MIXED_PROFILE, shape the launch shape of the queue-driven kernels. */
+dsmc_status dsmc_mixed_get_stats(dsmc_mixed* m, dsmc_stats* out);
+const char* dsmc_mixed_last_error(const dsmc_mixed* m);
+void dsmc_mixed_destroy(dsmc_mixed* m);
+
 /* ---- test hooks (step-level access for parity tests) ---------------- */
 
 /* Allocate for n_runs and set up the step-0 state (filled or empty) without

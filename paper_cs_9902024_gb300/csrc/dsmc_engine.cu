@@ -69,7 +69,7 @@ struct dsmc_ctx {
     void* V[2][3] = {};
     uint32_t* ID[2] = {};
     uint32_t* CI[2] = {};            // run-local cell index of each pool particle
-    uint32_t *gc = nullptr, *rank = nullptr, *lcr_dbg = nullptr;
+    uint32_t *gc = nullptr, *lcr_dbg = nullptr;
     uint2* lcr = nullptr;
     uint32_t *count = nullptr, *start = nullptr, *block_sums = nullptr;
     uint32_t *run_base = nullptr, *next_id = nullptr, *cand = nullptr, *accd = nullptr;
@@ -333,13 +333,12 @@ static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, in
         ctx->CI[b] = (uint32_t*)A(4 * cap_old);
     }
     ctx->gc = (uint32_t*)A(4 * slots);
-    ctx->rank = (uint32_t*)A(4 * slots);
     ctx->lcr = (uint2*)A(8 * cap_old);
     ctx->lcr_dbg = dbg ? (uint32_t*)A(4 * cap_old) : nullptr;
     ctx->count = (uint32_t*)A(4 * total_cells);
     ctx->start = (uint32_t*)A(4 * (total_cells + 2));
     const int scan_blocks = (int)((total_cells + kScanTile - 1) / kScanTile);
-    ctx->block_sums = (uint32_t*)A(4 * scan_blocks);
+    ctx->block_sums = (uint32_t*)A(4 * (scan_blocks + 1));
     ctx->run_base = (uint32_t*)A(4 * (n_launch + 1));
     ctx->next_id = (uint32_t*)A(4 * n_launch);
     ctx->rem = (double*)A(8 * total_cells);
@@ -420,7 +419,6 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.ci_o = ctx->CI[1 - cur];
     a.ido = ctx->ID[1 - cur];
     a.gc = ctx->gc;
-    a.rank = ctx->rank;
     a.lcr = ctx->lcr;
     a.lcr_dbg = ctx->lcr_dbg;
     a.count = ctx->count;
@@ -1393,6 +1391,386 @@ dsmc_status dsmc_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* ke
 
 
 // ---------------------------------------------------------------------------
+// Mixed-size ensembles: several contexts ("parts", one grid each) advanced
+// by one launch per kernel kind per step.  Each part keeps its own buffers,
+// counters and samples; the launches see the parts as an array of StepArgs
+// in device memory (one array per buffer parity) and the queue-driven
+// kernels claim (part, tile) items from shared counters.
+
+struct dsmc_mixed {
+    std::vector<dsmc_ctx*> parts;    // caller's order
+    std::vector<int> order;          // launch order: parts by decreasing cells per run
+    int device = 0, prec = DSMC_FP32, dim = 2, sms = 0, flags = 0;
+    cudaStream_t stream = nullptr;   // parts[0]'s stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::string err;
+    LaunchShape ls;
+    void* d_args[2] = {nullptr, nullptr};   // StepArgs<T>[n_parts] per buffer parity
+    size_t args_cap = 0;
+    uint32_t* d_queue = nullptr;
+    std::vector<unsigned char> margs[2];    // MultiArgs<T> per buffer parity
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    std::vector<uint64_t> graph_gen;        // parts' allocation generations of the graphs
+    std::vector<int> graph_runs;
+    int cur = 0;
+    std::vector<cudaEvent_t> events;
+    dsmc_stats stats;
+};
+
+static dsmc_status mfail(dsmc_mixed* m, dsmc_status s, const std::string& msg)
+{
+    m->err = msg;
+    return s;
+}
+
+#define CKM(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            m->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return DSMC_E_CUDA;                                                           \
+        }                                                                                 \
+    } while (0)
+
+static void mixed_destroy_graphs(dsmc_mixed* m)
+{
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 2; ++k)
+            if (m->gexec[p][k]) {
+                cudaGraphExecDestroy(m->gexec[p][k]);
+                m->gexec[p][k] = nullptr;
+            }
+    m->graph_gen.clear();
+    m->graph_runs.clear();
+}
+
+static cudaEvent_t mixed_event(dsmc_mixed* m, size_t i)
+{
+    while (m->events.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        m->events.push_back(e);
+    }
+    return m->events[i];
+}
+
+dsmc_status dsmc_mixed_create(dsmc_ctx* const* parts, int n_parts, int flags, dsmc_mixed** out)
+{
+    if (!out) return DSMC_E_INVALID;
+    *out = nullptr;
+    if (!parts || n_parts < 1 || n_parts > kMaxParts) return DSMC_E_INVALID;
+    for (int i = 0; i < n_parts; ++i) {
+        if (!parts[i]) return DSMC_E_INVALID;
+        if (parts[i]->device != parts[0]->device || parts[i]->prec != parts[0]->prec ||
+            parts[i]->dim != parts[0]->dim)
+            return DSMC_E_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (parts[j] == parts[i]) return DSMC_E_INVALID;
+    }
+    dsmc_mixed* m = new (std::nothrow) dsmc_mixed();
+    if (!m) return DSMC_E_OOM;
+    m->parts.assign(parts, parts + n_parts);
+    m->device = parts[0]->device;
+    m->prec = parts[0]->prec;
+    m->dim = parts[0]->dim;
+    m->sms = parts[0]->sms;
+    m->flags = flags;
+    m->stream = parts[0]->stream;
+    std::memset(&m->stats, 0, sizeof(m->stats));
+    m->stats.struct_size = sizeof(dsmc_stats);
+    // heaviest parts first in the item order: their tiles are claimed
+    // first, the small parts' tiles fill in at the end
+    m->order.resize(n_parts);
+    for (int i = 0; i < n_parts; ++i) m->order[i] = i;
+    std::stable_sort(m->order.begin(), m->order.end(),
+                     [&](int a, int b) { return parts[a]->ncells > parts[b]->ncells; });
+    bool ok = cudaSetDevice(m->device) == cudaSuccess;
+    ok = ok && cudaMalloc(&m->d_queue, 4 * kQueueKinds) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        dsmc_mixed_destroy(m);
+        return DSMC_E_CUDA;
+    }
+    m->ls.tile_budget = 0;
+    compute_multi_shape(m->prec, m->dim, m->sms, &m->ls);
+    *out = m;
+    return DSMC_OK;
+}
+
+void dsmc_mixed_destroy(dsmc_mixed* m)
+{
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    mixed_destroy_graphs(m);
+    for (int p = 0; p < 2; ++p)
+        if (m->d_args[p]) cudaFree(m->d_args[p]);
+    if (m->d_queue) cudaFree(m->d_queue);
+    for (cudaEvent_t e : m->events) cudaEventDestroy(e);
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_join) cudaEventDestroy(m->ev_join);
+    if (m->side) cudaStreamDestroy(m->side);
+    delete m;
+}
+
+const char* dsmc_mixed_last_error(const dsmc_mixed* m)
+{
+    if (!m) return g_static_err;
+    return m->err.c_str();
+}
+
+// the parts' StepArgs (both buffer parities) in device memory, and the
+// MultiArgs of each parity with the item prefix tables in launch order
+template <typename T>
+static dsmc_status mixed_upload_args(dsmc_mixed* m, const int32_t* n_runs)
+{
+    const int n = (int)m->parts.size();
+    const size_t bytes = sizeof(StepArgs<T>) * n;
+    if (m->args_cap < bytes) {
+        for (int p = 0; p < 2; ++p) {
+            if (m->d_args[p]) cudaFree(m->d_args[p]);
+            m->d_args[p] = nullptr;
+        }
+        m->args_cap = 0;
+        for (int p = 0; p < 2; ++p)
+            if (cudaMalloc(&m->d_args[p], bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return mfail(m, DSMC_E_OOM, "device allocation of the parts' arguments failed");
+            }
+        m->args_cap = bytes;
+    }
+    for (int p = 0; p < 2; ++p) {
+        std::vector<StepArgs<T>> h(n);
+        MultiArgs<T> ma;
+        std::memset(&ma, 0, sizeof(ma));
+        ma.parts = static_cast<const StepArgs<T>*>(m->d_args[p]);
+        ma.queue = m->d_queue;
+        ma.n_parts = n;
+        for (int k = 0; k < n; ++k) {
+            const int i = m->order[k];
+            dsmc_ctx* c = m->parts[i];
+            h[k] = args_for<T>(c, p, (int)c->opt.run_offset, n_runs[i]);
+            const int64_t cells = (int64_t)c->ncells * n_runs[i];
+            ma.tile_base[k + 1] = ma.tile_base[k] + (int32_t)((cells + kTileCells - 1) / kTileCells);
+            ma.ctile_base[k + 1] = ma.ctile_base[k] + (int32_t)((cells + kCollideCells - 1) / kCollideCells);
+            ma.scan_base[k + 1] = ma.scan_base[k] + h[k].scan_blocks;
+            ma.gen_base[k + 1] = ma.gen_base[k] + n_runs[i] * h[k].gen_groups;
+            ma.gcount_base[k + 1] = ma.gcount_base[k] + (h[k].gen_groups > 1 ? n_runs[i] * h[k].gen_groups : 0);
+        }
+        CKM(cudaMemcpy(m->d_args[p], h.data(), bytes, cudaMemcpyHostToDevice));
+        m->margs[p].resize(sizeof(ma));
+        std::memcpy(m->margs[p].data(), &ma, sizeof(ma));
+    }
+    return DSMC_OK;
+}
+
+// One time step of every part (as enqueue_step for one context).
+static void enqueue_mixed_step(dsmc_mixed* m, int cur, size_t* ev, bool fork, bool reduce)
+{
+    const void* ma = m->margs[cur].data();
+    const int p = m->prec;
+    const LaunchShape& ls = m->ls;
+    cudaStream_t s = m->stream;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(mixed_event(m, (*ev)++), s);
+    };
+    if (fork) {
+        cudaEventRecord(m->ev_fork, s);
+        cudaStreamWaitEvent(m->side, m->ev_fork, 0);
+        launch_m_generate(p, ma, ls, m->side);
+        cudaEventRecord(m->ev_join, m->side);
+        launch_m_move(p, ma, ls, s);
+        cudaStreamWaitEvent(s, m->ev_join, 0);
+    } else {
+        launch_m_generate(p, ma, ls, s); mark();
+        launch_m_move(p, ma, ls, s); mark();
+    }
+    launch_m_scan(p, ma, ls, s); mark();
+    launch_m_scatter(p, ma, ls, s); mark();
+    launch_m_cell(p, ma, ls, s); mark();
+    launch_m_cell_big(p, ma, ls, s); mark();
+    launch_m_collide_big(p, ma, ls, s); mark();
+    launch_m_collide(p, ma, ls, s); mark();
+    if (reduce) launch_m_reduce(p, ma, ls, s);
+    mark();
+    launch_m_step_end(p, ma, ls, s); mark();
+}
+
+static dsmc_status mixed_build_graphs(dsmc_mixed* m, const int32_t* n_runs)
+{
+    const int n = (int)m->parts.size();
+    bool same = m->gexec[0][0] && (int)m->graph_gen.size() == n;
+    for (int i = 0; same && i < n; ++i)
+        same = m->graph_gen[i] == m->parts[i]->generation && m->graph_runs[i] == n_runs[i];
+    if (same) return DSMC_OK;
+    mixed_destroy_graphs(m);
+    for (int p = 0; p < 2; ++p)
+        for (int smp = 0; smp < 2; ++smp) {
+            cudaGraph_t g = nullptr;
+            CKM(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+            enqueue_mixed_step(m, p, nullptr, true, smp != 0);
+            CKM(cudaStreamEndCapture(m->stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&m->gexec[p][smp], g, 0);
+            cudaGraphDestroy(g);
+            CKM(e);
+        }
+    for (int i = 0; i < n; ++i) {
+        m->graph_gen.push_back(m->parts[i]->generation);
+        m->graph_runs.push_back(n_runs[i]);
+    }
+    return DSMC_OK;
+}
+
+dsmc_status dsmc_mixed_run(dsmc_mixed* m, const int32_t* n_runs, double dt, int steps,
+                           const int32_t* sample_steps, int n_samples, uint64_t seed)
+{
+    NvtxRange range("dsmc_mixed_run");
+    if (!m || !n_runs) return DSMC_E_INVALID;
+    CKM(cudaSetDevice(m->device));
+    const int n = (int)m->parts.size();
+    // every part set up as dsmc_run_ensemble would set it up (buffers,
+    // configuration, sample table, zeroed sums and counters), with the
+    // mixed ensemble's common tile budget
+    for (int k = 0; k < n; ++k) {
+        const int i = m->order[k];
+        dsmc_ctx* c = m->parts[i];
+        dsmc_status st = validate_run(c, n_runs[i], dt, steps, sample_steps, sample_steps, n_samples);
+        if (!st) {
+            c->have_run = false;
+            c->dbg = false;
+            c->stats.h2d_bytes = 0;
+            c->stats.d2h_bytes = 0;
+            c->ls.tile_budget = m->ls.tile_budget;
+            st = prepare(c, n_runs[i], dt, steps, sample_steps, sample_steps, n_samples, seed,
+                         n_runs[i]);
+        }
+        if (!st && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(c, DSMC_E_CUDA, "stream synchronisation failed");
+        }
+        if (st) {
+            char buf[64];
+            std::snprintf(buf, sizeof buf, "part %d: ", i);
+            return mfail(m, st, buf + c->err);
+        }
+    }
+    CKM(prepare_multi_kernels(m->prec, m->dim, m->ls.tile_budget));
+    dsmc_status st = m->prec == DSMC_FP64 ? mixed_upload_args<double>(m, n_runs)
+                                          : mixed_upload_args<float>(m, n_runs);
+    if (st) return st;
+    CKM(cudaMemsetAsync(m->d_queue, 0, 4 * kQueueKinds, m->stream));
+    const bool profile = (m->flags & DSMC_MIXED_PROFILE) != 0;
+    const bool graph = !profile && !(m->flags & DSMC_MIXED_NO_GRAPH);
+    if (graph) {
+        st = mixed_build_graphs(m, n_runs);
+        if (st) return st;
+    }
+    std::vector<char> is_sample(steps + 1, 0);
+    for (int k = 0; k < n_samples; ++k) is_sample[sample_steps[k]] = 1;
+    cudaEvent_t e0 = mixed_event(m, 0), e1 = mixed_event(m, 1);
+    if (!e0 || !e1) return mfail(m, DSMC_E_CUDA, "cudaEventCreate failed");
+    // step-0 state of every part
+    for (int k = 0; k < n; ++k) {
+        const int i = m->order[k];
+        dsmc_ctx* c = m->parts[i];
+        AnyArgs u;
+        const void* a0 = build_args(c, u, 0, (int)c->opt.run_offset, n_runs[i]);
+        launch_init_cells(c->prec, a0, c->ls, m->stream);
+        launch_fill(c->prec, a0, c->ls, m->stream);
+    }
+    m->cur = 0;
+    CKM(cudaEventRecord(e0, m->stream));
+    size_t evn = 2;
+    for (int s = 1; s <= steps; ++s) {
+        if (graph) CKM(cudaGraphLaunch(m->gexec[m->cur][is_sample[s]], m->stream));
+        else enqueue_mixed_step(m, m->cur, profile ? &evn : nullptr, false, true);
+        m->cur ^= 1;
+    }
+    CKM(cudaEventRecord(e1, m->stream));
+    CKM(cudaGetLastError());
+    CKM(cudaStreamSynchronize(m->stream));
+    float ms_all = 0.f;
+    CKM(cudaEventElapsedTime(&ms_all, e0, e1));
+    dsmc_stats& ms = m->stats;
+    std::memset(&ms, 0, sizeof(ms));
+    ms.struct_size = sizeof(dsmc_stats);
+    ms.ms_steps = ms_all;
+    if (profile) {
+        size_t i = 2;
+        cudaEvent_t prev = e0;
+        for (int s = 1; s <= steps; ++s)
+            for (int k = 0; k < kStepKernels; ++k, ++i) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, prev, m->events[i]);
+                ms.ms_kernel[kKindOf[k]] += t;
+                ms.launches_kernel[kKindOf[k]] += 1;
+                prev = m->events[i];
+            }
+    }
+    ms.shape[0] = m->ls.move_blocks;
+    ms.shape[1] = m->ls.scatter_blocks;
+    ms.shape[2] = m->ls.tile_budget;
+    ms.shape[3] = m->ls.collide_blocks;
+    ms.steps_done = steps;
+    dsmc_status worst = DSMC_OK;
+    for (int i = 0; i < n; ++i) {
+        dsmc_ctx* c = m->parts[i];
+        Counters h;
+        st = read_counters(c, &h);
+        if (st) return mfail(m, st, c->err);
+        fill_stats(c, h);
+        c->stats.steps_done = steps;
+        c->stats.ms_steps = ms_all;
+        uint32_t total = 0;
+        CKM(cudaMemcpy(&total, c->run_base + n_runs[i], 4, cudaMemcpyDeviceToHost));
+        c->stats.particles_now = total;
+        c->cur = m->cur;
+        ms.particle_steps += h.particle_steps;
+        ms.generated += h.generated;
+        ms.removed += h.removed;
+        ms.wall_hits += h.wall_hits;
+        ms.candidates += h.candidates;
+        ms.collisions += h.collisions;
+        ms.clamps += h.clamps;
+        ms.bounce_limit += h.bounce_limit;
+        ms.reject_limit += h.reject_limit;
+        ms.pool_steps += h.pool_steps;
+        ms.big_pool_steps += h.big_pool_steps;
+        ms.error_word |= h.error;
+        ms.particles_now += total;
+        ms.capacity += c->cap_old;
+        st = check_error_word(c, h.error);
+        if (st) {
+            if (!worst) {
+                char buf[64];
+                std::snprintf(buf, sizeof buf, "part %d: ", i);
+                m->err = buf + c->err;
+            }
+            worst = worst ? worst : st;
+            continue;
+        }
+        c->have_run = true;
+        c->last_runs = n_runs[i];
+        c->last_steps = steps;
+        c->last_samples = n_samples;
+        c->win_len.assign(n_samples, 1);
+    }
+    return worst;
+}
+
+dsmc_status dsmc_mixed_get_stats(dsmc_mixed* m, dsmc_stats* out)
+{
+    if (!m || !out || out->struct_size < sizeof(dsmc_stats)) return DSMC_E_INVALID;
+    *out = m->stats;
+    out->struct_size = sizeof(dsmc_stats);
+    return DSMC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Ensemble run without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they want a
@@ -1476,13 +1854,12 @@ static size_t noalloc_layout(dsmc_ctx* ctx, unsigned char* base, int n_runs, int
         ctx->CI[b] = (uint32_t*)sc.take(4 * cap_old);
     }
     ctx->gc = (uint32_t*)sc.take(4 * slots);
-    ctx->rank = (uint32_t*)sc.take(4 * slots);
     ctx->lcr = (uint2*)sc.take(8 * cap_old);
     ctx->lcr_dbg = nullptr;
     ctx->count = (uint32_t*)sc.take(4 * total_cells);
     ctx->start = (uint32_t*)sc.take(4 * (total_cells + 2));
     const int scan_blocks = (int)((total_cells + kScanTile - 1) / kScanTile);
-    ctx->block_sums = (uint32_t*)sc.take(4 * scan_blocks);
+    ctx->block_sums = (uint32_t*)sc.take(4 * (scan_blocks + 1));
     ctx->run_base = (uint32_t*)sc.take(4 * (n_runs + 1));
     ctx->next_id = (uint32_t*)sc.take(4 * n_runs);
     ctx->rem = (double*)sc.take(8 * total_cells);
@@ -1509,14 +1886,72 @@ static size_t noalloc_layout(dsmc_ctx* ctx, unsigned char* base, int n_runs, int
 }
 
 // forget the scratch layout, so that a later dsmc_run_ensemble allocates its
-// own buffers
+// own buffers: the sizes that ensure_alloc compares are cleared and every
+// pointer into the shared scratch array is dropped
 static void noalloc_forget(dsmc_ctx* ctx)
 {
     ctx->n_launch = 0;
-    ctx->cap_old = 0;
+    ctx->cap_old = ctx->cap_new = ctx->gcap = ctx->max_big = 0;
+    ctx->total_cells = 0;
     ctx->steps_alloc = 0;
+    ctx->n_samples_alloc = 0;
+    ctx->G_alloc = 0;
     ctx->generation++;
     ctx->have_run = false;
+    ctx->d_cfg = nullptr;
+    ctx->d_ctr = nullptr;
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 3; ++a) ctx->X[b][a] = ctx->V[b][a] = nullptr;
+        ctx->ID[b] = ctx->CI[b] = nullptr;
+    }
+    ctx->gc = ctx->lcr_dbg = nullptr;
+    ctx->lcr = nullptr;
+    ctx->count = ctx->start = ctx->block_sums = ctx->run_base = ctx->next_id = nullptr;
+    ctx->cand = ctx->accd = ctx->big_list = ctx->slow_list = ctx->gen_tot = ctx->gen_done = nullptr;
+    ctx->rem = ctx->mom = ctx->acc = ctx->macro = nullptr;
+    ctx->smax = nullptr;
+    ctx->sample_slot = nullptr;
+}
+
+// The run proper of dsmc_run_ensemble_noalloc, on the buffers noalloc_layout
+// placed in the scratch: clears what must start from zero, builds the
+// sample table, advances the steps and copies the counters (and the group
+// sums) out.
+static dsmc_status noalloc_steps(dsmc_ctx* ctx, int n_runs, int steps, const int32_t* sample_steps,
+                                 int n_samples, int32_t* ss_dev, double* raw_out, size_t need,
+                                 Counters* h)
+{
+    const int G = ctx->G;
+    // every buffer that must start from zero (or from the dead key) is set
+    // here: the scratch keeps the previous call's contents
+    CK(cudaMemcpyAsync(ctx->d_cfg, &ctx->hcfg, sizeof(Cfg), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->gc, 0xFF, 4 * (size_t)(ctx->cap_old + ctx->cap_new), ctx->stream));
+    CK(cudaMemsetAsync(ctx->acc, 0, 8 * (size_t)std::max(n_samples, 1) * G * ctx->ncells * DSMC_NMOM,
+                       ctx->stream));
+    if (n_samples > 0)
+        CK(cudaMemcpyAsync(ss_dev, sample_steps, 4 * (size_t)n_samples, cudaMemcpyHostToDevice,
+                           ctx->stream));
+    k_noalloc_sample_table<<<1, 256, 0, ctx->stream>>>(ctx->sample_slot, steps + 2, ss_dev, n_samples);
+    CK(cudaGetLastError());
+    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
+    AnyArgs u;
+    enqueue_init(ctx, build_args(ctx, u, 0, (int)ctx->opt.run_offset, n_runs));
+    ctx->cur = 0;
+    for (int s = 1; s <= steps; ++s) {
+        AnyArgs v;
+        enqueue_step(ctx, build_args(ctx, v, ctx->cur, (int)ctx->opt.run_offset, n_runs), nullptr);
+        ctx->cur ^= 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && n_samples > 0)
+        e = cudaMemcpyAsync(raw_out, ctx->acc, 8 * need, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return fail(ctx, DSMC_E_CUDA, std::string("no-allocation run: ") + cudaGetErrorString(e));
+    return DSMC_OK;
 }
 
 dsmc_status dsmc_run_ensemble_noalloc(dsmc_ctx* ctx, int n_runs, double dt, int steps,
@@ -1554,37 +1989,13 @@ dsmc_status dsmc_run_ensemble_noalloc(dsmc_ctx* ctx, int n_runs, double dt, int 
                       bytes, kNoallocBytes);
         return fail(ctx, DSMC_E_INVALID, msg);
     }
-    // every buffer that must start from zero (or from the dead key) is set
-    // here: the scratch keeps the previous call's contents
-    CK(cudaMemcpyAsync(ctx->d_cfg, &ctx->hcfg, sizeof(Cfg), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
-    CK(cudaMemsetAsync(ctx->gc, 0xFF, 4 * (size_t)(ctx->cap_old + ctx->cap_new), ctx->stream));
-    CK(cudaMemsetAsync(ctx->acc, 0, 8 * (size_t)std::max(n_samples, 1) * G * ctx->ncells * DSMC_NMOM,
-                       ctx->stream));
-    if (n_samples > 0)
-        CK(cudaMemcpyAsync(ss_dev, sample_steps, 4 * (size_t)n_samples, cudaMemcpyHostToDevice,
-                           ctx->stream));
-    k_noalloc_sample_table<<<1, 256, 0, ctx->stream>>>(ctx->sample_slot, steps + 2, ss_dev, n_samples);
-    CK(cudaGetLastError());
-    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
-    AnyArgs u;
-    enqueue_init(ctx, build_args(ctx, u, 0, (int)ctx->opt.run_offset, n_runs));
-    ctx->cur = 0;
-    for (int s = 1; s <= steps; ++s) {
-        AnyArgs v;
-        enqueue_step(ctx, build_args(ctx, v, ctx->cur, (int)ctx->opt.run_offset, n_runs), nullptr);
-        ctx->cur ^= 1;
-    }
-    cudaError_t e = cudaGetLastError();
+    // every failure from here on goes through noalloc_forget, so that the
+    // context never keeps pointers into the shared scratch
     Counters h;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&h, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess && n_samples > 0)
-        e = cudaMemcpyAsync(raw_out, ctx->acc, 8 * need, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    const dsmc_status rs = noalloc_steps(ctx, n_runs, steps, sample_steps, n_samples, ss_dev,
+                                         raw_out, need, &h);
     noalloc_forget(ctx);
-    if (e != cudaSuccess) return fail(ctx, DSMC_E_CUDA, std::string("no-allocation run: ") +
-                                                            cudaGetErrorString(e));
+    if (rs) return rs;
     fill_stats(ctx, h);
     ctx->stats.steps_done = steps;
     return check_error_word(ctx, h.error);

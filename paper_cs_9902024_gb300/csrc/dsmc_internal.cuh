@@ -75,6 +75,7 @@ struct Counters {
     unsigned long long big_pool_steps;   // particles ordered by the big-cell kernel
     uint32_t error, step, n_big, n_slow;
     uint32_t probe;        // error bits of the timeout test hook only
+    uint32_t scan_ticket;  // CTAs of the scan's first pass done (reset by the last)
 };
 
 // The configuration constants that the streaming kernels use for every
@@ -116,13 +117,13 @@ struct StepArgs {
     T* xi[3]; T* vi[3]; uint32_t* idi; uint32_t* ci_i;
     T* xo[3]; T* vo[3]; uint32_t* ido; uint32_t* ci_o;
     uint32_t* gc;          // per slot: run-major cell key, or kDead
-    uint32_t* rank;        // per slot: rank within its cell (any order)
     uint2* lcr;            // per pool position: (slot, id), cell-grouped
     uint32_t* lcr_dbg;     // optional: slot of each sorted particle
-    uint32_t* count;       // per cell: particles (atomic target)
+    uint32_t* count;       // per cell: particles (Motion counts up, the LCR
+                           // scatter counts back down to zero)
     uint32_t* start;       // per cell (+2): exclusive prefix of count; entry
                            // total_cells + 1 keeps the pre-step pool size
-    uint32_t* block_sums;
+    uint32_t* block_sums;  // per scan CTA (+1): block sums, then their prefix
     uint32_t* run_base;    // per run (+1): first pool position of the run
     uint32_t* next_id;     // per run
     double* rem;           // per cell: NTC remainder
@@ -145,6 +146,29 @@ struct StepArgs {
     int32_t total_cells;
     int32_t scan_blocks;
     int32_t tile_budget;   // particles a tile CTA stages in shared memory
+};
+
+// Several problems advanced by one launch per kernel kind (the parts of a
+// mixed-size ensemble: each part one grid with its own runs, buffers and
+// counters).  The tile-shaped kernels take their items -- (part, tile) or
+// (part, chunk of slots) -- from device work-queue counters; items are
+// numbered part by part in the order of `parts`.
+constexpr int kMaxParts = 64;
+enum QueueKind : int { kQMove = 0, kQScatter = 1, kQCell = 2, kQCollide = 3, kQueueKinds = 4 };
+constexpr uint32_t kMoveChunk = 8192;      // slots per Motion item
+constexpr uint32_t kScatterChunk = 2048;   // groups of four slots per scatter item
+
+template <typename T>
+struct MultiArgs {
+    const StepArgs<T>* parts;     // device array, n_parts entries
+    uint32_t* queue;              // kQueueKinds claim counters, zeroed at each step's end
+    int32_t n_parts;
+    int32_t pad_;
+    int32_t tile_base[kMaxParts + 1];     // sort/gather tiles before each part
+    int32_t ctile_base[kMaxParts + 1];    // collision tiles before each part
+    int32_t scan_base[kMaxParts + 1];     // scan CTAs before each part
+    int32_t gen_base[kMaxParts + 1];      // Generation CTAs before each part
+    int32_t gcount_base[kMaxParts + 1];   // Generation counting CTAs before each part
 };
 
 // Launchers (dsmc_kernels.cu).  `prec` is DSMC_FP32 or DSMC_FP64 and selects
@@ -175,6 +199,22 @@ void launch_macro(int prec, const void* args, int sample, int n_runs, int window
                   cudaStream_t s);
 void launch_sample_now(int prec, const void* args, cudaStream_t s);
 cudaError_t prepare_kernels(int prec, int dim, int tile_budget);
+
+// the same steps over the parts of a MultiArgs<float> or MultiArgs<double>
+// (`margs`); `ls` holds the grid sizes of the queue-driven kernels
+// (move_blocks, scatter_blocks, cell_blocks, collide_blocks)
+void launch_m_generate(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_move(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_scan(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_scatter(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_cell(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_cell_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_collide_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_collide(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_reduce(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+void launch_m_step_end(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
+cudaError_t prepare_multi_kernels(int prec, int dim, int tile_budget);
+void compute_multi_shape(int prec, int dim, int sms, LaunchShape* ls);
 cudaError_t timeout_probe(Counters* ctr, uint32_t polls, cudaStream_t s);
 void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls);
 int big_cell_limit(int prec);

@@ -7,12 +7,13 @@
 //   k_generate   one CTA per run: inflow counts, entrants created and moved
 //                for their first fractional step (Generation + Motion)
 //   k_move       grid-stride over the particle pool: free flight (surface
-//                interaction in k_move_slow), new cell key and a rank
-//                inside the cell from an atomic count (Motion + Enumeration)
+//                interaction in k_move_slow), new cell key, the cell's
+//                count (Motion + Enumeration)
 //   k_scan1/2    exclusive prefix over the run-major cell counts: each
 //                cell's first pool position, each run's first position
 //                (Indexing)
-//   k_scatter    LCR[start[cell] + rank] = (slot, id)  (Indexing)
+//   k_scatter    LCR[start[cell] + r] = (slot, id), r counted down from
+//                the cell's count (Indexing)
 //   k_cell       one CTA per 256 cells: each cell's particles put in
 //                particle-id order and gathered into the next pool
 //                (Indexing)
@@ -384,6 +385,16 @@ __device__ __forceinline__ uint32_t atomic_add_l2_keep(uint32_t* p, uint32_t v)
     return old;
 }
 
+// atomicAdd without a returned value (red), with the same L2 evict-last
+// policy: Motion only counts, nothing waits for the old value
+__device__ __forceinline__ void red_add_l2_keep(uint32_t* p, uint32_t v)
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("red.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
+                 : "memory");
+}
+
 // load with an L2 evict-last policy (per-cell tables that later kernels of
 // the step read again)
 __device__ __forceinline__ uint32_t ld_l2_keep(const uint32_t* p)
@@ -543,6 +554,8 @@ __global__ void k_fill_particles(StepArgs<T> a)
          i < a.total_cells; i += warps) {
         const uint32_t rl = (uint32_t)(i / c.ncells), cell = (uint32_t)(i - (int64_t)rl * c.ncells);
         const uint32_t beg = a.start[i], N = a.start[i + 1] - beg;
+        // the counts start the first step at zero (the scan leaves them)
+        if (lane == 0) a.count[i] = 0u;
         if ((int64_t)beg + N > a.cap_old) {
             if (lane == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
             continue;
@@ -607,13 +620,12 @@ __device__ __forceinline__ uint32_t element_entrants(const Cfg& c, uint32_t run,
 // CTA per (run, group), so that the creating pass can number each group's
 // entrants without waiting for the groups before it.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
+__device__ __forceinline__ void gen_count_block(const StepArgs<T>& a, uint32_t blk)
 {
-    pdl_enter();
     const Cfg& c = *a.cfg;
     __shared__ uint32_t s_warp[32];
     const uint32_t G = (uint32_t)a.gen_groups;
-    const uint32_t rl = blockIdx.x / G, grp = blockIdx.x - rl * G;
+    const uint32_t rl = blk / G, grp = blk - rl * G;
     const uint32_t run = a.run0 + rl;
     const uint32_t step = a.ctr->step;
     const int64_t e0 = (int64_t)grp * kGenElems;
@@ -625,6 +637,13 @@ __global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
     if (threadIdx.x == 0) a.gen_tot[(int64_t)rl * G + grp] = total;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
+{
+    pdl_enter();
+    gen_count_block(a, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Generation: one CTA per (run, group of kGenElems inflow elements).
 // Elements are taken in segment-list order; each element's count is
@@ -632,14 +651,13 @@ __global__ void __launch_bounds__(256) k_gen_count(StepArgs<T> a)
 // in (element, k) order -- a group starts after the entrants of the groups
 // before it -- created from their draws and moved for R_f dt.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
+__device__ __forceinline__ void generate_block(const StepArgs<T>& a, uint32_t blk)
 {
-    pdl_enter();
     const Cfg& c = *a.cfg;
     __shared__ uint32_t s_off[257];
     __shared__ uint32_t s_warp[32];
     const uint32_t GG = (uint32_t)a.gen_groups;
-    const uint32_t rl = blockIdx.x / GG, grp = blockIdx.x - rl * GG;
+    const uint32_t rl = blk / GG, grp = blk - rl * GG;
     const uint32_t run = a.run0 + rl;
     const uint32_t step = a.ctr->step;
     const uint32_t n_old = min(a.run_base[rl + 1], (uint32_t)a.cap_old) -
@@ -723,13 +741,12 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) a.vi[ax][slot] = v[ax];
             a.idi[slot] = id;
-            uint32_t key = kDead, rk = 0;
+            uint32_t key = kDead;
             if (alive) {
                 key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
-                rk = atomic_add_l2_keep(&a.count[key], 1u);
+                red_add_l2_keep(&a.count[key], 1u);
             }
             a.gc[slot] = key;
-            a.rank[slot] = rk;
         }
         running += total;
         __syncthreads();
@@ -758,6 +775,13 @@ __global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
     }
 }
 
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_generate(StepArgs<T> a)
+{
+    pdl_enter();
+    generate_block<T, DIM>(a, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // run of a run-major cell key: key / ncells by a 64-bit multiply-high
 // (exact for every 32-bit key, see the host's magic number)
@@ -769,20 +793,54 @@ __device__ __forceinline__ uint32_t run_of_key(const C& c, uint32_t key)
 
 // Motion of the pool, straight-flight part: one particle per thread with
 // few registers, so that many warps keep their loads in flight.  Each
-// particle's run and cell come from its stored cell key.  The rank inside
-// the new cell comes from one atomic per distinct cell of the warp (the pool
-// is cell-ordered, so a warp's particles share few cells), with an L2
-// evict-last hint on the counters.  A particle whose flight may meet a
-// surface is appended to the slow list (one atomic per warp) and moved by
-// k_move_slow.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
+// particle's run and cell come from its stored cell key.  The new cell's
+// count (Enumeration) takes one atomic add per distinct cell of the warp
+// (the pool is cell-ordered, so a warp's particles share few cells), with
+// no returned value and an L2 evict-last hint on the counters.  A particle
+// whose flight may meet a surface is appended to the slow list (one atomic
+// per warp) and moved by k_move_slow.
+// pool particles before which Motion stops: after a pool overflow (reported
+// through the error word) the recorded size can exceed the buffers, so it
+// never walks past them
+template <typename T>
+__device__ __forceinline__ uint32_t move_total(const StepArgs<T>& a)
 {
-    pdl_enter();
+    return min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
+}
+
+// four consecutive values from 16-byte aligned p (one vector load, two for
+// doubles), and back
+__device__ __forceinline__ void ld4(const float* p, float* o)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* o)
+{
+    const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* o)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* o)
+{
+    reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+}
+
+// Motion of the slots [4 q, 4 q + 4) for the quads q = first + 32 w + lane
+// of this thread's warp w, advancing by `stride` quads while 4 q < `end`
+// (a warp-aligned first; end <= move_total): four particles per thread
+// with their loads issued together (vector loads where all four are in
+// range), so that each thread keeps several loads in flight.
+template <typename T, int DIM>
+__device__ __forceinline__ void move_span(const StepArgs<T>& a, uint32_t first, uint32_t end,
+                                          uint32_t stride)
+{
     const Hot<T>& c = a.hot;
-    // after a pool overflow (reported through the error word) the recorded
-    // size can exceed the buffers: never walk past them
-    const uint32_t n_total = min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
     const T dt = c.dt;
     T* __restrict__ xp0 = a.xi[0];
     T* __restrict__ xp1 = a.xi[1];
@@ -793,67 +851,130 @@ __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
     const uint32_t* __restrict__ cip = a.ci_i;
     uint32_t* __restrict__ count = a.count;
     uint32_t* __restrict__ gc = a.gc;
-    uint32_t* __restrict__ rank = a.rank;
     const uint32_t lane = lane_id();
-    const uint32_t stride = gridDim.x * blockDim.x;
-    // warp-uniform trip count (the slow-list append is a warp operation)
-    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n_total; base += stride) {
-        const uint32_t s = base + lane;
-        bool slow = false;
-        uint32_t key = kDead;   // no rank needed (past the end, or slow)
-        if (s < n_total && cip[s] >= (uint32_t)a.total_cells) {
-            // a slot no kernel wrote (possible only after an error already in
-            // the error word): dropped, so no counter outside the table moves
-            atomicOr(&a.ctr->error, DSMC_ERR_POOL);
-            gc[s] = kDead;
-        } else if (s < n_total) {
-            const uint32_t kold = cip[s];
-            T x[3], v[3];
-            x[0] = xp0[s]; x[1] = xp1[s]; v[0] = vp0[s]; v[1] = vp1[s];
-            if (DIM == 3) { x[2] = xp2[s]; v[2] = vp2[s]; } else { x[2] = (T)0; v[2] = (T)0; }
-            const uint32_t rl = run_of_key(c, kold);
-            int ci[3];
-            decode_cell<DIM>(c, kold - rl * (uint32_t)c.ncells, ci);
-            if (try_free_flight<T, DIM>(c, ci, x, v, dt)) {
-                xp0[s] = x[0];
-                xp1[s] = x[1];
-                if (DIM == 3) xp2[s] = x[2];
-                key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
-                gc[s] = key;
-            } else {
-                slow = true;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t nq = (end + 3u) / 4u;
+    // warp-uniform trip count (the count and slow-list updates are warp
+    // operations)
+    for (uint32_t qb = first; qb < nq; qb += stride) {
+        const uint32_t s0 = 4u * (qb + lane);
+        T x0[4], x1[4], x2[4], v0[4], v1[4], v2[4];
+        uint32_t kold[4];
+        const bool full = s0 + 4u <= end;
+        if (full) {
+            const uint4 kv = *reinterpret_cast<const uint4*>(cip + s0);
+            kold[0] = kv.x; kold[1] = kv.y; kold[2] = kv.z; kold[3] = kv.w;
+            ld4(xp0 + s0, x0);
+            ld4(xp1 + s0, x1);
+            ld4(vp0 + s0, v0);
+            ld4(vp1 + s0, v1);
+            if (DIM == 3) { ld4(xp2 + s0, x2); ld4(vp2 + s0, v2); }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const bool in = s0 + b < end;
+                kold[b] = in ? cip[s0 + b] : kDead;
+                x0[b] = in ? xp0[s0 + b] : (T)0;
+                x1[b] = in ? xp1[s0 + b] : (T)0;
+                v0[b] = in ? vp0[s0 + b] : (T)0;
+                v1[b] = in ? vp1[s0 + b] : (T)0;
+                if (DIM == 3) {
+                    x2[b] = in ? xp2[s0 + b] : (T)0;
+                    v2[b] = in ? vp2[s0 + b] : (T)0;
+                }
             }
         }
-        const uint32_t act = __ballot_sync(0xFFFFFFFFu, key != kDead);
-        if (key != kDead) {
-            const uint32_t peers = __match_any_sync(act, key);
-            const uint32_t leader = __ffs(peers) - 1;
-            uint32_t b = 0;
-            if (lane == leader) b = atomic_add_l2_keep(count + key, (uint32_t)__popc(peers));
-            b = __shfl_sync(peers, b, leader);
-            rank[s] = b + __popc(peers & ((1u << lane) - 1u));
+        uint32_t key[4];
+        bool slow[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            key[b] = kDead;   // not counted here (past the end, or slow)
+            slow[b] = false;
+            if (s0 + b >= end) continue;
+            if (kold[b] >= (uint32_t)a.total_cells) {
+                // a slot no kernel wrote (possible only after an error already
+                // in the error word): dropped, so no counter outside the table
+                // moves
+                atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+                continue;
+            }
+            T x[3] = {x0[b], x1[b], DIM == 3 ? x2[b] : (T)0};
+            const T v[3] = {v0[b], v1[b], DIM == 3 ? v2[b] : (T)0};
+            const uint32_t rl = run_of_key(c, kold[b]);
+            int ci[3];
+            decode_cell<DIM>(c, kold[b] - rl * (uint32_t)c.ncells, ci);
+            if (try_free_flight<T, DIM>(c, ci, x, v, dt)) {
+                x0[b] = x[0];
+                x1[b] = x[1];
+                if (DIM == 3) x2[b] = x[2];
+                key[b] = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
+            } else {
+                slow[b] = true;
+            }
         }
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, slow);
-        if (m) {
+        // a slow particle keeps its offsets (k_move_slow moves it and writes
+        // its key)
+        if (full) {
+            st4(xp0 + s0, x0);
+            st4(xp1 + s0, x1);
+            if (DIM == 3) st4(xp2 + s0, x2);
+            *reinterpret_cast<uint4*>(gc + s0) = make_uint4(key[0], key[1], key[2], key[3]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (s0 + b >= end) continue;
+                xp0[s0 + b] = x0[b];
+                xp1[s0 + b] = x1[b];
+                if (DIM == 3) xp2[s0 + b] = x2[b];
+                gc[s0 + b] = key[b];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t act = __ballot_sync(0xFFFFFFFFu, key[b] != kDead);
+            if (key[b] != kDead) {
+                const uint32_t peers = __match_any_sync(act, key[b]);
+                if (lane == (uint32_t)(__ffs(peers) - 1))
+                    red_add_l2_keep(count + key[b], (uint32_t)__popc(peers));
+            }
+        }
+        uint32_t m[4], tot = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            m[b] = __ballot_sync(0xFFFFFFFFu, slow[b]);
+            tot += (uint32_t)__popc(m[b]);
+        }
+        if (tot) {
             uint32_t base_i = 0;
-            if (lane == 0) base_i = atomicAdd(&a.ctr->n_slow, (uint32_t)__popc(m));
+            if (lane == 0) base_i = atomicAdd(&a.ctr->n_slow, tot);
             base_i = __shfl_sync(0xFFFFFFFFu, base_i, 0);
-            if (slow) a.slow_list[base_i + __popc(m & ((1u << lane) - 1u))] = s;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (slow[b]) a.slow_list[base_i + __popc(m[b] & below)] = s0 + b;
+                base_i += (uint32_t)__popc(m[b]);
+            }
         }
     }
 }
 
-// Motion with surface events for the particles k_move set aside.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
+__global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
     pdl_enter();
+    move_span<T, DIM>(a, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), move_total(a),
+                      gridDim.x * blockDim.x);   // in quads of four slots
+}
+
+// Motion with surface events for the particles k_move set aside.
+template <typename T, int DIM>
+__device__ __forceinline__ void move_slow_span(const StepArgs<T>& a, uint32_t first, uint32_t stride)
+{
     const Cfg& c = *a.cfg;
     const uint32_t n = min(a.ctr->n_slow, (uint32_t)a.cap_old);
     const uint32_t step = a.ctr->step;
     const T dt = (T)c.dt;
     LocalCounters lc;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (uint32_t i = first; i < n; i += stride) {
         const uint32_t s = a.slow_list[i];
         const uint32_t kold = a.ci_i[s];
         T x[3], v[3];
@@ -867,7 +988,7 @@ __global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
         decode_cell<DIM>(c, kold - rl * (uint32_t)c.ncells, ci);
         uint32_t vmask = 0;
         const bool alive = move_particle<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
-        uint32_t key = kDead, rk = 0;
+        uint32_t key = kDead;
         if (alive) {
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xi[ax][s] = x[ax];
@@ -875,57 +996,90 @@ __global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
             for (int ax = 0; ax < 3; ++ax)
                 if (vmask & (1u << ax)) a.vi[ax][s] = v[ax];
             key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
-            rk = atomic_add_l2_keep(a.count + key, 1u);
+            red_add_l2_keep(a.count + key, 1u);
         }
         a.gc[s] = key;
-        a.rank[s] = rk;
     }
     // every thread reaches this point: the warp reductions are full-warp
     flush_counters(a.ctr, lc);
 }
 
-// ---------------------------------------------------------------------------
-// Indexing, part 1: exclusive prefix over the run-major cell counts.
-__global__ void __launch_bounds__(kScanThreads) k_scan1(const uint32_t* __restrict__ count,
-                                                        uint32_t* block_sums, int total)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_move_slow(StepArgs<T> a)
 {
     pdl_enter();
+    move_slow_span<T, DIM>(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Indexing, part 1: exclusive prefix over the run-major cell counts, in two
+// passes.  (a) Each CTA sums the counts of its kScanTile cells; the CTA that
+// finishes last (a ticket counter) turns the block sums into their
+// exclusive prefix in place, the total after them.  (b) Each CTA scans its
+// cells from its block's prefix: each cell's first pool position, and each
+// run's first position.
+template <typename T>
+__device__ __forceinline__ void scan1_block(const StepArgs<T>& a, uint32_t b)
+{
     __shared__ uint32_t s_warp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    __shared__ uint32_t s_last;
+    const int total = a.total_cells;
+    const uint32_t nblocks = (uint32_t)a.scan_blocks;
+    const int64_t base = (int64_t)b * kScanTile;
     uint32_t v = 0;
-    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
         const int64_t i = base + k;
-        if (i < total) v += count[i];
+        if (i < total) v += a.count[i];
     }
     v = __reduce_add_sync(0xFFFFFFFFu, v);
     if (lane_id() == 0) s_warp[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
-        uint32_t s = s_warp[threadIdx.x];
-        s = __reduce_add_sync(0xFFFFFFFFu, s);
-        if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
+        uint32_t x = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0u;
+        x = __reduce_add_sync(0xFFFFFFFFu, x);
+        if (threadIdx.x == 0) {
+            a.block_sums[b] = x;
+            __threadfence();
+            s_last = atomicAdd(&a.ctr->scan_ticket, 1u) == nblocks - 1u ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // the last CTA: every other CTA's block sum is visible (its fence came
+    // before its ticket); read them past L1
+    __threadfence();
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < nblocks; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const uint32_t x = i < nblocks ? __ldcg(a.block_sums + i) : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(x, s_warp, tot);
+        if (i < nblocks) a.block_sums[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        a.block_sums[nblocks] = carry;
+        a.ctr->scan_ticket = 0u;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
+__global__ void __launch_bounds__(kScanThreads) k_scan1(StepArgs<T> a)
 {
     pdl_enter();
+    scan1_block(a, blockIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void scan2_block(const StepArgs<T>& a, uint32_t b)
+{
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_red[32];
     const int total = a.total_cells;
     const int ncells = a.cfg->ncells;
-    // prefix of the preceding tiles
-    uint32_t p = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) p += a.block_sums[b];
-    p = __reduce_add_sync(0xFFFFFFFFu, p);
-    if (lane_id() == 0) s_red[threadIdx.x >> 5] = p;
-    __syncthreads();
-    uint32_t prefix = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) prefix += s_red[w];
-    __syncthreads();
+    const uint32_t nblocks = (uint32_t)a.scan_blocks;
+    const uint32_t prefix = __ldcg(a.block_sums + b);
     // each thread: 4 consecutive cells
-    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 4;
+    const int64_t i0 = (int64_t)b * kScanTile + threadIdx.x * 4;
     uint32_t v[4];
     uint32_t sum = 0;
 #pragma unroll
@@ -940,60 +1094,112 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
         const int64_t i = i0 + k;
         if (i < total) {
             a.start[i] = ex;
-            a.count[i] = 0u;
             if (i % ncells == 0) a.run_base[i / ncells] = ex;
         }
         ex += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        a.start[total] = prefix + tile_total;
-        a.run_base[a.n_runs] = prefix + tile_total;
+    if (b == nblocks - 1u && threadIdx.x == 0) {
+        const uint32_t all = __ldcg(a.block_sums + nblocks);
+        a.start[total] = all;
+        a.run_base[a.n_runs] = all;
     }
 }
 
-// Indexing, part 2: LCR[start[cell] + rank] = (slot, id) for every live
-// particle (the rank is any order inside a cell: the next kernel orders
-// each cell by id; the id rides along so that it needs no gather to do so).
-// Four consecutive slots per thread, keys and ranks read as 16-byte vectors.
 template <typename T>
-__global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
+__global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
 {
     pdl_enter();
-    // the pool holds run_base[n_runs] particles after this step's scan, but
-    // the slots to scatter are those of the pre-step pool: its size is kept
-    // at start[total + 1] by the previous step
+    scan2_block(a, blockIdx.x);
+}
+
+// Indexing, part 2: LCR[start[cell] + r] = (slot, id) for every live
+// particle, r taken from the cell's count, which Motion left at the cell's
+// particle count and which this pass counts back down to zero (ready for
+// the next step's Motion): one atomic subtract per distinct cell of a warp,
+// the lanes of a cell taking consecutive places below the returned value.
+// The order inside a cell is any: the next kernel orders each cell by id
+// (the id rides along so that it needs no gather to do so).  Four
+// consecutive slots per thread, keys read as 16-byte vectors.
+__device__ __forceinline__ uint32_t atomic_sub_l2_keep(uint32_t* p, uint32_t v)
+{
+    return atomic_add_l2_keep(p, 0u - v);
+}
+
+// the scatter's index space: groups of four slots of the old pool [0,
+// n_old), then of the entrants' region [cap_old, cap_old + cap_new) (both
+// start on a multiple of 4 slots).  The pool holds run_base[n_runs]
+// particles after this step's scan, but the slots to scatter are those of
+// the pre-step pool: its size is kept at start[total + 1] by the previous
+// step.
+template <typename T>
+__device__ __forceinline__ uint64_t scatter_quads(const StepArgs<T>& a, uint64_t* q_old_out)
+{
+    const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
+    *q_old_out = (n_old + 3) / 4;
+    return (n_old + 3) / 4 + ((uint64_t)a.cap_new + 3) / 4;
+}
+
+// quads [first + 32 w, ...) of this thread's warp w, advancing by `stride`
+// while below `end` (warp-aligned first; end <= scatter_quads)
+template <typename T>
+__device__ __forceinline__ void scatter_span(const StepArgs<T>& a, uint64_t first, uint64_t end,
+                                             uint64_t stride)
+{
+    uint64_t q_old;
+    scatter_quads(a, &q_old);
     const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
     uint32_t* __restrict__ gc = a.gc;
-    const uint32_t* __restrict__ rank = a.rank;
+    uint32_t* __restrict__ count = a.count;
     const uint32_t* __restrict__ start = a.start;
     uint2* __restrict__ lcr2 = a.lcr;
     bool overflow = false;
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    // the old pool [0, n_old) and the entrants' region [cap_old, cap_old +
-    // cap_new) (both start on a multiple of 4 slots), as one index space
-    const uint64_t q_old = (n_old + 3) / 4, q_new = ((uint64_t)a.cap_new + 3) / 4;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_old + q_new; q += nthreads) {
+    const uint32_t lane = lane_id();
+    const uint32_t below = (1u << lane) - 1u;
+    // warp-uniform trip count (the count updates are warp operations)
+    for (uint64_t qb = first; qb < end; qb += stride) {
+        const uint64_t q = qb + lane;
+        const bool valid = q < end;
         const bool in_new = q >= q_old;
         const uint64_t s0 = in_new ? (uint64_t)a.cap_old + 4 * (q - q_old) : 4 * q;
-        const uint64_t lim = in_new ? (uint64_t)a.cap_old + (uint64_t)a.cap_new : n_old;
-        uint32_t key[4], rk[4];
+        const uint64_t lim = !valid ? 0 : (in_new ? (uint64_t)a.cap_old + (uint64_t)a.cap_new : n_old);
+        uint32_t key[4], idv[4];
         if (s0 + 4 <= lim) {
             const uint4 kv = *reinterpret_cast<const uint4*>(gc + s0);
-            const uint4 rv = *reinterpret_cast<const uint4*>(rank + s0);
             key[0] = kv.x; key[1] = kv.y; key[2] = kv.z; key[3] = kv.w;
-            rk[0] = rv.x; rk[1] = rv.y; rk[2] = rv.z; rk[3] = rv.w;
+            const uint4 iv = *reinterpret_cast<const uint4*>(a.idi + s0);
+            idv[0] = iv.x; idv[1] = iv.y; idv[2] = iv.z; idv[3] = iv.w;
         } else {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 key[b] = s0 + b < lim ? gc[s0 + b] : kDead;
-                rk[b] = s0 + b < lim ? rank[s0 + b] : 0u;
+                idv[b] = key[b] != kDead ? a.idi[s0 + b] : 0u;
             }
         }
-        uint32_t st[4], idv[4];
+        // the four slots' start loads and count updates are independent:
+        // all are issued before any result is used
+        uint32_t st[4], peers[4], old[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) st[b] = key[b] != kDead ? ld_l2_keep(start + key[b]) : 0u;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            st[b] = key[b] != kDead ? ld_l2_keep(start + key[b]) : 0u;
-            idv[b] = key[b] != kDead ? a.idi[s0 + b] : 0u;
+            const bool live = key[b] != kDead;
+            const uint32_t act = __ballot_sync(0xFFFFFFFFu, live);
+            peers[b] = live ? __match_any_sync(act, key[b]) : 0u;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            old[b] = 0u;
+            if (peers[b] && lane == (uint32_t)(__ffs(peers[b]) - 1))
+                old[b] = atomic_sub_l2_keep(count + key[b], (uint32_t)__popc(peers[b]));
+        }
+        uint32_t rk[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            rk[b] = 0u;
+            if (peers[b]) {
+                const uint32_t o = __shfl_sync(peers[b], old[b], __ffs(peers[b]) - 1);
+                rk[b] = o - 1u - (uint32_t)__popc(peers[b] & below);
+            }
         }
         if (in_new && (key[0] != kDead || key[1] != kDead || key[2] != kDead || key[3] != kDead)) {
             // re-kill the entrants' keys for the next step
@@ -1005,11 +1211,21 @@ __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
         for (int b = 0; b < 4; ++b) {
             if (key[b] == kDead) continue;
             const uint64_t pos = (uint64_t)st[b] + rk[b];
-            if (pos >= (uint64_t)a.cap_old) { overflow = true; continue; }
+            if (pos >= (uint64_t)a.cap_old || rk[b] >= 0x80000000u) { overflow = true; continue; }
             lcr2[pos] = make_uint2((uint32_t)(s0 + b), idv[b]);
         }
     }
     if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
+{
+    pdl_enter();
+    uint64_t q_old;
+    const uint64_t nq = scatter_quads(a, &q_old);
+    scatter_span(a, (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), nq,
+                 (uint64_t)gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1074,19 +1290,11 @@ __device__ __forceinline__ bool ntc_accept(T u, T sc, T smax) { return u < sc / 
 template <>
 __device__ __forceinline__ bool ntc_accept<float>(float u, float sc, float smax) { return u * smax < sc; }
 
-// (cos eps, sin eps) of the azimuth eps = 2 pi u: FP64 by sincospi; FP32 by
-// the fast intrinsic on theta = pi (2u - 1) in [-pi, pi) (its accurate
-// range, absolute error ~4e-7), eps = theta + pi
+// (cos eps, sin eps) of the azimuth eps = 2 pi u (sincospi, accurate in
+// both precisions: the azimuth's rounding stays at the working precision's
+// unit roundoff, relative to the pair's relative speed)
 template <typename T>
 __device__ __forceinline__ void azimuth(T u, T* s, T* c) { dsincospi((T)2.0 * u, s, c); }
-template <>
-__device__ __forceinline__ void azimuth<float>(float u, float* s, float* c)
-{
-    float st, ct;
-    __sincosf(3.14159265358979f * (2.0f * u - 1.0f), &st, &ct);
-    *s = -st;
-    *c = -ct;
-}
 
 // one accepted collision: isotropic scattering of the relative velocity
 template <typename T>
@@ -1351,148 +1559,183 @@ constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather
 // cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
 // kernel; a tile whose particles exceed the budget is taken in consecutive
 // cell ranges that fit it.
+// shared memory of the sort/gather tile kernel: the tile's start table, its
+// LCR entries (two spare for the 16-byte aligned superset) and cell tags
+struct CellSmem {
+    uint32_t* s_start;
+    uint2* s_lcr;
+    uint16_t* s_cellof;
+    unsigned char* raw;
+    uint64_t* bar;
+};
+
+__device__ __forceinline__ CellSmem cell_smem(unsigned char* raw, uint64_t* bar, uint32_t budget)
+{
+    CellSmem m;
+    m.raw = raw;
+    m.bar = bar;
+    m.s_start = reinterpret_cast<uint32_t*>(raw);
+    m.s_lcr = reinterpret_cast<uint2*>(raw + (kTileCells + 4) * sizeof(uint32_t));
+    m.s_cellof = reinterpret_cast<uint16_t*>(m.s_lcr + budget + 2);
+    return m;
+}
+
+// One tile of kTileCells cells (every thread of the CTA calls it; the
+// mbarrier's phase is carried across calls).
+template <typename T, int DIM>
+__device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, const CellSmem& sm,
+                                          uint32_t& phase)
+{
+    const Cfg& c = *a.cfg;
+    const uint32_t budget = (uint32_t)a.tile_budget;
+    uint32_t* s_start = sm.s_start;
+    uint2* s_lcr = sm.s_lcr;
+    uint16_t* s_cellof = sm.s_cellof;
+    unsigned char* smem_raw = sm.raw;
+    uint64_t& s_bar = *sm.bar;
+    const int tid = threadIdx.x;
+    const int64_t c0 = tile * kTileCells;
+    const int nct = (int)min((int64_t)kTileCells, (int64_t)a.total_cells - c0);
+    for (int i = tid; i <= kTileCells; i += blockDim.x) s_start[i] = a.start[c0 + min(i, nct)];
+    __syncthreads();
+    const uint32_t B = s_start[0], E = s_start[nct];
+    if (E < B || (uint64_t)E > (uint64_t)a.cap_old) {
+        // an inconsistent start table (a state already flagged corrupt):
+        // cell by cell through the warp path, which checks every cell
+        unsigned char* ws = smem_raw + (kTileCells + 4) * sizeof(uint32_t) +
+                            (size_t)(tid >> 5) * warp_scratch_bytes<T>();
+        for (int q = tid >> 5; q < nct; q += kTileCells / 32)
+            cell_warp_path<T, DIM>(a, c, c0 + q, ws);
+        __syncthreads();
+        return;
+    }
+    // the tile's cells in consecutive ranges [q0, q1) of at most `budget`
+    // particles, one range when the whole tile fits; a range of one cell
+    // above the budget (a cell above kWarpMax) is only listed for the
+    // big-cell kernel
+    int q0 = 0;
+    while (q0 < nct) {
+        const uint32_t Bq = s_start[q0];
+        int q1 = nct;
+        if (E - Bq > budget) {
+            q1 = q0 + __syncthreads_count(tid >= q0 && tid < nct && s_start[tid + 1] - Bq <= budget);
+            if (q1 == q0) {
+                if (tid == q0) push_big(a, c0 + q0);
+                q0 += 1;
+                continue;
+            }
+        }
+        const uint32_t Eq = s_start[q1];
+        const uint32_t Tn = Eq - Bq;
+        if (Eq < Bq || Tn > budget) {
+            // not a nondecreasing start table: flagged, the rest skipped
+            if (tid == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
+            __syncthreads();   // every thread has read the table
+            break;
+        }
+        // [lo, hi): the 16-byte aligned superset of [Bq, Eq); the LCR
+        // holds cap_old entries, an even number, so hi stays inside it
+        const uint32_t lo = Bq & ~1u;
+        const uint32_t sh = Bq - lo;
+        if (tid == 0 && Tn > 0) {
+            const uint32_t hi = (Eq + 1u) & ~1u;
+            const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint2);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar, bytes);
+            bulk_g2s(s_lcr, a.lcr + lo, bytes, &s_bar);
+        }
+        if (tid >= q0 && tid < q1) {
+            const uint32_t cb = s_start[tid] - Bq, ce = s_start[tid + 1] - Bq;
+            const bool big = ce - cb > (uint32_t)kWarpMax;
+            if (big) push_big(a, c0 + tid);
+            const uint16_t mark = big ? (uint16_t)0xFFFF : (uint16_t)tid;
+            for (uint32_t k = cb; k < ce; ++k) s_cellof[k] = mark;
+        }
+        if (Tn > 0) {
+            if (!mbar_wait(&s_bar, phase)) {
+                atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
+                mbar_wait(&s_bar, phase);
+            }
+            phase ^= 1u;
+        }
+        __syncthreads();
+        const uint2* tl = s_lcr + sh;
+        for (uint32_t k0 = tid; k0 < Tn; k0 += kGatherBatch * kTileCells) {
+            // kGatherBatch particles per pass, every load issued before any store
+            uint32_t kk[kGatherBatch], sl[kGatherBatch];
+            int lo2[kGatherBatch];
+            T px[kGatherBatch][3], pv[kGatherBatch][3];
+#pragma unroll
+            for (int b = 0; b < kGatherBatch; ++b) {
+                kk[b] = k0 + (uint32_t)b * kTileCells;
+                lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
+                sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
+            }
+#pragma unroll
+            for (int b = 0; b < kGatherBatch; ++b) {
+                if (lo2[b] == 0xFFFF) continue;
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
+                pv[b][0] = a.vi[0][sl[b]];
+                pv[b][1] = a.vi[1][sl[b]];
+                pv[b][2] = a.vi[2][sl[b]];
+            }
+#pragma unroll
+            for (int b = 0; b < kGatherBatch; ++b) {
+                if (lo2[b] == 0xFFFF) continue;
+                const uint32_t cb = s_start[lo2[b]] - Bq, ce = s_start[lo2[b] + 1] - Bq;
+                const uint32_t my = tl[kk[b]].y;
+                // ids are unique within a run; a duplicate (possible only in a
+                // state already flagged corrupt) leaves a hole, never an access
+                // outside the cell's range
+                uint32_t r = 0;
+                for (uint32_t j = cb; j < ce; ++j) r += tl[j].y < my ? 1u : 0u;
+                const uint32_t o = Bq + cb + r;
+#pragma unroll
+                for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
+                a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
+                a.ido[o] = my;
+                a.vo[0][o] = pv[b][0];
+                a.vo[1][o] = pv[b][1];
+                a.vo[2][o] = pv[b][2];
+                if (a.lcr_dbg) a.lcr_dbg[o] = sl[b];
+            }
+        }
+        __syncthreads();
+        q0 = q1;
+    }
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 {
     pdl_enter();
-    const Cfg& c = *a.cfg;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
-    const uint32_t budget = (uint32_t)a.tile_budget;
-    uint32_t* s_start = reinterpret_cast<uint32_t*>(smem_raw);
-    uint2* s_lcr = reinterpret_cast<uint2*>(smem_raw + (kTileCells + 4) * sizeof(uint32_t));
-    uint16_t* s_cellof = reinterpret_cast<uint16_t*>(s_lcr + budget + 2);
-    const int tid = threadIdx.x;
-    if (tid == 0) mbar_init(&s_bar, 1u);
+    const CellSmem sm = cell_smem(smem_raw, &s_bar, (uint32_t)a.tile_budget);
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
     uint32_t phase = 0;
     const int64_t ntiles = ((int64_t)a.total_cells + kTileCells - 1) / kTileCells;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t c0 = tile * kTileCells;
-        const int nct = (int)min((int64_t)kTileCells, (int64_t)a.total_cells - c0);
-        for (int i = tid; i <= kTileCells; i += blockDim.x) s_start[i] = a.start[c0 + min(i, nct)];
-        __syncthreads();
-        const uint32_t B = s_start[0], E = s_start[nct];
-        if (E < B || (uint64_t)E > (uint64_t)a.cap_old) {
-            // an inconsistent start table (a state already flagged corrupt):
-            // cell by cell through the warp path, which checks every cell
-            unsigned char* ws = smem_raw + (kTileCells + 4) * sizeof(uint32_t) +
-                                (size_t)(tid >> 5) * warp_scratch_bytes<T>();
-            for (int q = tid >> 5; q < nct; q += kTileCells / 32)
-                cell_warp_path<T, DIM>(a, c, c0 + q, ws);
-            __syncthreads();
-            continue;
-        }
-        // the tile's cells in consecutive ranges [q0, q1) of at most `budget`
-        // particles, one range when the whole tile fits; a range of one cell
-        // above the budget (a cell above kWarpMax) is only listed for the
-        // big-cell kernel
-        int q0 = 0;
-        while (q0 < nct) {
-            const uint32_t Bq = s_start[q0];
-            int q1 = nct;
-            if (E - Bq > budget) {
-                q1 = q0 + __syncthreads_count(tid >= q0 && tid < nct && s_start[tid + 1] - Bq <= budget);
-                if (q1 == q0) {
-                    if (tid == q0) push_big(a, c0 + q0);
-                    q0 += 1;
-                    continue;
-                }
-            }
-            const uint32_t Eq = s_start[q1];
-            const uint32_t Tn = Eq - Bq;
-            if (Eq < Bq || Tn > budget) {
-                // not a nondecreasing start table: flagged, the rest skipped
-                if (tid == 0) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
-                __syncthreads();   // every thread has read the table
-                break;
-            }
-            // [lo, hi): the 16-byte aligned superset of [Bq, Eq); the LCR
-            // holds cap_old entries, an even number, so hi stays inside it
-            const uint32_t lo = Bq & ~1u;
-            const uint32_t sh = Bq - lo;
-            if (tid == 0 && Tn > 0) {
-                const uint32_t hi = (Eq + 1u) & ~1u;
-                const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint2);
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s_bar, bytes);
-                bulk_g2s(s_lcr, a.lcr + lo, bytes, &s_bar);
-            }
-            if (tid >= q0 && tid < q1) {
-                const uint32_t cb = s_start[tid] - Bq, ce = s_start[tid + 1] - Bq;
-                const bool big = ce - cb > (uint32_t)kWarpMax;
-                if (big) push_big(a, c0 + tid);
-                const uint16_t mark = big ? (uint16_t)0xFFFF : (uint16_t)tid;
-                for (uint32_t k = cb; k < ce; ++k) s_cellof[k] = mark;
-            }
-            if (Tn > 0) {
-                if (!mbar_wait(&s_bar, phase)) {
-                    atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
-                    mbar_wait(&s_bar, phase);
-                }
-                phase ^= 1u;
-            }
-            __syncthreads();
-            const uint2* tl = s_lcr + sh;
-            for (uint32_t k0 = tid; k0 < Tn; k0 += kGatherBatch * kTileCells) {
-                // kGatherBatch particles per pass, every load issued before any store
-                uint32_t kk[kGatherBatch], sl[kGatherBatch];
-                int lo2[kGatherBatch];
-                T px[kGatherBatch][3], pv[kGatherBatch][3];
-#pragma unroll
-                for (int b = 0; b < kGatherBatch; ++b) {
-                    kk[b] = k0 + (uint32_t)b * kTileCells;
-                    lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
-                    sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
-                }
-#pragma unroll
-                for (int b = 0; b < kGatherBatch; ++b) {
-                    if (lo2[b] == 0xFFFF) continue;
-#pragma unroll
-                    for (int ax = 0; ax < DIM; ++ax) px[b][ax] = a.xi[ax][sl[b]];
-                    pv[b][0] = a.vi[0][sl[b]];
-                    pv[b][1] = a.vi[1][sl[b]];
-                    pv[b][2] = a.vi[2][sl[b]];
-                }
-#pragma unroll
-                for (int b = 0; b < kGatherBatch; ++b) {
-                    if (lo2[b] == 0xFFFF) continue;
-                    const uint32_t cb = s_start[lo2[b]] - Bq, ce = s_start[lo2[b] + 1] - Bq;
-                    const uint32_t my = tl[kk[b]].y;
-                    // ids are unique within a run; a duplicate (possible only in a
-                    // state already flagged corrupt) leaves a hole, never an access
-                    // outside the cell's range
-                    uint32_t r = 0;
-                    for (uint32_t j = cb; j < ce; ++j) r += tl[j].y < my ? 1u : 0u;
-                    const uint32_t o = Bq + cb + r;
-#pragma unroll
-                    for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
-                    a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
-                    a.ido[o] = my;
-                    a.vo[0][o] = pv[b][0];
-                    a.vo[1][o] = pv[b][1];
-                    a.vo[2][o] = pv[b][2];
-                    if (a.lcr_dbg) a.lcr_dbg[o] = sl[b];
-                }
-            }
-            __syncthreads();
-            q0 = q1;
-        }
-    }
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        cell_tile<T, DIM>(a, tile, sm, phase);
 }
 
-// Interaction and Sampling: one thread per cell of at most kWarpMax
-// particles (larger cells are done whole by the big-cell kernel), on
-// the cell's velocities in the next pool, now in id order.  A CTA takes
-// kCollideCells consecutive cells.  (1) Thread 0 starts bulk copies (TMA) of
-// the tile's velocities, up to kCollideStage particles, into shared memory;
-// meanwhile every thread forms its cell's NTC candidate count (coalesced
-// remainder and (sigma c_r)_max accesses) and the staged range is cut to
-// whole cells.  (2) The cells are handed to the threads grouped by
-// candidate count (a 32-bin counting sort), so that the cells of one warp
-// run similar numbers of candidates.  (3) Each thread collides its cell --
-// in shared memory if staged, else in place in global memory, with the same
-// arithmetic -- and forms the cell's moments at sample steps.  (4) The
-// staged velocities are stored back with coalesced stores.
+// Interaction and Sampling: cells of at most kWarpMax particles (larger
+// cells are done whole by the big-cell kernels), on the cells' velocities
+// in the next pool, now in id order.  A CTA takes kCollideCells consecutive
+// cells.  (1) Thread 0 starts bulk copies (TMA) of the tile's velocities,
+// up to kCollideStage particles, into shared memory; meanwhile every thread
+// forms its cell's NTC candidate count (coalesced remainder and (sigma
+// c_r)_max accesses) and the staged range is cut to whole cells.  (2) The
+// staged cells with candidates form a work list in decreasing candidate
+// count (a 32-bin counting sort).  (3) Every thread takes the next cell of
+// the list as soon as it has finished its previous one (a shared-memory
+// counter) and runs its candidates in shared memory, one candidate per
+// loop trip, so the lanes of a warp stay busy until the list is used up and
+// the tile's last cells are its shortest.  Cells beyond the stage collide
+// in place in global memory, with the same arithmetic.  (4) The cells'
+// moments at sample steps; the staged velocities are stored back with
+// coalesced stores.
 template <typename T, class C>
 __device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2, uint32_t run,
                                                  uint32_t step, uint32_t cell, uint32_t M, uint32_t N,
@@ -1505,19 +1748,30 @@ __device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2
 template <typename T>
 __host__ __device__ constexpr int collide_stage_pitch() { return kCollideStage + 8; }
 
+// shared memory of the collision kernel: the staged velocities (three
+// components, kCollideStage + 8 each) and the mbarrier of their bulk copies
 template <typename T>
-__global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
+struct CollideSmem {
+    T* s0;
+    T* s1;
+    T* s2;
+    uint64_t* bar;
+};
+
+// One tile of kCollideCells cells (every thread of the CTA calls it; the
+// mbarrier's phase and the thread's tallies are carried across calls).
+template <typename T>
+__device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
+                                             const CollideSmem<T>& sm, uint32_t& phase,
+                                             CellTally& tl)
 {
-    pdl_enter();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int kPitch = collide_stage_pitch<T>();
     constexpr uint32_t kVec = 16u / sizeof(T);   // elements per 16 bytes
-    T* s0 = reinterpret_cast<T*>(smem_raw);
-    T* s1 = s0 + kPitch;
-    T* s2 = s1 + kPitch;
-    __shared__ __align__(8) uint64_t s_bar;
-    __shared__ uint32_t s_b0, s_n, s_nload, s_sh;
-    __shared__ uint32_t s_bin[32];
+    T* s0 = sm.s0;
+    T* s1 = sm.s1;
+    T* s2 = sm.s2;
+    uint64_t& s_bar = *sm.bar;
+    __shared__ uint32_t s_b0, s_n, s_nload, s_sh, s_next;
+    __shared__ uint32_t s_bin[33];
     __shared__ uint32_t s_beg[kCollideCells], s_N[kCollideCells], s_M[kCollideCells];
     __shared__ uint32_t s_ord[kCollideCells];
     __shared__ T s_smax[kCollideCells];
@@ -1526,156 +1780,211 @@ __global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     const uint32_t tid = threadIdx.x;
     constexpr uint32_t kOff = 0xFFFFFFFFu;   // s_N of a cell this kernel skips
-    if (tid == 0) mbar_init(&s_bar, 1u);
-    uint32_t phase = 0;
-    CellTally tl;
-    const int64_t ntiles = (a.total_cells + kCollideCells - 1) / kCollideCells;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t c0 = tile * kCollideCells;
-        const int64_t rest = a.total_cells - c0;
-        const uint32_t nc = rest < kCollideCells ? (uint32_t)rest : (uint32_t)kCollideCells;
-        const int64_t gcell = c0 + tid;
-        const bool mine = tid < nc;
-        uint32_t beg = 0, N = 0;
-        if (mine) {
-            beg = a.start[gcell];
-            N = a.start[gcell + 1] - beg;
-        }
-        if (tid == 0) {
-            // the tile's particles [beg, end), clipped to the stage and the pool
-            const uint32_t end = a.start[c0 + nc];
-            const int64_t room = a.cap_old - (int64_t)beg;
-            int64_t n = end > beg ? (int64_t)(end - beg) : 0;
-            if (n > kCollideStage) n = kCollideStage;
-            if (n > room) n = room > 0 ? room : 0;
-            s_b0 = beg;
-            s_n = (uint32_t)n;
-            s_nload = (uint32_t)n;
-            if (n > 0) {
-                // 16-byte aligned superset [lo, hi) of [beg, beg + n); hi stays
-                // inside the pool, whose capacity is a multiple of 256
-                const uint32_t lo = beg & ~(kVec - 1u);
-                const uint32_t hi = (beg + (uint32_t)n + kVec - 1u) & ~(kVec - 1u);
-                const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(T);
-                s_sh = beg - lo;
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s_bar, 3u * bytes);
-                bulk_g2s(s0, a.vo[0] + lo, bytes, &s_bar);
-                bulk_g2s(s1, a.vo[1] + lo, bytes, &s_bar);
-                bulk_g2s(s2, a.vo[2] + lo, bytes, &s_bar);
-            }
-        }
-        if (tid < 32) s_bin[tid] = 0u;
-        __syncthreads();
-        const uint32_t b0 = s_b0;
-        const uint32_t nload = s_nload;
-        // cut the staged range at the first cell that does not fit whole
-        if (mine) {
-            const uint32_t rel = beg - b0;
-            const uint64_t end = (uint64_t)rel + N;
-            if (beg < b0) atomicMin(&s_n, 0u);
-            else if (rel < nload && end > (uint64_t)nload) atomicMin(&s_n, rel);
-        }
-        // NTC candidate count of this thread's cell; the remainder is final
-        const bool act = mine && N <= (uint32_t)kWarpMax && (uint64_t)beg + N <= (uint64_t)a.cap_old;
-        uint32_t M32 = 0;
-        if (act) {
-            double rem = a.rem[gcell];
-            const T smax = a.smax[gcell];
-            const int64_t M = ntc_count<T>(c, N, smax, rem);
-            if (N >= 2) a.rem[gcell] = rem;
-            M32 = M > (int64_t)0x7FFFFFFF ? 0x7FFFFFFFu : (uint32_t)M;
-            s_smax[tid] = smax;
-        }
-        s_beg[tid] = beg;
-        s_N[tid] = act ? N : kOff;
-        s_M[tid] = M32;
-        const uint32_t bin = M32 < 31u ? M32 : 31u;
-        const uint32_t in_bin = atomicAdd(&s_bin[bin], 1u);
-        __syncthreads();
-        const uint32_t n_st = s_n;
-        const uint32_t sh = s_sh;
-        if (tid < 32) {
-            // exclusive prefix over the 32 bins
-            const uint32_t v = s_bin[tid];
-            uint32_t x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-                if (tid >= (uint32_t)o) x += y;
-            }
-            s_bin[tid] = x - v;
-        }
-        __syncthreads();
-        s_ord[s_bin[bin] + in_bin] = tid;
-        if (nload > 0) {
-            if (!mbar_wait(&s_bar, phase)) {
-                atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
-                mbar_wait(&s_bar, phase);
-            }
-            phase ^= 1u;
-        }
-        __syncthreads();
-        const uint32_t q = s_ord[tid];
-        const uint32_t Nq = s_N[q];
-        if (Nq != kOff) {
-            const int64_t gq = c0 + q;
-            const uint32_t begq = s_beg[q];
-            const uint32_t Mq = s_M[q];
-            const T smax = s_smax[q];
-            const uint32_t rl = run_of_key(c, (uint32_t)gq);
-            const uint32_t cell = (uint32_t)gq - rl * (uint32_t)c.ncells;
-            const bool staged = begq >= b0 && (uint64_t)(begq - b0) + Nq <= (uint64_t)n_st;
-            T seen = (T)0;
-            uint32_t nacc = 0, nclamp = 0;
-            const uint32_t o = sh + (begq - b0);
-            T* v0 = staged ? s0 + o : a.vo[0] + begq;
-            T* v1 = staged ? s1 + o : a.vo[1] + begq;
-            T* v2 = staged ? s2 + o : a.vo[2] + begq;
-            // one call per address space, so that staged cells use
-            // shared-memory loads and stores
-            if (staged)
-                collide_cell_run<T>(c, s0 + o, s1 + o, s2 + o, a.run0 + rl, step, cell, Mq, Nq, smax,
-                                    seen, nacc, nclamp);
-            else
-                collide_cell_run<T>(c, a.vo[0] + begq, a.vo[1] + begq, a.vo[2] + begq, a.run0 + rl,
-                                    step, cell, Mq, Nq, smax, seen, nacc, nclamp);
-            if (seen > smax) a.smax[gq] = seen;
-            if (a.cand) { a.cand[gq] = Mq; a.accd[gq] = nacc; }
-            tl.cand += Mq;
-            tl.acc += nacc;
-            tl.clamp += nclamp;
-            if (slot_t >= 0) {
-                double m[DSMC_NMOM];
-                cell_moments<T>(v0, v1, v2, Nq, m);
-                double* mo = a.mom + gq * DSMC_NMOM;
-                if (slot_t & kSlotFirst)
-                    for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] = m[qq];
-                else
-                    for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] += m[qq];
-            }
-        }
-        __syncthreads();
-        {
-            T* g0 = a.vo[0] + b0;
-            T* g1 = a.vo[1] + b0;
-            T* g2 = a.vo[2] + b0;
-            for (uint32_t p = tid; p < n_st; p += kCollideCells) {
-                g0[p] = s0[sh + p];
-                g1[p] = s1[sh + p];
-                g2[p] = s2[sh + p];
-            }
-        }
-        __syncthreads();
+    const int64_t c0 = tile * kCollideCells;
+    const int64_t rest = a.total_cells - c0;
+    const uint32_t nc = rest < kCollideCells ? (uint32_t)rest : (uint32_t)kCollideCells;
+    const int64_t gcell = c0 + tid;
+    const bool mine = tid < nc;
+    uint32_t beg = 0, N = 0;
+    if (mine) {
+        beg = a.start[gcell];
+        N = a.start[gcell + 1] - beg;
     }
+    if (tid == 0) {
+        // the tile's particles [beg, end), clipped to the stage and the pool
+        const uint32_t end = a.start[c0 + nc];
+        const int64_t room = a.cap_old - (int64_t)beg;
+        int64_t n = end > beg ? (int64_t)(end - beg) : 0;
+        if (n > kCollideStage) n = kCollideStage;
+        if (n > room) n = room > 0 ? room : 0;
+        s_b0 = beg;
+        s_n = (uint32_t)n;
+        s_nload = (uint32_t)n;
+        s_next = kCollideCells;
+        if (n > 0) {
+            // 16-byte aligned superset [lo, hi) of [beg, beg + n); hi stays
+            // inside the pool, whose capacity is a multiple of 256
+            const uint32_t lo = beg & ~(kVec - 1u);
+            const uint32_t hi = (beg + (uint32_t)n + kVec - 1u) & ~(kVec - 1u);
+            const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(T);
+            s_sh = beg - lo;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar, 3u * bytes);
+            bulk_g2s(s0, a.vo[0] + lo, bytes, &s_bar);
+            bulk_g2s(s1, a.vo[1] + lo, bytes, &s_bar);
+            bulk_g2s(s2, a.vo[2] + lo, bytes, &s_bar);
+        }
+    }
+    if (tid < 33) s_bin[tid] = 0u;
+    __syncthreads();
+    const uint32_t b0 = s_b0;
+    const uint32_t nload = s_nload;
+    // cut the staged range at the first cell that does not fit whole
+    if (mine) {
+        const uint32_t rel = beg - b0;
+        const uint64_t end = (uint64_t)rel + N;
+        if (beg < b0) atomicMin(&s_n, 0u);
+        else if (rel < nload && end > (uint64_t)nload) atomicMin(&s_n, rel);
+    }
+    // NTC candidate count of this thread's cell; the remainder is final
+    const bool act = mine && N <= (uint32_t)kWarpMax && (uint64_t)beg + N <= (uint64_t)a.cap_old;
+    uint32_t M32 = 0;
+    if (act) {
+        double rem = a.rem[gcell];
+        const T smax = a.smax[gcell];
+        const int64_t M = ntc_count<T>(c, N, smax, rem);
+        if (N >= 2) a.rem[gcell] = rem;
+        M32 = M > (int64_t)0x7FFFFFFF ? 0x7FFFFFFFu : (uint32_t)M;
+        s_smax[tid] = smax;
+        if (a.cand && M32 == 0u) { a.cand[gcell] = 0u; a.accd[gcell] = 0u; }
+    }
+    s_beg[tid] = beg;
+    s_N[tid] = act ? N : kOff;
+    s_M[tid] = M32;
+    __syncthreads();
+    const uint32_t n_st = s_n;
+    const uint32_t sh = s_sh;
+    const bool staged = act && beg >= b0 && (uint64_t)(beg - b0) + N <= (uint64_t)n_st;
+    // the work list: staged cells with candidates, most candidates first
+    const bool work = staged && M32 > 0u;
+    const uint32_t bin = M32 < 32u ? 32u - M32 : 0u;   // 0: 32 candidates or more
+    const uint32_t in_bin = work ? atomicAdd(&s_bin[bin], 1u) : 0u;
+    __syncthreads();
+    if (tid < 32) {
+        // exclusive prefix over the bins 0..31 (bin 32 holds no work:
+        // M32 = 0), the total in s_bin[32]
+        const uint32_t v = s_bin[tid];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (tid >= (uint32_t)o) x += y;
+        }
+        s_bin[tid] = x - v;
+        if (tid == 31) s_bin[32] = x;
+    }
+    __syncthreads();
+    if (work) s_ord[s_bin[bin] + in_bin] = tid;
+    const uint32_t nwork = s_bin[32];
+    if (nload > 0) {
+        if (!mbar_wait(&s_bar, phase)) {
+            atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
+            mbar_wait(&s_bar, phase);
+        }
+        phase ^= 1u;
+    }
+    __syncthreads();
+    // (3) one candidate per trip; a thread whose cell is done takes the
+    // next cell of the list
+    {
+        uint32_t item = tid, q = 0, Nq = 0, Mq = 0, k = 0, o = 0, run = 0, cell = 0;
+        T smax = (T)0, seen = (T)0;
+        uint32_t nacc = 0, nclamp = 0;
+        bool have = false;
+        while (true) {
+            if (k == Mq) {
+                if (have) {
+                    const int64_t gq = c0 + q;
+                    if (seen > smax) a.smax[gq] = seen;
+                    if (a.cand) { a.cand[gq] = Mq; a.accd[gq] = nacc; }
+                    tl.cand += Mq;
+                    tl.acc += nacc;
+                    tl.clamp += nclamp;
+                    item = atomicAdd(&s_next, 1u);
+                }
+                if (item >= nwork) break;
+                q = s_ord[item];
+                Nq = s_N[q];
+                Mq = s_M[q];
+                smax = s_smax[q];
+                o = sh + (s_beg[q] - b0);
+                const uint32_t gq = (uint32_t)(c0 + q);
+                const uint32_t rl = run_of_key(c, gq);
+                run = a.run0 + rl;
+                cell = gq - rl * (uint32_t)c.ncells;
+                k = 0;
+                seen = (T)0;
+                nacc = nclamp = 0;
+                have = true;
+            }
+            collide_candidate_lazy<T>(c, s0 + o, s1 + o, s2 + o, run, step, cell, k, Nq, smax, seen,
+                                      nacc, nclamp);
+            ++k;
+        }
+    }
+    // cells beyond the stage: in place in global memory
+    if (act && !staged && M32 > 0u) {
+        const uint32_t rl = run_of_key(c, (uint32_t)gcell);
+        const uint32_t cell = (uint32_t)gcell - rl * (uint32_t)c.ncells;
+        const T smax = s_smax[tid];
+        T seen = (T)0;
+        uint32_t nacc = 0, nclamp = 0;
+        collide_cell_run<T>(c, a.vo[0] + beg, a.vo[1] + beg, a.vo[2] + beg, a.run0 + rl, step, cell,
+                            M32, N, smax, seen, nacc, nclamp);
+        if (seen > smax) a.smax[gcell] = seen;
+        if (a.cand) { a.cand[gcell] = M32; a.accd[gcell] = nacc; }
+        tl.cand += M32;
+        tl.acc += nacc;
+        tl.clamp += nclamp;
+    }
+    __syncthreads();
+    // (4) moments at sample steps, thread per cell
+    if (slot_t >= 0 && act) {
+        const uint32_t o = sh + (beg - b0);
+        double m[DSMC_NMOM];
+        if (staged) cell_moments<T>(s0 + o, s1 + o, s2 + o, N, m);
+        else cell_moments<T>(a.vo[0] + beg, a.vo[1] + beg, a.vo[2] + beg, N, m);
+        double* mo = a.mom + gcell * DSMC_NMOM;
+        if (slot_t & kSlotFirst)
+            for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] = m[qq];
+        else
+            for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] += m[qq];
+    }
+    {
+        T* g0 = a.vo[0] + b0;
+        T* g1 = a.vo[1] + b0;
+        T* g2 = a.vo[2] + b0;
+        for (uint32_t p = tid; p < n_st; p += kCollideCells) {
+            g0[p] = s0[sh + p];
+            g1[p] = s1[sh + p];
+            g2[p] = s2[sh + p];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void flush_tally(Counters* ctr, const CellTally& tl)
+{
     const unsigned long long cs = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.cand);
     const unsigned long long as = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.acc);
     const unsigned long long ks = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)tl.clamp);
     if (lane_id() == 0) {
-        if (cs) atomicAdd(&a.ctr->candidates, cs);
-        if (as) atomicAdd(&a.ctr->collisions, as);
-        if (ks) atomicAdd(&a.ctr->clamps, ks);
+        if (cs) atomicAdd(&ctr->candidates, cs);
+        if (as) atomicAdd(&ctr->collisions, as);
+        if (ks) atomicAdd(&ctr->clamps, ks);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    constexpr int kPitch = collide_stage_pitch<T>();
+    CollideSmem<T> sm;
+    sm.s0 = reinterpret_cast<T*>(smem_raw);
+    sm.s1 = sm.s0 + kPitch;
+    sm.s2 = sm.s1 + kPitch;
+    sm.bar = &s_bar;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
+    uint32_t phase = 0;
+    CellTally tl;
+    const int64_t ntiles = (a.total_cells + kCollideCells - 1) / kCollideCells;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        collide_tile<T>(a, tile, sm, phase, tl);
+    flush_tally<T>(a.ctr, tl);
 }
 
 // ---------------------------------------------------------------------------
@@ -1871,17 +2180,17 @@ __device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell,
     order_sync<THREADS>(bar);   // buffers free for the group's next cell
 }
 
+// the big cells of one problem, CTA `blk` of `nblk` (every thread of the
+// CTA calls it)
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
+__device__ __forceinline__ void cell_big_part(const StepArgs<T>& a, uint32_t blk, uint32_t nblk,
+                                              unsigned char* smem_raw, uint32_t* s_red)
 {
-    pdl_enter();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t s_red[2 * (kBigThreads / 32)];
     constexpr int kMax = big_max_of<T>();
     const uint32_t tid = threadIdx.x;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
     // (1) cells above kBigThreads particles: the whole CTA per cell
-    for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+    for (uint32_t bi = blk; bi < nb; bi += nblk) {
         const uint32_t gcell = a.big_list[bi];
         const uint32_t beg = a.start[gcell];
         const uint32_t N = a.start[gcell + 1] - beg;
@@ -1910,7 +2219,7 @@ __global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
     const uint32_t g = tid / kMidThreads, tg = tid % kMidThreads;
     unsigned char* sm = smem_raw + (size_t)g * order_smem<kMidThreads, kBigThreads>();
     uint32_t* red = s_red + g * 2 * (kMidThreads / 32);
-    for (uint32_t bi = blockIdx.x * kMidGroups + g; bi < nb; bi += gridDim.x * kMidGroups) {
+    for (uint32_t bi = blk * kMidGroups + g; bi < nb; bi += nblk * kMidGroups) {
         const uint32_t gcell = a.big_list[bi];
         const uint32_t beg = a.start[gcell];
         const uint32_t N = a.start[gcell + 1] - beg;
@@ -1924,22 +2233,30 @@ __global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
     }
 }
 
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_red[2 * (kBigThreads / 32)];
+    cell_big_part<T, DIM>(a, blockIdx.x, gridDim.x, smem_raw, s_red);
+}
+
 // Cells above kWarpMax particles, part 2: one warp per cell, on the cell's
 // velocities in the next pool (id order): NTC count, candidates applied by
 // collide_cell_warp (disjoint pairs side by side, in-order result), and the
 // cell's moments at sample steps.  Many large cells proceed at once.
+// the big cells of one problem, warp `wid` of `warps`
 template <typename T>
-__global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
+__device__ __forceinline__ void collide_big_part(const StepArgs<T>& a, uint32_t wid, uint32_t warps)
 {
-    pdl_enter();
     const Cfg& c = *a.cfg;
     constexpr int kMax = big_max_of<T>();
     const uint32_t step = a.ctr->step;
     const int slot_t = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     const uint32_t nb = a.ctr->n_big < a.max_big ? a.ctr->n_big : (uint32_t)a.max_big;
     const uint32_t lane = lane_id();
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < nb; bi += warps) {
+    for (uint32_t bi = wid; bi < nb; bi += warps) {
         const uint32_t gcell = a.big_list[bi];
         const uint32_t beg = a.start[gcell];
         const uint32_t N = a.start[gcell + 1] - beg;
@@ -1978,15 +2295,22 @@ __global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
+{
+    pdl_enter();
+    collide_big_part<T>(a, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                        gridDim.x * (blockDim.x >> 5));
+}
+
 // ---------------------------------------------------------------------------
 // Sampling over runs, at the last step of a sample window: acc[k][g] +=
 // sum of the launch's runs of group g (each run's sums over the window's
 // steps), in increasing run order (the same order in batched and plain
 // modes).
 template <typename T>
-__global__ void k_reduce(StepArgs<T> a)
+__device__ __forceinline__ void reduce_part(const StepArgs<T>& a, int64_t first, int64_t stride)
 {
-    pdl_enter();
     const uint32_t step = a.ctr->step;
     const int slot_v = step < (uint32_t)a.n_slot ? a.sample_slot[step] : -1;
     if (slot_v < 0 || !(slot_v & kSlotLast)) return;
@@ -1994,8 +2318,7 @@ __global__ void k_reduce(StepArgs<T> a)
     const int ncells = a.cfg->ncells;
     const int64_t per = (int64_t)ncells * DSMC_NMOM;
     const int64_t n = (int64_t)a.G * per;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = first; i < n; i += stride) {
         const int g = (int)(i / per);
         const int64_t ck = i - (int64_t)g * per;
         double* dst = a.acc + ((int64_t)slot_t * a.G + g) * per + ck;
@@ -2008,9 +2331,15 @@ __global__ void k_reduce(StepArgs<T> a)
 }
 
 template <typename T>
-__global__ void k_step_end(StepArgs<T> a)
+__global__ void k_reduce(StepArgs<T> a)
 {
     pdl_enter();
+    reduce_part(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void step_end_part(const StepArgs<T>& a)
+{
     a.ctr->step += 1u;
     a.ctr->n_big = 0u;
     a.ctr->n_slow = 0u;
@@ -2018,6 +2347,13 @@ __global__ void k_step_end(StepArgs<T> a)
     // remember this step's pool size for the next scatter (the slot range of
     // the old pool): start[total + 1] = run_base[n_runs]
     a.start[a.total_cells + 1] = a.run_base[a.n_runs];
+}
+
+template <typename T>
+__global__ void k_step_end(StepArgs<T> a)
+{
+    pdl_enter();
+    step_end_part(a);
 }
 
 // moments of the current pool (test hook), one warp per cell
@@ -2097,6 +2433,253 @@ __global__ void k_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, ui
                                make_uint2(key[2 * i], key[2 * i + 1]));
         out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Several problems per launch (the parts of a mixed-size ensemble).  Every
+// kernel below runs the bodies of the single-problem kernels above on each
+// part's StepArgs, copied into shared memory when a CTA turns to that part.
+// The tile-shaped work -- Motion chunks, scatter chunks, sort/gather tiles,
+// collision tiles -- is claimed from a device work-queue counter per kernel
+// kind: a CTA takes the next item (part, tile) as soon as it has finished
+// its previous one, so CTAs move between the parts' runs as the load
+// requires, the way the paper's dynamic scheme hands processors that have
+// finished their share to runs with work left (Sec. 3).  The other kernels
+// map CTAs to (part, block) statically or loop over the parts.
+
+// part p with base[p] <= i < base[p + 1] (base[0] = 0, nondecreasing)
+__device__ __forceinline__ int part_of(const int32_t* base, int n, int64_t i)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)base[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// the CTA's copy of part p's StepArgs (every thread calls it)
+template <typename T>
+__device__ __forceinline__ void load_part(StepArgs<T>& dst, const StepArgs<T>* parts, int p)
+{
+    static_assert(sizeof(StepArgs<T>) % 4 == 0, "StepArgs copied in 4-byte words");
+    __syncthreads();   // every thread is done with the previous part
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(parts + p);
+    uint32_t* d = reinterpret_cast<uint32_t*>(&dst);
+    for (uint32_t i = threadIdx.x; i < sizeof(StepArgs<T>) / 4; i += blockDim.x) d[i] = src[i];
+    __syncthreads();
+}
+
+// The work-queue loop of one CTA: item ids from *q until `total`; the next
+// claim is issued while the current item is processed, and broadcast
+// through two alternating shared words.
+template <class F>
+__device__ __forceinline__ void claim_items(uint32_t* q, uint32_t total, F&& f)
+{
+    __shared__ uint32_t s_item[2];
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(q, 1u);
+    __syncthreads();
+    uint32_t buf = 0, item = s_item[0];
+    while (item < total) {
+        uint32_t nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(q, 1u);
+        f(item);
+        if (threadIdx.x == 0) s_item[buf ^ 1u] = nxt;
+        __syncthreads();
+        buf ^= 1u;
+        item = s_item[buf];
+    }
+}
+
+// per-part item counts of a queue-driven kernel with a device-side size,
+// as a prefix table in shared memory (thread p counts part p)
+template <class F>
+__device__ __forceinline__ void item_prefix(int n_parts, int32_t* base, F&& count_of)
+{
+    if (threadIdx.x < (uint32_t)n_parts) base[threadIdx.x + 1] = (int32_t)count_of((int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        base[0] = 0;
+        for (int p = 0; p < n_parts; ++p) base[p + 1] += base[p];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) mk_gen_count(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    const int p = part_of(m.gcount_base, m.n_parts, blockIdx.x);
+    load_part(sa, m.parts, p);
+    gen_count_block(sa, blockIdx.x - (uint32_t)m.gcount_base[p]);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) mk_generate(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    const int p = part_of(m.gen_base, m.n_parts, blockIdx.x);
+    load_part(sa, m.parts, p);
+    generate_block<T, DIM>(sa, blockIdx.x - (uint32_t)m.gen_base[p]);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) mk_move(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    __shared__ int32_t s_base[kMaxParts + 1];
+    item_prefix(m.n_parts, s_base, [&](int p) {
+        return (move_total(m.parts[p]) + kMoveChunk - 1) / kMoveChunk;
+    });
+    int cur = -1;
+    claim_items(m.queue + kQMove, (uint32_t)s_base[m.n_parts], [&](uint32_t item) {
+        const int p = part_of(s_base, m.n_parts, item);
+        if (p != cur) { load_part(sa, m.parts, p); cur = p; }
+        const uint32_t first = (item - (uint32_t)s_base[p]) * kMoveChunk;
+        const uint32_t end = min(first + kMoveChunk, move_total(sa));
+        move_span<T, DIM>(sa, first / 4u + (threadIdx.x & ~31u), end, blockDim.x);
+    });
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) mk_move_slow(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    for (int p = 0; p < m.n_parts; ++p) {
+        load_part(sa, m.parts, p);
+        move_slow_span<T, DIM>(sa, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) mk_scan1(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    const int p = part_of(m.scan_base, m.n_parts, blockIdx.x);
+    load_part(sa, m.parts, p);
+    scan1_block(sa, blockIdx.x - (uint32_t)m.scan_base[p]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) mk_scan2(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    const int p = part_of(m.scan_base, m.n_parts, blockIdx.x);
+    load_part(sa, m.parts, p);
+    scan2_block(sa, blockIdx.x - (uint32_t)m.scan_base[p]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) mk_scatter(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    __shared__ int32_t s_base[kMaxParts + 1];
+    item_prefix(m.n_parts, s_base, [&](int p) {
+        uint64_t q_old;
+        return (uint32_t)((scatter_quads(m.parts[p], &q_old) + kScatterChunk - 1) / kScatterChunk);
+    });
+    int cur = -1;
+    claim_items(m.queue + kQScatter, (uint32_t)s_base[m.n_parts], [&](uint32_t item) {
+        const int p = part_of(s_base, m.n_parts, item);
+        if (p != cur) { load_part(sa, m.parts, p); cur = p; }
+        uint64_t q_old;
+        const uint64_t nq = scatter_quads(sa, &q_old);
+        const uint64_t first = (uint64_t)(item - (uint32_t)s_base[p]) * kScatterChunk;
+        const uint64_t end = first + kScatterChunk < nq ? first + kScatterChunk : nq;
+        scatter_span(sa, first + (threadIdx.x & ~31u), end, blockDim.x);
+    });
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kTileCells, 4) mk_cell(MultiArgs<T> m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ StepArgs<T> sa;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
+    uint32_t phase = 0;
+    int cur = -1;
+    CellSmem sm;
+    claim_items(m.queue + kQCell, (uint32_t)m.tile_base[m.n_parts], [&](uint32_t item) {
+        const int p = part_of(m.tile_base, m.n_parts, item);
+        if (p != cur) {
+            load_part(sa, m.parts, p);
+            cur = p;
+            sm = cell_smem(smem_raw, &s_bar, (uint32_t)sa.tile_budget);
+        }
+        cell_tile<T, DIM>(sa, (int64_t)(item - (uint32_t)m.tile_base[p]), sm, phase);
+    });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCollideCells, 6) mk_collide(MultiArgs<T> m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ StepArgs<T> sa;
+    constexpr int kPitch = collide_stage_pitch<T>();
+    CollideSmem<T> sm;
+    sm.s0 = reinterpret_cast<T*>(smem_raw);
+    sm.s1 = sm.s0 + kPitch;
+    sm.s2 = sm.s1 + kPitch;
+    sm.bar = &s_bar;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
+    uint32_t phase = 0;
+    int cur = -1;
+    CellTally tl;
+    claim_items(m.queue + kQCollide, (uint32_t)m.ctile_base[m.n_parts], [&](uint32_t item) {
+        const int p = part_of(m.ctile_base, m.n_parts, item);
+        if (p != cur) {
+            // the tallies belong to the part they were counted in
+            if (cur >= 0) { flush_tally<T>(sa.ctr, tl); tl = CellTally(); }
+            load_part(sa, m.parts, p);
+            cur = p;
+        }
+        collide_tile<T>(sa, (int64_t)(item - (uint32_t)m.ctile_base[p]), sm, phase, tl);
+    });
+    if (cur >= 0) flush_tally<T>(sa.ctr, tl);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBigThreads, 2) mk_cell_big(MultiArgs<T> m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_red[2 * (kBigThreads / 32)];
+    __shared__ StepArgs<T> sa;
+    for (int p = 0; p < m.n_parts; ++p) {
+        load_part(sa, m.parts, p);
+        cell_big_part<T, DIM>(sa, blockIdx.x, gridDim.x, smem_raw, s_red);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) mk_collide_big(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    for (int p = 0; p < m.n_parts; ++p) {
+        load_part(sa, m.parts, p);
+        collide_big_part<T>(sa, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                            gridDim.x * (blockDim.x >> 5));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) mk_reduce(MultiArgs<T> m)
+{
+    __shared__ StepArgs<T> sa;
+    for (int p = 0; p < m.n_parts; ++p) {
+        load_part(sa, m.parts, p);
+        reduce_part(sa, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    }
+}
+
+// the step's end of every part, and the claim counters zeroed for the next
+// step (every queue-driven kernel of this step has completed)
+template <typename T>
+__global__ void mk_step_end(MultiArgs<T> m)
+{
+    if (threadIdx.x < (uint32_t)m.n_parts) step_end_part(m.parts[threadIdx.x]);
+    if (threadIdx.x < (uint32_t)kQueueKinds) m.queue[threadIdx.x] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -2184,8 +2767,7 @@ void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t
 {
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
-        launch_pdl(ls, k_scan1, a.scan_blocks, kScanThreads, 0, s, (const uint32_t*)a.count, a.block_sums,
-                   a.total_cells);
+        launch_pdl(ls, k_scan1<T>, a.scan_blocks, kScanThreads, 0, s, a);
         launch_pdl(ls, k_scan2<T>, a.scan_blocks, kScanThreads, 0, s, a);
     });
 }
@@ -2328,6 +2910,118 @@ cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
     }));
     if (e == cudaSuccess) e = raise_cell_smem_limit(prec, dim, cell_smem_bytes(prec, tile_budget));
     return e;
+}
+
+// ---- several problems per launch ----------------------------------------
+template <typename T>
+static const MultiArgs<T>& MA(const void* p) { return *static_cast<const MultiArgs<T>*>(p); }
+
+void launch_m_generate(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, {
+        const MultiArgs<T>& m = MA<T>(margs);
+        if (m.gcount_base[m.n_parts] > 0) mk_gen_count<T><<<m.gcount_base[m.n_parts], 256, 0, s>>>(m);
+        DISPATCH_DIM(ls.dim, (mk_generate<T, D><<<m.gen_base[m.n_parts], 256, 0, s>>>(m)));
+    });
+}
+
+void launch_m_move(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
+        const MultiArgs<T>& m = MA<T>(margs);
+        mk_move<T, D><<<ls.move_blocks, 256, 0, s>>>(m);
+        mk_move_slow<T, D><<<ls.sms * 2, 256, 0, s>>>(m);
+    }));
+}
+
+void launch_m_scan(int prec, const void* margs, const LaunchShape&, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, {
+        const MultiArgs<T>& m = MA<T>(margs);
+        mk_scan1<T><<<m.scan_base[m.n_parts], kScanThreads, 0, s>>>(m);
+        mk_scan2<T><<<m.scan_base[m.n_parts], kScanThreads, 0, s>>>(m);
+    });
+}
+
+void launch_m_scatter(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (mk_scatter<T><<<ls.scatter_blocks, 256, 0, s>>>(MA<T>(margs))));
+}
+
+void launch_m_cell(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, (mk_cell<T, D><<<ls.cell_blocks, kTileCells,
+                                                             cell_smem_bytes(prec, ls.tile_budget), s>>>(
+                                                   MA<T>(margs)))));
+}
+
+void launch_m_cell_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, (mk_cell_big<T, D><<<ls.big_blocks, kBigThreads,
+                                                                 big_smem(prec), s>>>(MA<T>(margs)))));
+}
+
+void launch_m_collide_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (mk_collide_big<T><<<ls.sms * 2, 256, 0, s>>>(MA<T>(margs))));
+}
+
+void launch_m_collide(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (mk_collide<T><<<ls.collide_blocks, kCollideCells, collide_smem(prec), s>>>(
+                             MA<T>(margs))));
+}
+
+void launch_m_reduce(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (mk_reduce<T><<<ls.sms * 4, 256, 0, s>>>(MA<T>(margs))));
+}
+
+void launch_m_step_end(int prec, const void* margs, const LaunchShape&, cudaStream_t s)
+{
+    DISPATCH_PREC(prec, (mk_step_end<T><<<1, kMaxParts, 0, s>>>(MA<T>(margs))));
+}
+
+cudaError_t prepare_multi_kernels(int prec, int dim, int tile_budget)
+{
+    cudaError_t e = cudaSuccess;
+    DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
+        e = cudaFuncSetAttribute(mk_cell_big<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)big_smem(prec));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mk_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)collide_smem(prec));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mk_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cell_smem_bytes(prec, tile_budget));
+    }));
+    return e;
+}
+
+// grids of the queue-driven kernels: as many CTAs as fit on the GPU at once
+void compute_multi_shape(int prec, int dim, int sms, LaunchShape* ls)
+{
+    ls->dim = dim;
+    ls->sms = sms;
+    if (ls->tile_budget <= 0) ls->tile_budget = 6144;
+    ls->tile_budget = (ls->tile_budget + 7) / 8 * 8;
+    prepare_multi_kernels(prec, dim, ls->tile_budget);
+    int bm = 0, bs = 0, bc = 0, bl = 0;
+    DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, mk_move<T, D>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, mk_scatter<T>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, mk_cell<T, D>, kTileCells,
+                                                      cell_smem_bytes(prec, ls->tile_budget));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, mk_collide<T>, kCollideCells,
+                                                      collide_smem(prec));
+    }));
+    ls->move_threads = 256;
+    ls->move_blocks = sms * (bm > 0 ? bm : 4);
+    ls->scatter_blocks = sms * (bs > 0 ? bs : 4);
+    ls->cell_blocks = sms * (bc > 0 ? bc : 2);
+    ls->collide_blocks = sms * (bl > 0 ? bl : 3);
+    ls->big_blocks = sms * 2;
+    ls->pdl = 0;
 }
 
 // Test hook for the bounded waits: an mbarrier expects 16 bytes that no

@@ -32,7 +32,10 @@ EXPORTS = [
     "dsmc_debug_set_state", "dsmc_debug_get_cells", "dsmc_debug_get_cell_state",
     "dsmc_debug_set_cell_state", "dsmc_debug_sample", "dsmc_debug_philox",
     "dsmc_run_ensemble_noalloc", "dsmc_debug_timeout_probe", "dsmc_run_ensemble_windows",
+    "dsmc_mixed_create", "dsmc_mixed_run", "dsmc_mixed_get_stats", "dsmc_mixed_last_error",
+    "dsmc_mixed_destroy",
 ]
+MIXED_PROFILE, MIXED_NO_GRAPH = 1, 2
 
 
 class DsmcError(RuntimeError):
@@ -127,9 +130,17 @@ def load_library(path=LIB_PATH):
                                                   C.c_uint64]
         lib.dsmc_run_ensemble_noalloc.argtypes = [P, C.c_int, C.c_double, C.c_int, ip, C.c_int,
                                                   C.c_uint64, dp, C.c_size_t]
+        lib.dsmc_mixed_create.argtypes = [C.POINTER(P), C.c_int, C.c_int, C.POINTER(P)]
+        lib.dsmc_mixed_run.argtypes = [P, ip, C.c_double, C.c_int, ip, C.c_int, C.c_uint64]
+        lib.dsmc_mixed_get_stats.argtypes = [P, C.POINTER(Stats)]
+        lib.dsmc_mixed_last_error.argtypes = [P]
+        lib.dsmc_mixed_last_error.restype = C.c_char_p
+        lib.dsmc_mixed_destroy.argtypes = [P]
+        lib.dsmc_mixed_destroy.restype = None
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype if name in (
-                "dsmc_destroy", "dsmc_last_error") else C.c_int
+                "dsmc_destroy", "dsmc_last_error", "dsmc_mixed_last_error",
+                "dsmc_mixed_destroy") else C.c_int
         _lib = lib
     return _lib
 
@@ -327,13 +338,7 @@ class Ensemble:
     def stats(self):
         s = Stats(struct_size=C.sizeof(Stats))
         self._check(self.lib.dsmc_get_stats(self.h, C.byref(s)), "dsmc_get_stats")
-        d = {k: getattr(s, k) for k, _ in Stats._fields_
-             if k not in ("ms_kernel", "launches_kernel", "shape")}
-        d["shape"] = {k: s.shape[i] for i, k in enumerate(SHAPE_KEYS)}
-        d["ms_kernel"] = {KERNEL_KINDS[i]: s.ms_kernel[i] for i in range(len(KERNEL_KINDS))}
-        d["launches_kernel"] = {KERNEL_KINDS[i]: int(s.launches_kernel[i])
-                                for i in range(len(KERNEL_KINDS))}
-        return d
+        return _stats_dict(s)
 
     # -- test hooks ------------------------------------------------------
     def debug_begin(self, runs=None, dt=None, seed=None):
@@ -419,36 +424,92 @@ def philox_gpu(ctr, key):
     return out
 
 
+def _stats_dict(s):
+    d = {k: getattr(s, k) for k, _ in Stats._fields_
+         if k not in ("ms_kernel", "launches_kernel", "shape")}
+    d["shape"] = {k: s.shape[i] for i, k in enumerate(SHAPE_KEYS)}
+    d["ms_kernel"] = {KERNEL_KINDS[i]: s.ms_kernel[i] for i in range(len(KERNEL_KINDS))}
+    d["launches_kernel"] = {KERNEL_KINDS[i]: int(s.launches_kernel[i])
+                            for i in range(len(KERNEL_KINDS))}
+    return d
+
+
 class MixedEnsemble:
     """A mixed-size ensemble (workloads.mixed): the runs that share a grid
-    form one batched context (their global run indices through
-    run_offset), and all contexts advance at once, one host thread and one
-    CUDA stream each, the GPU's block scheduler sharing the SMs among their
-    kernels.  Each group keeps its own samples (group sums over its runs)."""
+    form one part (a context; its runs' global indices through
+    run_offset).  mode "single" (default): every time step is one launch
+    per kernel kind over all parts (dsmc_mixed_run), the CTAs claiming
+    (part, tile) work items from device counters.  mode "concurrent": one
+    batched context per part, all advanced at once from one host thread
+    and one CUDA stream each (the GPU's block scheduler sharing the SMs).
+    Both give every part the samples dsmc_run_ensemble gives it alone."""
 
-    def __init__(self, m, precision="fp32", device=0, **kw):
+    def __init__(self, m, precision="fp32", device=0, mode="single", profile=False,
+                 use_graph=True, **kw):
         import torch
         self.m = m
+        self.mode = mode
         self.parts = []
+        self.lib = load_library()
+        self.h = None
         for w in m["groups"]:
-            stream = torch.cuda.Stream(device=device)
+            stream = torch.cuda.Stream(device=device) if mode == "concurrent" else None
+            if mode != "concurrent" and self.parts:
+                stream = self.parts[0].stream
             self.parts.append(Ensemble(w, precision=precision, device=device, stream=stream,
                                        run_offset=w["run0"], **kw))
+        if mode == "single":
+            arr = (C.c_void_p * len(self.parts))(*[e.h.value for e in self.parts])
+            h = C.c_void_p()
+            flags = (MIXED_PROFILE if profile else 0) | (0 if use_graph else MIXED_NO_GRAPH)
+            st = self.lib.dsmc_mixed_create(arr, len(self.parts), flags, C.byref(h))
+            if st != OK:
+                raise DsmcError(st, "dsmc_mixed_create failed")
+            self.h = h
 
-    def run(self):
-        from concurrent.futures import ThreadPoolExecutor
-        with ThreadPoolExecutor(max_workers=len(self.parts)) as ex:
-            for f in [ex.submit(e.run) for e in self.parts]:
-                f.result()
+    def run(self, steps=None, sample_steps=None, seed=None):
+        w0 = self.m["groups"][0]
+        if self.mode == "concurrent":
+            from concurrent.futures import ThreadPoolExecutor
+            with ThreadPoolExecutor(max_workers=len(self.parts)) as ex:
+                for f in [ex.submit(e.run, steps=steps, sample_steps=sample_steps, seed=seed)
+                          for e in self.parts]:
+                    f.result()
+            return self
+        steps = w0["steps"] if steps is None else steps
+        ss = np.ascontiguousarray(w0["sample_steps"] if sample_steps is None else sample_steps,
+                                  dtype=np.int32)
+        seed = w0["seed"] if seed is None else seed
+        runs = np.ascontiguousarray([w["runs"] for w in self.m["groups"]], dtype=np.int32)
+        st = self.lib.dsmc_mixed_run(self.h, _ptr(runs, C.c_int32), w0["dt"], steps,
+                                     _ptr(ss, C.c_int32) if len(ss) else None, len(ss), seed)
+        if st != OK:
+            msg = self.lib.dsmc_mixed_last_error(self.h)
+            raise DsmcError(st, "dsmc_mixed_run: %s" % (msg.decode() if msg else ""))
+        for e, w in zip(self.parts, self.m["groups"]):
+            e.runs = w["runs"]
+            e.n_samples = len(ss)
         return self
 
     def raw(self, group, t):
         return self.parts[group].raw(t)
 
+    def macro(self, group, t):
+        return self.parts[group].macro(t)
+
+    def mixed_stats(self):
+        """Totals of the last single-launch run (device time of its step
+        loop; per-kernel times in profile mode)."""
+        s = Stats(struct_size=C.sizeof(Stats))
+        st = self.lib.dsmc_mixed_get_stats(self.h, C.byref(s))
+        if st != OK:
+            raise DsmcError(st, "dsmc_mixed_get_stats failed")
+        return _stats_dict(s)
+
     def stats(self):
         per = [e.stats() for e in self.parts]
         keys = ("particle_steps", "generated", "removed", "wall_hits", "candidates", "collisions",
-                "particles_now")
+                "particles_now", "pool_steps", "big_pool_steps")
         out = {k: sum(int(s[k]) for s in per) for k in keys}
         out["error_word"] = 0
         for s in per:
@@ -457,6 +518,15 @@ class MixedEnsemble:
         return out
 
     def close(self):
+        if self.h is not None:
+            self.lib.dsmc_mixed_destroy(self.h)
+            self.h = None
         for e in self.parts:
             e.close()
         self.parts = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

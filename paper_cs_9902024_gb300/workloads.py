@@ -80,11 +80,13 @@ def _clip_ranges(w):
 
 
 def duct(nx=64, ny=32, runs=8, steps=200, n_samples=4, seed=1, ppc=20.0,
-         name="duct"):
-    """2-D rectangular duct, initially empty, impulsively started inflow on
-    the left face (n=1e20 m^-3, T=300 K, drift 400 m/s), diffuse walls at
-    300 K top and bottom, outflow on the right; cell = 1 mean free path,
-    dt = 0.2 mean collision time, ~`ppc` particles per cell at full fill."""
+         name="duct", filled=False):
+    """2-D rectangular duct, impulsively started inflow on the left face
+    (n=1e20 m^-3, T=300 K, drift 400 m/s), diffuse walls at 300 K top and
+    bottom, outflow on the right; cell = 1 mean free path, dt = 0.2 mean
+    collision time, ~`ppc` particles per cell at full fill.  The duct starts
+    empty, or (`filled`) filled with the inflow state (the same n, T and
+    drift), so that it holds ~`ppc` particles per cell from the first step."""
     n_in, T_in, U_in = 1.0e20, 300.0, 400.0
     lam = mean_free_path(D_HS, n_in)
     depth = 1.0
@@ -94,7 +96,8 @@ def duct(nx=64, ny=32, runs=8, steps=200, n_samples=4, seed=1, ppc=20.0,
     w = dict(
         name=name, dim=2, ncell=[nx, ny, 1], L=[nx * lam, ny * lam, depth],
         gas=dict(mass=M_AR, d_ref=D_HS, T_ref=T_in, omega=0.5, F_N=F_N),
-        fill=dict(kind=0, n=0.0, T=T_in, U=[0.0, 0.0, 0.0]),
+        fill=(dict(kind=1, n=n_in, T=T_in, U=[U_in, 0.0, 0.0]) if filled
+              else dict(kind=0, n=0.0, T=T_in, U=[0.0, 0.0, 0.0])),
         bcs=[
             bc(INFLOW, XMIN, n=n_in, T=T_in, U=(U_in, 0.0, 0.0)),
             bc(OUTFLOW, XMAX),
@@ -209,34 +212,38 @@ def plate128x64x64_n16(**kw):
 
 
 def mixed(n_runs=1024, cells_lo=32 * 16, cells_hi=512 * 256, steps=300, n_samples=4, seed=1,
-          draw_seed=12345, name="duct_mixed"):
+          draw_seed=12345, name="duct_mixed", grids=None, filled=True):
     """Mixed-size ensemble: n_runs runs of the duct, each on its own grid,
-    the cell count drawn log-uniformly in [cells_lo, cells_hi] (so the
-    particles a run holds at full fill, ~20 per cell, are log-uniform from
-    ~10k to ~2.6M) with aspect 2:1 and nx a multiple of 16.  Runs that drew
-    the same grid form one group (one batched context); run r keeps global
-    index r, so its draws do not depend on the grouping.  Returns
-    dict(name, runs, steps, groups): each group is a duct workload with
-    `runs` its run count and `run0` the global index of its first run
+    the cell count drawn log-uniformly in [cells_lo, cells_hi] with aspect
+    2:1 and nx a multiple of 16.  The runs start filled with the inflow
+    state (`filled`), so that a run holds ~20 particles per cell from the
+    first step: log-uniform from ~10k to ~2.6M particles per run over the
+    default range.  `grids`, a list of (nx, runs), replaces the draw with
+    those grids (ny = nx / 2).  Runs that share a grid form one group; run
+    r keeps global index r, so its draws do not depend on the grouping.
+    Returns dict(name, runs, steps, groups): each group is a duct workload
+    with `runs` its run count and `run0` the global index of its first run
     (global indices are handed out grid by grid, so each group's runs are
     one consecutive range)."""
     import numpy as np
-    rng = np.random.default_rng(draw_seed)
-    cells = np.exp(rng.uniform(np.log(cells_lo), np.log(cells_hi), size=n_runs))
-    nx = np.clip(np.round(np.sqrt(2.0 * cells) / 16.0) * 16, 32, 512).astype(int)
-    order = np.argsort(nx, kind="stable")
+    if grids is None:
+        rng = np.random.default_rng(draw_seed)
+        cells = np.exp(rng.uniform(np.log(cells_lo), np.log(cells_hi), size=n_runs))
+        nx = np.clip(np.round(np.sqrt(2.0 * cells) / 16.0) * 16, 32, 512).astype(int)
+        grids = [(g, int((nx == g).sum())) for g in sorted(set(nx.tolist()))]
+    else:
+        n_runs = sum(r for _, r in grids)
     groups = []
     # global run indices are assigned in grid order, so that every group is
-    # one consecutive range of runs (one run_offset per context)
+    # one consecutive range of runs (one run_offset per group)
     start = 0
-    for g in sorted(set(nx.tolist())):
-        cnt = int((nx == g).sum())
+    for g, cnt in grids:
         w = duct(nx=g, ny=g // 2, runs=cnt, steps=steps, n_samples=n_samples, seed=seed,
-                 name="%s_%dx%d" % (name, g, g // 2))
+                 name="%s_%dx%d" % (name, g, g // 2), filled=filled)
         w["run0"] = start
         groups.append(w)
         start += cnt
-    assert start == n_runs and len(order) == n_runs
+    assert start == n_runs
     return dict(name=name, runs=n_runs, steps=steps, groups=groups)
 
 

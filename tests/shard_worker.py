@@ -1,7 +1,8 @@
-"""One rank of the two-process sharding test (run as a module under the
-gloo backend; CPU only).  Each rank runs its share of the ensemble through
-the oracle with its global run offset, and the group sums are reduced with
-the same helper bench.py uses across GPUs."""
+"""One rank of the two-process sharding tests (run as a module under the
+gloo backend).  Each rank runs its share of the ensemble with its global
+run offset -- through the oracle on the CPU, or (--gpu fp32|fp64) through
+the library on the device -- and the group sums are reduced over the ranks
+on the host with the same helper bench.py uses across GPUs."""
 import argparse
 import os
 import sys
@@ -25,13 +26,26 @@ def main():
     p.add_argument("--port", type=int, required=True)
     p.add_argument("--per", type=int, default=16)
     p.add_argument("--out", required=True)
+    p.add_argument("--gpu", default=None, choices=[None, "fp32", "fp64"])
     a = p.parse_args()
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(a.port)
     dist.init_process_group("gloo", rank=a.rank, world_size=a.world)
     w = W.duct64x32_n8(steps=40, n_samples=2)
     G = shard.groups(a.per, a.world)
-    acc, st = run_ensemble(w, runs=a.per, run0=shard.run_offset(a.rank, a.per), groups=G)
+    if a.gpu:
+        # the device ensemble of this rank's runs (both ranks share the one
+        # GPU of a test box: independent ensembles, nothing waits across them)
+        import __graft_entry__ as g
+        g.build()
+        from paper_cs_9902024_gb300.dsmc import Ensemble
+        ens = Ensemble(w, precision=a.gpu, run_offset=shard.run_offset(a.rank, a.per))
+        ens.run(runs=a.per)
+        acc = np.stack([ens.raw(t) for t in range(len(w["sample_steps"]))])
+        st = ens.stats()
+        ens.close()
+    else:
+        acc, st = run_ensemble(w, runs=a.per, run0=shard.run_offset(a.rank, a.per), groups=G)
     tot = shard.allreduce_group_sums(acc)
     ps = shard.allreduce_sum(st["particle_steps"])
     if a.rank == 0:

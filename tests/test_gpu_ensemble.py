@@ -5,6 +5,7 @@ import pytest
 
 from oracle import Oracle, macro_from_acc, run_ensemble
 from paper_cs_9902024_gb300 import workloads as W
+from tests.parity import zscores
 
 pytestmark = pytest.mark.gpu
 
@@ -18,18 +19,9 @@ def D():
 
 
 def _zscores(mg, mo, nmin_mask):
-    out = []
-    for q, se in (("density", "se_density"), ("temperature", "se_temperature")):
-        d = mg[q] - mo[q]
-        s = np.sqrt(mg[se] ** 2 + mo[se] ** 2)
-        z = d[nmin_mask] / s[nmin_mask]
-        out.append(z[np.isfinite(z)])
-    for a in range(3):
-        d = mg["velocity"][..., a] - mo["velocity"][..., a]
-        s = np.sqrt(mg["se_velocity"][..., a] ** 2 + mo["se_velocity"][..., a] ** 2)
-        z = d[nmin_mask] / s[nmin_mask]
-        out.append(z[np.isfinite(z)])
-    return np.concatenate(out)
+    z, excluded = zscores(mg, mo, nmin_mask)
+    assert excluded <= 0.01 * max(z.size, 1), excluded
+    return z
 
 
 def _gpu_macro(ens, T):

@@ -49,13 +49,16 @@ def _lockstep(D, w, runs, steps, precision="fp64", every=1):
     return ens, orc, results
 
 
-def _assert_exact(results, tol_x=1e-12, tol_v=1e-10):
+def _assert_exact(results, tol_x=1e-10, tol_v=1e-10):
+    """Bit-exact integer outputs; per-particle errors (positions in cell
+    sizes, velocities relative to the particle's own speed, see
+    tests/parity.py) within tol_x / tol_v."""
     for per_step in results:
         for res in per_step:
             assert res["mismatch"] == 0
             assert res["ids_equal"] and res["count_equal"] and res["lcr_equal"]
             assert res["cand_equal"] and res["acc_equal"]
-            assert res["err_x"] <= tol_x and res["err_v"] <= tol_v
+            assert res["err_x_cell"] <= tol_x and res["err_v"] <= tol_v
 
 
 def test_fp64_duct_every_step(D):
@@ -100,7 +103,7 @@ def test_fp64_jet_big_cells_and_pulse(D):
     w = W.pulsed_jet(nx=24, ny=16, runs=2, steps=10, n_samples=2, orifice=4, pulse=5,
                      F_N=4.49e10 * 4)
     ens, orc, res = _lockstep(D, w, runs=2, steps=10)
-    _assert_exact(res, tol_x=1e-12, tol_v=1e-9)
+    _assert_exact(res, tol_x=1e-10, tol_v=1e-9)
     cnt = res[4][0]["cnt"]
     assert cnt.max() > 128, cnt.max()          # big-cell path taken
     assert ens.stats()["collisions"] > 0
@@ -223,8 +226,10 @@ def test_fp64_specular_and_tiny_cells(D):
 def test_fp32_one_step_from_identical_state(D):
     """FP32 device state, one step from the oracle's state (rounded to
     binary32 on both sides): cell assignments differ only where a particle
-    sits within float rounding of a cell face, per-particle relative error
-    <= 1e-5, and the integer outputs agree in every cell the mismatches do
+    sits within float rounding of a cell face, every particle's own error
+    <= 1e-5 (position in cell sizes -- the stricter measure -- and velocity
+    relative to its own speed with the 0.1 c_mp floor), and the integer
+    outputs agree in every cell the mismatches do
     not touch -- except where the oracle's NTC value x = M + rem lies within
     binary32 rounding of an integer (the device forms the product in FP32
     and only carries the remainder in FP64)."""
@@ -250,7 +255,8 @@ def test_fp32_one_step_from_identical_state(D):
             res = compare_run(ens, orc, r, w, 0, 0)
             total_mis += res["mismatch"]
             total_n += res["n"]
-            assert res["err_x"] <= 1e-5 and res["err_v"] <= 1e-5, res
+            assert res["err_x_cell"] <= 1e-5 and res["err_v"] <= 1e-5, (
+                res["err_x_cell"], res["err_v"])
             diff = res["cnt"] != res["co"]
             assert diff.sum() <= 2 * res["mismatch"]
             rem_o, _ = orc.get_cell_state(r)
@@ -263,32 +269,58 @@ def test_fp32_one_step_from_identical_state(D):
 
 
 def test_fp32_short_horizon(D):
-    """FP32 device state from t = 0: every step up to the first float-driven
-    change of a cell assignment matches the oracle exactly in its integer
-    outputs and to 1e-5 in positions and velocities; the horizon is
-    reported."""
-    w = W.duct64x32_n8(runs=8)
+    """FP32 device state from t = 0, 8 runs: each run's short horizon is its
+    first step with a float-driven difference -- a particle in another
+    cell, or an NTC candidate / accepted count that differs (binary32
+    (sigma c_r)_max and acceptance ratios).  Every step before a run's
+    horizon matches the oracle exactly in its integer outputs (ids, cell
+    counts, LCR, NTC counts), and every particle's own relative error is
+    <= 1e-5: its position relative to its position vector (floored at one
+    cell) and its velocity relative to its own speed (floored at 0.1 c_mp).
+    The position error in cell sizes, which grows with the steps as the
+    velocity's rounding is integrated, is reported beside it.  The horizon
+    is reported per run and must reach at least 10 steps in every run."""
+    runs = 8
+    w = W.duct64x32_n8(runs=runs)
     ens = D.Ensemble(w, precision="fp32", debug=True)
-    ens.debug_begin(runs=8)
-    orc = Oracle(w, runs=8)
-    for r in range(8):
+    ens.debug_begin(runs=runs)
+    orc = Oracle(w, runs=runs)
+    for r in range(runs):
         orc.init_run(r)
-    horizon, kind = None, None
-    for s in range(1, 61):
+    horizon = [None] * runs
+    kind = [None] * runs
+    worst_x = [0.0] * runs
+    worst_c = [0.0] * runs
+    worst_v = [0.0] * runs
+    checked = [0] * runs
+    max_steps = 80
+    for s in range(1, max_steps + 1):
         ens.debug_step(1)
-        for r in range(8):
+        live = [r for r in range(runs) if horizon[r] is None]
+        for r in range(runs):
             orc.step(r, s)
-        res = [compare_run(ens, orc, r, w, 0, 0) for r in range(8)]
-        if any(x["mismatch"] for x in res):
-            horizon, kind = s, "cell assignment"
+        for r in live:
+            x = compare_run(ens, orc, r, w)
+            if x["mismatch"]:
+                horizon[r], kind[r] = s, "cell assignment"
+                continue
+            if not (x["cand_equal"] and x["acc_equal"]):
+                horizon[r], kind[r] = s, "collision count"
+                continue
+            assert x["ids_equal"] and x["count_equal"] and x["lcr_equal"], (r, s)
+            assert x["err_x"] <= 1e-5 and x["err_v"] <= 1e-5, (r, s, x["err_x"], x["err_v"])
+            worst_x[r] = max(worst_x[r], x["err_x"])
+            worst_c[r] = max(worst_c[r], x["err_x_cell"])
+            worst_v[r] = max(worst_v[r], x["err_v"])
+            checked[r] += x["n_compared"]
+        if all(h is not None for h in horizon):
             break
-        # binary32 (sigma c_r)_max and acceptance ratios can flip an NTC
-        # count or an acceptance before any cell changes
-        if not all(x["cand_equal"] and x["acc_equal"] for x in res):
-            horizon, kind = s, "collision count"
-            break
-        for x in res:
-            assert x["ids_equal"] and x["count_equal"] and x["lcr_equal"]
-            assert x["err_x"] <= 1e-5 and x["err_v"] <= 1e-5
-    print("fp32 horizon over 8 runs: first differing step", horizon, kind)
-    assert horizon is None or horizon >= 2
+    for r in range(runs):
+        print("fp32 run %d: horizon %s (%s); up to it max per-particle relative error: "
+              "x %.2e (%.2e cells), v %.2e; %d particle-steps compared" % (
+                  r, horizon[r] if horizon[r] else ">%d" % max_steps, kind[r] or "none",
+                  worst_x[r], worst_c[r], worst_v[r], checked[r]))
+    reached = [h if h is not None else max_steps + 1 for h in horizon]
+    assert min(reached) >= 10, reached
+    # every run compared many particles before its horizon
+    assert min(checked) >= 10000, checked

@@ -42,13 +42,38 @@ def test_algorithmic_bytes_split_between_tile_and_big_cell_kernels():
     w = W.duct64x32_n8()
     st = {"particle_steps": 1000, "generated": 100, "pool_steps": 1200, "big_pool_steps": 300,
           "collisions": 50}
-    a = bench.algorithmic_bytes(w, st, steps=10, runs=8)
+    method, layout = bench.algorithmic_bytes(w, st, steps=10, runs=8)
+    # the method's bytes per particle-step (2-D): Motion 28, Indexing 60 (12
+    # scatter + 48 permute), Interaction 16
+    assert method["move"] == 900 * 28
+    assert method["scatter"] == 1200 * 12
+    assert method["cell"] == 900 * 48 and method["cell_big"] == 300 * 48
+    assert method["scatter"] + method["cell"] + method["cell_big"] == 1200 * 60
+    assert method["collide"] + method["collide_big"] == 1200 * 16
+    # this build's layout bytes
     gather = 8 + 2 * (2 * 4 + 3 * 4) + 8
     cells = 8 * 64 * 32
-    assert a["cell"] == (1200 - 300) * gather + cells * 10 * 4
-    assert a["cell_big"] == 300 * gather
-    assert a["move"] == 900 * (3 * 2 * 4 + 12)
-    assert a["scatter"] == 1200 * 20
+    assert layout["cell"] == (1200 - 300) * gather + cells * 10 * 4
+    assert layout["cell_big"] == 300 * gather
+    assert layout["move"] == 900 * (3 * 2 * 4 + 8)
+    assert layout["scatter"] == 1200 * 16
     st0 = dict(st, big_pool_steps=0)
-    a0 = bench.algorithmic_bytes(w, st0, steps=10, runs=8)
-    assert a0["cell"] + a0["cell_big"] == a["cell"] + a["cell_big"]
+    m0, l0 = bench.algorithmic_bytes(w, st0, steps=10, runs=8)
+    assert l0["cell"] + l0["cell_big"] == layout["cell"] + layout["cell_big"]
+    assert m0["cell"] + m0["cell_big"] == method["cell"] + method["cell_big"]
+    # 3-D: Motion 40, permute 56
+    w3 = W.plate3d(nx=8, ny=4, nz=4, runs=1)
+    m3, _ = bench.algorithmic_bytes(w3, st0, steps=10, runs=1)
+    assert m3["move"] == 900 * 40 and m3["cell"] == 1200 * 56
+
+
+def test_method_rows_are_bytes_over_summed_kernel_time():
+    sys.path.insert(0, ROOT)
+    import bench
+    method = {"move": 28e9, "scatter": 12e9, "cell": 48e9, "cell_big": 0, "scan": 0,
+              "collide": 16e9, "collide_big": 0}
+    ms = {"move": 10.0, "scan": 1.0, "scatter": 4.0, "cell": 15.0, "collide": 8.0}
+    rows = bench.method_rows(method, ms, peak=4000.0)
+    assert abs(rows["motion"]["achieved_gbs"] - 2800.0) < 1e-6
+    assert abs(rows["indexing"]["achieved_gbs"] - 60e9 / 0.020 / 1e9) < 1e-6
+    assert abs(rows["interaction"]["frac"] - 2000.0 / 4000.0) < 1e-12
