@@ -47,7 +47,7 @@ def parse():
                    help="skip the plain-mode, profile and CPU-baseline legs")
     p.add_argument("--workload", default="duct64x32_n512",
                    choices=["duct64x32_n8", "duct64x32_n512", "jet256x128_n64",
-                            "plate128x64x64_n16"],
+                            "plate128x64x64_n16", "mixed_n1024"],
                    help="workload (default: the 512-run duct the metric is quoted on; the others "
                         "are the parity workloads, measured the same way)")
     return p.parse_args()
@@ -65,6 +65,8 @@ WORKLOAD_TEXT = {
     "duct64x32_n512": "2-D duct 64x32, HS, 512 runs x 400 steps, 8 sample times",
     "jet256x128_n64": "2-D pulsed VHS jet 256x128, 64 runs x 1000 steps, 20 sample times",
     "plate128x64x64_n16": "3-D plate box 128x64x64, HS, 16 runs x 600 steps, 12 sample times",
+    "mixed_n1024": "1024 duct runs on 31 grids 32x16..512x256 (log-uniform cells), filled, "
+                   "300 steps, 4 sample times, one launch per kernel kind per step",
 }
 
 
@@ -217,7 +219,7 @@ METHOD_ROWS = {"motion": ("move",), "indexing": ("scan", "scatter", "cell", "cel
                "interaction": ("collide", "collide_big")}
 
 
-def algorithmic_bytes(w, st, steps, runs):
+def algorithmic_bytes(w, st, steps, runs, cells=None):
     """Bytes each kernel group moves over one ensemble (FP32 state).
 
     "method": the algorithmic bytes of the method's step that the kernel
@@ -230,7 +232,8 @@ def algorithmic_bytes(w, st, steps, runs):
     velocities."""
     D = w["dim"]
     t = 4
-    cells = runs * w["ncell"][0] * w["ncell"][1] * (w["ncell"][2] if D == 3 else 1)
+    if cells is None:
+        cells = runs * w["ncell"][0] * w["ncell"][1] * (w["ncell"][2] if D == 3 else 1)
     moved_old = st["particle_steps"] - st["generated"]
     pool = st["pool_steps"]
     big = st.get("big_pool_steps", 0)
@@ -326,10 +329,140 @@ def run_reference(args):
     }), flush=True)
 
 
+def roofline_of(w, prs, steps, runs, cells=None):
+    """Per-kernel-kind times of a profile-mode run -> the kernels' table, the
+    dominant kernel's roofline entry and the method steps' rows."""
+    algo, layout = algorithmic_bytes(w, prs, steps, runs, cells)
+    peak, src = measured_peaks()
+    kern = {}
+    total_ms = sum(prs["ms_kernel"].values())
+    for k, msk in prs["ms_kernel"].items():
+        if msk <= 0:
+            continue
+        e = {"ms": msk, "share": msk / total_ms, "launches": prs["launches_kernel"][k]}
+        if algo.get(k):
+            e["achieved_gbs"] = algo[k] / (msk / 1e3) / 1e9
+            e["frac_of_%s_hbm" % src] = e["achieved_gbs"] / peak
+        if layout.get(k):
+            e["layout_gbs"] = layout[k] / (msk / 1e3) / 1e9
+            e["layout_frac_of_%s_hbm" % src] = e["layout_gbs"] / peak
+        kern[k] = e
+    dom = max((k for k in kern if algo.get(k)), key=lambda k: kern[k]["ms"])
+    achieved = kern[dom]["achieved_gbs"]
+    roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+            "bytes_per_launch": algo[dom] / prs["launches_kernel"][dom],
+            "bytes": "the method's algorithmic bytes of the kernel's step",
+            "layout_achieved": kern[dom].get("layout_gbs"),
+            "layout_frac": (kern[dom].get("layout_gbs") or 0.0) / peak}
+    return kern, roof, method_rows(algo, prs["ms_kernel"], peak), dom
+
+
+def bench_mixed(args):
+    """The mixed-size ensemble: every step one launch per kernel kind over
+    the 1024 runs of 31 grids (work queues), device-timed; end to end with
+    every part's group sums copied to the host; the same ensemble as 31
+    concurrent per-grid contexts for comparison; per-kernel roofline from a
+    profile-mode run; the FP64 oracle on a bounded sample."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_cs_9902024_gb300 import workloads as W
+    from paper_cs_9902024_gb300.dsmc import MixedEnsemble
+    m = W.mixed_n1024()
+    steps = m["steps"]
+    T = len(m["groups"][0]["sample_steps"])
+    me = MixedEnsemble(m)
+    for _ in range(max(args.warmup, 3)):
+        me.run()
+    ps = me.stats()["particle_steps"]
+    stream = me.parts[0].stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            me.run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    value = ps * args.steps / (ms / 1e3)
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        me.run()
+        raws = [np.stack([me.raw(gi, t) for t in range(T)]) for gi in range(len(m["groups"]))]
+        for st in me.stats()["groups"]:
+            h2d += st["h2d_bytes"]
+            d2h += st["d2h_bytes"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    del raws
+    stats = me.stats()
+    n_launch = len(me.parts)
+    me.close()
+    # -- the same ensemble as concurrent per-grid contexts ----------------
+    mc = MixedEnsemble(m, mode="concurrent")
+    mc.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mc.run()
+    torch.cuda.synchronize()
+    conc_s = time.perf_counter() - t0
+    mc.close()
+    # -- per-kernel-kind device times (profile mode) ---------------------
+    mp = MixedEnsemble(m, profile=True)
+    mp.run()
+    prs = dict(mp.mixed_stats())
+    mp.close()
+    cells = sum(w["runs"] * w["ncell"][0] * w["ncell"][1] for w in m["groups"])
+    kern, roof, rows, dom = roofline_of(m["groups"][0], prs, steps, m["runs"], cells)
+    # -- the FP64 oracle on a bounded sample: the first steps of 16 runs of
+    #    the median grid, threads over run groups ------------------------
+    from oracle import run_ensemble
+    wm = m["groups"][len(m["groups"]) // 2]
+    cores = min(cpu_cores(), 16)
+    t0 = time.perf_counter()
+    _, sto = run_ensemble(wm, runs=min(16, wm["runs"]), steps=20, sample_steps=[], threads=cores)
+    dto = time.perf_counter() - t0
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": m["name"] + " (" + WORKLOAD_TEXT["mixed_n1024"] + ")",
+                   "runs": m["runs"], "grids": len(m["groups"]), "steps_per_run": steps,
+                   "sample_times": T, "mode": "one launch per kernel kind per step, work queues, "
+                   "CUDA graph per step", "state": "fp32", "sampling": "fp64 group sums",
+                   "l2": "inputs larger than L2 (pool ~30 GB)"},
+        "clocks": clk.summary(),
+        "e2e": {"value": ps * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": args.steps * (steps * 11 + 6 * n_launch + T),
+        "particle_steps_per_step": ps,
+        "particles_at_end": stats["particles_now"],
+        "concurrent_contexts": {"value": ps / conc_s, "unit": UNIT, "contexts": n_launch,
+                                "note": "one batched context per grid, each on its own stream "
+                                        "and host thread; wall clock of one ensemble"},
+        "roofline": roof, "method_steps": rows, "kernels": kern,
+        "cpu_baseline": {"value": sto["particle_steps"] / dto, "unit": UNIT, "cores": cores,
+                         "kind": "oracle",
+                         "sample": "16 runs of the %dx%d grid x 20 of the 300 steps, FP64, %d "
+                                   "thread(s) over run groups, %.1f s"
+                                   % (wm["ncell"][0], wm["ncell"][1], cores, dto)},
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mixed_n1024":
+        return bench_mixed(args)
     ws, rank, local = dist_env()
     import numpy as np
     import torch
@@ -460,24 +593,7 @@ def main():
         for key in ("ms_kernel", "launches_kernel"):
             prs[key] = {k: sum(p[key][k] for p in passes) / len(passes) for k in passes[-1][key]}
         prs["ms_steps"] = sum(p["ms_steps"] for p in passes) / len(passes)
-        algo, layout = algorithmic_bytes(w, prs, steps, runs)
-        peak, src = measured_peaks()
-        kern = {}
-        total_ms = sum(prs["ms_kernel"].values())
-        for k, msk in prs["ms_kernel"].items():
-            if msk <= 0:
-                continue
-            e = {"ms": msk, "share": msk / total_ms, "launches": prs["launches_kernel"][k]}
-            if algo.get(k):
-                e["achieved_gbs"] = algo[k] / (msk / 1e3) / 1e9
-                e["frac_of_%s_hbm" % src] = e["achieved_gbs"] / peak
-            if layout.get(k):
-                e["layout_gbs"] = layout[k] / (msk / 1e3) / 1e9
-                e["layout_frac_of_%s_hbm" % src] = e["layout_gbs"] / peak
-            kern[k] = e
-        dom = max((k for k in kern if algo.get(k)), key=lambda k: kern[k]["ms"])
-        achieved = kern[dom]["achieved_gbs"]
-        traffic = None
+        kern, roof, rows, dom = roofline_of(w, prs, steps, runs)
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
             try:
@@ -488,18 +604,11 @@ def main():
                     units = prs["pool_steps"]
                     if dom == "cell":
                         units -= prs["big_pool_steps"]
-                    traffic = per_particle * units / prs["launches_kernel"][dom]
+                    roof["traffic"] = per_particle * units / prs["launches_kernel"][dom]
             except Exception:
-                traffic = None
-        out["roofline"] = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved,
-                           "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                           "traffic": traffic, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"
-                           if src == "measured" else src,
-                           "bytes_per_launch": algo[dom] / prs["launches_kernel"][dom],
-                           "bytes": "the method's algorithmic bytes of the kernel's step",
-                           "layout_achieved": kern[dom].get("layout_gbs"),
-                           "layout_frac": (kern[dom].get("layout_gbs") or 0.0) / peak}
-        out["method_steps"] = method_rows(algo, prs["ms_kernel"], peak)
+                roof["traffic"] = None
+        out["roofline"] = roof
+        out["method_steps"] = rows
         out["kernels"] = kern
         out["profile_run_ms"] = prs["ms_steps"]
         out["profile_shape"] = passes[-1]["shape"]

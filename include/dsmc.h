@@ -59,6 +59,7 @@ enum { DSMC_FACE_XMIN = 0, DSMC_FACE_XMAX = 1, DSMC_FACE_YMIN = 2, DSMC_FACE_YMA
        DSMC_FACE_ZMIN = 4, DSMC_FACE_ZMAX = 5, DSMC_FACE_PLATE = 6 };
 enum { DSMC_MODE_BATCHED = 0, DSMC_MODE_PLAIN = 1 };
 enum { DSMC_FP32 = 0, DSMC_FP64 = 1 };
+enum { DSMC_TUNE_OFF = 0, DSMC_TUNE_SEARCH = 1, DSMC_TUNE_LOAD = 2 };
 
 typedef enum {
     DSMC_Q_RAW_MOMENTS = 0,        /* [G][ncells][7] group sums, see below */
@@ -148,15 +149,23 @@ typedef struct {
     int64_t run_offset;       /* global index of run 0 of this context: the
                                  runs draw as runs run_offset.. (sharding an
                                  ensemble over processes or GPUs) */
-    int32_t autotune;         /* batched mode: 1 = on the first run of a
+    int32_t autotune;         /* batched mode, runs of >= 100 steps:
+                                 DSMC_TUNE_SEARCH = on the first run of a
                                  problem size, advance a trial ensemble to
                                  mid-run and time candidate launch shapes
                                  (sort/gather tile budget, grid sizes of the
                                  Motion, scatter and collision kernels) over
                                  short windows, keeping the fastest per kernel
                                  time per particle; the real run then starts
-                                 from t = 0.  Results do not depend on the
-                                 shapes.  0 = fixed shapes (default) */
+                                 from t = 0.  DSMC_TUNE_LOAD = take the shape
+                                 stored in the file `tune_cache` for this GPU
+                                 and problem (device name, SM count,
+                                 precision, grid, runs, steps and a hash of
+                                 the domain, gas and boundaries); if there is
+                                 none, search as above and append the result
+                                 to the file.  Results do not depend on the
+                                 shapes.  DSMC_TUNE_OFF = fixed shapes
+                                 (default) */
     int32_t shape[4];         /* batched mode: entries > 0 replace the default
                                  launch shape (as dsmc_stats.shape: Motion
                                  CTAs, scatter CTAs, sort/gather tile budget
@@ -167,7 +176,22 @@ typedef struct {
                                  multiple of 8); else DSMC_E_INVALID.  With
                                  autotune the tuned shape replaces it.
                                  Results do not depend on the shape. */
+    int32_t checks;           /* 1: after every run a device pass verifies the
+                                 final pool -- each particle's cell key inside
+                                 the table and its position inside that
+                                 cell's range, ids increasing within a cell,
+                                 offsets inside the cell, finite velocities;
+                                 a failure makes the run return DSMC_E_STATE
+                                 with the count and the first failing
+                                 position.  0: no check (default) */
+    int32_t reserved_;
+    const char* tune_cache;   /* DSMC_TUNE_LOAD: path of the launch-shape
+                                 cache (a text file of "key shape" lines; the
+                                 library reads it and appends to it) */
 } dsmc_options;
+/* Callers built against an older dsmc_options (without checks and
+ * tune_cache: struct_size = offsetof(dsmc_options, checks)) are accepted;
+ * the fields they do not have are zero. */
 
 typedef struct {
     uint32_t struct_size;
@@ -191,7 +215,8 @@ typedef struct {
     int32_t shape[4];         /* launch shape in use: Motion CTAs, scatter
                                  CTAs, sort/gather tile budget (particles),
                                  collision CTAs */
-    int32_t tuned;            /* 1 if the shape came from options.autotune */
+    int32_t tuned;            /* 1: the shape came from an autotune search; 2:
+                                 from the tune cache file */
     uint64_t big_pool_steps;  /* the part of pool_steps in cells above 128
                                  particles (ordered and gathered one cell per
                                  CTA) */

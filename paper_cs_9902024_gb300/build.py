@@ -1,6 +1,6 @@
 """In-tree build of libdsmc.so for sm_103a with nvcc (no cmake).
 
-The two translation units compile in parallel; the shared library links the
+The translation units compile in parallel; the shared library links the
 CUDA runtime dynamically (same soname as the one PyTorch loads) with an rpath
 to the toolkit.
 """
@@ -15,10 +15,15 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libdsmc.so")
-SOURCES = ["dsmc_kernels.cu", "dsmc_engine.cu"]
+# (source, object, extra flags): the kernels twice -- FP32 state with fused
+# multiply-add contraction, FP64 state without it (rounded as the FP64
+# oracle rounds) -- and the host engine
+UNITS = [("dsmc_kernels.cu", "dsmc_kernels_f32.o", ["-fmad=true"]),
+         ("dsmc_kernels.cu", "dsmc_kernels_f64.o", ["-fmad=false", "-DDSMC_KERNELS_FP64"]),
+         ("dsmc_engine.cu", "dsmc_engine.o", ["-fmad=false"])]
 HEADERS = [os.path.join(CSRC, "dsmc_internal.cuh"), os.path.join(ROOT, "include", "dsmc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
+NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
 
@@ -42,12 +47,12 @@ def build(force=False, verbose=False):
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     objs, procs = [], []
-    for src in SOURCES:
+    for src, obj_name, extra in UNITS:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD_DIR, obj_name)
         objs.append(obj)
-        if force or _stale(obj, [path] + HEADERS):
-            cmd = [nvcc] + NVCC_FLAGS + ["-c", path, "-o", obj + ".tmp"]
+        if force or _stale(obj, [path] + HEADERS + [os.path.abspath(__file__)]):
+            cmd = [nvcc] + NVCC_FLAGS + extra + ["-c", path, "-o", obj + ".tmp"]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((subprocess.Popen(cmd), obj))

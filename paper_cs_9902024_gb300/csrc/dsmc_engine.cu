@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -89,6 +90,8 @@ struct dsmc_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t graph_key = ~0ull;
     uint64_t tuned_key = 0;          // (runs << 1) | 1 once options.autotune ran
+    int tuned_how = 0;               // 1: searched, 2: read from the tune cache
+    std::string tune_cache;          // options.tune_cache
     // last run
     bool have_run = false;
     int last_runs = 0, last_steps = 0, last_samples = 0;
@@ -566,7 +569,7 @@ static void fill_stats(dsmc_ctx* ctx, const Counters& h)
     s.shape[1] = ctx->ls.scatter_blocks;
     s.shape[2] = ctx->ls.tile_budget;
     s.shape[3] = ctx->ls.collide_blocks;
-    s.tuned = ctx->tuned_key != 0 ? 1 : 0;
+    s.tuned = ctx->tuned_key != 0 ? ctx->tuned_how : 0;
 }
 
 static dsmc_status check_error_word(dsmc_ctx* ctx, uint32_t e)
@@ -679,7 +682,8 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     if (!domain || !cells || !gas || (n_b > 0 && !b) || n_b < 0 || n_b > DSMC_MAX_BC)
         return DSMC_E_INVALID;
     if (domain->struct_size < sizeof(dsmc_domain) || cells->struct_size < sizeof(dsmc_cells) ||
-        gas->struct_size < sizeof(dsmc_gas) || (opt && opt->struct_size < sizeof(dsmc_options)))
+        gas->struct_size < sizeof(dsmc_gas) ||
+        (opt && opt->struct_size < offsetof(dsmc_options, checks)))
         return DSMC_E_INVALID;
     if (domain->dim != 2 && domain->dim != 3) return DSMC_E_INVALID;
     for (int a = 0; a < domain->dim; ++a)
@@ -712,6 +716,10 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
         if (s.hi[0] > n0 || s.hi[1] > n1) return DSMC_E_INVALID;
         if (s.step_from < 0 || s.step_to < 0) return DSMC_E_INVALID;
     }
+    if (opt && opt->struct_size >= sizeof(dsmc_options) &&
+        (opt->autotune < DSMC_TUNE_OFF || opt->autotune > DSMC_TUNE_LOAD ||
+         (opt->autotune == DSMC_TUNE_LOAD && !opt->tune_cache)))
+        return DSMC_E_INVALID;
     if (opt) {
         for (int i = 0; i < 4; ++i) {
             const int32_t v = opt->shape[i];
@@ -730,8 +738,13 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     std::memset(&ctx->opt, 0, sizeof(ctx->opt));
     ctx->opt.struct_size = sizeof(dsmc_options);
     ctx->opt.use_graph = 1;
-    if (opt) ctx->opt = *opt;
+    // an older caller's struct is shorter: the fields it lacks stay zero
+    if (opt) std::memcpy(&ctx->opt, opt, std::min<size_t>(opt->struct_size, sizeof(dsmc_options)));
     ctx->opt.struct_size = sizeof(dsmc_options);
+    if (ctx->opt.tune_cache) {
+        ctx->tune_cache = ctx->opt.tune_cache;   // the library keeps its own copy
+        ctx->opt.tune_cache = nullptr;
+    }
     ctx->prec = ctx->opt.precision == DSMC_FP64 ? DSMC_FP64 : DSMC_FP32;
     ctx->dim = domain->dim;
     ctx->ncells = (int)nc;
@@ -889,6 +902,102 @@ static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
     return DSMC_OK;
 }
 
+// ---- launch-shape cache (options.autotune = DSMC_TUNE_LOAD) ------------
+// One line per entry: "<key> <move CTAs> <scatter CTAs> <tile budget>
+// <collision CTAs>"; the last line with a key wins.  The key names the GPU
+// (name, SM count), the precision, the run count and steps, and hashes the
+// problem description (FNV-1a over domain, grid, gas and boundaries).
+static uint64_t fnv1a(uint64_t h, const void* p, size_t n)
+{
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static std::string tune_key(const dsmc_ctx* ctx, int n_runs, int steps)
+{
+    uint64_t h = 14695981039346656037ull;
+    const dsmc_domain& d = ctx->dom;
+    h = fnv1a(h, &d.dim, sizeof d.dim);
+    h = fnv1a(h, d.extent, sizeof d.extent);
+    h = fnv1a(h, &d.fill, sizeof d.fill);
+    h = fnv1a(h, &d.fill_n, sizeof d.fill_n);
+    h = fnv1a(h, &d.fill_T, sizeof d.fill_T);
+    h = fnv1a(h, d.fill_U, sizeof d.fill_U);
+    h = fnv1a(h, ctx->cells.n, sizeof ctx->cells.n);
+    const double g[5] = {ctx->gas.mass, ctx->gas.d_ref, ctx->gas.T_ref, ctx->gas.omega, ctx->gas.F_N};
+    h = fnv1a(h, g, sizeof g);
+    for (const dsmc_boundary& b : ctx->bcs) {
+        const int32_t iv[8] = {b.kind, b.face, b.lo[0], b.lo[1], b.hi[0], b.hi[1], b.step_from, b.step_to};
+        const double dv[5] = {b.n, b.T, b.U[0], b.U[1], b.U[2]};
+        h = fnv1a(h, iv, sizeof iv);
+        h = fnv1a(h, dv, sizeof dv);
+        h = fnv1a(h, &b.plate_axis, sizeof b.plate_axis);
+        h = fnv1a(h, &b.plate_index, sizeof b.plate_index);
+    }
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess) name = prop.name;
+    else cudaGetLastError();
+    for (char& c : name)
+        if (c == ' ' || c == '\t') c = '_';
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%s/sm%d/%s/runs%d/steps%d/%016llx", name.c_str(), ctx->sms,
+                  ctx->prec == DSMC_FP64 ? "fp64" : "fp32", n_runs, steps, (unsigned long long)h);
+    return buf;
+}
+
+static bool tune_load(const std::string& path, const std::string& key, int shape[4])
+{
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    char k[256];
+    int v[4];
+    bool found = false;
+    while (std::fscanf(f, "%255s %d %d %d %d", k, &v[0], &v[1], &v[2], &v[3]) == 5) {
+        if (key == k && v[0] >= 1 && v[1] >= 1 && v[2] >= 256 && v[2] <= kMaxTileBudget && v[3] >= 1) {
+            for (int i = 0; i < 4; ++i) shape[i] = v[i];
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void tune_store(const std::string& path, const std::string& key, const LaunchShape& ls)
+{
+    FILE* f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), ls.move_blocks, ls.scatter_blocks,
+                 ls.tile_budget, ls.collide_blocks);
+    std::fclose(f);
+}
+
+// options.checks: the consistency pass over the pool the last step wrote
+// (buffer `cur`), read back; a failure is DSMC_E_STATE.
+static dsmc_status run_checks(dsmc_ctx* ctx, int cur, int run0, int n_launch)
+{
+    CK(cudaMemsetAsync(&ctx->d_ctr->check_fail, 0, sizeof(uint32_t), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->d_ctr->check_first, 0xFF, sizeof(uint32_t), ctx->stream));
+    AnyArgs u;
+    launch_check(ctx->prec, build_args(ctx, u, cur, run0, n_launch), ctx->ls, ctx->stream);
+    CK(cudaGetLastError());
+    Counters h;
+    dsmc_status st = read_counters(ctx, &h);
+    if (st) return st;
+    if (h.check_fail) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf,
+                      "consistency check failed at %u pool positions (first: %u)", h.check_fail,
+                      h.check_first);
+        return fail(ctx, DSMC_E_STATE, buf);
+    }
+    return DSMC_OK;
+}
+
 static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
                                const int32_t* first, const int32_t* last, int n_samples,
                                uint64_t seed)
@@ -910,11 +1019,27 @@ static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     // room to reach mid-run)
     if (ctx->opt.autotune && !plain && steps >= 100 &&
         ctx->tuned_key != (((uint64_t)n_runs << 1) | 1u)) {
-        st = autotune(ctx, n_runs, steps);
-        if (st) return st;
-        destroy_graphs(ctx);
-        st = prepare(ctx, n_runs, dt, steps, first, last, n_samples, seed, n_launch);
-        if (st) return st;
+        const bool use_cache = ctx->opt.autotune == DSMC_TUNE_LOAD && !ctx->tune_cache.empty();
+        const std::string key = use_cache ? tune_key(ctx, n_runs, steps) : std::string();
+        int shape[4];
+        if (use_cache && tune_load(ctx->tune_cache, key, shape)) {
+            ctx->ls.tile_budget = shape[2];
+            compute_launch_shape(ctx->prec, ctx->dim, ctx->sms, &ctx->ls);
+            ctx->ls.move_blocks = shape[0];
+            ctx->ls.scatter_blocks = shape[1];
+            ctx->ls.collide_blocks = shape[3];
+            CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
+            ctx->tuned_key = ((uint64_t)n_runs << 1) | 1u;
+            ctx->tuned_how = 2;
+        } else {
+            st = autotune(ctx, n_runs, steps);
+            if (st) return st;
+            ctx->tuned_how = 1;
+            if (use_cache) tune_store(ctx->tune_cache, key, ctx->ls);
+            destroy_graphs(ctx);
+            st = prepare(ctx, n_runs, dt, steps, first, last, n_samples, seed, n_launch);
+            if (st) return st;
+        }
     }
     const bool profile = ctx->opt.profile != 0;
     const bool graph = !plain && !profile && ctx->opt.use_graph;
@@ -954,6 +1079,12 @@ static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
             }
             ctx->cur ^= 1;
         }
+        if (ctx->opt.checks && plain && r + 1 < n_runs) {
+            // each run of the plain loop is checked before the next one
+            // reuses the buffers (the last one after the timed loop)
+            st = run_checks(ctx, ctx->cur, r0, n_launch);
+            if (st) return st;
+        }
     }
     cudaEvent_t e2 = event_at(ctx, evn);
     if (!e2) return fail(ctx, DSMC_E_CUDA, "cudaEventCreate failed");
@@ -989,6 +1120,10 @@ static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
     ctx->stats.particles_now = total;
     st = check_error_word(ctx, h.error);
     if (st) return st;
+    if (ctx->opt.checks) {
+        st = run_checks(ctx, ctx->cur, (int)ctx->opt.run_offset + (plain ? n_runs - 1 : 0), n_launch);
+        if (st) return st;
+    }
     ctx->have_run = true;
     ctx->last_runs = n_runs;
     ctx->last_steps = steps;
@@ -1104,7 +1239,9 @@ dsmc_status dsmc_debug_step(dsmc_ctx* ctx, int n_steps)
     dsmc_status st = read_counters(ctx, &h);
     if (st) return st;
     fill_stats(ctx, h);
-    return check_error_word(ctx, h.error);
+    st = check_error_word(ctx, h.error);
+    if (!st && ctx->opt.checks) st = run_checks(ctx, ctx->cur, 0, n);
+    return st;
 }
 
 // run-local cell index <-> per-axis indices
@@ -1744,6 +1881,7 @@ dsmc_status dsmc_mixed_run(dsmc_mixed* m, const int32_t* n_runs, double dt, int 
         ms.particles_now += total;
         ms.capacity += c->cap_old;
         st = check_error_word(c, h.error);
+        if (!st && c->opt.checks) st = run_checks(c, m->cur, (int)c->opt.run_offset, n_runs[i]);
         if (st) {
             if (!worst) {
                 char buf[64];

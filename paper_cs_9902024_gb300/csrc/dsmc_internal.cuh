@@ -76,6 +76,8 @@ struct Counters {
     uint32_t error, step, n_big, n_slow;
     uint32_t probe;        // error bits of the timeout test hook only
     uint32_t scan_ticket;  // CTAs of the scan's first pass done (reset by the last)
+    uint32_t check_fail;   // options.checks: pool positions that failed the check
+    uint32_t check_first;  // the first of them (0xFFFFFFFF: none)
 };
 
 // The configuration constants that the streaming kernels use for every
@@ -155,8 +157,8 @@ struct StepArgs {
 // numbered part by part in the order of `parts`.
 constexpr int kMaxParts = 64;
 enum QueueKind : int { kQMove = 0, kQScatter = 1, kQCell = 2, kQCollide = 3, kQueueKinds = 4 };
-constexpr uint32_t kMoveChunk = 8192;      // slots per Motion item
-constexpr uint32_t kScatterChunk = 2048;   // groups of four slots per scatter item
+constexpr uint32_t kMoveChunk = 8192;      // slots per Motion item (a multiple of 1024)
+constexpr uint32_t kScatterChunk = 8192;   // slots per scatter item (a multiple of 1024)
 
 template <typename T>
 struct MultiArgs {
@@ -171,8 +173,7 @@ struct MultiArgs {
     int32_t gcount_base[kMaxParts + 1];   // Generation counting CTAs before each part
 };
 
-// Launchers (dsmc_kernels.cu).  `prec` is DSMC_FP32 or DSMC_FP64 and selects
-// the instantiation; `args` points to a StepArgs<float> or StepArgs<double>.
+// Launch shape of the step kernels.
 struct LaunchShape {
     int dim;
     int sms;
@@ -183,41 +184,87 @@ struct LaunchShape {
                // dependent launch); 0 while a step is captured into a graph
 };
 
-void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_fill(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_move(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_collide_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_step_end(int prec, const void* args, const LaunchShape& ls, cudaStream_t s);
-void launch_macro(int prec, const void* args, int sample, int n_runs, int window, double* out,
-                  cudaStream_t s);
-void launch_sample_now(int prec, const void* args, cudaStream_t s);
-cudaError_t prepare_kernels(int prec, int dim, int tile_budget);
+// The kernels are compiled twice (dsmc_kernels.cu): once for FP32 particle
+// state with fused multiply-add contraction allowed (namespace f32), once
+// for FP64 state without contraction, so that it rounds every operation as
+// the FP64 oracle does (namespace f64).  The functions below pick the
+// instantiation by `prec`.
+#define DSMC_PREC_LAUNCHERS                                                                    \
+    void launch_init_cells(const void* args, const LaunchShape& ls, cudaStream_t s);          \
+    void launch_fill(const void* args, const LaunchShape& ls, cudaStream_t s);                \
+    void launch_generate(const void* args, const LaunchShape& ls, cudaStream_t s);            \
+    void launch_move(const void* args, const LaunchShape& ls, cudaStream_t s);                \
+    void launch_scan(const void* args, const LaunchShape& ls, cudaStream_t s);                \
+    void launch_scatter(const void* args, const LaunchShape& ls, cudaStream_t s);             \
+    void launch_cell(const void* args, const LaunchShape& ls, cudaStream_t s);                \
+    void launch_cell_big(const void* args, const LaunchShape& ls, cudaStream_t s);            \
+    void launch_collide_big(const void* args, const LaunchShape& ls, cudaStream_t s);         \
+    void launch_collide(const void* args, const LaunchShape& ls, cudaStream_t s);             \
+    void launch_reduce(const void* args, const LaunchShape& ls, cudaStream_t s);              \
+    void launch_step_end(const void* args, const LaunchShape& ls, cudaStream_t s);            \
+    void launch_macro(const void* args, int sample, int n_runs, int window, double* out,      \
+                      cudaStream_t s);                                                         \
+    void launch_sample_now(const void* args, cudaStream_t s);                                 \
+    void launch_check(const void* args, const LaunchShape& ls, cudaStream_t s);               \
+    cudaError_t prepare_kernels(int dim, int tile_budget);                                    \
+    void launch_m_generate(const void* margs, const LaunchShape& ls, cudaStream_t s);         \
+    void launch_m_move(const void* margs, const LaunchShape& ls, cudaStream_t s);             \
+    void launch_m_scan(const void* margs, const LaunchShape& ls, cudaStream_t s);             \
+    void launch_m_scatter(const void* margs, const LaunchShape& ls, cudaStream_t s);          \
+    void launch_m_cell(const void* margs, const LaunchShape& ls, cudaStream_t s);             \
+    void launch_m_cell_big(const void* margs, const LaunchShape& ls, cudaStream_t s);         \
+    void launch_m_collide_big(const void* margs, const LaunchShape& ls, cudaStream_t s);      \
+    void launch_m_collide(const void* margs, const LaunchShape& ls, cudaStream_t s);          \
+    void launch_m_reduce(const void* margs, const LaunchShape& ls, cudaStream_t s);           \
+    void launch_m_step_end(const void* margs, const LaunchShape& ls, cudaStream_t s);         \
+    cudaError_t prepare_multi_kernels(int dim, int tile_budget);                              \
+    void compute_multi_shape(int dim, int sms, LaunchShape* ls);                              \
+    void compute_launch_shape(int dim, int sms, LaunchShape* ls);                             \
+    int big_cell_limit();
 
-// the same steps over the parts of a MultiArgs<float> or MultiArgs<double>
-// (`margs`); `ls` holds the grid sizes of the queue-driven kernels
-// (move_blocks, scatter_blocks, cell_blocks, collide_blocks)
-void launch_m_generate(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_move(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_scan(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_scatter(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_cell(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_cell_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_collide_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_collide(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_reduce(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-void launch_m_step_end(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s);
-cudaError_t prepare_multi_kernels(int prec, int dim, int tile_budget);
-void compute_multi_shape(int prec, int dim, int sms, LaunchShape* ls);
+namespace f32 { DSMC_PREC_LAUNCHERS }
+namespace f64 { DSMC_PREC_LAUNCHERS }
+
+#define DSMC_PICK(prec, call) ((prec) == DSMC_FP64 ? f64::call : f32::call)
+
+// `args` points to a StepArgs<float> or StepArgs<double> (`margs` to a
+// MultiArgs<float> or MultiArgs<double>) as `prec` says; the multi-part
+// launchers' `ls` holds the grid sizes of the queue-driven kernels
+// (move_blocks, scatter_blocks, cell_blocks, collide_blocks).
+inline void launch_init_cells(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_init_cells(a, ls, s)); }
+inline void launch_fill(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_fill(a, ls, s)); }
+inline void launch_generate(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_generate(a, ls, s)); }
+inline void launch_move(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_move(a, ls, s)); }
+inline void launch_scan(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_scan(a, ls, s)); }
+inline void launch_scatter(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_scatter(a, ls, s)); }
+inline void launch_cell(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_cell(a, ls, s)); }
+inline void launch_cell_big(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_cell_big(a, ls, s)); }
+inline void launch_collide_big(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_collide_big(a, ls, s)); }
+inline void launch_collide(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_collide(a, ls, s)); }
+inline void launch_reduce(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_reduce(a, ls, s)); }
+inline void launch_step_end(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_step_end(a, ls, s)); }
+inline void launch_macro(int p, const void* a, int sample, int n_runs, int window, double* out,
+                         cudaStream_t s) { DSMC_PICK(p, launch_macro(a, sample, n_runs, window, out, s)); }
+inline void launch_sample_now(int p, const void* a, cudaStream_t s) { DSMC_PICK(p, launch_sample_now(a, s)); }
+inline void launch_check(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_check(a, ls, s)); }
+inline cudaError_t prepare_kernels(int p, int dim, int tile_budget) { return DSMC_PICK(p, prepare_kernels(dim, tile_budget)); }
+inline void launch_m_generate(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_generate(m, ls, s)); }
+inline void launch_m_move(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_move(m, ls, s)); }
+inline void launch_m_scan(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_scan(m, ls, s)); }
+inline void launch_m_scatter(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_scatter(m, ls, s)); }
+inline void launch_m_cell(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_cell(m, ls, s)); }
+inline void launch_m_cell_big(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_cell_big(m, ls, s)); }
+inline void launch_m_collide_big(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_collide_big(m, ls, s)); }
+inline void launch_m_collide(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_collide(m, ls, s)); }
+inline void launch_m_reduce(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_reduce(m, ls, s)); }
+inline void launch_m_step_end(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_step_end(m, ls, s)); }
+inline cudaError_t prepare_multi_kernels(int p, int dim, int tile_budget) { return DSMC_PICK(p, prepare_multi_kernels(dim, tile_budget)); }
+inline void compute_multi_shape(int p, int dim, int sms, LaunchShape* ls) { DSMC_PICK(p, compute_multi_shape(dim, sms, ls)); }
+inline void compute_launch_shape(int p, int dim, int sms, LaunchShape* ls) { DSMC_PICK(p, compute_launch_shape(dim, sms, ls)); }
+inline int big_cell_limit(int p) { return DSMC_PICK(p, big_cell_limit()); }
+
+// precision-independent (defined in the FP32 compilation)
 cudaError_t timeout_probe(Counters* ctr, uint32_t polls, cudaStream_t s);
-void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls);
-int big_cell_limit(int prec);
 cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s);
 

@@ -39,7 +39,23 @@
 
 #include "dsmc_internal.cuh"
 
+// This file is compiled twice: with DSMC_KERNELS_FP64 for FP64 particle
+// state (no fused multiply-add contraction: every operation rounded as the
+// FP64 oracle rounds it), and without it for FP32 state (contraction
+// allowed).  Each compilation instantiates the kernels for its precision
+// only and defines its launchers in namespace dsmc::f64 or dsmc::f32.
+#if defined(DSMC_KERNELS_FP64)
+#define DSMC_KT double
+#define DSMC_KNS f64
+#define DSMC_KPREC DSMC_FP64
+#else
+#define DSMC_KT float
+#define DSMC_KNS f32
+#define DSMC_KPREC DSMC_FP32
+#endif
+
 namespace dsmc {
+namespace DSMC_KNS {
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its definition.
@@ -393,6 +409,28 @@ __device__ __forceinline__ void red_add_l2_keep(uint32_t* p, uint32_t v)
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     asm volatile("red.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
                  : "memory");
+}
+
+// Runs of equal cell keys in consecutive lanes: in a cell-ordered pool the
+// 32 consecutive slots of a warp hold few cells, each in one or a few runs.
+// Live lanes whose key equals the previous lane's (live) key continue that
+// lane's run; the first lane of a run is its head.  Gives this lane's head
+// and, on the head, the run's length.  (A key that reappears after another
+// key starts a second run of its own: runs only aggregate, every lane still
+// belongs to exactly one run.)
+__device__ __forceinline__ void key_runs(uint32_t key, bool live, uint32_t lane, uint32_t& head,
+                                         uint32_t& len)
+{
+    const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+    const uint32_t live_mask = __ballot_sync(0xFFFFFFFFu, live);
+    const bool prev_live = lane > 0u && ((live_mask >> (lane - 1u)) & 1u);
+    const uint32_t heads = __ballot_sync(0xFFFFFFFFu, live && (!prev_live || prev != key));
+    const uint32_t upto = 0xFFFFFFFFu >> (31u - lane);            // lanes 0 .. lane
+    const uint32_t le = heads & upto;
+    head = le ? 31u - (uint32_t)__clz(le) : lane;
+    const uint32_t stop = (heads | ~live_mask) & ~upto;            // heads or dead lanes above
+    const uint32_t end = stop ? (uint32_t)__ffs(stop) - 1u : 32u;
+    len = end - head;
 }
 
 // load with an L2 evict-last policy (per-cell tables that later kernels of
@@ -831,11 +869,13 @@ __device__ __forceinline__ void st4(double* p, const double* o)
     reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
 }
 
-// Motion of the slots [4 q, 4 q + 4) for the quads q = first + 32 w + lane
-// of this thread's warp w, advancing by `stride` quads while 4 q < `end`
-// (a warp-aligned first; end <= move_total): four particles per thread
-// with their loads issued together (vector loads where all four are in
-// range), so that each thread keeps several loads in flight.
+// Motion of the slots [s0, s0 + 4), s0 = base + 4 lane, for the warp bases
+// base = first + 128 w of this thread's warp w, advancing by `stride` slots
+// while below `end` (first a multiple of 4; end <= move_total): four
+// particles per thread with their loads issued together (vector loads
+// where all four are in range), so that each thread keeps several loads in
+// flight.  The cells' counts take one add per run of equal keys in
+// consecutive lanes (per position b of the four).
 template <typename T, int DIM>
 __device__ __forceinline__ void move_span(const StepArgs<T>& a, uint32_t first, uint32_t end,
                                           uint32_t stride)
@@ -853,11 +893,10 @@ __device__ __forceinline__ void move_span(const StepArgs<T>& a, uint32_t first, 
     uint32_t* __restrict__ gc = a.gc;
     const uint32_t lane = lane_id();
     const uint32_t below = (1u << lane) - 1u;
-    const uint32_t nq = (end + 3u) / 4u;
     // warp-uniform trip count (the count and slow-list updates are warp
     // operations)
-    for (uint32_t qb = first; qb < nq; qb += stride) {
-        const uint32_t s0 = 4u * (qb + lane);
+    for (uint32_t base = first; base < end; base += stride) {
+        const uint32_t s0 = base + 4u * lane;
         T x0[4], x1[4], x2[4], v0[4], v1[4], v2[4];
         uint32_t kold[4];
         const bool full = s0 + 4u <= end;
@@ -878,10 +917,8 @@ __device__ __forceinline__ void move_span(const StepArgs<T>& a, uint32_t first, 
                 x1[b] = in ? xp1[s0 + b] : (T)0;
                 v0[b] = in ? vp0[s0 + b] : (T)0;
                 v1[b] = in ? vp1[s0 + b] : (T)0;
-                if (DIM == 3) {
-                    x2[b] = in ? xp2[s0 + b] : (T)0;
-                    v2[b] = in ? vp2[s0 + b] : (T)0;
-                }
+                x2[b] = (DIM == 3 && in) ? xp2[s0 + b] : (T)0;
+                v2[b] = (DIM == 3 && in) ? vp2[s0 + b] : (T)0;
             }
         }
         uint32_t key[4];
@@ -912,8 +949,8 @@ __device__ __forceinline__ void move_span(const StepArgs<T>& a, uint32_t first, 
                 slow[b] = true;
             }
         }
-        // a slow particle keeps its offsets (k_move_slow moves it and writes
-        // its key)
+        // a slow particle keeps its offsets; k_move_slow moves it and writes
+        // its key
         if (full) {
             st4(xp0 + s0, x0);
             st4(xp1 + s0, x1);
@@ -931,12 +968,9 @@ __device__ __forceinline__ void move_span(const StepArgs<T>& a, uint32_t first, 
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const uint32_t act = __ballot_sync(0xFFFFFFFFu, key[b] != kDead);
-            if (key[b] != kDead) {
-                const uint32_t peers = __match_any_sync(act, key[b]);
-                if (lane == (uint32_t)(__ffs(peers) - 1))
-                    red_add_l2_keep(count + key[b], (uint32_t)__popc(peers));
-            }
+            uint32_t head, len;
+            key_runs(key[b], key[b] != kDead, lane, head, len);
+            if (key[b] != kDead && head == lane) red_add_l2_keep(count + key[b], len);
         }
         uint32_t m[4], tot = 0;
 #pragma unroll
@@ -961,8 +995,8 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_move(StepArgs<T> a)
 {
     pdl_enter();
-    move_span<T, DIM>(a, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), move_total(a),
-                      gridDim.x * blockDim.x);   // in quads of four slots
+    move_span<T, DIM>(a, 4u * (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)), move_total(a),
+                      4u * gridDim.x * blockDim.x);
 }
 
 // Motion with surface events for the particles k_move set aside.
@@ -1112,58 +1146,59 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(StepArgs<T> a)
     scan2_block(a, blockIdx.x);
 }
 
+// the scatter's index space: the old pool's slots [0, n_old), padded to a
+// multiple of 128, then the entrants' region [cap_old, cap_old + cap_new).
+// The pool holds run_base[n_runs] particles after this step's scan, but
+// the slots to scatter are those of the pre-step pool: its size is kept at
+// start[total + 1] by the previous step.
+template <typename T>
+__device__ __forceinline__ uint64_t scatter_extent(const StepArgs<T>& a, uint64_t* n_old_out,
+                                                   uint64_t* pad_out)
+{
+    const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
+    const uint64_t pad = (n_old + 127) / 128 * 128;
+    *n_old_out = n_old;
+    *pad_out = pad;
+    return pad + (uint64_t)a.cap_new;
+}
+
 // Indexing, part 2: LCR[start[cell] + r] = (slot, id) for every live
 // particle, r taken from the cell's count, which Motion left at the cell's
 // particle count and which this pass counts back down to zero (ready for
-// the next step's Motion): one atomic subtract per distinct cell of a warp,
-// the lanes of a cell taking consecutive places below the returned value.
-// The order inside a cell is any: the next kernel orders each cell by id
-// (the id rides along so that it needs no gather to do so).  Four
-// consecutive slots per thread, keys read as 16-byte vectors.
+// the next step's Motion): one atomic subtract per run of equal keys in
+// consecutive lanes, the run's lanes taking consecutive places below the
+// returned value.  The order inside a cell is any: the next kernel orders
+// each cell by id (the id rides along so that it needs no gather to do so).
+// Indices v0 .. v0 + 3, v0 = base + 4 lane, for the warp bases base = first
+// + 128 w, advancing by `stride` while below `end`; all four slots' loads
+// and count updates are issued before their results are used.
 __device__ __forceinline__ uint32_t atomic_sub_l2_keep(uint32_t* p, uint32_t v)
 {
     return atomic_add_l2_keep(p, 0u - v);
 }
 
-// the scatter's index space: groups of four slots of the old pool [0,
-// n_old), then of the entrants' region [cap_old, cap_old + cap_new) (both
-// start on a multiple of 4 slots).  The pool holds run_base[n_runs]
-// particles after this step's scan, but the slots to scatter are those of
-// the pre-step pool: its size is kept at start[total + 1] by the previous
-// step.
-template <typename T>
-__device__ __forceinline__ uint64_t scatter_quads(const StepArgs<T>& a, uint64_t* q_old_out)
-{
-    const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
-    *q_old_out = (n_old + 3) / 4;
-    return (n_old + 3) / 4 + ((uint64_t)a.cap_new + 3) / 4;
-}
-
-// quads [first + 32 w, ...) of this thread's warp w, advancing by `stride`
-// while below `end` (warp-aligned first; end <= scatter_quads)
 template <typename T>
 __device__ __forceinline__ void scatter_span(const StepArgs<T>& a, uint64_t first, uint64_t end,
                                              uint64_t stride)
 {
-    uint64_t q_old;
-    scatter_quads(a, &q_old);
-    const uint64_t n_old = min((uint64_t)a.start[a.total_cells + 1], (uint64_t)a.cap_old);
+    uint64_t n_old, pad;
+    scatter_extent(a, &n_old, &pad);
     uint32_t* __restrict__ gc = a.gc;
     uint32_t* __restrict__ count = a.count;
     const uint32_t* __restrict__ start = a.start;
     uint2* __restrict__ lcr2 = a.lcr;
     bool overflow = false;
     const uint32_t lane = lane_id();
-    const uint32_t below = (1u << lane) - 1u;
     // warp-uniform trip count (the count updates are warp operations)
-    for (uint64_t qb = first; qb < end; qb += stride) {
-        const uint64_t q = qb + lane;
-        const bool valid = q < end;
-        const bool in_new = q >= q_old;
-        const uint64_t s0 = in_new ? (uint64_t)a.cap_old + 4 * (q - q_old) : 4 * q;
-        const uint64_t lim = !valid ? 0 : (in_new ? (uint64_t)a.cap_old + (uint64_t)a.cap_new : n_old);
-        uint32_t key[4], idv[4];
-        if (s0 + 4 <= lim) {
+    for (uint64_t base = first; base < end; base += stride) {
+        uint32_t key[4], idv[4], st[4];
+        uint64_t slot[4];
+        // index v0 + b -> slot; v0 is a multiple of 4 and so is the padded
+        // old-pool size, so the four lie in one region
+        const uint64_t v0 = base + 4u * lane;
+        const uint64_t s0 = v0 < pad ? v0 : (uint64_t)a.cap_old + (v0 - pad);
+        const uint64_t lim = v0 < pad ? n_old : (uint64_t)a.cap_old + (uint64_t)a.cap_new;
+        if (v0 + 4 <= end && s0 + 4 <= lim) {
             const uint4 kv = *reinterpret_cast<const uint4*>(gc + s0);
             key[0] = kv.x; key[1] = kv.y; key[2] = kv.z; key[3] = kv.w;
             const uint4 iv = *reinterpret_cast<const uint4*>(a.idi + s0);
@@ -1171,48 +1206,32 @@ __device__ __forceinline__ void scatter_span(const StepArgs<T>& a, uint64_t firs
         } else {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                key[b] = s0 + b < lim ? gc[s0 + b] : kDead;
-                idv[b] = key[b] != kDead ? a.idi[s0 + b] : 0u;
+                const bool in = v0 + b < end && s0 + b < lim;
+                key[b] = in ? gc[s0 + b] : kDead;
+                idv[b] = in ? a.idi[s0 + b] : 0u;
             }
         }
-        // the four slots' start loads and count updates are independent:
-        // all are issued before any result is used
-        uint32_t st[4], peers[4], old[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) slot[b] = s0 + b;
 #pragma unroll
         for (int b = 0; b < 4; ++b) st[b] = key[b] != kDead ? ld_l2_keep(start + key[b]) : 0u;
+        uint32_t head[4], old[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const bool live = key[b] != kDead;
-            const uint32_t act = __ballot_sync(0xFFFFFFFFu, live);
-            peers[b] = live ? __match_any_sync(act, key[b]) : 0u;
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
+            uint32_t len;
+            key_runs(key[b], key[b] != kDead, lane, head[b], len);
             old[b] = 0u;
-            if (peers[b] && lane == (uint32_t)(__ffs(peers[b]) - 1))
-                old[b] = atomic_sub_l2_keep(count + key[b], (uint32_t)__popc(peers[b]));
-        }
-        uint32_t rk[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            rk[b] = 0u;
-            if (peers[b]) {
-                const uint32_t o = __shfl_sync(peers[b], old[b], __ffs(peers[b]) - 1);
-                rk[b] = o - 1u - (uint32_t)__popc(peers[b] & below);
-            }
-        }
-        if (in_new && (key[0] != kDead || key[1] != kDead || key[2] != kDead || key[3] != kDead)) {
-            // re-kill the entrants' keys for the next step
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (s0 + b < lim) gc[s0 + b] = kDead;
+            if (key[b] != kDead && head[b] == lane) old[b] = atomic_sub_l2_keep(count + key[b], len);
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
+            const uint32_t o = __shfl_sync(0xFFFFFFFFu, old[b], head[b]);
             if (key[b] == kDead) continue;
-            const uint64_t pos = (uint64_t)st[b] + rk[b];
-            if (pos >= (uint64_t)a.cap_old || rk[b] >= 0x80000000u) { overflow = true; continue; }
-            lcr2[pos] = make_uint2((uint32_t)(s0 + b), idv[b]);
+            if (slot[b] >= (uint64_t)a.cap_old) gc[slot[b]] = kDead;   // re-kill the entrant's key
+            const uint32_t rk = o - 1u - (lane - head[b]);
+            const uint64_t pos = (uint64_t)st[b] + rk;
+            if (pos >= (uint64_t)a.cap_old || rk >= 0x80000000u) { overflow = true; continue; }
+            lcr2[pos] = make_uint2((uint32_t)slot[b], idv[b]);
         }
     }
     if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
@@ -1222,10 +1241,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(StepArgs<T> a)
 {
     pdl_enter();
-    uint64_t q_old;
-    const uint64_t nq = scatter_quads(a, &q_old);
-    scatter_span(a, (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), nq,
-                 (uint64_t)gridDim.x * blockDim.x);
+    uint64_t n_old, pad;
+    const uint64_t nv = scatter_extent(a, &n_old, &pad);
+    scatter_span(a, 4ull * ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)), nv,
+                 4ull * gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1727,15 +1746,14 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 // up to kCollideStage particles, into shared memory; meanwhile every thread
 // forms its cell's NTC candidate count (coalesced remainder and (sigma
 // c_r)_max accesses) and the staged range is cut to whole cells.  (2) The
-// staged cells with candidates form a work list in decreasing candidate
-// count (a 32-bin counting sort).  (3) Every thread takes the next cell of
-// the list as soon as it has finished its previous one (a shared-memory
-// counter) and runs its candidates in shared memory, one candidate per
-// loop trip, so the lanes of a warp stay busy until the list is used up and
-// the tile's last cells are its shortest.  Cells beyond the stage collide
-// in place in global memory, with the same arithmetic.  (4) The cells'
-// moments at sample steps; the staged velocities are stored back with
-// coalesced stores.
+// cells are handed to the threads grouped by candidate count (a 32-bin
+// counting sort), so that the cells of one warp run similar numbers of
+// candidates.  (3) Each thread collides its cell -- in shared memory if
+// staged, else in place in global memory, with the same arithmetic.  (4)
+// The cells' moments at sample steps; the staged velocities are stored back
+// with coalesced stores.  (Handing each thread the next cell of a list in
+// decreasing candidate order as it finishes measured slower: a tile has
+// about one cell per thread, so nothing is left to balance.)
 template <typename T, class C>
 __device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2, uint32_t run,
                                                  uint32_t step, uint32_t cell, uint32_t M, uint32_t N,
@@ -1770,8 +1788,8 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
     T* s1 = sm.s1;
     T* s2 = sm.s2;
     uint64_t& s_bar = *sm.bar;
-    __shared__ uint32_t s_b0, s_n, s_nload, s_sh, s_next;
-    __shared__ uint32_t s_bin[33];
+    __shared__ uint32_t s_b0, s_n, s_nload, s_sh;
+    __shared__ uint32_t s_bin[32];
     __shared__ uint32_t s_beg[kCollideCells], s_N[kCollideCells], s_M[kCollideCells];
     __shared__ uint32_t s_ord[kCollideCells];
     __shared__ T s_smax[kCollideCells];
@@ -1800,7 +1818,6 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
         s_b0 = beg;
         s_n = (uint32_t)n;
         s_nload = (uint32_t)n;
-        s_next = kCollideCells;
         if (n > 0) {
             // 16-byte aligned superset [lo, hi) of [beg, beg + n); hi stays
             // inside the pool, whose capacity is a multiple of 256
@@ -1815,7 +1832,7 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
             bulk_g2s(s2, a.vo[2] + lo, bytes, &s_bar);
         }
     }
-    if (tid < 33) s_bin[tid] = 0u;
+    if (tid < 32) s_bin[tid] = 0u;
     __syncthreads();
     const uint32_t b0 = s_b0;
     const uint32_t nload = s_nload;
@@ -1845,14 +1862,13 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
     const uint32_t n_st = s_n;
     const uint32_t sh = s_sh;
     const bool staged = act && beg >= b0 && (uint64_t)(beg - b0) + N <= (uint64_t)n_st;
-    // the work list: staged cells with candidates, most candidates first
-    const bool work = staged && M32 > 0u;
-    const uint32_t bin = M32 < 32u ? 32u - M32 : 0u;   // 0: 32 candidates or more
-    const uint32_t in_bin = work ? atomicAdd(&s_bin[bin], 1u) : 0u;
+    // (2) cells handed to threads grouped by candidate count (32 bins,
+    // ascending), so that the lanes of a warp run similar numbers of
+    // candidates
+    const uint32_t bin = M32 < 31u ? M32 : 31u;
+    const uint32_t in_bin = atomicAdd(&s_bin[bin], 1u);
     __syncthreads();
     if (tid < 32) {
-        // exclusive prefix over the bins 0..31 (bin 32 holds no work:
-        // M32 = 0), the total in s_bin[32]
         const uint32_t v = s_bin[tid];
         uint32_t x = v;
 #pragma unroll
@@ -1861,11 +1877,9 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
             if (tid >= (uint32_t)o) x += y;
         }
         s_bin[tid] = x - v;
-        if (tid == 31) s_bin[32] = x;
     }
     __syncthreads();
-    if (work) s_ord[s_bin[bin] + in_bin] = tid;
-    const uint32_t nwork = s_bin[32];
+    s_ord[s_bin[bin] + in_bin] = tid;
     if (nload > 0) {
         if (!mbar_wait(&s_bar, phase)) {
             atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
@@ -1874,58 +1888,36 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
         phase ^= 1u;
     }
     __syncthreads();
-    // (3) one candidate per trip; a thread whose cell is done takes the
-    // next cell of the list
+    // (3) the candidates of the thread's cell, in shared memory if staged,
+    // else in place in global memory (the same arithmetic)
     {
-        uint32_t item = tid, q = 0, Nq = 0, Mq = 0, k = 0, o = 0, run = 0, cell = 0;
-        T smax = (T)0, seen = (T)0;
-        uint32_t nacc = 0, nclamp = 0;
-        bool have = false;
-        while (true) {
-            if (k == Mq) {
-                if (have) {
-                    const int64_t gq = c0 + q;
-                    if (seen > smax) a.smax[gq] = seen;
-                    if (a.cand) { a.cand[gq] = Mq; a.accd[gq] = nacc; }
-                    tl.cand += Mq;
-                    tl.acc += nacc;
-                    tl.clamp += nclamp;
-                    item = atomicAdd(&s_next, 1u);
-                }
-                if (item >= nwork) break;
-                q = s_ord[item];
-                Nq = s_N[q];
-                Mq = s_M[q];
-                smax = s_smax[q];
-                o = sh + (s_beg[q] - b0);
-                const uint32_t gq = (uint32_t)(c0 + q);
-                const uint32_t rl = run_of_key(c, gq);
-                run = a.run0 + rl;
-                cell = gq - rl * (uint32_t)c.ncells;
-                k = 0;
-                seen = (T)0;
-                nacc = nclamp = 0;
-                have = true;
-            }
-            collide_candidate_lazy<T>(c, s0 + o, s1 + o, s2 + o, run, step, cell, k, Nq, smax, seen,
-                                      nacc, nclamp);
-            ++k;
+        const uint32_t q = s_ord[tid];
+        const uint32_t Nq = s_N[q];
+        if (Nq != kOff && s_M[q] > 0u) {
+            const int64_t gq = c0 + q;
+            const uint32_t begq = s_beg[q];
+            const uint32_t Mq = s_M[q];
+            const T smax = s_smax[q];
+            const uint32_t rl = run_of_key(c, (uint32_t)gq);
+            const uint32_t cell = (uint32_t)gq - rl * (uint32_t)c.ncells;
+            const bool stq = begq >= b0 && (uint64_t)(begq - b0) + Nq <= (uint64_t)n_st;
+            T seen = (T)0;
+            uint32_t nacc = 0, nclamp = 0;
+            const uint32_t o = sh + (begq - b0);
+            // one call per address space, so that staged cells use
+            // shared-memory loads and stores
+            if (stq)
+                collide_cell_run<T>(c, s0 + o, s1 + o, s2 + o, a.run0 + rl, step, cell, Mq, Nq, smax,
+                                    seen, nacc, nclamp);
+            else
+                collide_cell_run<T>(c, a.vo[0] + begq, a.vo[1] + begq, a.vo[2] + begq, a.run0 + rl,
+                                    step, cell, Mq, Nq, smax, seen, nacc, nclamp);
+            if (seen > smax) a.smax[gq] = seen;
+            if (a.cand) { a.cand[gq] = Mq; a.accd[gq] = nacc; }
+            tl.cand += Mq;
+            tl.acc += nacc;
+            tl.clamp += nclamp;
         }
-    }
-    // cells beyond the stage: in place in global memory
-    if (act && !staged && M32 > 0u) {
-        const uint32_t rl = run_of_key(c, (uint32_t)gcell);
-        const uint32_t cell = (uint32_t)gcell - rl * (uint32_t)c.ncells;
-        const T smax = s_smax[tid];
-        T seen = (T)0;
-        uint32_t nacc = 0, nclamp = 0;
-        collide_cell_run<T>(c, a.vo[0] + beg, a.vo[1] + beg, a.vo[2] + beg, a.run0 + rl, step, cell,
-                            M32, N, smax, seen, nacc, nclamp);
-        if (seen > smax) a.smax[gcell] = seen;
-        if (a.cand) { a.cand[gcell] = M32; a.accd[gcell] = nacc; }
-        tl.cand += M32;
-        tl.acc += nacc;
-        tl.clamp += nclamp;
     }
     __syncthreads();
     // (4) moments at sample steps, thread per cell
@@ -2356,6 +2348,45 @@ __global__ void k_step_end(StepArgs<T> a)
     step_end_part(a);
 }
 
+// Consistency check of the pool after a run (options.checks): every pool
+// position p holds a particle whose stored cell key lies inside the table,
+// whose cell's range [start[key], start[key + 1]) contains p, whose id is
+// larger than its predecessor's in the same cell (the (cell, id) order of
+// the readdressing array), whose offsets lie inside its cell and whose
+// velocity is finite.  Counts the positions that fail and keeps the first.
+template <typename T, int DIM>
+__global__ void k_check(StepArgs<T> a)
+{
+    const uint32_t n = min(a.run_base[a.n_runs], (uint32_t)a.cap_old);
+    const T* x[3] = {a.xi[0], a.xi[1], a.xi[2]};
+    uint32_t bad = 0, first = 0xFFFFFFFFu;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t key = a.ci_i[p];
+        bool ok = key < (uint32_t)a.total_cells;
+        if (ok) {
+            const uint32_t cs = a.start[key], ce = a.start[key + 1];
+            ok = cs <= p && p < ce;
+            if (ok && p > cs) ok = a.idi[p - 1] < a.idi[p];
+        }
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) {
+            const T f = x[ax][p];
+            const T d = a.hot.d[ax];
+            ok = ok && f >= (T)0 && f <= d * (T)(1.0 + 1e-6);
+        }
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) ok = ok && isfinite(a.vi[ax][p]);
+        if (!ok) {
+            ++bad;
+            first = min(first, p);
+        }
+    }
+    if (bad) {
+        atomicAdd(&a.ctr->check_fail, bad);
+        atomicMin(&a.ctr->check_first, first);
+    }
+}
+
 // moments of the current pool (test hook), one warp per cell
 template <typename T>
 __global__ void k_sample_now(StepArgs<T> a, const T* v0, const T* v1, const T* v2)
@@ -2425,6 +2456,7 @@ __global__ void k_macro(StepArgs<T> a, int t, int n_runs, int window, double* ou
     }
 }
 
+#if !defined(DSMC_KERNELS_FP64)
 __global__ void k_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -2434,6 +2466,7 @@ __global__ void k_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, ui
         out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
     }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Several problems per launch (the parts of a mixed-size ensemble).  Every
@@ -2537,7 +2570,7 @@ __global__ void __launch_bounds__(256) mk_move(MultiArgs<T> m)
         if (p != cur) { load_part(sa, m.parts, p); cur = p; }
         const uint32_t first = (item - (uint32_t)s_base[p]) * kMoveChunk;
         const uint32_t end = min(first + kMoveChunk, move_total(sa));
-        move_span<T, DIM>(sa, first / 4u + (threadIdx.x & ~31u), end, blockDim.x);
+        move_span<T, DIM>(sa, first + 4u * (threadIdx.x & ~31u), end, 4u * blockDim.x);
     });
 }
 
@@ -2575,18 +2608,19 @@ __global__ void __launch_bounds__(256) mk_scatter(MultiArgs<T> m)
     __shared__ StepArgs<T> sa;
     __shared__ int32_t s_base[kMaxParts + 1];
     item_prefix(m.n_parts, s_base, [&](int p) {
-        uint64_t q_old;
-        return (uint32_t)((scatter_quads(m.parts[p], &q_old) + kScatterChunk - 1) / kScatterChunk);
+        uint64_t n_old, pad;
+        return (uint32_t)((scatter_extent(m.parts[p], &n_old, &pad) + kScatterChunk - 1) /
+                          kScatterChunk);
     });
     int cur = -1;
     claim_items(m.queue + kQScatter, (uint32_t)s_base[m.n_parts], [&](uint32_t item) {
         const int p = part_of(s_base, m.n_parts, item);
         if (p != cur) { load_part(sa, m.parts, p); cur = p; }
-        uint64_t q_old;
-        const uint64_t nq = scatter_quads(sa, &q_old);
+        uint64_t n_old, pad;
+        const uint64_t nv = scatter_extent(sa, &n_old, &pad);
         const uint64_t first = (uint64_t)(item - (uint32_t)s_base[p]) * kScatterChunk;
-        const uint64_t end = first + kScatterChunk < nq ? first + kScatterChunk : nq;
-        scatter_span(sa, first + (threadIdx.x & ~31u), end, blockDim.x);
+        const uint64_t end = first + kScatterChunk < nv ? first + kScatterChunk : nv;
+        scatter_span(sa, first + 4u * (threadIdx.x & ~31u), end, 4u * blockDim.x);
     });
 }
 
@@ -2687,10 +2721,12 @@ __global__ void mk_step_end(MultiArgs<T> m)
 template <typename T>
 static const StepArgs<T>& A(const void* p) { return *static_cast<const StepArgs<T>*>(p); }
 
+// this compilation's precision (see the top of the file)
 #define DISPATCH_PREC(prec, ...)                                      \
     do {                                                              \
-        if ((prec) == DSMC_FP64) { using T = double; __VA_ARGS__; }   \
-        else { using T = float; __VA_ARGS__; }                        \
+        (void)(prec);                                                 \
+        using T = DSMC_KT;                                            \
+        __VA_ARGS__;                                                  \
     } while (0)
 
 #define DISPATCH_DIM(dim, ...)                                        \
@@ -2698,6 +2734,18 @@ static const StepArgs<T>& A(const void* p) { return *static_cast<const StepArgs<
         if ((dim) == 3) { constexpr int D = 3; __VA_ARGS__; }         \
         else { constexpr int D = 2; __VA_ARGS__; }                    \
     } while (0)
+
+
+// A kernel's dynamic shared-memory limit.  (The shared-memory carveout is
+// left to the driver: it takes the smallest carveout that holds the
+// resident CTAs, which leaves the rest of the SM's 256 KB to the L1 cache
+// that the gathers of the sort/gather kernel hit; a larger carveout, or 6
+// KB more shared memory per tile CTA, measured 40% slower there.)
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 // launch a step kernel with programmatic stream serialisation (see
 // pdl_enter) when ls.pdl is set: its launch overlaps the end of the
@@ -2729,24 +2777,27 @@ static void launch_pdl(const LaunchShape& ls, void (*kernel)(P...), unsigned gri
     }
 }
 
-void launch_init_cells(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_init_cells(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (k_init_cells<T><<<ls.sms * 4, 256, 0, s>>>(A<T>(args))));
 }
 
-void launch_fill(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_fill(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
         k_fill_count<T><<<ls.sms * 4, 256, 0, s>>>(a);
-        launch_scan(prec, args, ls, s);
+        launch_scan(args, ls, s);
         DISPATCH_DIM(ls.dim, (k_fill_particles<T, D><<<ls.sms * 8, 256, 0, s>>>(a)));
         k_fill_ids<T><<<(a.n_runs + 255) / 256, 256, 0, s>>>(a);
     });
 }
 
-void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_generate(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
         const unsigned grid = (unsigned)a.n_runs * (unsigned)a.gen_groups;
@@ -2755,16 +2806,18 @@ void launch_generate(int prec, const void* args, const LaunchShape& ls, cudaStre
     });
 }
 
-void launch_move(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_move(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
         launch_pdl(ls, k_move<T, D>, ls.move_blocks, ls.move_threads, 0, s, A<T>(args));
         launch_pdl(ls, k_move_slow<T, D>, ls.sms * 2, 256, 0, s, A<T>(args));
     }));
 }
 
-void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_scan(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
         launch_pdl(ls, k_scan1<T>, a.scan_blocks, kScanThreads, 0, s, a);
@@ -2772,8 +2825,9 @@ void launch_scan(int prec, const void* args, const LaunchShape& ls, cudaStream_t
     });
 }
 
-void launch_scatter(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_scatter(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, launch_pdl(ls, k_scatter<T>, ls.scatter_blocks, 256, 0, s, A<T>(args)));
 }
 
@@ -2787,8 +2841,9 @@ size_t cell_smem_bytes(int prec, int budget)
     return head + (tile > warps ? tile : warps);
 }
 
-void launch_cell(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_cell(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
         const StepArgs<T>& a = A<T>(args);
         launch_pdl(ls, k_cell<T, D>, ls.cell_blocks, kTileCells, cell_smem_bytes(prec, a.tile_budget), s, a);
@@ -2801,48 +2856,60 @@ static size_t collide_smem(int prec)
                              : (size_t)3 * collide_stage_pitch<float>() * 4;
 }
 
-void launch_collide(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_collide(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, launch_pdl(ls, k_collide<T>, ls.collide_blocks, kCollideCells, collide_smem(prec),
                                    s, A<T>(args)));
 }
 
-int big_cell_limit(int prec) { return prec == DSMC_FP64 ? big_max_of<double>() : big_max_of<float>(); }
+int big_cell_limit() { return big_max_of<DSMC_KT>(); }
 
 static size_t big_smem(int) { return big_smem_bytes(); }
 
-void launch_cell_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_cell_big(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, launch_pdl(ls, k_cell_big<T, D>, ls.big_blocks, kBigThreads,
                                                         big_smem(prec), s, A<T>(args))));
 }
 
-void launch_collide_big(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_collide_big(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, launch_pdl(ls, k_collide_big<T>, ls.sms * 2, 256, 0, s, A<T>(args)));
 }
 
-void launch_reduce(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_reduce(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, launch_pdl(ls, k_reduce<T>, ls.sms * 4, 256, 0, s, A<T>(args)));
 }
 
-void launch_step_end(int prec, const void* args, const LaunchShape& ls, cudaStream_t s)
+void launch_step_end(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, launch_pdl(ls, k_step_end<T>, 1, 1, 0, s, A<T>(args)));
 }
 
-void launch_sample_now(int prec, const void* args, cudaStream_t s)
+void launch_check(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
+    DISPATCH_DIM(ls.dim, (k_check<DSMC_KT, D><<<ls.sms * 4, 256, 0, s>>>(A<DSMC_KT>(args))));
+}
+
+void launch_sample_now(const void* args, cudaStream_t s)
+{
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, {
         const StepArgs<T>& a = A<T>(args);
         k_sample_now<T><<<128, 256, 0, s>>>(a, a.vi[0], a.vi[1], a.vi[2]);
     });
 }
 
-void launch_macro(int prec, const void* args, int sample, int n_runs, int window, double* out,
+void launch_macro(const void* args, int sample, int n_runs, int window, double* out,
                   cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (k_macro<T><<<64, 128, 0, s>>>(A<T>(args), sample, n_runs, window, out)));
 }
 
@@ -2859,15 +2926,15 @@ static cudaError_t raise_cell_smem_limit(int prec, int dim, size_t bytes)
     if (bytes <= cur) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
-        e = cudaFuncSetAttribute(k_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
+        e = set_smem(k_cell<T, D>, bytes);
     }));
     if (e == cudaSuccess) cur = bytes;
     return e;
 }
 
-void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
+void compute_launch_shape(int dim, int sms, LaunchShape* ls)
 {
+    constexpr int prec = DSMC_KPREC;
     ls->dim = dim;
     ls->sms = sms;
     // tile budget: 6144 staged particles (LCR entries and cell tags, 61 KB),
@@ -2889,8 +2956,7 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
     ls->cell_blocks = sms * (bc > 0 ? bc : 2);
     int bl = 0;
     DISPATCH_PREC(prec, {
-        cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)collide_smem(prec));
+        set_smem(k_collide<T>, collide_smem(prec));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_collide<T>, kCollideCells,
                                                       collide_smem(prec));
     });
@@ -2898,15 +2964,14 @@ void compute_launch_shape(int prec, int dim, int sms, LaunchShape* ls)
     ls->big_blocks = sms * 2;
 }
 
-cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
+cudaError_t prepare_kernels(int dim, int tile_budget)
 {
+    constexpr int prec = DSMC_KPREC;
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
-        e = cudaFuncSetAttribute(k_cell_big<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)big_smem(prec));
+        e = set_smem(k_cell_big<T, D>, big_smem(prec));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)collide_smem(prec));
+            e = set_smem(k_collide<T>, collide_smem(prec));
     }));
     if (e == cudaSuccess) e = raise_cell_smem_limit(prec, dim, cell_smem_bytes(prec, tile_budget));
     return e;
@@ -2916,8 +2981,9 @@ cudaError_t prepare_kernels(int prec, int dim, int tile_budget)
 template <typename T>
 static const MultiArgs<T>& MA(const void* p) { return *static_cast<const MultiArgs<T>*>(p); }
 
-void launch_m_generate(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_generate(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, {
         const MultiArgs<T>& m = MA<T>(margs);
         if (m.gcount_base[m.n_parts] > 0) mk_gen_count<T><<<m.gcount_base[m.n_parts], 256, 0, s>>>(m);
@@ -2925,8 +2991,9 @@ void launch_m_generate(int prec, const void* margs, const LaunchShape& ls, cudaS
     });
 }
 
-void launch_m_move(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_move(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, {
         const MultiArgs<T>& m = MA<T>(margs);
         mk_move<T, D><<<ls.move_blocks, 256, 0, s>>>(m);
@@ -2934,8 +3001,9 @@ void launch_m_move(int prec, const void* margs, const LaunchShape& ls, cudaStrea
     }));
 }
 
-void launch_m_scan(int prec, const void* margs, const LaunchShape&, cudaStream_t s)
+void launch_m_scan(const void* margs, const LaunchShape&, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, {
         const MultiArgs<T>& m = MA<T>(margs);
         mk_scan1<T><<<m.scan_base[m.n_parts], kScanThreads, 0, s>>>(m);
@@ -2943,69 +3011,75 @@ void launch_m_scan(int prec, const void* margs, const LaunchShape&, cudaStream_t
     });
 }
 
-void launch_m_scatter(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_scatter(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (mk_scatter<T><<<ls.scatter_blocks, 256, 0, s>>>(MA<T>(margs))));
 }
 
-void launch_m_cell(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_cell(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, (mk_cell<T, D><<<ls.cell_blocks, kTileCells,
                                                              cell_smem_bytes(prec, ls.tile_budget), s>>>(
                                                    MA<T>(margs)))));
 }
 
-void launch_m_cell_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_cell_big(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, DISPATCH_DIM(ls.dim, (mk_cell_big<T, D><<<ls.big_blocks, kBigThreads,
                                                                  big_smem(prec), s>>>(MA<T>(margs)))));
 }
 
-void launch_m_collide_big(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_collide_big(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (mk_collide_big<T><<<ls.sms * 2, 256, 0, s>>>(MA<T>(margs))));
 }
 
-void launch_m_collide(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_collide(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (mk_collide<T><<<ls.collide_blocks, kCollideCells, collide_smem(prec), s>>>(
                              MA<T>(margs))));
 }
 
-void launch_m_reduce(int prec, const void* margs, const LaunchShape& ls, cudaStream_t s)
+void launch_m_reduce(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (mk_reduce<T><<<ls.sms * 4, 256, 0, s>>>(MA<T>(margs))));
 }
 
-void launch_m_step_end(int prec, const void* margs, const LaunchShape&, cudaStream_t s)
+void launch_m_step_end(const void* margs, const LaunchShape&, cudaStream_t s)
 {
+    constexpr int prec = DSMC_KPREC;
     DISPATCH_PREC(prec, (mk_step_end<T><<<1, kMaxParts, 0, s>>>(MA<T>(margs))));
 }
 
-cudaError_t prepare_multi_kernels(int prec, int dim, int tile_budget)
+cudaError_t prepare_multi_kernels(int dim, int tile_budget)
 {
+    constexpr int prec = DSMC_KPREC;
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
-        e = cudaFuncSetAttribute(mk_cell_big<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)big_smem(prec));
+        e = set_smem(mk_cell_big<T, D>, big_smem(prec));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mk_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)collide_smem(prec));
+            e = set_smem(mk_collide<T>, collide_smem(prec));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mk_cell<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)cell_smem_bytes(prec, tile_budget));
+            e = set_smem(mk_cell<T, D>, cell_smem_bytes(prec, tile_budget));
     }));
     return e;
 }
 
 // grids of the queue-driven kernels: as many CTAs as fit on the GPU at once
-void compute_multi_shape(int prec, int dim, int sms, LaunchShape* ls)
+void compute_multi_shape(int dim, int sms, LaunchShape* ls)
 {
+    constexpr int prec = DSMC_KPREC;
     ls->dim = dim;
     ls->sms = sms;
     if (ls->tile_budget <= 0) ls->tile_budget = 6144;
     ls->tile_budget = (ls->tile_budget + 7) / 8 * 8;
-    prepare_multi_kernels(prec, dim, ls->tile_budget);
+    prepare_multi_kernels(dim, ls->tile_budget);
     int bm = 0, bs = 0, bc = 0, bl = 0;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, mk_move<T, D>, 256, 0);
@@ -3024,6 +3098,7 @@ void compute_multi_shape(int prec, int dim, int sms, LaunchShape* ls)
     ls->pdl = 0;
 }
 
+#if !defined(DSMC_KERNELS_FP64)
 // Test hook for the bounded waits: an mbarrier expects 16 bytes that no
 // copy will deliver, so its wait gives up after `polls` polls and sets
 // DSMC_ERR_TIMEOUT (in the hook's own word, not the run's error word), as a
@@ -3040,18 +3115,25 @@ __global__ void k_timeout_probe(Counters* ctr, uint32_t polls)
         if (!done) atomicOr(&ctr->probe, DSMC_ERR_TIMEOUT);
     }
 }
+#endif
+
+}  // namespace DSMC_KNS
+
+#if !defined(DSMC_KERNELS_FP64)
 
 cudaError_t timeout_probe(Counters* ctr, uint32_t polls, cudaStream_t s)
 {
-    k_timeout_probe<<<1, 32, 0, s>>>(ctr, polls);
+    f32::k_timeout_probe<<<1, 32, 0, s>>>(ctr, polls);
     return cudaGetLastError();
 }
 
 cudaError_t philox_device(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s)
 {
-    k_philox<<<64, 256, 0, s>>>(n, ctr, key, out);
+    f32::k_philox<<<64, 256, 0, s>>>(n, ctr, key, out);
     return cudaGetLastError();
 }
+
+#endif
 
 }  // namespace dsmc

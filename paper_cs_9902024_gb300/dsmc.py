@@ -79,7 +79,9 @@ class Options(C.Structure):
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("stream", C.c_void_p), ("use_graph", C.c_int32), ("debug", C.c_int32),
                 ("device", C.c_int32), ("profile", C.c_int32), ("run_offset", C.c_int64),
-                ("autotune", C.c_int32), ("shape", C.c_int32 * 4)]
+                ("autotune", C.c_int32), ("shape", C.c_int32 * 4), ("checks", C.c_int32),
+                ("reserved_", C.c_int32), ("tune_cache", C.c_char_p)]
+TUNE_OFF, TUNE_SEARCH, TUNE_LOAD = 0, 1, 2
 
 
 class Stats(C.Structure):
@@ -186,14 +188,16 @@ class Ensemble:
 
     `mode`: "batched" (all runs per launch, CUDA graphs) or "plain" (one run
     after another); `precision`: "fp32" or "fp64" particle state;
-    `autotune`: search the launch shape on the first run of a size;
-    `shape`: a dict with any of SHAPE_KEYS replacing the default launch
-    shape (e.g. stats()["shape"] of a tuned ensemble)."""
+    `autotune`: True (or "search") searches the launch shape on the first
+    run of a size, "load" takes it from the file `tune_cache` (searching
+    and storing it there when absent); `shape`: a dict with any of
+    SHAPE_KEYS replacing the default launch shape (e.g. stats()["shape"] of
+    a tuned ensemble); `checks`: verify the pool after every run."""
 
     def __init__(self, w, mode="batched", precision="fp32", capacity_factor=0.0,
                  capacity_per_run=0, debug=False, profile=False, use_graph=True, device=0,
                  torch_memory=True, stream=None, run_offset=0, autotune=False,
-                 shape=None):
+                 shape=None, checks=False, tune_cache=None):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise DsmcError(E_CUDA, "no CUDA device: the DSMC path has no CPU fallback")
@@ -213,7 +217,11 @@ class Ensemble:
         opt.profile = 1 if profile else 0
         opt.device = device
         opt.run_offset = run_offset
-        opt.autotune = 1 if autotune else 0
+        opt.autotune = (TUNE_LOAD if autotune == "load" else
+                        TUNE_SEARCH if autotune else TUNE_OFF)
+        opt.checks = 1 if checks else 0
+        self._tune_cache = tune_cache.encode() if tune_cache else None
+        opt.tune_cache = self._tune_cache
         if shape:
             for i, k in enumerate(SHAPE_KEYS):
                 opt.shape[i] = int(shape.get(k, 0))

@@ -49,11 +49,12 @@ def test_ctypes_layout_matches_header():
     int main(void) {
       printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dsmc_domain), sizeof(dsmc_cells),
              sizeof(dsmc_gas), sizeof(dsmc_boundary), sizeof(dsmc_options), sizeof(dsmc_stats));
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsmc_boundary, n),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsmc_boundary, n),
              offsetof(dsmc_options, stream), offsetof(dsmc_options, profile),
              offsetof(dsmc_options, autotune), offsetof(dsmc_options, shape),
              offsetof(dsmc_stats, ms_steps), offsetof(dsmc_stats, launches_kernel),
-             offsetof(dsmc_stats, shape));
+             offsetof(dsmc_stats, shape), offsetof(dsmc_options, checks),
+             offsetof(dsmc_options, tune_cache));
       return 0;
     }
     """
@@ -69,7 +70,8 @@ def test_ctypes_layout_matches_header():
     offs = [int(x) for x in lines[1].split()]
     assert offs == [D.Boundary.n.offset, D.Options.stream.offset, D.Options.profile.offset,
                     D.Options.autotune.offset, D.Options.shape.offset,
-                    D.Stats.ms_steps.offset, D.Stats.launches_kernel.offset, D.Stats.shape.offset]
+                    D.Stats.ms_steps.offset, D.Stats.launches_kernel.offset, D.Stats.shape.offset,
+                    D.Options.checks.offset, D.Options.tune_cache.offset]
 
 
 def _args():

@@ -212,3 +212,67 @@ def test_sample_windows_match_oracle_and_modes(D):
     Vc = d[0] * d[1] * w["L"][2]
     n_expect = raw[..., 0].sum(axis=0) * w["gas"]["F_N"] / (5 * 21 * Vc)
     assert np.allclose(m["density"], n_expect, rtol=1e-12)
+
+
+def test_checks_pass_on_normal_runs(D):
+    """options.checks: the device pass over the final pool (cell keys inside
+    the table and inside their cell's range, ids increasing within a cell,
+    offsets inside the cell, finite velocities) passes after ordinary
+    runs -- batched FP32, FP64, plain, and a filled 3-D box -- and leaves
+    the results as they are without it."""
+    w = W.duct64x32_n8(runs=6, steps=60, n_samples=2)
+    for kw in (dict(), dict(precision="fp64"), dict(mode="plain")):
+        a = D.Ensemble(w, checks=True, **kw).run()
+        b = D.Ensemble(w, **kw).run()
+        for t in range(2):
+            assert np.array_equal(a.raw(t), b.raw(t)), kw
+        a.close()
+        b.close()
+    w3 = W.plate3d(nx=24, ny=12, nz=12, plate=6, plate_x=8, ppc=6, runs=2, steps=8, n_samples=1)
+    D.Ensemble(w3, checks=True).run().close()
+
+
+def test_checks_catch_a_corrupted_pool(D):
+    """A state whose ids repeat inside a cell (impossible in a run, set here
+    through the test hook) leaves the readdressing array inconsistent after
+    a step; the check reports it as DSMC_E_STATE with the failing
+    positions, and nothing faults."""
+    from tests.helpers import box
+    w = box(dim=2, ncell=(4, 4, 1), ppc=20, dt=1e-7, runs=1, steps=1, fill=0)
+    rng = np.random.default_rng(3)
+    n = 60
+    d = w["L"][0] / 4
+    x = np.zeros((n, 3))
+    x[:, 0] = (1 + rng.uniform(0.1, 0.9, n)) * d
+    x[:, 1] = (2 + rng.uniform(0.1, 0.9, n)) * d
+    v = rng.normal(0.0, 1.0, (n, 3))
+    ids = np.arange(n, dtype=np.uint32)
+    ids[10:20] = 5                       # ten particles share one id
+    ens = D.Ensemble(w, precision="fp64", debug=True, checks=True, capacity_per_run=1024)
+    ens.debug_begin(runs=1)
+    ens.set_state(0, x, v, ids, n)
+    with pytest.raises(D.DsmcError) as e:
+        ens.debug_step(1)
+    assert e.value.status == D.E_STATE and "consistency check failed" in str(e.value)
+    ens.close()
+
+
+def test_tune_cache_stores_then_loads_the_shape(D, tmp_path):
+    """autotune="load": the first ensemble searches the launch shape and
+    appends it to the cache file; a second context reads it back (no
+    search) and gives bit-identical sums."""
+    path = str(tmp_path / "shapes.txt")
+    w = W.duct64x32_n8(runs=32, steps=120, n_samples=2)
+    a = D.Ensemble(w, autotune="load", tune_cache=path).run()
+    sa = a.stats()
+    assert sa["tuned"] == 1
+    lines = open(path).read().split("\n")
+    assert len([ln for ln in lines if ln.strip()]) == 1
+    b = D.Ensemble(w, autotune="load", tune_cache=path).run()
+    sb = b.stats()
+    assert sb["tuned"] == 2 and sb["shape"] == sa["shape"]
+    for t in range(2):
+        assert np.array_equal(a.raw(t), b.raw(t))
+    assert len([ln for ln in open(path).read().split("\n") if ln.strip()]) == 1
+    a.close()
+    b.close()
