@@ -441,6 +441,9 @@ def bench_mixed(args):
         "clocks": clk.summary(),
         "e2e": {"value": ps * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        # every step: generate, move, move_slow, scan (two passes), scatter,
+        # cell, cell_big, collide_big, collide, step_end (+ reduce at sample
+        # steps); each part's fill: 6
         "gpu_launches": args.steps * (steps * 11 + 6 * n_launch + T),
         "particle_steps_per_step": ps,
         "particles_at_end": stats["particles_now"],
@@ -493,9 +496,10 @@ def main():
         ens.run()
     st = ens.stats()
     ps_per_step = st["particle_steps"]
-    # fill: 6 launches; every time step: generate, move, move_slow, scan1,
-    # scan2, scatter, cell, cell_big, collide_big, collide, step_end, and
-    # reduce at the sample steps only
+    # fill: 6 launches (cells, counts, scan (two passes), particles, ids);
+    # every time step: generate, move, move_slow, scan1, scan2, scatter,
+    # cell, cell_big, collide_big, collide, step_end, and reduce at the
+    # sample steps only
     launches_per_step = 6 + steps * 11 + n_samples
     # -- device-timed region: inputs resident, results stay on the device --
     ev0 = torch.cuda.Event(enable_timing=True)

@@ -867,7 +867,7 @@ static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
     // sort/gather tile budget (sets the tile kernel's grid from occupancy;
     // the other grids go back to their defaults and are searched next)
     {
-        const int cand[3] = {4608, 6144, 7680};
+        const int cand[3] = {2048, 3072, 4608};
         int best = ls.tile_budget;
         double best_cost = 1e300;
         for (int k = 0; k < 3; ++k) {
