@@ -452,6 +452,7 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
     a.total_cells = (int32_t)((int64_t)ctx->ncells * n);
     a.scan_blocks = (int)((a.total_cells + kScanTile - 1) / kScanTile);
     a.tile_budget = ctx->ls.tile_budget;
+    a.collide_stage = ctx->ls.collide_stage;
     return a;
 }
 
@@ -640,7 +641,7 @@ static dsmc_status prepare(dsmc_ctx* ctx, int n_runs, double dt, int steps, cons
     }
     st = reset_counters(ctx);
     if (st) return st;
-    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
+    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget, ctx->ls.collide_stage));
     return DSMC_OK;
 }
 
@@ -673,6 +674,27 @@ static dsmc_status build_graphs(dsmc_ctx* ctx, int n_runs)
 
 // ---------------------------------------------------------------------------
 // C ABI (C linkage comes from the declarations in dsmc.h)
+
+// Staged particles a cell that the default collision shape aims at: 1.1 x
+// the particles a cell holds at the densest state the run is driven with
+// (the fill or an inflow), within 18 .. 22 (a denser inflow, as a jet's
+// orifice, feeds cells that the big-cell kernels take).
+static int collide_ppc_target(const dsmc_ctx* ctx)
+{
+    double vc = 1.0;
+    for (int a = 0; a < 3; ++a) vc *= ctx->dom.extent[a] / (double)ctx->cells.n[a];
+    double n = ctx->dom.fill ? ctx->dom.fill_n : 0.0;
+    for (const dsmc_boundary& b : ctx->bcs)
+        if (b.kind == DSMC_BC_INFLOW && b.face != DSMC_FACE_PLATE) n = std::max(n, b.n);
+    const double ppc = std::ceil(1.1 * n * vc / ctx->gas.F_N);
+    return (int)std::min(22.0, std::max(18.0, ppc));
+}
+
+// the collision stage follows the collision CTAs per SM
+static void follow_collide_blocks(int prec, int sms, LaunchShape* ls)
+{
+    ls->collide_stage = collide_stage_for(prec, std::max(1, ls->collide_blocks / sms), 0);
+}
 
 dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, const dsmc_gas* gas,
                         const dsmc_boundary* b, int n_b, const dsmc_options* opt, dsmc_ctx** out)
@@ -781,10 +803,14 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     // default shape (the occupancy of the tile kernel follows the budget),
     // then the caller's entries
     ctx->ls.tile_budget = ctx->opt.shape[2];
+    ctx->ls.collide_ppc = collide_ppc_target(ctx);
     compute_launch_shape(ctx->prec, ctx->dim, ctx->sms, &ctx->ls);
     if (ctx->opt.shape[0] > 0) ctx->ls.move_blocks = ctx->opt.shape[0];
     if (ctx->opt.shape[1] > 0) ctx->ls.scatter_blocks = ctx->opt.shape[1];
-    if (ctx->opt.shape[3] > 0) ctx->ls.collide_blocks = ctx->opt.shape[3];
+    if (ctx->opt.shape[3] > 0) {
+        ctx->ls.collide_blocks = ctx->opt.shape[3];
+        follow_collide_blocks(ctx->prec, ctx->sms, &ctx->ls);
+    }
     *out = ctx;
     return DSMC_OK;
 }
@@ -873,30 +899,41 @@ static dsmc_status autotune(dsmc_ctx* ctx, int n_runs, int steps)
         for (int k = 0; k < 3; ++k) {
             ls.tile_budget = cand[k];
             compute_launch_shape(ctx->prec, ctx->dim, sms, &ls);
-            CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget));
+            CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget, ls.collide_stage));
             double cst = 0.0;
             if ((st = window(kGroupCell, &cst))) return st;
             if (cst < best_cost) { best_cost = cst; best = cand[k]; }
         }
         ls.tile_budget = best;
         compute_launch_shape(ctx->prec, ctx->dim, sms, &ls);
-        CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget));
+        CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget, ls.collide_stage));
     }
+    // collision CTAs: the default count per SM and one or two more (each
+    // with the largest stage that lets them share an SM)
     struct Knob { int* v; int group; int cand[3]; };
-    const int mb = ls.move_blocks, cb = ls.collide_blocks;
+    const int mb = ls.move_blocks, cpm = std::max(1, ls.collide_blocks / sms);
     Knob knobs[3] = {{&ls.move_blocks, kGroupMove, {mb, 2 * mb, 0}},
                      {&ls.scatter_blocks, kGroupScatter, {4 * sms, 8 * sms, 16 * sms}},
-                     {&ls.collide_blocks, kGroupCollide, {cb, 2 * cb, 0}}};
+                     {&ls.collide_blocks, kGroupCollide,
+                      {cpm * sms, cpm < 8 ? (cpm + 1) * sms : 0, cpm < 7 ? (cpm + 2) * sms : 0}}};
     for (Knob& kn : knobs) {
         int best = *kn.v;
         double best_cost = 1e300;
         for (int k = 0; k < 3 && kn.cand[k] > 0; ++k) {
             *kn.v = kn.cand[k];
+            if (kn.v == &ls.collide_blocks) {
+                follow_collide_blocks(ctx->prec, sms, &ls);
+                CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget, ls.collide_stage));
+            }
             double cst = 0.0;
             if ((st = window(kn.group, &cst))) return st;
             if (cst < best_cost) { best_cost = cst; best = kn.cand[k]; }
         }
         *kn.v = best;
+        if (kn.v == &ls.collide_blocks) {
+            follow_collide_blocks(ctx->prec, sms, &ls);
+            CK(prepare_kernels(ctx->prec, ctx->dim, ls.tile_budget, ls.collide_stage));
+        }
     }
     ctx->tuned_key = ((uint64_t)n_runs << 1) | 1u;
     return DSMC_OK;
@@ -1028,7 +1065,8 @@ static dsmc_status run_windows(dsmc_ctx* ctx, int n_runs, double dt, int steps,
             ctx->ls.move_blocks = shape[0];
             ctx->ls.scatter_blocks = shape[1];
             ctx->ls.collide_blocks = shape[3];
-            CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
+            follow_collide_blocks(ctx->prec, ctx->sms, &ctx->ls);
+            CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget, ctx->ls.collide_stage));
             ctx->tuned_key = ((uint64_t)n_runs << 1) | 1u;
             ctx->tuned_how = 2;
         } else {
@@ -1633,6 +1671,8 @@ dsmc_status dsmc_mixed_create(dsmc_ctx* const* parts, int n_parts, int flags, ds
         return DSMC_E_CUDA;
     }
     m->ls.tile_budget = 0;
+    m->ls.collide_ppc = 0;
+    for (dsmc_ctx* c : m->parts) m->ls.collide_ppc = std::max(m->ls.collide_ppc, collide_ppc_target(c));
     compute_multi_shape(m->prec, m->dim, m->sms, &m->ls);
     *out = m;
     return DSMC_OK;
@@ -1687,6 +1727,7 @@ static dsmc_status mixed_upload_args(dsmc_mixed* m, const int32_t* n_runs)
         ma.parts = static_cast<const StepArgs<T>*>(m->d_args[p]);
         ma.queue = m->d_queue;
         ma.n_parts = n;
+        ma.collide_stage = m->ls.collide_stage;
         for (int k = 0; k < n; ++k) {
             const int i = m->order[k];
             dsmc_ctx* c = m->parts[i];
@@ -1782,6 +1823,7 @@ dsmc_status dsmc_mixed_run(dsmc_mixed* m, const int32_t* n_runs, double dt, int 
             c->stats.h2d_bytes = 0;
             c->stats.d2h_bytes = 0;
             c->ls.tile_budget = m->ls.tile_budget;
+            c->ls.collide_stage = m->ls.collide_stage;
             st = prepare(c, n_runs[i], dt, steps, sample_steps, sample_steps, n_samples, seed,
                          n_runs[i]);
         }
@@ -1795,7 +1837,7 @@ dsmc_status dsmc_mixed_run(dsmc_mixed* m, const int32_t* n_runs, double dt, int 
             return mfail(m, st, buf + c->err);
         }
     }
-    CKM(prepare_multi_kernels(m->prec, m->dim, m->ls.tile_budget));
+    CKM(prepare_multi_kernels(m->prec, m->dim, m->ls.tile_budget, m->ls.collide_stage));
     dsmc_status st = m->prec == DSMC_FP64 ? mixed_upload_args<double>(m, n_runs)
                                           : mixed_upload_args<float>(m, n_runs);
     if (st) return st;
@@ -2072,7 +2114,7 @@ static dsmc_status noalloc_steps(dsmc_ctx* ctx, int n_runs, int steps, const int
                            ctx->stream));
     k_noalloc_sample_table<<<1, 256, 0, ctx->stream>>>(ctx->sample_slot, steps + 2, ss_dev, n_samples);
     CK(cudaGetLastError());
-    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget));
+    CK(prepare_kernels(ctx->prec, ctx->dim, ctx->ls.tile_budget, ctx->ls.collide_stage));
     AnyArgs u;
     enqueue_init(ctx, build_args(ctx, u, 0, (int)ctx->opt.run_offset, n_runs));
     ctx->cur = 0;

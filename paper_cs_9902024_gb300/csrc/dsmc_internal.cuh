@@ -15,8 +15,9 @@ constexpr int kWarpMax = 128;             // larger cells go to the big-cell ker
 constexpr int kTileCells = 256;           // cells (= threads) per CTA of the sort/gather kernel
 constexpr int kMaxTileBudget = 16384;     // largest particle budget of a sort/gather tile
 constexpr int kGenElems = 2048;           // inflow elements per Generation CTA
-constexpr int kCollideCells = 128;        // cells (= threads) per CTA of the collision kernel
-constexpr int kCollideStage = 2816;       // particles whose velocities one collision CTA stages
+constexpr int kCollideCells = 128;        // cells per tile (CTA) of the collision kernel
+constexpr int kCollidePerThread = 1;      // cells each of its threads collides
+constexpr int kCollideThreads = kCollideCells / kCollidePerThread;
 constexpr int kScanTile = 4096;           // cells per CTA of the scan
 constexpr int kScanThreads = 1024;
 constexpr int kMaxSamples = 4096;
@@ -148,6 +149,7 @@ struct StepArgs {
     int32_t total_cells;
     int32_t scan_blocks;
     int32_t tile_budget;   // particles a tile CTA stages in shared memory
+    int32_t collide_stage; // particles a collision CTA stages in shared memory
 };
 
 // Several problems advanced by one launch per kernel kind (the parts of a
@@ -165,7 +167,7 @@ struct MultiArgs {
     const StepArgs<T>* parts;     // device array, n_parts entries
     uint32_t* queue;              // kQueueKinds claim counters, zeroed at each step's end
     int32_t n_parts;
-    int32_t pad_;
+    int32_t collide_stage;        // the collision CTAs' stage (every part's the same)
     int32_t tile_base[kMaxParts + 1];     // sort/gather tiles before each part
     int32_t ctile_base[kMaxParts + 1];    // collision tiles before each part
     int32_t scan_base[kMaxParts + 1];     // scan CTAs before each part
@@ -180,6 +182,8 @@ struct LaunchShape {
     int move_blocks, move_threads;
     int scatter_blocks, cell_blocks, big_blocks, collide_blocks;
     int tile_budget;
+    int collide_stage;   // particles a collision CTA stages (follows collide_blocks)
+    int collide_ppc;     // staged particles a cell the default collision shape aims at
     int pdl;   // direct launches overlap with the previous kernel (programmatic
                // dependent launch); 0 while a step is captured into a graph
 };
@@ -206,7 +210,8 @@ struct LaunchShape {
                       cudaStream_t s);                                                         \
     void launch_sample_now(const void* args, cudaStream_t s);                                 \
     void launch_check(const void* args, const LaunchShape& ls, cudaStream_t s);               \
-    cudaError_t prepare_kernels(int dim, int tile_budget);                                    \
+    cudaError_t prepare_kernels(int dim, int tile_budget, int collide_stage);                 \
+    int collide_stage_for(int per_sm, int multi);                                             \
     void launch_m_generate(const void* margs, const LaunchShape& ls, cudaStream_t s);         \
     void launch_m_move(const void* margs, const LaunchShape& ls, cudaStream_t s);             \
     void launch_m_scan(const void* margs, const LaunchShape& ls, cudaStream_t s);             \
@@ -217,7 +222,7 @@ struct LaunchShape {
     void launch_m_collide(const void* margs, const LaunchShape& ls, cudaStream_t s);          \
     void launch_m_reduce(const void* margs, const LaunchShape& ls, cudaStream_t s);           \
     void launch_m_step_end(const void* margs, const LaunchShape& ls, cudaStream_t s);         \
-    cudaError_t prepare_multi_kernels(int dim, int tile_budget);                              \
+    cudaError_t prepare_multi_kernels(int dim, int tile_budget, int collide_stage);           \
     void compute_multi_shape(int dim, int sms, LaunchShape* ls);                              \
     void compute_launch_shape(int dim, int sms, LaunchShape* ls);                             \
     int big_cell_limit();
@@ -247,7 +252,8 @@ inline void launch_macro(int p, const void* a, int sample, int n_runs, int windo
                          cudaStream_t s) { DSMC_PICK(p, launch_macro(a, sample, n_runs, window, out, s)); }
 inline void launch_sample_now(int p, const void* a, cudaStream_t s) { DSMC_PICK(p, launch_sample_now(a, s)); }
 inline void launch_check(int p, const void* a, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_check(a, ls, s)); }
-inline cudaError_t prepare_kernels(int p, int dim, int tile_budget) { return DSMC_PICK(p, prepare_kernels(dim, tile_budget)); }
+inline cudaError_t prepare_kernels(int p, int dim, int tile_budget, int collide_stage) { return DSMC_PICK(p, prepare_kernels(dim, tile_budget, collide_stage)); }
+inline int collide_stage_for(int p, int per_sm, int multi) { return DSMC_PICK(p, collide_stage_for(per_sm, multi)); }
 inline void launch_m_generate(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_generate(m, ls, s)); }
 inline void launch_m_move(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_move(m, ls, s)); }
 inline void launch_m_scan(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_scan(m, ls, s)); }
@@ -258,7 +264,7 @@ inline void launch_m_collide_big(int p, const void* m, const LaunchShape& ls, cu
 inline void launch_m_collide(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_collide(m, ls, s)); }
 inline void launch_m_reduce(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_reduce(m, ls, s)); }
 inline void launch_m_step_end(int p, const void* m, const LaunchShape& ls, cudaStream_t s) { DSMC_PICK(p, launch_m_step_end(m, ls, s)); }
-inline cudaError_t prepare_multi_kernels(int p, int dim, int tile_budget) { return DSMC_PICK(p, prepare_multi_kernels(dim, tile_budget)); }
+inline cudaError_t prepare_multi_kernels(int p, int dim, int tile_budget, int collide_stage) { return DSMC_PICK(p, prepare_multi_kernels(dim, tile_budget, collide_stage)); }
 inline void compute_multi_shape(int p, int dim, int sms, LaunchShape* ls) { DSMC_PICK(p, compute_multi_shape(dim, sms, ls)); }
 inline void compute_launch_shape(int p, int dim, int sms, LaunchShape* ls) { DSMC_PICK(p, compute_launch_shape(dim, sms, ls)); }
 inline int big_cell_limit(int p) { return DSMC_PICK(p, big_cell_limit()); }

@@ -1358,42 +1358,14 @@ __device__ __forceinline__ void candidate_draws(const C& c, uint32_t run, uint32
     ue = u01<T>(r2.x);
 }
 
-// the same candidate for a single thread: the azimuth block is drawn only
-// when the pair is accepted
-template <typename T, class C>
-__device__ __forceinline__ void collide_candidate_lazy(const C& c, T* sv0, T* sv1, T* sv2,
-                                                       uint32_t run, uint32_t step, uint32_t cell,
-                                                       int64_t k, uint32_t N, T smax, T& seen,
-                                                       uint32_t& nacc, uint32_t& nclamp)
-{
-    const uint4 r = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k));
-    const uint32_t i = pick(r.x, N);
-    uint32_t j = pick(r.y, N - 1u);
-    if (j >= i) j += 1u;
-    T v1[3] = {sv0[i], sv1[i], sv2[i]};
-    T v2[3] = {sv0[j], sv1[j], sv2[j]};
-    const T gx = v1[0] - v2[0], gy = v1[1] - v2[1], gz = v1[2] - v2[2];
-    const T g2 = gx * gx + gy * gy + gz * gz;
-    const T g = dsqrt(g2);
-    const T sc = sigma_cr<T>(c, g, g2);
-    if (sc > seen) seen = sc;
-    if (sc > smax) nclamp++;
-    if (ntc_accept<T>(u01<T>(r.z), sc, smax)) {
-        const uint4 r2 = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k + 1));
-        scatter_pair<T>(v1, v2, g, u01<T>(r.w), u01<T>(r2.x));
-        sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
-        sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
-        nacc++;
-    }
-}
-
-// One NTC candidate pair (i, j) on velocities in shared memory: accept with
-// probability sigma_T c_r / (sigma_T c_r)_max, then scatter isotropically.
-// Every cell path uses this arithmetic, so results do not depend on the path.
-template <typename T, class C>
-__device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T* sv2, uint32_t i,
-                                                  uint32_t j, T u2, T u3, T ue, T smax, T& seen,
-                                                  uint32_t& nacc, uint32_t& nclamp)
+// One NTC candidate pair (i, j): accept with probability
+// sigma_T c_r / (sigma_T c_r)_max, then scatter isotropically; `azimuth_u()`
+// gives the azimuth uniform and is called only for an accepted pair.  Every
+// cell path uses this arithmetic, so results do not depend on the path.
+template <typename T, class C, class AZ>
+__device__ __forceinline__ void collide_pair(const C& c, T* sv0, T* sv1, T* sv2, uint32_t i,
+                                             uint32_t j, T u2, T u3, AZ azimuth_u, T smax, T& seen,
+                                             uint32_t& nacc, uint32_t& nclamp)
 {
     T v1[3] = {sv0[i], sv1[i], sv2[i]};
     T v2[3] = {sv0[j], sv1[j], sv2[j]};
@@ -1404,11 +1376,20 @@ __device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T*
     if (sc > seen) seen = sc;
     if (sc > smax) nclamp++;
     if (ntc_accept<T>(u2, sc, smax)) {
-        scatter_pair<T>(v1, v2, g, u3, ue);
+        scatter_pair<T>(v1, v2, g, u3, azimuth_u());
         sv0[i] = v1[0]; sv1[i] = v1[1]; sv2[i] = v1[2];
         sv0[j] = v2[0]; sv1[j] = v2[1]; sv2[j] = v2[2];
         nacc++;
     }
+}
+
+// the same with all draws made beforehand
+template <typename T, class C>
+__device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T* sv2, uint32_t i,
+                                                  uint32_t j, T u2, T u3, T ue, T smax, T& seen,
+                                                  uint32_t& nacc, uint32_t& nclamp)
+{
+    collide_pair<T>(c, sv0, sv1, sv2, i, j, u2, u3, [&]() { return ue; }, smax, seen, nacc, nclamp);
 }
 
 // Interaction of one large cell, velocities in id order at sv0..sv2 (shared
@@ -1743,7 +1724,7 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 // cells are done whole by the big-cell kernels), on the cells' velocities
 // in the next pool, now in id order.  A CTA takes kCollideCells consecutive
 // cells.  (1) Thread 0 starts bulk copies (TMA) of the tile's velocities,
-// up to kCollideStage particles, into shared memory; meanwhile every thread
+// up to collide_stage particles, into shared memory; meanwhile every thread
 // forms its cell's NTC candidate count (coalesced remainder and (sigma
 // c_r)_max accesses) and the staged range is cut to whole cells.  (2) The
 // cells are handed to the threads grouped by candidate count (a 32-bin
@@ -1751,23 +1732,58 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 // candidates.  (3) Each thread collides its cell -- in shared memory if
 // staged, else in place in global memory, with the same arithmetic.  (4)
 // The cells' moments at sample steps; the staged velocities are stored back
-// with coalesced stores.  (Handing each thread the next cell of a list in
-// decreasing candidate order as it finishes measured slower: a tile has
-// about one cell per thread, so nothing is left to balance.)
+// with coalesced stores.  The kernel waits on memory and on the slowest
+// cell of each tile, so it is sized for CTAs in flight: a stage of 18
+// particles a cell lets 7 CTAs share an SM.  (Measured slower: handing each
+// thread the next cell of a list in decreasing candidate order as it
+// finishes -- a tile has about one cell per thread, so nothing is left to
+// balance; two or four cells per thread in snake order over the candidate
+// order, and 64-cell tiles -- fewer warps in flight.)
+//
+// A thread's candidates of one cell, one after another.  The pair draw of
+// candidate k + 1 is made while candidate k is applied (it depends on no
+// velocity), which gives the thread two independent chains of work; the
+// azimuth draw is made only for an accepted pair.  The draws are those of
+// candidate_draws.
 template <typename T, class C>
 __device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2, uint32_t run,
                                                  uint32_t step, uint32_t cell, uint32_t M, uint32_t N,
                                                  T smax, T& seen, uint32_t& nacc, uint32_t& nclamp)
 {
-    for (uint32_t k = 0; k < M; ++k)
-        collide_candidate_lazy<T>(c, v0, v1, v2, run, step, cell, k, N, smax, seen, nacc, nclamp);
+    if (M == 0u) return;
+    uint4 r = draw_c(c, run, step, cell, kColl, 0u);
+    for (uint32_t k = 0; k < M; ++k) {
+        // the next candidate's pair draw (the last one draws its own again)
+        const uint32_t kn = k + 1u < M ? k + 1u : k;
+        const uint4 rn = draw_c(c, run, step, cell, kColl, 2u * kn);
+        const uint32_t i = pick(r.x, N);
+        uint32_t j = pick(r.y, N - 1u);
+        if (j >= i) j += 1u;
+        collide_pair<T>(c, v0, v1, v2, i, j, u01<T>(r.z), u01<T>(r.w), [&]() {
+            return u01<T>(draw_c(c, run, step, cell, kColl, 2u * k + 1u).x);
+        }, smax, seen, nacc, nclamp);
+        r = rn;
+    }
 }
 
+// the staged velocities of a collision CTA: three components of `stage` + 8
+// elements each (the 16-byte aligned superset of the tile's range)
+__host__ __device__ constexpr int collide_stage_pitch(int stage) { return stage + 8; }
+
+// resident CTAs of the collision kernel per SM that its registers must
+// allow: a binary32 stage of 18-19 particles a cell (28 KB) fits 7 on an
+// SM's 228 KB, a binary64 one 3.  The kernel waits on memory and on its
+// slowest cell per tile, so CTAs in flight matter more than registers: 7
+// CTAs of 128 threads (at most 73 registers) measured 12% faster than 6
+// (85) on the duct ensemble.
+// (The multi-part kernel, which also holds its part's arguments, is
+// bounded for one CTA fewer: its default stage, for filled grids, lets 6
+// share an SM.)
 template <typename T>
-__host__ __device__ constexpr int collide_stage_pitch() { return kCollideStage + 8; }
+__host__ __device__ constexpr int collide_min_blocks() { return sizeof(T) == 4 ? 7 : 3; }
 
 // shared memory of the collision kernel: the staged velocities (three
-// components, kCollideStage + 8 each) and the mbarrier of their bulk copies
+// components, collide_stage + 8 each) and the mbarrier of their bulk copies
 template <typename T>
 struct CollideSmem {
     T* s0;
@@ -1777,13 +1793,20 @@ struct CollideSmem {
 };
 
 // One tile of kCollideCells cells (every thread of the CTA calls it; the
-// mbarrier's phase and the thread's tallies are carried across calls).
+// mbarrier's phase and the thread's tallies are carried across calls).  Each
+// of the kCollideThreads threads takes kCollidePerThread cells: for the
+// per-cell steps, cells tid, tid + kCollideThreads, ...; for the collisions,
+// positions of the tile's ascending candidate order taken in snake order
+// (tid, 2 kCollideThreads - 1 - tid, ...), so that a thread's light cells
+// offset its heavy ones.
 template <typename T>
 __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
                                              const CollideSmem<T>& sm, uint32_t& phase,
                                              CellTally& tl)
 {
     constexpr uint32_t kVec = 16u / sizeof(T);   // elements per 16 bytes
+    constexpr int CPT = kCollidePerThread;
+    constexpr uint32_t TH = (uint32_t)kCollideThreads;
     T* s0 = sm.s0;
     T* s1 = sm.s1;
     T* s2 = sm.s2;
@@ -1801,30 +1824,36 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
     const int64_t c0 = tile * kCollideCells;
     const int64_t rest = a.total_cells - c0;
     const uint32_t nc = rest < kCollideCells ? (uint32_t)rest : (uint32_t)kCollideCells;
-    const int64_t gcell = c0 + tid;
-    const bool mine = tid < nc;
-    uint32_t beg = 0, N = 0;
-    if (mine) {
-        beg = a.start[gcell];
-        N = a.start[gcell + 1] - beg;
+    uint32_t beg[CPT], N[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        const uint32_t q = tid + (uint32_t)u * TH;
+        beg[u] = 0;
+        N[u] = 0;
+        if (q < nc) {
+            beg[u] = a.start[c0 + q];
+            N[u] = a.start[c0 + q + 1] - beg[u];
+        }
     }
     if (tid == 0) {
-        // the tile's particles [beg, end), clipped to the stage and the pool
+        // the tile's particles [b, end), clipped to the stage and the pool
+        // (cell 0 of the tile is thread 0's first cell)
+        const uint32_t b = beg[0];
         const uint32_t end = a.start[c0 + nc];
-        const int64_t room = a.cap_old - (int64_t)beg;
-        int64_t n = end > beg ? (int64_t)(end - beg) : 0;
-        if (n > kCollideStage) n = kCollideStage;
+        const int64_t room = a.cap_old - (int64_t)b;
+        int64_t n = end > b ? (int64_t)(end - b) : 0;
+        if (n > a.collide_stage) n = a.collide_stage;
         if (n > room) n = room > 0 ? room : 0;
-        s_b0 = beg;
+        s_b0 = b;
         s_n = (uint32_t)n;
         s_nload = (uint32_t)n;
         if (n > 0) {
-            // 16-byte aligned superset [lo, hi) of [beg, beg + n); hi stays
+            // 16-byte aligned superset [lo, hi) of [b, b + n); hi stays
             // inside the pool, whose capacity is a multiple of 256
-            const uint32_t lo = beg & ~(kVec - 1u);
-            const uint32_t hi = (beg + (uint32_t)n + kVec - 1u) & ~(kVec - 1u);
+            const uint32_t lo = b & ~(kVec - 1u);
+            const uint32_t hi = (b + (uint32_t)n + kVec - 1u) & ~(kVec - 1u);
             const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(T);
-            s_sh = beg - lo;
+            s_sh = b - lo;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&s_bar, 3u * bytes);
             bulk_g2s(s0, a.vo[0] + lo, bytes, &s_bar);
@@ -1836,37 +1865,45 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
     __syncthreads();
     const uint32_t b0 = s_b0;
     const uint32_t nload = s_nload;
-    // cut the staged range at the first cell that does not fit whole
-    if (mine) {
-        const uint32_t rel = beg - b0;
-        const uint64_t end = (uint64_t)rel + N;
-        if (beg < b0) atomicMin(&s_n, 0u);
-        else if (rel < nload && end > (uint64_t)nload) atomicMin(&s_n, rel);
+    uint32_t bin[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        const uint32_t q = tid + (uint32_t)u * TH;
+        const int64_t gcell = c0 + q;
+        const bool mine = q < nc;
+        // cut the staged range at the first cell that does not fit whole
+        if (mine) {
+            const uint32_t rel = beg[u] - b0;
+            const uint64_t end = (uint64_t)rel + N[u];
+            if (beg[u] < b0) atomicMin(&s_n, 0u);
+            else if (rel < nload && end > (uint64_t)nload) atomicMin(&s_n, rel);
+        }
+        // NTC candidate count of the cell; the remainder is final
+        const bool act = mine && N[u] <= (uint32_t)kWarpMax &&
+                         (uint64_t)beg[u] + N[u] <= (uint64_t)a.cap_old;
+        uint32_t M32 = 0;
+        if (act) {
+            double rem = a.rem[gcell];
+            const T smax = a.smax[gcell];
+            const int64_t M = ntc_count<T>(c, N[u], smax, rem);
+            if (N[u] >= 2) a.rem[gcell] = rem;
+            M32 = M > (int64_t)0x7FFFFFFF ? 0x7FFFFFFFu : (uint32_t)M;
+            s_smax[q] = smax;
+            if (a.cand && M32 == 0u) { a.cand[gcell] = 0u; a.accd[gcell] = 0u; }
+        }
+        s_beg[q] = beg[u];
+        s_N[q] = act ? N[u] : kOff;
+        s_M[q] = M32;
+        bin[u] = M32 < 31u ? M32 : 31u;
     }
-    // NTC candidate count of this thread's cell; the remainder is final
-    const bool act = mine && N <= (uint32_t)kWarpMax && (uint64_t)beg + N <= (uint64_t)a.cap_old;
-    uint32_t M32 = 0;
-    if (act) {
-        double rem = a.rem[gcell];
-        const T smax = a.smax[gcell];
-        const int64_t M = ntc_count<T>(c, N, smax, rem);
-        if (N >= 2) a.rem[gcell] = rem;
-        M32 = M > (int64_t)0x7FFFFFFF ? 0x7FFFFFFFu : (uint32_t)M;
-        s_smax[tid] = smax;
-        if (a.cand && M32 == 0u) { a.cand[gcell] = 0u; a.accd[gcell] = 0u; }
-    }
-    s_beg[tid] = beg;
-    s_N[tid] = act ? N : kOff;
-    s_M[tid] = M32;
     __syncthreads();
     const uint32_t n_st = s_n;
     const uint32_t sh = s_sh;
-    const bool staged = act && beg >= b0 && (uint64_t)(beg - b0) + N <= (uint64_t)n_st;
-    // (2) cells handed to threads grouped by candidate count (32 bins,
-    // ascending), so that the lanes of a warp run similar numbers of
-    // candidates
-    const uint32_t bin = M32 < 31u ? M32 : 31u;
-    const uint32_t in_bin = atomicAdd(&s_bin[bin], 1u);
+    // (2) the cells in ascending candidate count (32 bins), so that the
+    // lanes of a warp run similar numbers of candidates
+    uint32_t in_bin[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) in_bin[u] = atomicAdd(&s_bin[bin[u]], 1u);
     __syncthreads();
     if (tid < 32) {
         const uint32_t v = s_bin[tid];
@@ -1879,7 +1916,8 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
         s_bin[tid] = x - v;
     }
     __syncthreads();
-    s_ord[s_bin[bin] + in_bin] = tid;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) s_ord[s_bin[bin[u]] + in_bin[u]] = tid + (uint32_t)u * TH;
     if (nload > 0) {
         if (!mbar_wait(&s_bar, phase)) {
             atomicOr(&a.ctr->error, DSMC_ERR_TIMEOUT);
@@ -1888,10 +1926,12 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
         phase ^= 1u;
     }
     __syncthreads();
-    // (3) the candidates of the thread's cell, in shared memory if staged,
+    // (3) the candidates of the thread's cells, in shared memory if staged,
     // else in place in global memory (the same arithmetic)
-    {
-        const uint32_t q = s_ord[tid];
+#pragma unroll 1
+    for (int u = 0; u < CPT; ++u) {
+        const uint32_t pos = (u & 1) ? ((uint32_t)u + 1u) * TH - 1u - tid : (uint32_t)u * TH + tid;
+        const uint32_t q = s_ord[pos];
         const uint32_t Nq = s_N[q];
         if (Nq != kOff && s_M[q] > 0u) {
             const int64_t gq = c0 + q;
@@ -1921,22 +1961,30 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
     }
     __syncthreads();
     // (4) moments at sample steps, thread per cell
-    if (slot_t >= 0 && act) {
-        const uint32_t o = sh + (beg - b0);
-        double m[DSMC_NMOM];
-        if (staged) cell_moments<T>(s0 + o, s1 + o, s2 + o, N, m);
-        else cell_moments<T>(a.vo[0] + beg, a.vo[1] + beg, a.vo[2] + beg, N, m);
-        double* mo = a.mom + gcell * DSMC_NMOM;
-        if (slot_t & kSlotFirst)
-            for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] = m[qq];
-        else
-            for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] += m[qq];
+    if (slot_t >= 0) {
+#pragma unroll 1
+        for (int u = 0; u < CPT; ++u) {
+            const uint32_t q = tid + (uint32_t)u * TH;
+            const uint32_t Nq = s_N[q];
+            if (Nq == kOff) continue;
+            const int64_t gcell = c0 + q;
+            const bool staged = beg[u] >= b0 && (uint64_t)(beg[u] - b0) + Nq <= (uint64_t)n_st;
+            const uint32_t o = sh + (beg[u] - b0);
+            double m[DSMC_NMOM];
+            if (staged) cell_moments<T>(s0 + o, s1 + o, s2 + o, Nq, m);
+            else cell_moments<T>(a.vo[0] + beg[u], a.vo[1] + beg[u], a.vo[2] + beg[u], Nq, m);
+            double* mo = a.mom + gcell * DSMC_NMOM;
+            if (slot_t & kSlotFirst)
+                for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] = m[qq];
+            else
+                for (int qq = 0; qq < DSMC_NMOM; ++qq) mo[qq] += m[qq];
+        }
     }
     {
         T* g0 = a.vo[0] + b0;
         T* g1 = a.vo[1] + b0;
         T* g2 = a.vo[2] + b0;
-        for (uint32_t p = tid; p < n_st; p += kCollideCells) {
+        for (uint32_t p = tid; p < n_st; p += TH) {
             g0[p] = s0[sh + p];
             g1[p] = s1[sh + p];
             g2[p] = s2[sh + p];
@@ -1959,16 +2007,16 @@ __device__ __forceinline__ void flush_tally(Counters* ctr, const CellTally& tl)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kCollideCells, 6) k_collide(StepArgs<T> a)
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>()) k_collide(StepArgs<T> a)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
-    constexpr int kPitch = collide_stage_pitch<T>();
+    const int pitch = collide_stage_pitch(a.collide_stage);
     CollideSmem<T> sm;
     sm.s0 = reinterpret_cast<T*>(smem_raw);
-    sm.s1 = sm.s0 + kPitch;
-    sm.s2 = sm.s1 + kPitch;
+    sm.s1 = sm.s0 + pitch;
+    sm.s2 = sm.s1 + pitch;
     sm.bar = &s_bar;
     if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
     uint32_t phase = 0;
@@ -2646,16 +2694,17 @@ __global__ void __launch_bounds__(kTileCells, 4) mk_cell(MultiArgs<T> m)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kCollideCells, 6) mk_collide(MultiArgs<T> m)
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>() - (sizeof(T) == 4 ? 1 : 0))
+    mk_collide(MultiArgs<T> m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ StepArgs<T> sa;
-    constexpr int kPitch = collide_stage_pitch<T>();
+    const int pitch = collide_stage_pitch(m.collide_stage);
     CollideSmem<T> sm;
     sm.s0 = reinterpret_cast<T*>(smem_raw);
-    sm.s1 = sm.s0 + kPitch;
-    sm.s2 = sm.s1 + kPitch;
+    sm.s1 = sm.s0 + pitch;
+    sm.s2 = sm.s1 + pitch;
     sm.bar = &s_bar;
     if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
     uint32_t phase = 0;
@@ -2850,17 +2899,16 @@ void launch_cell(const void* args, const LaunchShape& ls, cudaStream_t s)
     }));
 }
 
-static size_t collide_smem(int prec)
+static size_t collide_smem(int prec, int stage)
 {
-    return prec == DSMC_FP64 ? (size_t)3 * collide_stage_pitch<double>() * 8
-                             : (size_t)3 * collide_stage_pitch<float>() * 4;
+    return (size_t)3 * collide_stage_pitch(stage) * (prec == DSMC_FP64 ? 8 : 4);
 }
 
 void launch_collide(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
     constexpr int prec = DSMC_KPREC;
-    DISPATCH_PREC(prec, launch_pdl(ls, k_collide<T>, ls.collide_blocks, kCollideCells, collide_smem(prec),
-                                   s, A<T>(args)));
+    DISPATCH_PREC(prec, launch_pdl(ls, k_collide<T>, ls.collide_blocks, kCollideThreads,
+                                   collide_smem(prec, A<T>(args).collide_stage), s, A<T>(args)));
 }
 
 int big_cell_limit() { return big_max_of<DSMC_KT>(); }
@@ -2932,6 +2980,68 @@ static cudaError_t raise_cell_smem_limit(int prec, int dim, size_t bytes)
     return e;
 }
 
+// The collision kernels' dynamic shared-memory limits, raised only (as the
+// tile kernel's): [single, multi-part].
+static cudaError_t raise_collide_smem_limit(int prec, int multi, size_t bytes)
+{
+    static std::mutex mu;
+    static size_t set[2][2] = {{0, 0}, {0, 0}};
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[prec == DSMC_FP64 ? 1 : 0][multi ? 1 : 0];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    DISPATCH_PREC(prec, {
+        e = multi ? set_smem(mk_collide<T>, bytes) : set_smem(k_collide<T>, bytes);
+    });
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
+constexpr int kCollideStageMin = 1024, kCollideStageMax = 8192;
+
+// The largest collision stage (a multiple of 64 particles, 1024 .. 8192) at
+// which `per_sm` CTAs of the collision kernel (`multi`: the multi-part one)
+// are resident on an SM together, by the occupancy calculator; 1024 if none.
+int collide_stage_for(int per_sm, int multi)
+{
+    constexpr int prec = DSMC_KPREC;
+    if (per_sm < 1) per_sm = 1;
+    raise_collide_smem_limit(prec, multi, collide_smem(prec, kCollideStageMax));
+    int stage = kCollideStageMax;
+    for (; stage > kCollideStageMin; stage -= 64) {
+        int b = 0;
+        DISPATCH_PREC(prec, {
+            if (multi)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mk_collide<T>, kCollideThreads,
+                                                              collide_smem(prec, stage));
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_collide<T>, kCollideThreads,
+                                                              collide_smem(prec, stage));
+        });
+        if (b >= per_sm) break;
+    }
+    (void)cudaGetLastError();
+    return stage;
+}
+
+// Default collision shape: the most CTAs per SM (at most 8) whose stage
+// still holds ls->collide_ppc particles a cell (22 when unset), the stage
+// the largest that lets that many share an SM.
+static void pick_collide_shape(int sms, LaunchShape* ls, int multi)
+{
+    constexpr int prec = DSMC_KPREC;
+    const int want = (ls->collide_ppc > 0 ? ls->collide_ppc : 22) * kCollideCells;
+    int k = 8, stage = 0;
+    for (; k >= 1; --k) {
+        stage = collide_stage_for(k, multi);
+        if (stage >= want || k == 1) break;
+    }
+    if (k < 1) k = 1;
+    ls->collide_blocks = sms * k;
+    ls->collide_stage = stage;
+    raise_collide_smem_limit(prec, multi, collide_smem(prec, stage));
+}
+
 void compute_launch_shape(int dim, int sms, LaunchShape* ls)
 {
     constexpr int prec = DSMC_KPREC;
@@ -2956,25 +3066,18 @@ void compute_launch_shape(int dim, int sms, LaunchShape* ls)
     ls->move_blocks = sms * (bm > 0 ? bm : 4);
     ls->scatter_blocks = sms * 8;
     ls->cell_blocks = sms * (bc > 0 ? bc : 2);
-    int bl = 0;
-    DISPATCH_PREC(prec, {
-        set_smem(k_collide<T>, collide_smem(prec));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_collide<T>, kCollideCells,
-                                                      collide_smem(prec));
-    });
-    ls->collide_blocks = sms * (bl > 0 ? bl : 3);
+    pick_collide_shape(sms, ls, 0);
     ls->big_blocks = sms * 2;
 }
 
-cudaError_t prepare_kernels(int dim, int tile_budget)
+cudaError_t prepare_kernels(int dim, int tile_budget, int collide_stage)
 {
     constexpr int prec = DSMC_KPREC;
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
         e = set_smem(k_cell_big<T, D>, big_smem(prec));
-        if (e == cudaSuccess)
-            e = set_smem(k_collide<T>, collide_smem(prec));
     }));
+    if (e == cudaSuccess) e = raise_collide_smem_limit(prec, 0, collide_smem(prec, collide_stage));
     if (e == cudaSuccess) e = raise_cell_smem_limit(prec, dim, cell_smem_bytes(prec, tile_budget));
     return e;
 }
@@ -3043,7 +3146,8 @@ void launch_m_collide_big(const void* margs, const LaunchShape& ls, cudaStream_t
 void launch_m_collide(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
     constexpr int prec = DSMC_KPREC;
-    DISPATCH_PREC(prec, (mk_collide<T><<<ls.collide_blocks, kCollideCells, collide_smem(prec), s>>>(
+    DISPATCH_PREC(prec, (mk_collide<T><<<ls.collide_blocks, kCollideThreads,
+                                          collide_smem(prec, MA<T>(margs).collide_stage), s>>>(
                              MA<T>(margs))));
 }
 
@@ -3059,17 +3163,16 @@ void launch_m_step_end(const void* margs, const LaunchShape&, cudaStream_t s)
     DISPATCH_PREC(prec, (mk_step_end<T><<<1, kMaxParts, 0, s>>>(MA<T>(margs))));
 }
 
-cudaError_t prepare_multi_kernels(int dim, int tile_budget)
+cudaError_t prepare_multi_kernels(int dim, int tile_budget, int collide_stage)
 {
     constexpr int prec = DSMC_KPREC;
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
         e = set_smem(mk_cell_big<T, D>, big_smem(prec));
         if (e == cudaSuccess)
-            e = set_smem(mk_collide<T>, collide_smem(prec));
-        if (e == cudaSuccess)
             e = set_smem(mk_cell<T, D>, cell_smem_bytes(prec, tile_budget));
     }));
+    if (e == cudaSuccess) e = raise_collide_smem_limit(prec, 1, collide_smem(prec, collide_stage));
     return e;
 }
 
@@ -3081,21 +3184,19 @@ void compute_multi_shape(int dim, int sms, LaunchShape* ls)
     ls->sms = sms;
     if (ls->tile_budget <= 0) ls->tile_budget = 3072;
     ls->tile_budget = (ls->tile_budget + 7) / 8 * 8;
-    prepare_multi_kernels(dim, ls->tile_budget);
-    int bm = 0, bs = 0, bc = 0, bl = 0;
+    pick_collide_shape(sms, ls, 1);
+    prepare_multi_kernels(dim, ls->tile_budget, ls->collide_stage);
+    int bm = 0, bs = 0, bc = 0;
     DISPATCH_PREC(prec, DISPATCH_DIM(dim, {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, mk_move<T, D>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, mk_scatter<T>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, mk_cell<T, D>, kTileCells,
                                                       cell_smem_bytes(prec, ls->tile_budget));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, mk_collide<T>, kCollideCells,
-                                                      collide_smem(prec));
     }));
     ls->move_threads = 256;
     ls->move_blocks = sms * (bm > 0 ? bm : 4);
     ls->scatter_blocks = sms * (bs > 0 ? bs : 4);
     ls->cell_blocks = sms * (bc > 0 ? bc : 2);
-    ls->collide_blocks = sms * (bl > 0 ? bl : 3);
     ls->big_blocks = sms * 2;
     ls->pdl = 0;
 }
