@@ -602,12 +602,17 @@ def main():
         if os.path.exists(tp):
             try:
                 tj = json.load(open(tp))
-                ent = tj.get(dom)
+                # entries per workload family (grid and gas, any run count)
+                ent = tj.get(args.workload.rsplit("_n", 1)[0], {}).get(dom)
                 if ent and ent.get("kernel_hash") == kernel_hash():
+                    # bytes per particle of the captured launch, times the
+                    # particles the kernel processed per launch here
                     per_particle = ent["dram_bytes"] / ent["particles"]
                     units = prs["pool_steps"]
-                    if dom == "cell":
+                    if dom in ("cell", "collide"):
                         units -= prs["big_pool_steps"]
+                    elif dom in ("cell_big", "collide_big"):
+                        units = prs["big_pool_steps"]
                     roof["traffic"] = per_particle * units / prs["launches_kernel"][dom]
             except Exception:
                 roof["traffic"] = None

@@ -2,12 +2,14 @@
 launch shapes), for a profiler to capture chosen launches of it.
 
     python -m paper_cs_9902024_gb300.profile_run duct 256 301
+    python -m paper_cs_9902024_gb300.profile_run duct 256 301 760,2432,3072,1216
     python -m paper_cs_9902024_gb300.profile_run jet 8 60
 
 Arguments: workload (duct: the 64x32 channel, HS, its 8 sample times; jet:
 the 256x128 pulsed jet, VHS; plate: the 128x64x64 box with a plate; mixed:
 runs on grids of 32x16 to 256x128 cells; the last three with 2 sample
-times), runs, steps.  Each step launches the step's kernels once, in
+times), runs, steps, and optionally a launch shape (move CTAs, scatter
+CTAs, sort/gather tile budget, collision CTAs; 0 keeps a default).  Each step launches the step's kernels once, in
 a fixed order, so the n-th launch of a kernel is its n-th step.  Prints the
 particle-steps done and the device error word (non-zero exit if set)."""
 import sys
@@ -20,10 +22,14 @@ def main(argv):
     name = argv[0] if argv else "duct"
     runs = int(argv[1]) if len(argv) > 1 else 256
     steps = int(argv[2]) if len(argv) > 2 else 301
+    shape = None
+    if len(argv) > 3:
+        from .dsmc import SHAPE_KEYS
+        shape = dict(zip(SHAPE_KEYS, (int(v) for v in argv[3].split(","))))
     if name == "mixed":
         m = W.mixed(grids=[(32, runs), (64, runs), (128, runs), (256, runs)], steps=steps,
                     n_samples=2)
-        e = MixedEnsemble(m, use_graph=False).run()
+        e = MixedEnsemble(m, use_graph=False, shape=shape).run()
         st, err = e.stats(), e.mixed_stats()["error_word"]
     else:
         if name == "duct":
@@ -31,13 +37,14 @@ def main(argv):
         else:
             make = {"jet": W.jet256x128_n64, "plate": W.plate128x64x64_n16}[name]
             w = make(runs=runs, steps=steps, n_samples=2)
-        e = Ensemble(w, use_graph=False).run()
+        e = Ensemble(w, use_graph=False, shape=shape).run()
         st = e.stats()
         err = st["error_word"]
     print("%s: %d runs x %d steps, particle_steps %d, pool_steps %d (in cells above 128: %d), "
-          "particles now %d, error word %d" % (name, runs, steps, st["particle_steps"],
-                                               st["pool_steps"], st.get("big_pool_steps", 0),
-                                               st["particles_now"], err))
+          "particles now %d, error word %d, shape %s" % (
+              name, runs, steps, st["particle_steps"], st["pool_steps"],
+              st.get("big_pool_steps", 0), st["particles_now"], err,
+              st.get("shape", e.parts[0].stats()["shape"] if name == "mixed" else None)))
     e.close()
     return 1 if err else 0
 
