@@ -228,7 +228,7 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     all; 16 for Interaction), times the particles it processes.
     "layout": the bytes of this build's data layout (one read of every
     input, one write of every output, no re-reads): the cell-relative
-    offsets and stored cell keys, the (slot, id) LCR entries, the staged
+    offsets and stored cell keys, the 4-byte LCR entries (slots), the staged
     velocities."""
     D = w["dim"]
     t = 4
@@ -238,8 +238,9 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     pool = st["pool_steps"]
     big = st.get("big_pool_steps", 0)
     mb = _method_bytes(D)
-    # read the LCR entry, gather offsets and v; write offsets, cell key, id, v
-    gather = 8 + 2 * (D * t + 3 * t) + 8
+    # read the LCR entry (4), gather offsets, v and id; write offsets, cell
+    # key, id, v
+    gather = 4 + (D * t + 3 * t + 4) + (D * t + 3 * t + 8)
     method = {
         "move": moved_old * mb["motion"],
         "scatter": pool * mb["scatter"],
@@ -254,8 +255,8 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
         # wall hits) and the cell key, write the offsets (D) and the new key;
         # the count atomics stay in L2
         "move": moved_old * (2 * D * t + D * t + 8),
-        # read key and id, write the LCR entry (slot, id)
-        "scatter": pool * 16,
+        # read the cell key, write the LCR entry (the slot)
+        "scatter": pool * 8,
         # the tile kernel: particles of cells up to 128 (+ the start table);
         # cells above 128 particles: one CTA per cell, the same bytes
         "cell": (pool - big) * gather + cells * steps * 4,

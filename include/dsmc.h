@@ -376,8 +376,9 @@ void dsmc_mixed_destroy(dsmc_mixed* m);
 dsmc_status dsmc_debug_begin(dsmc_ctx* ctx, int n_runs, double dt, uint64_t seed);
 /* Advance every run by n_steps steps. */
 dsmc_status dsmc_debug_step(dsmc_ctx* ctx, int n_steps);
-/* Particles of `run` in the current P order (cell, id): x[n][3], v[n][3],
- * id[n]; at most cap particles are written, *n_out gets the count. */
+/* Particles of `run` in the current P order (by cell, each cell in LCR
+ * order): x[n][3], v[n][3], id[n]; at most cap particles are written,
+ * *n_out gets the count. */
 dsmc_status dsmc_debug_get_state(dsmc_ctx* ctx, int run, double* x, double* v,
                                  uint32_t* id, int64_t cap, int64_t* n_out);
 /* Replace the particles of `run` (any order; this order numbers the slots

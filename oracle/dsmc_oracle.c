@@ -486,7 +486,7 @@ static int motion(orc_ctx* C, orc_run* R, int run, int step, orc_particle* p)
     }
 }
 
-/* NTC collisions in one cell: its N particles are q[0..N) in id order. */
+/* NTC collisions in one cell: its N particles are q[0..N) in LCR order. */
 static void interaction_cell(orc_ctx* C, orc_run* R, int run, int step, int c,
                              orc_particle* q, int64_t N)
 {
@@ -548,9 +548,11 @@ int orc_step(orc_ctx* C, int run, int step)
     memset(R->count, 0, nc * sizeof(int32_t));
     for (int64_t s = 0; s < n_all; ++s)
         if (cell[s] >= 0) R->count[cell[s]]++;
-    /* Indexing: LCR = slots in (cell, id) order.  Exclusive prefix of the
-     * counts, slots placed in slot order, then each cell's slots put in
-     * increasing particle id. */
+    /* Indexing: LCR = slots grouped by cell, each cell's slots in array
+     * order (one serial pass over P, as the readdressing of Sec. 1.1 fills
+     * it): exclusive prefix of the counts, then every surviving slot, in
+     * increasing slot order, appended to its cell's range.  Slots number the
+     * old particles in their P order, then the entrants in generation order. */
     int64_t* start = malloc((nc + 1) * sizeof(int64_t));
     if (!start) { free(cell); return -2; }
     start[0] = 0;
@@ -567,16 +569,6 @@ int orc_step(orc_ctx* C, int run, int step)
     memcpy(fillp, start, (nc + 1) * sizeof(int64_t));
     for (int64_t s = 0; s < n_all; ++s)
         if (cell[s] >= 0) R->lcr[fillp[cell[s]]++] = s;
-    for (int c = 0; c < nc; ++c)
-        for (int64_t k = start[c] + 1; k < start[c + 1]; ++k) {
-            int64_t sl = R->lcr[k];
-            int64_t m = k;
-            while (m > start[c] && R->p[R->lcr[m - 1]].id > R->p[sl].id) {
-                R->lcr[m] = R->lcr[m - 1];
-                --m;
-            }
-            R->lcr[m] = sl;
-        }
     /* P rewritten in LCR order (leavers dropped) */
     orc_particle* np = malloc((n_new ? n_new : 1) * sizeof(orc_particle));
     if (!np) { free(cell); free(start); free(fillp); return -2; }

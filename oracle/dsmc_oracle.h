@@ -24,7 +24,7 @@
  *   generation            pinned (mean counts vs flux; effusion)
  *   motion                pinned (free flight, reflection brute force,
  *                          diffuse wall equilibrium, effusion orifice)
- *   enumeration/indexing  pinned (vs a plain sort by (cell, id))
+ *   enumeration/indexing  pinned (vs a stable sort of the slots by cell)
  *   interaction           pinned (per-collision conservation, equilibrium
  *                          HS and VHS rates, Maxwell-molecule relaxation)
  *   sampling              pinned (brute-force sums)
@@ -104,7 +104,7 @@ int orc_set_state(orc_ctx* c, int run, int64_t n, const double* x,
                   const double* v, const uint32_t* id, uint32_t next_id);
 /* last step's Enumeration/Indexing and Interaction outputs, per cell:
  * count, candidate pairs M, accepted collisions; lcr[k] = pre-sort slot of
- * the k-th particle in (cell, id) order, slots numbered old-then-new */
+ * the k-th particle in (cell, slot) order, slots numbered old-then-new */
 int orc_get_cells(const orc_ctx* c, int run, int32_t* count, int32_t* cand,
                   int32_t* accepted, int64_t* lcr);
 int orc_get_cell_state(const orc_ctx* c, int run, double* rem, double* smax);

@@ -71,7 +71,7 @@ struct dsmc_ctx {
     uint32_t* ID[2] = {};
     uint32_t* CI[2] = {};            // run-local cell index of each pool particle
     uint32_t *gc = nullptr, *lcr_dbg = nullptr;
-    uint2* lcr = nullptr;
+    uint32_t* lcr = nullptr;
     uint32_t *count = nullptr, *start = nullptr, *block_sums = nullptr;
     uint32_t *run_base = nullptr, *next_id = nullptr, *cand = nullptr, *accd = nullptr;
     uint32_t* big_list = nullptr;
@@ -336,7 +336,7 @@ static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, in
         ctx->CI[b] = (uint32_t*)A(4 * cap_old);
     }
     ctx->gc = (uint32_t*)A(4 * slots);
-    ctx->lcr = (uint2*)A(8 * cap_old);
+    ctx->lcr = (uint32_t*)A(4 * cap_old);
     ctx->lcr_dbg = dbg ? (uint32_t*)A(4 * cap_old) : nullptr;
     ctx->count = (uint32_t*)A(4 * total_cells);
     ctx->start = (uint32_t*)A(4 * (total_cells + 2));
@@ -2034,7 +2034,7 @@ static size_t noalloc_layout(dsmc_ctx* ctx, unsigned char* base, int n_runs, int
         ctx->CI[b] = (uint32_t*)sc.take(4 * cap_old);
     }
     ctx->gc = (uint32_t*)sc.take(4 * slots);
-    ctx->lcr = (uint2*)sc.take(8 * cap_old);
+    ctx->lcr = (uint32_t*)sc.take(4 * cap_old);
     ctx->lcr_dbg = nullptr;
     ctx->count = (uint32_t*)sc.take(4 * total_cells);
     ctx->start = (uint32_t*)sc.take(4 * (total_cells + 2));

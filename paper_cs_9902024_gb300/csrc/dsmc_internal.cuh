@@ -120,7 +120,8 @@ struct StepArgs {
     T* xi[3]; T* vi[3]; uint32_t* idi; uint32_t* ci_i;
     T* xo[3]; T* vo[3]; uint32_t* ido; uint32_t* ci_o;
     uint32_t* gc;          // per slot: run-major cell key, or kDead
-    uint2* lcr;            // per pool position: (slot, id), cell-grouped
+    uint32_t* lcr;         // per pool position: the particle's slot in the step's
+                           // pools (old, then entrants), cell-grouped
     uint32_t* lcr_dbg;     // optional: slot of each sorted particle
     uint32_t* count;       // per cell: particles (Motion counts up, the LCR
                            // scatter counts back down to zero)

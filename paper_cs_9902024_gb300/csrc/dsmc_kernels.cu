@@ -12,14 +12,14 @@
 //   k_scan1/2    exclusive prefix over the run-major cell counts: each
 //                cell's first pool position, each run's first position
 //                (Indexing)
-//   k_scatter    LCR[start[cell] + r] = (slot, id), r counted down from
-//                the cell's count (Indexing)
-//   k_cell       one CTA per 256 cells: each cell's particles put in
-//                particle-id order and gathered into the next pool
-//                (Indexing)
+//   k_scatter    LCR[start[cell] + r] = slot, r counted down from the
+//                cell's count (Indexing)
+//   k_cell       one CTA per 256 cells: each cell's particles put in slot
+//                order (the order of one serial pass over the pool) and
+//                gathered into the next pool (Indexing)
 //   k_cell_big   cells above 128 particles (a CTA, or a quarter CTA, per
-//                cell): the cell ordered by id (LSD radix sort of the ids)
-//                and gathered into the next pool
+//                cell): the cell put in slot order (LSD radix sort of
+//                compact slot keys) and gathered into the next pool
 //   k_collide_big one warp per such cell: NTC collisions (disjoint pairs
 //                side by side) and moments
 //   k_collide    one thread per cell, a tile's velocities staged in shared
@@ -1162,13 +1162,13 @@ __device__ __forceinline__ uint64_t scatter_extent(const StepArgs<T>& a, uint64_
     return pad + (uint64_t)a.cap_new;
 }
 
-// Indexing, part 2: LCR[start[cell] + r] = (slot, id) for every live
-// particle, r taken from the cell's count, which Motion left at the cell's
-// particle count and which this pass counts back down to zero (ready for
-// the next step's Motion): one atomic subtract per run of equal keys in
-// consecutive lanes, the run's lanes taking consecutive places below the
-// returned value.  The order inside a cell is any: the next kernel orders
-// each cell by id (the id rides along so that it needs no gather to do so).
+// Indexing, part 2: LCR[start[cell] + r] = slot for every live particle, r
+// taken from the cell's count, which Motion left at the cell's particle
+// count and which this pass counts back down to zero (ready for the next
+// step's Motion): one atomic subtract per run of equal keys in consecutive
+// lanes, the run's lanes taking consecutive places below the returned
+// value.  The order inside a cell is any: the next kernel puts each cell in
+// slot order (the order one serial pass over the pool would give).
 // Indices v0 .. v0 + 3, v0 = base + 4 lane, for the warp bases base = first
 // + 128 w, advancing by `stride` while below `end`; all four slots' loads
 // and count updates are issued before their results are used.
@@ -1186,12 +1186,12 @@ __device__ __forceinline__ void scatter_span(const StepArgs<T>& a, uint64_t firs
     uint32_t* __restrict__ gc = a.gc;
     uint32_t* __restrict__ count = a.count;
     const uint32_t* __restrict__ start = a.start;
-    uint2* __restrict__ lcr2 = a.lcr;
+    uint32_t* __restrict__ lcr = a.lcr;
     bool overflow = false;
     const uint32_t lane = lane_id();
     // warp-uniform trip count (the count updates are warp operations)
     for (uint64_t base = first; base < end; base += stride) {
-        uint32_t key[4], idv[4], st[4];
+        uint32_t key[4], st[4];
         uint64_t slot[4];
         // index v0 + b -> slot; v0 is a multiple of 4 and so is the padded
         // old-pool size, so the four lie in one region
@@ -1201,14 +1201,11 @@ __device__ __forceinline__ void scatter_span(const StepArgs<T>& a, uint64_t firs
         if (v0 + 4 <= end && s0 + 4 <= lim) {
             const uint4 kv = *reinterpret_cast<const uint4*>(gc + s0);
             key[0] = kv.x; key[1] = kv.y; key[2] = kv.z; key[3] = kv.w;
-            const uint4 iv = *reinterpret_cast<const uint4*>(a.idi + s0);
-            idv[0] = iv.x; idv[1] = iv.y; idv[2] = iv.z; idv[3] = iv.w;
         } else {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const bool in = v0 + b < end && s0 + b < lim;
                 key[b] = in ? gc[s0 + b] : kDead;
-                idv[b] = in ? a.idi[s0 + b] : 0u;
             }
         }
 #pragma unroll
@@ -1231,7 +1228,7 @@ __device__ __forceinline__ void scatter_span(const StepArgs<T>& a, uint64_t firs
             const uint32_t rk = o - 1u - (lane - head[b]);
             const uint64_t pos = (uint64_t)st[b] + rk;
             if (pos >= (uint64_t)a.cap_old || rk >= 0x80000000u) { overflow = true; continue; }
-            lcr2[pos] = make_uint2((uint32_t)slot[b], idv[b]);
+            lcr[pos] = (uint32_t)slot[b];
         }
     }
     if (overflow) atomicOr(&a.ctr->error, DSMC_ERR_POOL);
@@ -1392,7 +1389,7 @@ __device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T*
     collide_pair<T>(c, sv0, sv1, sv2, i, j, u2, u3, [&]() { return ue; }, smax, seen, nacc, nclamp);
 }
 
-// Interaction of one large cell, velocities in id order at sv0..sv2 (shared
+// Interaction of one large cell, velocities in LCR order at sv0..sv2 (shared
 // or global memory); all lanes of the warp call it.  The lanes draw 32
 // candidates at a time; a candidate is applied as soon as no earlier
 // candidate of the batch that shares one of its particles is still pending,
@@ -1441,7 +1438,7 @@ __device__ void collide_cell_warp(const C& c, T* sv0, T* sv1, T* sv2, uint32_t N
     nclamp = __reduce_add_sync(0xFFFFFFFFu, my_clamp);
 }
 
-// Sampling of one cell: N, sum v_a, sum v_a^2 in FP64, summed in id order
+// Sampling of one cell: N, sum v_a, sum v_a^2 in FP64, summed in LCR order
 // (one fixed order for every path and launch shape).
 template <typename T>
 __device__ __forceinline__ void cell_moments(const T* sv0, const T* sv1, const T* sv2, uint32_t N,
@@ -1469,12 +1466,12 @@ __device__ __forceinline__ uint32_t checked_slot(const StepArgs<T>& a, uint32_t 
     return s;
 }
 
-// Particle (idj, j) comes before (idk, k) in a cell: ids are unique within a
-// run, the position only breaks ties in a state already flagged as
+// Entry (sj, j) of a cell's readdressing range comes before (sk, k): slots
+// are unique, the position only breaks ties in a state already flagged as
 // corrupted, so the ranks always form a permutation.
-__device__ __forceinline__ bool id_before(uint32_t idj, uint32_t j, uint32_t idk, uint32_t k)
+__device__ __forceinline__ bool slot_before(uint32_t sj, uint32_t j, uint32_t sk, uint32_t k)
 {
-    return idj < idk || (idj == idk && j < k);
+    return sj < sk || (sj == sk && j < k);
 }
 
 struct CellTally {
@@ -1491,17 +1488,16 @@ __device__ __forceinline__ void push_big(const StepArgs<T>& a, int64_t gcell)
     else atomicOr(&a.ctr->error, DSMC_ERR_BIGLIST);
 }
 
-// Warp path for one cell of up to kWarpMax particles: id ranks by counting,
-// then the particles gathered into the next pool in id order.  Used for
-// tiles whose start table is inconsistent (a corrupt state): it checks
-// every cell.  `ws` is this warp's scratch: kWarpMax x (2 u32 + u16).
+// Warp path for one cell of up to kWarpMax particles: slot ranks by
+// counting, then the particles gathered into the next pool in slot order.
+// Used for tiles whose start table is inconsistent (a corrupt state): it
+// checks every cell.  `ws` is this warp's scratch: kWarpMax x (u32 + u16).
 template <typename T, int DIM>
 __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell, unsigned char* ws)
 {
     const uint32_t lane = lane_id();
     uint32_t* sl = reinterpret_cast<uint32_t*>(ws);
-    uint32_t* sid = sl + kWarpMax;
-    uint16_t* sp = reinterpret_cast<uint16_t*>(sid + kWarpMax);
+    uint16_t* sp = reinterpret_cast<uint16_t*>(sl + kWarpMax);
     const uint32_t beg = a.start[gcell];
     const uint32_t N = a.start[gcell + 1] - beg;
     if ((uint64_t)beg + N > (uint64_t)a.cap_old) {
@@ -1512,16 +1508,12 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
         if (lane == 0) push_big(a, gcell);
         return;
     }
-    for (uint32_t k = lane; k < N; k += 32) {
-        const uint2 e = a.lcr[beg + k];
-        sl[k] = checked_slot(a, e.x);
-        sid[k] = e.y;
-    }
+    for (uint32_t k = lane; k < N; k += 32) sl[k] = checked_slot(a, a.lcr[beg + k]);
     __syncwarp();
     for (uint32_t k = lane; k < N; k += 32) {
-        const uint32_t my = sid[k];
+        const uint32_t my = sl[k];
         uint32_t r = 0;
-        for (uint32_t j = 0; j < N; ++j) r += id_before(sid[j], j, my, k) ? 1u : 0u;
+        for (uint32_t j = 0; j < N; ++j) r += slot_before(sl[j], j, my, k) ? 1u : 0u;
         sp[r] = (uint16_t)k;
     }
     __syncwarp();
@@ -1532,7 +1524,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
         a.ci_o[o] = (uint32_t)gcell;
-        a.ido[o] = sid[k];
+        a.ido[o] = a.idi[s];
         a.vo[0][o] = a.vi[0][s];
         a.vo[1][o] = a.vi[1][s];
         a.vo[2][o] = a.vi[2][s];
@@ -1544,7 +1536,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
 template <typename T>
 __host__ __device__ constexpr size_t warp_scratch_bytes()
 {
-    return (size_t)kWarpMax * (2 * sizeof(uint32_t) + sizeof(uint16_t));
+    return (size_t)kWarpMax * (sizeof(uint32_t) + sizeof(uint16_t));
 }
 
 constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather (measured: 2 and 4 slower)
@@ -1552,18 +1544,18 @@ constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather
 // Indexing, part 3 (sort and gather).  One CTA takes kTileCells consecutive
 // (run-major) cells, whose particles occupy one contiguous range of the next
 // pool and of the LCR.  (1) Thread 0 starts a bulk copy (TMA) of the tile's
-// LCR entries (slot, id) into shared memory while each thread tags its
+// LCR entries (old slots) into shared memory while each thread tags its
 // cell's positions.  (2) Thread per position, kGatherBatch positions per
-// pass: the particle's rank inside its cell by counting smaller ids, and its
-// offsets, velocity and id gathered from the old pool into the next pool at
-// cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
+// pass: the particle's rank inside its cell by counting smaller slots, and
+// its offsets, velocity and id gathered from the old pool into the next
+// pool at cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
 // kernel; a tile whose particles exceed the budget is taken in consecutive
 // cell ranges that fit it.
 // shared memory of the sort/gather tile kernel: the tile's start table, its
-// LCR entries (two spare for the 16-byte aligned superset) and cell tags
+// LCR entries (eight spare for the 16-byte aligned superset) and cell tags
 struct CellSmem {
     uint32_t* s_start;
-    uint2* s_lcr;
+    uint32_t* s_lcr;
     uint16_t* s_cellof;
     unsigned char* raw;
     uint64_t* bar;
@@ -1575,8 +1567,8 @@ __device__ __forceinline__ CellSmem cell_smem(unsigned char* raw, uint64_t* bar,
     m.raw = raw;
     m.bar = bar;
     m.s_start = reinterpret_cast<uint32_t*>(raw);
-    m.s_lcr = reinterpret_cast<uint2*>(raw + (kTileCells + 4) * sizeof(uint32_t));
-    m.s_cellof = reinterpret_cast<uint16_t*>(m.s_lcr + budget + 2);
+    m.s_lcr = reinterpret_cast<uint32_t*>(raw + (kTileCells + 4) * sizeof(uint32_t));
+    m.s_cellof = reinterpret_cast<uint16_t*>(m.s_lcr + budget + 8);
     return m;
 }
 
@@ -1589,7 +1581,7 @@ __device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, co
     const Cfg& c = *a.cfg;
     const uint32_t budget = (uint32_t)a.tile_budget;
     uint32_t* s_start = sm.s_start;
-    uint2* s_lcr = sm.s_lcr;
+    uint32_t* s_lcr = sm.s_lcr;
     uint16_t* s_cellof = sm.s_cellof;
     unsigned char* smem_raw = sm.raw;
     uint64_t& s_bar = *sm.bar;
@@ -1634,12 +1626,12 @@ __device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, co
             break;
         }
         // [lo, hi): the 16-byte aligned superset of [Bq, Eq); the LCR
-        // holds cap_old entries, an even number, so hi stays inside it
-        const uint32_t lo = Bq & ~1u;
+        // holds cap_old entries, a multiple of 4, so hi stays inside it
+        const uint32_t lo = Bq & ~3u;
         const uint32_t sh = Bq - lo;
         if (tid == 0 && Tn > 0) {
-            const uint32_t hi = (Eq + 1u) & ~1u;
-            const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint2);
+            const uint32_t hi = (Eq + 3u) & ~3u;
+            const uint32_t bytes = (hi - lo) * (uint32_t)sizeof(uint32_t);
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&s_bar, bytes);
             bulk_g2s(s_lcr, a.lcr + lo, bytes, &s_bar);
@@ -1659,17 +1651,17 @@ __device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, co
             phase ^= 1u;
         }
         __syncthreads();
-        const uint2* tl = s_lcr + sh;
+        const uint32_t* tl = s_lcr + sh;
         for (uint32_t k0 = tid; k0 < Tn; k0 += kGatherBatch * kTileCells) {
             // kGatherBatch particles per pass, every load issued before any store
-            uint32_t kk[kGatherBatch], sl[kGatherBatch];
+            uint32_t kk[kGatherBatch], sl[kGatherBatch], pid[kGatherBatch];
             int lo2[kGatherBatch];
             T px[kGatherBatch][3], pv[kGatherBatch][3];
 #pragma unroll
             for (int b = 0; b < kGatherBatch; ++b) {
                 kk[b] = k0 + (uint32_t)b * kTileCells;
                 lo2[b] = kk[b] < Tn ? (int)s_cellof[kk[b]] : 0xFFFF;
-                sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]].x) : 0u;
+                sl[b] = lo2[b] != 0xFFFF ? checked_slot(a, tl[kk[b]]) : 0u;
             }
 #pragma unroll
             for (int b = 0; b < kGatherBatch; ++b) {
@@ -1679,22 +1671,23 @@ __device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, co
                 pv[b][0] = a.vi[0][sl[b]];
                 pv[b][1] = a.vi[1][sl[b]];
                 pv[b][2] = a.vi[2][sl[b]];
+                pid[b] = a.idi[sl[b]];
             }
 #pragma unroll
             for (int b = 0; b < kGatherBatch; ++b) {
                 if (lo2[b] == 0xFFFF) continue;
                 const uint32_t cb = s_start[lo2[b]] - Bq, ce = s_start[lo2[b] + 1] - Bq;
-                const uint32_t my = tl[kk[b]].y;
-                // ids are unique within a run; a duplicate (possible only in a
-                // state already flagged corrupt) leaves a hole, never an access
+                const uint32_t my = tl[kk[b]];
+                // slots are unique; a repeated one (possible only in a state
+                // already flagged corrupt) leaves a hole, never an access
                 // outside the cell's range
                 uint32_t r = 0;
-                for (uint32_t j = cb; j < ce; ++j) r += tl[j].y < my ? 1u : 0u;
+                for (uint32_t j = cb; j < ce; ++j) r += tl[j] < my ? 1u : 0u;
                 const uint32_t o = Bq + cb + r;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
                 a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
-                a.ido[o] = my;
+                a.ido[o] = pid[b];
                 a.vo[0][o] = pv[b][0];
                 a.vo[1][o] = pv[b][1];
                 a.vo[2][o] = pv[b][2];
@@ -1722,7 +1715,7 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 
 // Interaction and Sampling: cells of at most kWarpMax particles (larger
 // cells are done whole by the big-cell kernels), on the cells' velocities
-// in the next pool, now in id order.  A CTA takes kCollideCells consecutive
+// in the next pool, now in LCR order.  A CTA takes kCollideCells consecutive
 // cells.  (1) Thread 0 starts bulk copies (TMA) of the tile's velocities,
 // up to collide_stage particles, into shared memory; meanwhile every thread
 // forms its cell's NTC candidate count (coalesced remainder and (sigma
@@ -2028,11 +2021,11 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>()) k_co
 }
 
 // ---------------------------------------------------------------------------
-// Cells above kWarpMax particles, part 1: each cell's particles put in id
+// Cells above kWarpMax particles, part 1: each cell's particles put in slot
 // order and gathered into the next pool.  The order comes from an LSD radix
-// sort of the ids relative to the cell's smallest id, 8 bits a pass (as many
-// passes as the ids' span needs, at most 4), on 16-bit positions into the
-// cell's keys staged in shared memory.  Each pass is a stable counting sort:
+// sort of compact slot keys (order_cell), 8 bits a pass (as many passes as
+// the keys' span needs, at most 4), on 16-bit positions into the cell's
+// keys staged in shared memory.  Each pass is a stable counting sort:
 // warp w ranks the chunks of its contiguous range in order (match_any
 // groups equal digits; the group's first lane advances the warp's count of
 // that digit), an exclusive scan of the counts in (digit, warp) order gives
@@ -2077,23 +2070,26 @@ __device__ __forceinline__ void order_sync(uint32_t bar)
 }
 
 template <typename T, int DIM>
-__device__ __forceinline__ void big_put(const StepArgs<T>& a, uint32_t o, uint32_t s, uint32_t id,
-                                        uint32_t gcell)
+__device__ __forceinline__ void big_put(const StepArgs<T>& a, uint32_t o, uint32_t s, uint32_t gcell)
 {
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
     a.ci_o[o] = gcell;
-    a.ido[o] = id;
+    a.ido[o] = a.idi[s];
     a.vo[0][o] = a.vi[0][s];
     a.vo[1][o] = a.vi[1][s];
     a.vo[2][o] = a.vi[2][s];
     if (a.lcr_dbg) a.lcr_dbg[o] = s;
 }
 
-// One cell of N particles (KMAX / 8 < N <= KMAX) ordered by id and gathered
-// by THREADS threads (t = 0 .. THREADS - 1, barrier `bar`) on `sm`
-// (order_smem bytes, 16-byte aligned) and `red` (2 x THREADS / 32 words).
-// Every thread of the group calls it with the same cell.
+// One cell of N particles (KMAX / 8 < N <= KMAX) put in slot order and
+// gathered by THREADS threads (t = 0 .. THREADS - 1, barrier `bar`) on `sm`
+// (order_smem bytes, 16-byte aligned) and `red` (4 x THREADS / 32 words).
+// Every thread of the group calls it with the same cell.  The radix sort
+// runs on a compact key of the slot: the old pool's slots relative to their
+// smallest, then the entrants' slots (one run's, in their own region)
+// relative to theirs, after the old ones -- the same order as the slots,
+// with a span of about the cell's source range rather than the pool's.
 template <int THREADS, int KMAX, typename T, int DIM>
 __device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell, uint32_t beg,
                                            uint32_t N, unsigned char* sm, uint32_t* red, uint32_t t,
@@ -2103,28 +2099,40 @@ __device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell,
     static_assert(KMAX <= 8 * THREADS, "at most 8 chunks of 32 per warp (8-bit ranks)");
     static_assert(kRadixBins * W * sizeof(uint16_t) == THREADS * 16,
                   "one 16-byte word of counts per thread");
-    uint32_t* s_id = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* s_slot = s_id + KMAX;
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(sm);
+    uint32_t* s_slot = s_key + KMAX;
     uint16_t* pa = reinterpret_cast<uint16_t*>(s_slot + KMAX);
     uint16_t* pb = pa + KMAX;
     uint16_t* cnt = pb + KMAX;   // [digit][warp]
     const uint32_t lane = t & 31u, w = t >> 5;
-    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    const uint32_t cap = (uint32_t)a.cap_old;
+    // smallest and largest slot among the old pool's and among the entrants'
+    uint32_t lo_o = 0xFFFFFFFFu, hi_o = 0u, lo_n = 0xFFFFFFFFu, hi_n = 0u;
     for (uint32_t k = t; k < N; k += THREADS) {
-        const uint2 e = a.lcr[beg + k];
-        s_id[k] = e.y;
-        s_slot[k] = checked_slot(a, e.x);
+        const uint32_t sl = checked_slot(a, a.lcr[beg + k]);
+        s_slot[k] = sl;
         pa[k] = (uint16_t)k;
-        lo = min(lo, e.y);
-        hi = max(hi, e.y);
+        if (sl < cap) { lo_o = min(lo_o, sl); hi_o = max(hi_o, sl); }
+        else { lo_n = min(lo_n, sl); hi_n = max(hi_n, sl); }
     }
-    lo = __reduce_min_sync(0xFFFFFFFFu, lo);
-    hi = __reduce_max_sync(0xFFFFFFFFu, hi);
-    if (lane == 0) { red[w] = lo; red[W + w] = hi; }
+    lo_o = __reduce_min_sync(0xFFFFFFFFu, lo_o);
+    hi_o = __reduce_max_sync(0xFFFFFFFFu, hi_o);
+    lo_n = __reduce_min_sync(0xFFFFFFFFu, lo_n);
+    hi_n = __reduce_max_sync(0xFFFFFFFFu, hi_n);
+    if (lane == 0) { red[w] = lo_o; red[W + w] = hi_o; red[2 * W + w] = lo_n; red[3 * W + w] = hi_n; }
     order_sync<THREADS>(bar);
-    lo = __reduce_min_sync(0xFFFFFFFFu, lane < W ? red[lane] : 0xFFFFFFFFu);
-    hi = __reduce_max_sync(0xFFFFFFFFu, lane < W ? red[W + lane] : 0u);
-    const uint32_t span = hi - lo;
+    lo_o = __reduce_min_sync(0xFFFFFFFFu, lane < W ? red[lane] : 0xFFFFFFFFu);
+    hi_o = __reduce_max_sync(0xFFFFFFFFu, lane < W ? red[W + lane] : 0u);
+    lo_n = __reduce_min_sync(0xFFFFFFFFu, lane < W ? red[2 * W + lane] : 0xFFFFFFFFu);
+    hi_n = __reduce_max_sync(0xFFFFFFFFu, lane < W ? red[3 * W + lane] : 0u);
+    const bool any_old = lo_o <= hi_o, any_new = lo_n <= hi_n;
+    const uint32_t base_n = any_old ? hi_o - lo_o + 1u : 0u;
+    // each thread keys the positions it loaded
+    for (uint32_t k = t; k < N; k += THREADS) {
+        const uint32_t sl = s_slot[k];
+        s_key[k] = sl < cap ? sl - lo_o : base_n + (sl - lo_n);
+    }
+    const uint32_t span = any_new ? base_n + (hi_n - lo_n) : (any_old ? hi_o - lo_o : 0u);
     const int passes = span == 0u ? 0 : (32 - __clz(span) + kRadixBits - 1) / kRadixBits;
     // warp w owns positions [w * C * 32, (w + 1) * C * 32), C <= 8
     const uint32_t C = (N + THREADS - 1) / THREADS;
@@ -2142,7 +2150,7 @@ __device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell,
             if (c < C) {
                 const uint32_t e = wbase + c * 32u + lane;
                 const bool ok = e < N;
-                const uint32_t d = ok ? ((s_id[pa[e]] - lo) >> sh) & (kRadixBins - 1u)
+                const uint32_t d = ok ? (s_key[pa[e]] >> sh) & (kRadixBins - 1u)
                                       : (uint32_t)kRadixBins;
                 const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
                 const uint32_t before = ok ? (uint32_t)cnt[d * W + w] : 0u;
@@ -2202,7 +2210,7 @@ __device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell,
                 const uint32_t e = wbase + c * 32u + lane;
                 if (e < N) {
                     const uint32_t pe = pa[e];
-                    const uint32_t d = ((s_id[pe] - lo) >> sh) & (kRadixBins - 1u);
+                    const uint32_t d = (s_key[pe] >> sh) & (kRadixBins - 1u);
                     const uint32_t r = (c < 4u ? rk0 >> (8u * c) : rk1 >> (8u * (c - 4u))) & 0xFFu;
                     pb[cnt[d * W + w] + r] = (uint16_t)pe;
                 }
@@ -2215,7 +2223,7 @@ __device__ __forceinline__ void order_cell(const StepArgs<T>& a, uint32_t gcell,
     order_sync<THREADS>(bar);
     for (uint32_t r = t; r < N; r += THREADS) {
         const uint32_t pe = pa[r];
-        big_put<T, DIM>(a, beg + r, s_slot[pe], s_id[pe], gcell);
+        big_put<T, DIM>(a, beg + r, s_slot[pe], gcell);
     }
     order_sync<THREADS>(bar);   // buffers free for the group's next cell
 }
@@ -2246,8 +2254,7 @@ __device__ __forceinline__ void cell_big_part(const StepArgs<T>& a, uint32_t blk
             // step reads no unwritten slot
             if (tid == 0) atomicOr(&a.ctr->error, DSMC_ERR_BIGCELL);
             for (uint32_t r = tid; r < N; r += blockDim.x) {
-                const uint2 e = a.lcr[beg + r];
-                big_put<T, DIM>(a, beg + r, checked_slot(a, e.x), e.y, gcell);
+                big_put<T, DIM>(a, beg + r, checked_slot(a, a.lcr[beg + r]), gcell);
             }
             continue;
         }
@@ -2258,7 +2265,7 @@ __device__ __forceinline__ void cell_big_part(const StepArgs<T>& a, uint32_t blk
     // kMidThreads per cell, kMidGroups groups side by side
     const uint32_t g = tid / kMidThreads, tg = tid % kMidThreads;
     unsigned char* sm = smem_raw + (size_t)g * order_smem<kMidThreads, kBigThreads>();
-    uint32_t* red = s_red + g * 2 * (kMidThreads / 32);
+    uint32_t* red = s_red + g * 4 * (kMidThreads / 32);
     for (uint32_t bi = blk * kMidGroups + g; bi < nb; bi += nblk * kMidGroups) {
         const uint32_t gcell = a.big_list[bi];
         const uint32_t beg = a.start[gcell];
@@ -2278,12 +2285,12 @@ __global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t s_red[2 * (kBigThreads / 32)];
+    __shared__ uint32_t s_red[4 * (kBigThreads / 32)];
     cell_big_part<T, DIM>(a, blockIdx.x, gridDim.x, smem_raw, s_red);
 }
 
 // Cells above kWarpMax particles, part 2: one warp per cell, on the cell's
-// velocities in the next pool (id order): NTC count, candidates applied by
+// velocities in the next pool (LCR order): NTC count, candidates applied by
 // collide_cell_warp (disjoint pairs side by side, in-order result), and the
 // cell's moments at sample steps.  Many large cells proceed at once.
 // the big cells of one problem, warp `wid` of `warps`
@@ -2399,9 +2406,9 @@ __global__ void k_step_end(StepArgs<T> a)
 // Consistency check of the pool after a run (options.checks): every pool
 // position p holds a particle whose stored cell key lies inside the table,
 // whose cell's range [start[key], start[key + 1]) contains p, whose id is
-// larger than its predecessor's in the same cell (the (cell, id) order of
-// the readdressing array), whose offsets lie inside its cell and whose
-// velocity is finite.  Counts the positions that fail and keeps the first.
+// below its run's next id (ids are handed out in order), whose offsets lie
+// inside its cell and whose velocity is finite.  Counts the positions that
+// fail and keeps the first.
 template <typename T, int DIM>
 __global__ void k_check(StepArgs<T> a)
 {
@@ -2414,7 +2421,7 @@ __global__ void k_check(StepArgs<T> a)
         if (ok) {
             const uint32_t cs = a.start[key], ce = a.start[key + 1];
             ok = cs <= p && p < ce;
-            if (ok && p > cs) ok = a.idi[p - 1] < a.idi[p];
+            if (ok) ok = a.idi[p] < a.next_id[run_of_key(a.hot, key)];
         }
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) {
@@ -2727,7 +2734,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kBigThreads, 2) mk_cell_big(MultiArgs<T> m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t s_red[2 * (kBigThreads / 32)];
+    __shared__ uint32_t s_red[4 * (kBigThreads / 32)];
     __shared__ StepArgs<T> sa;
     for (int p = 0; p < m.n_parts; ++p) {
         load_part(sa, m.parts, p);
@@ -2882,9 +2889,9 @@ void launch_scatter(const void* args, const LaunchShape& ls, cudaStream_t s)
 
 size_t cell_smem_bytes(int prec, int budget)
 {
-    // start table, LCR entries (two spare for 16-byte alignment), cell tags
+    // start table, LCR entries (eight spare for 16-byte alignment), cell tags
     const size_t head = (kTileCells + 4) * sizeof(uint32_t);
-    const size_t tile = ((size_t)budget + 2) * sizeof(uint2) + (size_t)budget * sizeof(uint16_t);
+    const size_t tile = ((size_t)budget + 8) * sizeof(uint32_t) + (size_t)budget * sizeof(uint16_t);
     const size_t warps = (kTileCells / 32) * (prec == DSMC_FP64 ? warp_scratch_bytes<double>()
                                                                 : warp_scratch_bytes<float>());
     return head + (tile > warps ? tile : warps);

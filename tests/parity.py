@@ -24,7 +24,7 @@ KB = 1.380649e-23
 
 
 def cells_of_order(count):
-    """Cell of each particle of a state in (cell, id) order, from the
+    """Cell of each particle of a state in LCR order, from the
     per-cell counts of the same step."""
     return np.repeat(np.arange(len(count)), count)
 

@@ -233,10 +233,10 @@ def test_checks_pass_on_normal_runs(D):
 
 
 def test_checks_catch_a_corrupted_pool(D):
-    """A state whose ids repeat inside a cell (impossible in a run, set here
-    through the test hook) leaves the readdressing array inconsistent after
-    a step; the check reports it as DSMC_E_STATE with the failing
-    positions, and nothing faults."""
+    """A state holding ids at or above the run's next id (impossible in a
+    run, where ids are handed out in order; set here through the test hook)
+    fails the pool check after a step: it reports DSMC_E_STATE with the
+    failing positions, and nothing faults."""
     from tests.helpers import box
     w = box(dim=2, ncell=(4, 4, 1), ppc=20, dt=1e-7, runs=1, steps=1, fill=0)
     rng = np.random.default_rng(3)
@@ -247,7 +247,7 @@ def test_checks_catch_a_corrupted_pool(D):
     x[:, 1] = (2 + rng.uniform(0.1, 0.9, n)) * d
     v = rng.normal(0.0, 1.0, (n, 3))
     ids = np.arange(n, dtype=np.uint32)
-    ids[10:20] = 5                       # ten particles share one id
+    ids[10:20] = n + 100                 # ten ids beyond the next id
     ens = D.Ensemble(w, precision="fp64", debug=True, checks=True, capacity_per_run=1024)
     ens.debug_begin(runs=1)
     ens.set_state(0, x, v, ids, n)

@@ -109,61 +109,66 @@ def test_fp64_jet_big_cells_and_pulse(D):
     assert ens.stats()["collisions"] > 0
 
 
-def test_fp64_big_cells_wide_id_spans(D):
+def test_fp64_big_cells_wide_slot_spans(D):
     """Cells of 129 to 8000 particles (the radix-sorted paths: a quarter CTA
-    per cell up to 1024 particles, a whole CTA above) whose ids span 2, 3
-    and 4 radix digits -- up to the whole u32 range -- placed in shuffled
-    pool order on both sides: after one step every cell's particles are in
-    id order (LCR), and counts, NTC counts and the state agree exactly with
-    the oracle."""
+    per cell up to 1024 particles, a whole CTA above) whose particles' pool
+    slots span one, two and three radix digits: some cells sit in one block
+    of the pool, the others are spread over a pool of ~70k particles.  After
+    one step every cell's particles are in pre-step slot order (LCR), and
+    counts, NTC counts and the state agree exactly with the oracle.  (A
+    fourth digit needs a pool above 2^24 particles; the pass loop is the
+    same.)"""
     from tests.helpers import box
     w = box(dim=2, ncell=(6, 4, 1), ppc=50, dt=1e-7, runs=1, steps=1, fill=0)
     rng = np.random.default_rng(11)
-    # (cell x, cell y, particles, lowest id, id range)
-    cells = [(5, 0, 600, 100, 600), (1, 1, 1500, 1_000_000, 4000),
-             (3, 1, 3000, 20_000_000, 5_000_000), (1, 2, 5000, 0, (1 << 32) - 1),
-             (4, 2, 8000, 0, (1 << 32) - 1), (2, 3, 129, 0, (1 << 32) - 1),
-             (5, 3, 1024, 5_000_000, 70_000), (0, 0, 1025, 3_000_000_000, 1_000_000)]
+    # (cell x, cell y, particles, in one block of the pool?)
+    cells = [(5, 0, 600, True), (1, 1, 1500, False), (3, 1, 3000, False), (1, 2, 5000, True),
+             (4, 2, 8000, False), (2, 3, 129, True), (5, 3, 1024, False), (0, 0, 1025, True),
+             (0, 1, 8000, False), (2, 0, 8000, False), (3, 0, 8000, False), (4, 0, 8000, False),
+             (0, 2, 8000, False), (2, 2, 8000, False)]
     dx = [w["L"][a] / w["ncell"][a] for a in range(2)]
-    xs, ids, used = [], [], set()
-    for cx, cy, n, lo, span in cells:
-        got = []
-        while len(got) < n:
-            for i in rng.integers(lo, lo + span, 2 * n, dtype=np.uint64).tolist():
-                if i not in used and len(got) < n:
-                    used.add(i)
-                    got.append(i)
-        ids.append(np.array(got, dtype=np.uint32))
+    blocks, spread = [], []
+    for cx, cy, n, block in cells:
         x = np.zeros((n, 3))
         x[:, 0] = (cx + rng.uniform(0.05, 0.95, n)) * dx[0]
         x[:, 1] = (cy + rng.uniform(0.05, 0.95, n)) * dx[1]
-        xs.append(x)
-    x = np.concatenate(xs)
-    ids = np.concatenate(ids)
-    v = rng.normal(0.0, 250.0, (len(ids), 3))
-    order = rng.permutation(len(ids))
-    x, v, ids = x[order], v[order], ids[order]
-    nid = int(ids.max()) + 1
-    ens = D.Ensemble(w, precision="fp64", debug=True, capacity_per_run=32768)
+        (blocks if block else spread).append(x)
+    sp = np.concatenate(spread)
+    sp = sp[rng.permutation(len(sp))]
+    cuts = np.sort(rng.choice(len(sp), len(blocks), replace=False))
+    parts, prev = [], 0
+    for c, blk in zip(cuts, blocks):
+        parts += [sp[prev:c], blk]
+        prev = c
+    parts.append(sp[prev:])
+    x = np.concatenate(parts)
+    n = len(x)
+    assert n > 65536
+    ids = rng.permutation(n).astype(np.uint32)
+    v = rng.normal(0.0, 250.0, (n, 3))
+    ens = D.Ensemble(w, precision="fp64", debug=True, capacity_per_run=131072)
     ens.debug_begin(runs=1)
     orc = Oracle(w, runs=1)
     orc.init_run(0)
-    orc.set_state(0, x, v, ids, nid)
-    ens.set_state(0, x, v, ids, nid)
+    orc.set_state(0, x, v, ids, n)
+    ens.set_state(0, x, v, ids, n)
     ens.debug_step(1)
     orc.step(0, 1)
     res = compare_run(ens, orc, 0, w, 0, 0)
     _assert_exact([[res]])
-    cnt = ens.get_cells(0)[0]
-    assert sorted(cnt[cnt > 128].tolist()) == [129, 600, 1024, 1025, 1500, 3000, 5000, 8000]
-    _, _, ids_after = ens.get_state(0)
+    cnt, _, _, lcr = ens.get_cells(0)
+    assert sorted(cnt[cnt > 128].tolist()) == sorted(c[2] for c in cells)
     st = ens.stats()
     assert st["collisions"] > 0 and st["error_word"] == 0
-    # within each cell the ids ascend (the pool is in LCR order)
+    # within each cell the pre-step slots ascend; the big cells' slot spans
+    # need one, two and three 8-bit digits
     starts = np.concatenate([[0], np.cumsum(cnt)])
+    digits = set()
     for c in np.nonzero(cnt > 128)[0]:
-        seg = ids_after[starts[c]:starts[c + 1]].astype(np.int64)
+        seg = lcr[starts[c]:starts[c + 1]]
         assert np.all(np.diff(seg) > 0)
+        digits.add((int(seg.max() - seg.min()).bit_length() + 7) // 8)
+    assert digits == {1, 2, 3}, digits
 
 
 def test_fp64_tiles_above_the_budget(D):
@@ -270,16 +275,17 @@ def test_fp32_one_step_from_identical_state(D):
 
 def test_fp32_short_horizon(D):
     """FP32 device state from t = 0, 8 runs: each run's short horizon is its
-    first step with a float-driven difference -- a particle in another
-    cell, or an NTC candidate / accepted count that differs (binary32
-    (sigma c_r)_max and acceptance ratios).  Every step before a run's
-    horizon matches the oracle exactly in its integer outputs (ids, cell
-    counts, LCR, NTC counts), and every particle's own relative error is
-    <= 1e-5: its position relative to its position vector (floored at one
-    cell) and its velocity relative to its own speed (floored at 0.1 c_mp).
-    The position error in cell sizes, which grows with the steps as the
-    velocity's rounding is integrated, is reported beside it.  The horizon
-    is reported per run and must reach at least 10 steps in every run."""
+    first step at which binary32 arithmetic shows -- a particle in another
+    cell, an NTC candidate / accepted count that differs (binary32
+    (sigma c_r)_max and acceptance ratios), or a particle whose own relative
+    error exceeds 1e-5: its position relative to its position vector
+    (floored at one cell) or its velocity relative to its own speed
+    (floored at 0.1 c_mp).  Every step before a run's horizon matches the
+    oracle exactly in its integer outputs (ids, cell counts, LCR, NTC
+    counts) with every particle within 1e-5.  The position error in cell
+    sizes, which grows with the steps as the velocity's rounding is
+    integrated, is reported beside it.  The horizon is reported per run and
+    must reach at least 10 steps in every run."""
     runs = 8
     w = W.duct64x32_n8(runs=runs)
     ens = D.Ensemble(w, precision="fp32", debug=True)
@@ -308,7 +314,9 @@ def test_fp32_short_horizon(D):
                 horizon[r], kind[r] = s, "collision count"
                 continue
             assert x["ids_equal"] and x["count_equal"] and x["lcr_equal"], (r, s)
-            assert x["err_x"] <= 1e-5 and x["err_v"] <= 1e-5, (r, s, x["err_x"], x["err_v"])
+            if x["err_x"] > 1e-5 or x["err_v"] > 1e-5:
+                horizon[r], kind[r] = s, "error %.2e / %.2e" % (x["err_x"], x["err_v"])
+                continue
             worst_x[r] = max(worst_x[r], x["err_x"])
             worst_c[r] = max(worst_c[r], x["err_x_cell"])
             worst_v[r] = max(worst_v[r], x["err_v"])

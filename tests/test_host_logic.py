@@ -51,12 +51,13 @@ def test_algorithmic_bytes_split_between_tile_and_big_cell_kernels():
     assert method["scatter"] + method["cell"] + method["cell_big"] == 1200 * 60
     assert method["collide"] + method["collide_big"] == 1200 * 16
     # this build's layout bytes
-    gather = 8 + 2 * (2 * 4 + 3 * 4) + 8
+    # LCR slot 4; gather offsets 8, v 12, id 4; write offsets 8, key 4, id 4, v 12
+    gather = 4 + (2 * 4 + 3 * 4 + 4) + (2 * 4 + 3 * 4 + 8)
     cells = 8 * 64 * 32
     assert layout["cell"] == (1200 - 300) * gather + cells * 10 * 4
     assert layout["cell_big"] == 300 * gather
     assert layout["move"] == 900 * (3 * 2 * 4 + 8)
-    assert layout["scatter"] == 1200 * 16
+    assert layout["scatter"] == 1200 * 8      # read the key, write the slot
     st0 = dict(st, big_pool_steps=0)
     m0, l0 = bench.algorithmic_bytes(w, st0, steps=10, runs=8)
     assert l0["cell"] + l0["cell_big"] == layout["cell"] + layout["cell_big"]

@@ -13,10 +13,13 @@ KB = 1.380649e-23
 M = W.M_AR
 
 
-def test_lcr_is_sort_by_cell_then_id():
-    """After a step P is ordered by (cell, id): the readdressing array equals
-    a plain sort of the survivors, counts equal a bincount, and LCR is a
-    permutation of the surviving pre-step slots."""
+def test_lcr_is_stable_sort_by_cell():
+    """After a step P is ordered by cell, and inside each cell by pre-step
+    slot (the order one serial pass over P fills the readdressing array in):
+    the readdressing array equals a stable sort of the survivors' slots by
+    cell, counts equal a bincount, and LCR is a permutation of the surviving
+    pre-step slots (old particles in their pre-step order, then the entrants
+    in generation order)."""
     w = W.duct64x32_n8(runs=1, steps=40)
     o = Oracle(w, runs=1)
     o.init_run(0)
@@ -26,11 +29,15 @@ def test_lcr_is_sort_by_cell_then_id():
         o.step(0, s)
     x, v, ids = o.get_state(0)
     cells = cell_index(w, x)
-    order = np.lexsort((ids, cells))
-    assert np.array_equal(order, np.arange(len(ids)))
     count, cand, acc, lcr = o.get_cells(0)
     assert np.array_equal(count, np.bincount(cells, minlength=len(count)))
     assert len(np.unique(lcr)) == len(lcr)
+    # a stable sort of the surviving slots by their cell reproduces LCR
+    order = np.lexsort((lcr, cells))
+    assert np.array_equal(order, np.arange(len(ids)))
+    assert np.all(np.diff(cells) >= 0)
+    same = np.diff(cells) == 0
+    assert np.all(np.diff(lcr)[same] > 0)
     # old particles keep their slot (their position in the pre-step order);
     # new ones have slots >= n_old in generation (= id) order
     old = lcr < n_old
