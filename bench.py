@@ -238,9 +238,9 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     pool = st["pool_steps"]
     big = st.get("big_pool_steps", 0)
     mb = _method_bytes(D)
-    # read the LCR entry (4), gather offsets, v and id; write offsets, cell
-    # key, id, v
-    gather = 4 + (D * t + 3 * t + 4) + (D * t + 3 * t + 8)
+    # read the LCR entry (4), gather offsets and v; write offsets, cell key,
+    # v (ids are carried in debug mode only)
+    gather = 4 + (D * t + 3 * t) + (D * t + 3 * t + 4)
     method = {
         "move": moved_old * mb["motion"],
         "scatter": pool * mb["scatter"],
@@ -268,8 +268,8 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
         "collide_big": big * 3 * t,
         # read counts, write starts
         "scan": cells * steps * 8,
-        # write the entrants (x, v, id, key)
-        "generate": st["generated"] * (D * t + 3 * t + 8),
+        # write the entrants (x, v, key)
+        "generate": st["generated"] * (D * t + 3 * t + 4),
     }
     return method, layout
 

@@ -407,8 +407,11 @@ static int generation(orc_ctx* C, orc_run* R, int run, int step)
 
 /* Motion: free flight for f*dt with the surface events taken in time order
  * (ties: x, then y, then z faces, then plates in list order).  Returns 1 if
- * the particle stays in the domain, 0 if it left through an open face. */
-static int motion(orc_ctx* C, orc_run* R, int run, int step, orc_particle* p)
+ * the particle stays in the domain, 0 if it left through an open face.
+ * `slot` is the particle's place in P this step (old particles in P order,
+ * then the entrants in generation order): it keys the particle's wall
+ * draws. */
+static int motion(orc_ctx* C, orc_run* R, int run, int step, orc_particle* p, int64_t slot)
 {
     const orc_config* g = &C->cfg;
     const int dim = g->dim;
@@ -476,7 +479,7 @@ static int motion(orc_ctx* C, orc_run* R, int run, int step, orc_particle* p)
             p->v[axis] = -p->v[axis];
         } else {
             double u[4], z0, z1;
-            orc_draw(C->seed, C->run0 + run, step, p->id, P_WALL, (uint32_t)bounce, u);
+            orc_draw(C->seed, C->run0 + run, step, (uint32_t)slot, P_WALL, (uint32_t)bounce, u);
             double sw = sqrt(KB * Tw / g->mass);
             orc_gauss2(u[1], u[2], &z0, &z1);
             p->v[axis] = dir * (sw * sqrt(-2.0 * log(u[0])));
@@ -543,7 +546,7 @@ int orc_step(orc_ctx* C, int run, int step)
     int32_t* cell = malloc((n_all ? n_all : 1) * sizeof(int32_t));
     if (!cell) return -2;
     for (int64_t s = 0; s < n_all; ++s)
-        cell[s] = motion(C, R, run, step, &R->p[s]) ? cell_of(C, R->p[s].x) : -1;
+        cell[s] = motion(C, R, run, step, &R->p[s], s) ? cell_of(C, R->p[s].x) : -1;
     /* Enumeration: particles per cell */
     memset(R->count, 0, nc * sizeof(int32_t));
     for (int64_t s = 0; s < n_all; ++s)

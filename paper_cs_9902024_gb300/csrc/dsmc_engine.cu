@@ -332,7 +332,7 @@ static dsmc_status ensure_alloc(dsmc_ctx* ctx, int n_launch, int64_t cap_run, in
             ctx->X[b][a] = a < ctx->dim ? A(ts * slots) : nullptr;
             ctx->V[b][a] = A(ts * slots);
         }
-        ctx->ID[b] = (uint32_t*)A(4 * slots);
+        ctx->ID[b] = dbg ? (uint32_t*)A(4 * slots) : nullptr;   // ids: debug bookkeeping only
         ctx->CI[b] = (uint32_t*)A(4 * cap_old);
     }
     ctx->gc = (uint32_t*)A(4 * slots);
@@ -2030,7 +2030,7 @@ static size_t noalloc_layout(dsmc_ctx* ctx, unsigned char* base, int n_runs, int
             ctx->X[b][a] = a < ctx->dim ? sc.take(ts * slots) : nullptr;
             ctx->V[b][a] = sc.take(ts * slots);
         }
-        ctx->ID[b] = (uint32_t*)sc.take(4 * slots);
+        ctx->ID[b] = nullptr;
         ctx->CI[b] = (uint32_t*)sc.take(4 * cap_old);
     }
     ctx->gc = (uint32_t*)sc.take(4 * slots);

@@ -115,8 +115,9 @@ struct StepArgs {
     Hot<T> hot;
     Counters* ctr;
     // pool: in/out buffers of positions (dim used), velocities (3), ids
-    // positions are offsets inside the particle's cell; ci_* hold the
-    // run-major cell key (run * ncells + cell) of each particle of the pool
+    // (ids only in debug mode, else null: no step reads them); positions are
+    // offsets inside the particle's cell; ci_* hold the run-major cell key
+    // (run * ncells + cell) of each particle of the pool
     T* xi[3]; T* vi[3]; uint32_t* idi; uint32_t* ci_i;
     T* xo[3]; T* vo[3]; uint32_t* ido; uint32_t* ci_o;
     uint32_t* gc;          // per slot: run-major cell key, or kDead

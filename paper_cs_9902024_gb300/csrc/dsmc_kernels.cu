@@ -258,15 +258,17 @@ __device__ __forceinline__ bool try_free_flight(const C& c, int* ci, T* f, const
 }
 
 template <typename T, int DIM>
-__device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, uint32_t run,
+__device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t place, uint32_t run,
                               uint32_t step, T tau, LocalCounters& lc, uint32_t& vmask);
 
 // Motion of one particle for time tau: free flight with the surface events
 // taken in time order (ties: x, y, z faces, then plates in list order).
 // Returns false if the particle left through an open face.  vmask collects
-// the velocity components that changed.
+// the velocity components that changed.  `place` -- the particle's place in
+// its run's particle order this step (old particles in pool order, then the
+// entrants in generation order) -- keys its wall draws.
 template <typename T, int DIM>
-__device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, uint32_t run,
+__device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t place, uint32_t run,
                               uint32_t step, T tau, LocalCounters& lc, uint32_t& vmask)
 {
     for (int bounce = 0;; ++bounce) {
@@ -360,7 +362,7 @@ __device__ bool move_particle(const Cfg& c, int* ci, T* f, T* v, uint32_t id, ui
             v[axis] = -v[axis];
             vmask |= 1u << axis;
         } else {
-            const uint4 r = draw_bits(c.seed, run, step, id, kWall, (uint32_t)bounce);
+            const uint4 r = draw_bits(c.seed, run, step, place, kWall, (uint32_t)bounce);
             const T sw = (T)Tsd;
             T z0, z1;
             gauss2<T>(u01<T>(r.y), u01<T>(r.z), z0, z1);
@@ -611,7 +613,7 @@ __global__ void k_fill_particles(StepArgs<T> a)
             for (int ax = 0; ax < DIM; ++ax) a.xi[ax][p] = ub[ax] * (T)c.d[ax];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) a.vi[ax][p] = (T)c.fill_U[ax] + sd * z[ax];
-            a.idi[p] = (beg - a.run_base[rl]) + k;
+            if (a.idi) a.idi[p] = (beg - a.run_base[rl]) + k;
             a.ci_i[p] = (uint32_t)i;
         }
     }
@@ -769,16 +771,18 @@ __device__ __forceinline__ void generate_block(const StepArgs<T>& a, uint32_t bl
             v[b.axis] = (T)b.dir * (T)b.cmp * xi;
             v[b.t0] = (T)b.U[b.t0] + (T)b.sd * z0;
             v[b.t1] = (T)b.U[b.t1] + (T)b.sd * z1;
-            const uint32_t id = id0 + local;
             const T tau = u01<T>(b0.z) * (T)c.dt;
             uint32_t vmask = 0;
-            const bool alive = move_particle<T, DIM>(c, ci, x, v, id, run, step, tau, lc, vmask);
+            // wall draws keyed by the entrant's place in the run's step
+            // order: after the n_old old particles, in generation order
+            const bool alive = move_particle<T, DIM>(c, ci, x, v, n_old + local, run, step, tau, lc,
+                                                     vmask);
             const int64_t slot = gen_base + local;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) a.xi[ax][slot] = x[ax];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) a.vi[ax][slot] = v[ax];
-            a.idi[slot] = id;
+            if (a.idi) a.idi[slot] = id0 + local;
             uint32_t key = kDead;
             if (alive) {
                 key = rl * (uint32_t)c.ncells + encode_cell<DIM>(c, ci);
@@ -1021,7 +1025,9 @@ __device__ __forceinline__ void move_slow_span(const StepArgs<T>& a, uint32_t fi
         int ci[3];
         decode_cell<DIM>(c, kold - rl * (uint32_t)c.ncells, ci);
         uint32_t vmask = 0;
-        const bool alive = move_particle<T, DIM>(c, ci, x, v, a.idi[s], a.run0 + rl, step, dt, lc, vmask);
+        // wall draws keyed by the particle's place in its run's old pool
+        const bool alive = move_particle<T, DIM>(c, ci, x, v, s - a.run_base[rl], a.run0 + rl, step,
+                                                 dt, lc, vmask);
         uint32_t key = kDead;
         if (alive) {
 #pragma unroll
@@ -1524,7 +1530,7 @@ __device__ void cell_warp_path(const StepArgs<T>& a, const Cfg& c, int64_t gcell
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
         a.ci_o[o] = (uint32_t)gcell;
-        a.ido[o] = a.idi[s];
+        if (a.ido) a.ido[o] = a.idi[s];
         a.vo[0][o] = a.vi[0][s];
         a.vo[1][o] = a.vi[1][s];
         a.vo[2][o] = a.vi[2][s];
@@ -1671,7 +1677,7 @@ __device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, co
                 pv[b][0] = a.vi[0][sl[b]];
                 pv[b][1] = a.vi[1][sl[b]];
                 pv[b][2] = a.vi[2][sl[b]];
-                pid[b] = a.idi[sl[b]];
+                if (a.ido) pid[b] = a.idi[sl[b]];
             }
 #pragma unroll
             for (int b = 0; b < kGatherBatch; ++b) {
@@ -1687,7 +1693,7 @@ __device__ __forceinline__ void cell_tile(const StepArgs<T>& a, int64_t tile, co
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = px[b][ax];
                 a.ci_o[o] = (uint32_t)(c0 + lo2[b]);
-                a.ido[o] = pid[b];
+                if (a.ido) a.ido[o] = pid[b];
                 a.vo[0][o] = pv[b][0];
                 a.vo[1][o] = pv[b][1];
                 a.vo[2][o] = pv[b][2];
@@ -2075,7 +2081,7 @@ __device__ __forceinline__ void big_put(const StepArgs<T>& a, uint32_t o, uint32
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) a.xo[ax][o] = a.xi[ax][s];
     a.ci_o[o] = gcell;
-    a.ido[o] = a.idi[s];
+    if (a.ido) a.ido[o] = a.idi[s];
     a.vo[0][o] = a.vi[0][s];
     a.vo[1][o] = a.vi[1][s];
     a.vo[2][o] = a.vi[2][s];
@@ -2421,7 +2427,7 @@ __global__ void k_check(StepArgs<T> a)
         if (ok) {
             const uint32_t cs = a.start[key], ce = a.start[key + 1];
             ok = cs <= p && p < ce;
-            if (ok) ok = a.idi[p] < a.next_id[run_of_key(a.hot, key)];
+            if (ok && a.idi) ok = a.idi[p] < a.next_id[run_of_key(a.hot, key)];
         }
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) {

@@ -89,6 +89,24 @@ def test_plain_equals_batched_bitwise(D, precision):
         assert sa[k] == sb[k]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_particle_ids_are_bookkeeping_only(D, precision):
+    """Particle ids are kept only in debug mode (the test hooks report them);
+    no step reads them -- wall draws are keyed by a particle's place in its
+    run's order -- so an ensemble with ids and one without give
+    bit-identical sums and counters (duct with diffuse walls and inflow,
+    19 runs)."""
+    w = W.duct64x32_n8(runs=19, steps=60, n_samples=3)
+    a = D.Ensemble(w, precision=precision, debug=True).run()
+    b = D.Ensemble(w, precision=precision).run()
+    for t in range(3):
+        assert np.array_equal(a.raw(t), b.raw(t)), t
+    sa, sb = a.stats(), b.stats()
+    for k in ("generated", "removed", "wall_hits", "candidates", "collisions", "particle_steps"):
+        assert sa[k] == sb[k], k
+    assert sa["wall_hits"] > 0
+
+
 def test_edge_cases(D):
     # one run, sample at step 1 and at the last step
     w = W.duct64x32_n8(runs=1, steps=5)
