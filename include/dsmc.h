@@ -237,10 +237,13 @@ enum { DSMC_K_GENERATE = 0, DSMC_K_MOVE = 1, DSMC_K_SCAN = 2, DSMC_K_SCATTER = 3
 typedef struct dsmc_ctx dsmc_ctx;
 
 /* Create a context for one problem: domain and grid, gas model, `n_b`
- * boundary segments (n_b <= DSMC_MAX_BC) and options (NULL: defaults).  No
- * device memory is allocated until the first run.  *out receives the
- * context; release it with dsmc_destroy.  Errors: DSMC_E_INVALID (bad
- * geometry, gas or boundary description), DSMC_E_CUDA (device selection). */
+ * boundary segments (n_b <= DSMC_MAX_BC) and options (NULL: defaults) --
+ * the data of one unsteady run of the paper's Sec. 1.1 (the computational
+ * grid and the arrays P, LCR and C are sized from them at the first run;
+ * the boundary conditions drive Generation and Motion).  No device memory
+ * is allocated until the first run.  *out receives the context; release it
+ * with dsmc_destroy.  Errors: DSMC_E_INVALID (bad geometry, gas or boundary
+ * description), DSMC_E_CUDA (device selection). */
 dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells,
                         const dsmc_gas* gas, const dsmc_boundary* b, int n_b,
                         const dsmc_options* opt, dsmc_ctx** out);
