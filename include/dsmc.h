@@ -141,8 +141,10 @@ typedef struct {
     void* alloc_user;
     void* stream;             /* cudaStream_t; NULL: the library's own stream */
     int32_t use_graph;        /* batched mode: capture one step per graph */
-    int32_t debug;            /* keep per-cell candidate / accepted counts and
-                                 the LCR of the last step (test hooks) */
+    int32_t debug;            /* keep per-cell candidate / accepted counts,
+                                 the LCR of the last step and particle ids
+                                 (test hooks; no step reads them, so the
+                                 results are the same either way) */
     int32_t device;           /* CUDA device ordinal */
     int32_t profile;          /* time every kernel with CUDA events (direct
                                  launches, no graph); see dsmc_stats */

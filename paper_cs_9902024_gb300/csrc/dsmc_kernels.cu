@@ -583,7 +583,7 @@ __global__ void k_fill_count(StepArgs<T> a)
 }
 
 // freestream fill, part 2: one warp per cell writes its particles in
-// (cell, k) order; ids count per run in that order
+// (cell, k) order; ids (debug mode) count per run in that order
 template <typename T, int DIM>
 __global__ void k_fill_particles(StepArgs<T> a)
 {
@@ -1553,8 +1553,8 @@ constexpr int kGatherBatch = 3;   // positions per thread and pass of the gather
 // LCR entries (old slots) into shared memory while each thread tags its
 // cell's positions.  (2) Thread per position, kGatherBatch positions per
 // pass: the particle's rank inside its cell by counting smaller slots, and
-// its offsets, velocity and id gathered from the old pool into the next
-// pool at cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
+// its offsets and velocity (and its id, in debug mode) gathered from the old
+// pool into the next pool at cell start + rank.  Cells above kWarpMax go to the one-CTA-per-cell
 // kernel; a tile whose particles exceed the budget is taken in consecutive
 // cell ranges that fit it.
 // shared memory of the sort/gather tile kernel: the tile's start table, its
@@ -2050,7 +2050,7 @@ template <typename T>
 __host__ __device__ constexpr int big_max_of() { return 8192; }
 
 // shared memory of order_cell for THREADS threads and cells up to KMAX
-// particles: ids (u32), slots (u32), two position buffers (u16), the
+// particles: sort keys (u32), slots (u32), two position buffers (u16), the
 // (digit, warp) counts (u16; one 16-byte word per thread)
 template <int THREADS, int KMAX>
 __host__ __device__ constexpr size_t order_smem()
@@ -2411,8 +2411,9 @@ __global__ void k_step_end(StepArgs<T> a)
 
 // Consistency check of the pool after a run (options.checks): every pool
 // position p holds a particle whose stored cell key lies inside the table,
-// whose cell's range [start[key], start[key + 1]) contains p, whose id is
-// below its run's next id (ids are handed out in order), whose offsets lie
+// whose cell's range [start[key], start[key + 1]) contains p, whose id (when
+// ids are kept) is below its run's next id (ids are handed out in order),
+// whose offsets lie
 // inside its cell and whose velocity is finite.  Counts the positions that
 // fail and keeps the first.
 template <typename T, int DIM>
