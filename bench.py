@@ -226,7 +226,7 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     carries out (28 B per moved particle for Motion in 2-D, 40 in 3-D; 12
     for the LCR scatter and 48 [56] for the permute of Indexing, 60 [68] in
     all; 16 for Interaction), times the particles it processes.
-    "layout": the bytes of this build's data layout (one read of every
+    "layout": the bytes of this data layout (one read of every
     input, one write of every output, no re-reads): the cell-relative
     offsets and stored cell keys, the 4-byte LCR entries (slots), the staged
     velocities."""

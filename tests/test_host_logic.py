@@ -50,7 +50,7 @@ def test_algorithmic_bytes_split_between_tile_and_big_cell_kernels():
     assert method["cell"] == 900 * 48 and method["cell_big"] == 300 * 48
     assert method["scatter"] + method["cell"] + method["cell_big"] == 1200 * 60
     assert method["collide"] + method["collide_big"] == 1200 * 16
-    # this build's layout bytes
+    # the implementation's layout bytes
     # LCR slot 4; gather offsets 8, v 12; write offsets 8, key 4, v 12
     gather = 4 + (2 * 4 + 3 * 4) + (2 * 4 + 3 * 4 + 4)
     cells = 8 * 64 * 32
