@@ -274,6 +274,32 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     return method, layout
 
 
+def traffic_per_launch(workload, kernel, prs, path=None, khash=None):
+    """DRAM bytes per launch of `kernel` from the ncu counters kept in
+    profiles/traffic.json for the workload's family (grid and gas, any run
+    count): bytes per particle of the captured launch times the particles
+    the kernel processed per launch in this profile pass (cells up to 128
+    particles for the tile kernels, the larger ones for the big-cell
+    kernels).  None when there is no entry or the device code has changed
+    since the capture (its hash differs)."""
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tj = json.load(f)
+        ent = tj.get(workload.rsplit("_n", 1)[0], {}).get(kernel)
+        if not ent or ent.get("kernel_hash") != (khash or kernel_hash()):
+            return None
+        per_particle = ent["dram_bytes"] / ent["particles"]
+        units = prs["pool_steps"]
+        if kernel in ("cell", "collide"):
+            units -= prs["big_pool_steps"]
+        elif kernel in ("cell_big", "collide_big"):
+            units = prs["big_pool_steps"]
+        return per_particle * units / prs["launches_kernel"][kernel]
+    except (OSError, ValueError, KeyError, ZeroDivisionError):
+        return None
+
+
 def method_rows(method, kern_ms, peak):
     """Achieved bandwidth of each of the method's steps on its algorithmic
     bytes: the bytes of the step's kernels over their summed time."""
@@ -599,24 +625,7 @@ def main():
             prs[key] = {k: sum(p[key][k] for p in passes) / len(passes) for k in passes[-1][key]}
         prs["ms_steps"] = sum(p["ms_steps"] for p in passes) / len(passes)
         kern, roof, rows, dom = roofline_of(w, prs, steps, runs)
-        tp = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tp):
-            try:
-                tj = json.load(open(tp))
-                # entries per workload family (grid and gas, any run count)
-                ent = tj.get(args.workload.rsplit("_n", 1)[0], {}).get(dom)
-                if ent and ent.get("kernel_hash") == kernel_hash():
-                    # bytes per particle of the captured launch, times the
-                    # particles the kernel processed per launch here
-                    per_particle = ent["dram_bytes"] / ent["particles"]
-                    units = prs["pool_steps"]
-                    if dom in ("cell", "collide"):
-                        units -= prs["big_pool_steps"]
-                    elif dom in ("cell_big", "collide_big"):
-                        units = prs["big_pool_steps"]
-                    roof["traffic"] = per_particle * units / prs["launches_kernel"][dom]
-            except Exception:
-                roof["traffic"] = None
+        roof["traffic"] = traffic_per_launch(args.workload, dom, prs)
         out["roofline"] = roof
         out["method_steps"] = rows
         out["kernels"] = kern

@@ -78,3 +78,26 @@ def test_method_rows_are_bytes_over_summed_kernel_time():
     assert abs(rows["motion"]["achieved_gbs"] - 2800.0) < 1e-6
     assert abs(rows["indexing"]["achieved_gbs"] - 60e9 / 0.020 / 1e9) < 1e-6
     assert abs(rows["interaction"]["frac"] - 2000.0 / 4000.0) < 1e-12
+
+
+def test_traffic_scales_the_captured_bytes_per_particle(tmp_path):
+    """The bench's DRAM traffic per launch: the captured bytes per particle
+    of the same workload family times the particles the kernel processed per
+    launch (tile kernels: cells up to 128 particles; big-cell kernels: the
+    rest); nothing when the family, the kernel or the device-code hash does
+    not match."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    path = tmp_path / "traffic.json"
+    json.dump({"duct64x32": {"cell": {"kernel_hash": "abc", "dram_bytes": 4.0e8, "particles": 1.0e7},
+                             "cell_big": {"kernel_hash": "abc", "dram_bytes": 6.0e8, "particles": 1.0e7}}},
+              open(path, "w"))
+    prs = {"pool_steps": 1000, "big_pool_steps": 200, "launches_kernel": {"cell": 10, "cell_big": 5}}
+    t = bench.traffic_per_launch("duct64x32_n512", "cell", prs, path=str(path), khash="abc")
+    assert t == 40.0 * 800 / 10
+    t = bench.traffic_per_launch("duct64x32_n8", "cell_big", prs, path=str(path), khash="abc")
+    assert t == 60.0 * 200 / 5
+    assert bench.traffic_per_launch("duct64x32_n512", "cell", prs, path=str(path), khash="xyz") is None
+    assert bench.traffic_per_launch("jet256x128_n64", "cell", prs, path=str(path), khash="abc") is None
+    assert bench.traffic_per_launch("duct64x32_n512", "move", prs, path=str(path), khash="abc") is None
