@@ -6,8 +6,8 @@ never calls it.
 """
 from .oracle import (Oracle, build_oracle, oracle_lib, run_ensemble, philox,
                      draw, inflow_flux, sample_xi, sigma_cr, scatter,
-                     macro_from_acc, NMOM)
+                     partner, macro_from_acc, NMOM)
 
 __all__ = ["Oracle", "build_oracle", "oracle_lib", "run_ensemble", "philox",
            "draw", "inflow_flux", "sample_xi", "sigma_cr", "scatter",
-           "macro_from_acc", "NMOM"]
+           "partner", "macro_from_acc", "NMOM"]

@@ -272,7 +272,9 @@ static int push(orc_run* R, const orc_particle* q)
 orc_ctx* orc_create(const orc_config* cfg, int n_runs, double dt, uint64_t seed)
 {
     if (!cfg || (cfg->dim != 2 && cfg->dim != 3) || n_runs < 1 || !(dt > 0.0) ||
-        cfg->n_bc < 0 || cfg->n_bc > ORC_MAX_BC)
+        cfg->n_bc < 0 || cfg->n_bc > ORC_MAX_BC ||
+        cfg->partner < ORC_PARTNER_UNIFORM || cfg->partner > ORC_PARTNER_NEAREST ||
+        (cfg->partner == ORC_PARTNER_SUBCELL && cfg->n_sub < 1))
         return NULL;
     orc_ctx* C = calloc(1, sizeof(orc_ctx));
     if (!C) return NULL;
@@ -489,6 +491,91 @@ static int motion(orc_ctx* C, orc_run* R, int run, int step, orc_particle* p, in
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Choice of the collision partner.  The NTC scheme draws a candidate pair of
+ * a cell; the paper's Interaction leaves the choice of the pair to the gas
+ * model of Bird (1994), whose refinements select the second particle close
+ * to the first so that collision partners are nearer than the cell size.
+ * The variants restated here: the first particle i is uniform over the
+ * cell's N particles; the second is
+ *   uniform  -- uniform over the other N-1 (the r-th other in LCR order,
+ *               r = floor(u1 (N-1)));
+ *   subcell  -- the cell is split into n_sub subcells per axis; uniform over
+ *               the other particles of i's subcell (the r-th of those K in
+ *               LCR order, r = floor(u1 K)); if i is alone there, the
+ *               uniform rule;
+ *   nearest  -- the other particle at the smallest Euclidean distance from
+ *               i (over the grid's axes); of equal distances, the first in
+ *               LCR order.
+ * Positions are read through `stride` bytes per particle.                  */
+
+/* subcell of a particle of cell c: per axis floor(n_sub f / d) of its
+ * offset f = x - (cell's lower corner) (clamped to the cell's subcells),
+ * linear with axis 0 fastest */
+static int subcell_of(const orc_config* cfg, const double d[3], const int ci[3],
+                      const double* x)
+{
+    int s = 0;
+    for (int a = cfg->dim - 1; a >= 0; --a) {
+        double f = (x[a] - (double)ci[a] * d[a]) / d[a];
+        int k = (int)floor(f * (double)cfg->n_sub);
+        k = k < 0 ? 0 : (k > cfg->n_sub - 1 ? cfg->n_sub - 1 : k);
+        s = s * cfg->n_sub + k;
+    }
+    return s;
+}
+
+static int64_t choose_partner(const orc_config* cfg, const double d[3], int c, const char* xb,
+                              size_t stride, int64_t N, int64_t i, double u1)
+{
+#define POS_OF(m) ((const double*)(xb + (size_t)(m) * stride))
+    if (cfg->partner == ORC_PARTNER_NEAREST) {
+        const double* xi = POS_OF(i);
+        double best = INFINITY;
+        int64_t j = -1;
+        for (int64_t m = 0; m < N; ++m) {
+            if (m == i) continue;
+            const double* xm = POS_OF(m);
+            double dd = 0.0;
+            for (int a = 0; a < cfg->dim; ++a) {
+                double e = xm[a] - xi[a];
+                dd = dd + e * e;
+            }
+            if (dd < best) { best = dd; j = m; }
+        }
+        return j;
+    }
+    if (cfg->partner == ORC_PARTNER_SUBCELL) {
+        int n0 = cfg->ncell[0], n1 = cfg->ncell[1];
+        int ci[3] = { c % n0, (c / n0) % n1, c / (n0 * n1) };
+        int si = subcell_of(cfg, d, ci, POS_OF(i));
+        int64_t K = 0;
+        for (int64_t m = 0; m < N; ++m)
+            if (m != i && subcell_of(cfg, d, ci, POS_OF(m)) == si) ++K;
+        if (K > 0) {
+            int64_t r = (int64_t)floor(u1 * (double)K);
+            for (int64_t m = 0; m < N; ++m) {
+                if (m == i || subcell_of(cfg, d, ci, POS_OF(m)) != si) continue;
+                if (r == 0) return m;
+                --r;
+            }
+        }
+    }
+#undef POS_OF
+    int64_t j = (int64_t)floor(u1 * (double)(N - 1));
+    if (j >= i) j += 1;
+    return j;
+}
+
+int64_t orc_partner(const orc_config* cfg, int c, const double* x, int64_t N, int64_t i,
+                    double u1)
+{
+    if (!cfg || !x || N < 2 || i < 0 || i >= N) return -1;
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = cfg->L[a] / (a < cfg->dim ? cfg->ncell[a] : 1);
+    return choose_partner(cfg, d, c, (const char*)x, 3 * sizeof(double), N, i, u1);
+}
+
 /* NTC collisions in one cell: its N particles are q[0..N) in LCR order. */
 static void interaction_cell(orc_ctx* C, orc_run* R, int run, int step, int c,
                              orc_particle* q, int64_t N)
@@ -506,8 +593,8 @@ static void interaction_cell(orc_ctx* C, orc_run* R, int run, int step, int c,
         double u[4];
         orc_draw(C->seed, C->run0 + run, step, c, P_COLL, (uint32_t)(2 * k), u);
         int64_t i = (int64_t)floor(u[0] * (double)N);
-        int64_t j = (int64_t)floor(u[1] * (double)(N - 1));
-        if (j >= i) j += 1;
+        int64_t j = choose_partner(&C->cfg, C->d, c, (const char*)q[0].x,
+                                   sizeof(orc_particle), N, i, u[1]);
         double* v1 = q[i].v;
         double* v2 = q[j].v;
         double gx = v1[0] - v2[0], gy = v1[1] - v2[1], gz = v1[2] - v2[2];

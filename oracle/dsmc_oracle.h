@@ -27,6 +27,9 @@
  *   enumeration/indexing  pinned (vs a stable sort of the slots by cell)
  *   interaction           pinned (per-collision conservation, equilibrium
  *                          HS and VHS rates, Maxwell-molecule relaxation)
+ *   orc_partner           pinned (nearest: k-d tree search; subcell: one
+ *                          subcell reduces to the uniform rule, placed
+ *                          subcells, mean partner separation closed form)
  *   sampling              pinned (brute-force sums)
  */
 #ifndef DSMC_ORACLE_H
@@ -43,6 +46,11 @@ extern "C" {
 
 enum { ORC_OUTFLOW = 0, ORC_INFLOW = 1, ORC_SPECULAR = 2, ORC_DIFFUSE = 3 };
 enum { ORC_FACE_PLATE = 6 };
+/* choice of the second particle of an NTC candidate pair (the first is
+ * uniform over the cell): uniform over the cell's other particles; uniform
+ * over the other particles of the first one's subcell (n_sub per axis), the
+ * cell-wide rule when it has none; the nearest other particle of the cell */
+enum { ORC_PARTNER_UNIFORM = 0, ORC_PARTNER_SUBCELL = 1, ORC_PARTNER_NEAREST = 2 };
 
 typedef struct {
     int32_t kind;          /* ORC_OUTFLOW .. ORC_DIFFUSE */
@@ -64,6 +72,8 @@ typedef struct {
     double fill_n, fill_T, fill_U[3];
     int32_t n_bc;
     orc_bc bc[ORC_MAX_BC];
+    int32_t partner;       /* ORC_PARTNER_* */
+    int32_t n_sub;         /* subcells per axis (ORC_PARTNER_SUBCELL) */
 } orc_config;
 
 /* counters of one run, accumulated over all steps */
@@ -92,6 +102,11 @@ int orc_sample_xi(double s, uint64_t seed, uint32_t run, uint32_t step,
 double orc_sigma_cr(const orc_config* cfg, double g);
 /* post-collision velocities of an accepted pair: u3 gives cos(chi), u4 eps */
 void orc_scatter(double v1[3], double v2[3], double u3, double u4);
+/* the second particle of an NTC candidate whose first particle is i, among
+ * the N particles of cell c (absolute positions x[3*m .. 3*m+2], in LCR
+ * order), under cfg->partner; u1 is the candidate's second uniform */
+int64_t orc_partner(const orc_config* cfg, int c, const double* x, int64_t N, int64_t i,
+                    double u1);
 
 orc_ctx* orc_create(const orc_config* cfg, int n_runs, double dt, uint64_t seed);
 void orc_destroy(orc_ctx* c);

@@ -52,7 +52,8 @@ class Config(C.Structure):
                 ("omega", C.c_double), ("F_N", C.c_double),
                 ("fill", C.c_int32), ("fill_n", C.c_double), ("fill_T", C.c_double),
                 ("fill_U", C.c_double * 3),
-                ("n_bc", C.c_int32), ("bc", Bc * MAX_BC)]
+                ("n_bc", C.c_int32), ("bc", Bc * MAX_BC),
+                ("partner", C.c_int32), ("n_sub", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -85,6 +86,9 @@ def oracle_lib():
             lib.orc_sigma_cr.restype = C.c_double
             lib.orc_sigma_cr.argtypes = [C.POINTER(Config), C.c_double]
             lib.orc_scatter.argtypes = [dp, dp, C.c_double, C.c_double]
+            lib.orc_partner.restype = C.c_int64
+            lib.orc_partner.argtypes = [C.POINTER(Config), C.c_int, dp, C.c_int64, C.c_int64,
+                                        C.c_double]
             lib.orc_create.restype = P
             lib.orc_create.argtypes = [C.POINTER(Config), C.c_int, C.c_double, C.c_uint64]
             lib.orc_destroy.argtypes = [P]
@@ -132,6 +136,7 @@ def make_config(w, gas_override=None):
         g.update(gas_override)
     cfg.mass, cfg.d_ref, cfg.T_ref = g["mass"], g["d_ref"], g["T_ref"]
     cfg.omega, cfg.F_N = g["omega"], g["F_N"]
+    cfg.partner, cfg.n_sub = g.get("partner", 0), g.get("n_sub", 1)
     f = w["fill"]
     cfg.fill = f["kind"]
     cfg.fill_n, cfg.fill_T = f["n"], f["T"]
@@ -186,6 +191,15 @@ def sample_xi(s, seed, run, step, e, k):
 def sigma_cr(w, g, gas_override=None):
     cfg = make_config(w, gas_override)
     return oracle_lib().orc_sigma_cr(C.byref(cfg), g)
+
+
+def partner(w, cell, x, i, u1):
+    """The second particle of an NTC candidate whose first is i, for the
+    particles of `cell` at absolute positions x (N x 3, LCR order)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    cfg = make_config(w)
+    return int(oracle_lib().orc_partner(C.byref(cfg), int(cell), _ptr(x, C.c_double),
+                                        len(x), int(i), float(u1)))
 
 
 def scatter(v1, v2, u3, u4):

@@ -20,8 +20,8 @@ into numbers with the kinetic-theory definitions
 A workload is a plain dict:
 
     dim, ncell[3], L[3] (L[2] is the depth in 2-D), gas{mass,d_ref,T_ref,
-    omega,F_N}, fill{kind,n,T,U}, bcs[list of dict], runs, steps, dt,
-    sample_steps, seed, name
+    omega,F_N[,partner,n_sub]}, fill{kind,n,T,U}, bcs[list of dict], runs,
+    steps, dt, sample_steps, seed, name
 """
 from __future__ import annotations
 
@@ -249,6 +249,25 @@ def mixed(n_runs=1024, cells_lo=32 * 16, cells_hi=512 * 256, steps=300, n_sample
 
 def mixed_n1024(**kw):
     return mixed(**kw)
+
+
+# choice of the second particle of an NTC candidate pair (gas["partner"]):
+# uniform over the cell, within the first particle's subcell (gas["n_sub"]
+# subcells per axis), or the nearest other particle of the cell
+PARTNER_UNIFORM, PARTNER_SUBCELL, PARTNER_NEAREST = 0, 1, 2
+PARTNER_NAMES = {"uniform": PARTNER_UNIFORM, "subcell": PARTNER_SUBCELL,
+                 "nearest": PARTNER_NEAREST}
+
+
+def with_partner(w, scheme, n_sub=2):
+    """The same workload with another collision-partner choice (`scheme` a
+    PARTNER_NAMES key); its name gains the scheme (and subcell count)."""
+    p = PARTNER_NAMES[scheme]
+    w = dict(w)
+    w["gas"] = dict(w["gas"], partner=p, n_sub=n_sub if p == PARTNER_SUBCELL else 1)
+    if p != PARTNER_UNIFORM:
+        w["name"] = w["name"] + ("_sub%d" % n_sub if p == PARTNER_SUBCELL else "_nn")
+    return w
 
 
 def by_name(name, **kw):
