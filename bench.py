@@ -50,6 +50,9 @@ def parse():
                             "plate128x64x64_n16", "mixed_n1024"],
                    help="workload (default: the 512-run duct the metric is quoted on; the others "
                         "are the parity workloads, measured the same way)")
+    p.add_argument("--partner", default="uniform", choices=["uniform", "subcell", "nearest"],
+                   help="choice of the second collision partner (gas model variant)")
+    p.add_argument("--n-sub", type=int, default=2, help="subcells per axis (--partner subcell)")
     return p.parse_args()
 
 
@@ -70,11 +73,13 @@ WORKLOAD_TEXT = {
 }
 
 
-def workload(runs=None, name="duct64x32_n512"):
+def workload(runs=None, name="duct64x32_n512", partner="uniform", n_sub=2):
     from paper_cs_9902024_gb300 import workloads as W
     w = W.by_name(name)
     if runs:
         w = W.scaled(w, runs=runs)
+    if partner != "uniform":
+        w = W.with_partner(w, partner, n_sub)
     return w
 
 
@@ -206,13 +211,15 @@ def kernel_hash():
 # components and writes x and the cell index; Indexing reads the cell index
 # twice (histogram and scatter), writes the LCR and permutes the state
 # (x, v, id read once and written once); Interaction reads the cell's
-# velocities and writes the collided ones (with the cell data, ~16 B).
-def _method_bytes(D):
+# velocities and writes the collided ones (with the cell data, ~16 B), and,
+# when partners are chosen by position, reads every particle's position
+# once more (D x 4 B).
+def _method_bytes(D, positional=False):
     t = 4
     return {"motion": (2 * D + D) * t + 4 if D == 2 else 40,
             "scatter": 12,
             "permute": 2 * (D * t + 3 * t + 4),
-            "interaction": 16}
+            "interaction": 16 + (D * t if positional else 0)}
 
 
 METHOD_ROWS = {"motion": ("move",), "indexing": ("scan", "scatter", "cell", "cell_big"),
@@ -237,7 +244,9 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     moved_old = st["particle_steps"] - st["generated"]
     pool = st["pool_steps"]
     big = st.get("big_pool_steps", 0)
-    mb = _method_bytes(D)
+    positional = w["gas"].get("partner", 0) != 0
+    mb = _method_bytes(D, positional)
+    pos = D * t if positional else 0
     # read the LCR entry (4), gather offsets and v; write offsets, cell key,
     # v (ids are carried in debug mode only)
     gather = 4 + (D * t + 3 * t) + (D * t + 3 * t + 4)
@@ -264,8 +273,10 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
         # per cell: start, NTC remainder (read + write), (sigma c_r)_max;
         # every particle's velocity read once, both velocities of every
         # collision written
-        "collide": cells * steps * 24 + pool * 3 * t + st["collisions"] * 2 * 3 * t,
-        "collide_big": big * 3 * t,
+        # (positional partner choice: every particle's position read once)
+        "collide": (cells * steps * 24 + (pool - big) * (3 * t + pos)
+                    + st["collisions"] * 2 * 3 * t),
+        "collide_big": big * (3 * t + pos),
         # read counts, write starts
         "scan": cells * steps * 8,
         # write the entrants (x, v, key)
@@ -274,19 +285,21 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
     return method, layout
 
 
-def traffic_per_launch(workload, kernel, prs, path=None, khash=None):
+def traffic_per_launch(workload, kernel, prs, path=None, khash=None, partner="uniform"):
     """DRAM bytes per launch of `kernel` from the ncu counters kept in
     profiles/traffic.json for the workload's family (grid and gas, any run
-    count): bytes per particle of the captured launch times the particles
-    the kernel processed per launch in this profile pass (cells up to 128
-    particles for the tile kernels, the larger ones for the big-cell
-    kernels).  None when there is no entry or the device code has changed
-    since the capture (its hash differs)."""
+    count; a collision-partner variant is a family of its own): bytes per
+    particle of the captured launch times the particles the kernel processed
+    per launch in this profile pass (cells up to 128 particles for the tile
+    kernels, the larger ones for the big-cell kernels).  None when there is
+    no entry or the device code has changed since the capture (its hash
+    differs)."""
     path = path or os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             tj = json.load(f)
-        ent = tj.get(workload.rsplit("_n", 1)[0], {}).get(kernel)
+        family = workload.rsplit("_n", 1)[0] + ("" if partner == "uniform" else "_" + partner)
+        ent = tj.get(family, {}).get(kernel)
         if not ent or ent.get("kernel_hash") != (khash or kernel_hash()):
             return None
         per_particle = ent["dram_bytes"] / ent["particles"]
@@ -320,7 +333,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import run_ensemble
-    w = workload(name=args.workload)
+    w = workload(name=args.workload, partner=args.partner, n_sub=args.n_sub)
     cores = min(cpu_cores(), 16)
     sample_runs = min(64, w["runs"])
     probe = ORACLE_PROBE_STEPS[args.workload]
@@ -489,6 +502,8 @@ def bench_mixed(args):
 
 def main():
     args = parse()
+    if args.workload == "mixed_n1024" and args.partner != "uniform":
+        raise SystemExit("the mixed workload is measured with the uniform partner choice")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "mixed_n1024":
@@ -506,7 +521,7 @@ def main():
     g.build()
     from paper_cs_9902024_gb300.dsmc import Ensemble
     from paper_cs_9902024_gb300 import shard
-    w = workload(args.runs, args.workload)
+    w = workload(args.runs, args.workload, args.partner, args.n_sub)
     runs = w["runs"]
     shard.groups(runs, ws)          # every rank must hold >= 16 runs when sharded
     steps = w["steps"]
@@ -577,7 +592,9 @@ def main():
                    "sample_times": n_samples,
                    "mode": "batched, CUDA graph per step", "state": "fp32",
                    "sampling": "fp64 group sums", "l2": "inputs larger than L2 (pool ~1 GB)",
-                   "parallelism": "runs sharded over %d GPU(s)" % ws},
+                   "parallelism": "runs sharded over %d GPU(s)" % ws,
+                   "partner": args.partner + (" (%d subcells per axis)" % args.n_sub
+                                              if args.partner == "subcell" else "")},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -625,7 +642,7 @@ def main():
             prs[key] = {k: sum(p[key][k] for p in passes) / len(passes) for k in passes[-1][key]}
         prs["ms_steps"] = sum(p["ms_steps"] for p in passes) / len(passes)
         kern, roof, rows, dom = roofline_of(w, prs, steps, runs)
-        roof["traffic"] = traffic_per_launch(args.workload, dom, prs)
+        roof["traffic"] = traffic_per_launch(args.workload, dom, prs, partner=args.partner)
         out["roofline"] = roof
         out["method_steps"] = rows
         out["kernels"] = kern

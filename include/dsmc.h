@@ -94,10 +94,28 @@ typedef struct {
  *   sigma_T(c_r) = pi d_ref^2 (2 k T_ref / (m_r c_r^2))^(omega - 1/2)
  *                  / Gamma(5/2 - omega),  m_r = mass / 2;
  * omega = 0.5 is the hard sphere pi d_ref^2.  F_N = real molecules per
- * simulated particle. */
+ * simulated particle.
+ * `partner` chooses the second particle of an NTC candidate pair (the first
+ * is uniform over the cell; the paper's Interaction, Sec. 1.1, leaves the
+ * pair selection to the gas model):
+ *   DSMC_PARTNER_UNIFORM  uniform over the cell's other particles;
+ *   DSMC_PARTNER_SUBCELL  uniform over the other particles of the first
+ *                         one's subcell -- the cell split into n_sub (1..64)
+ *                         equal parts per axis, a particle's subcell per axis
+ *                         floor(n_sub * offset / cell size) -- or, if it is
+ *                         alone there, uniform over the cell's others;
+ *   DSMC_PARTNER_NEAREST  the other particle of the cell nearest to it
+ *                         (Euclidean distance over the grid's axes; of equal
+ *                         distances the first in LCR order).
+ * A caller whose struct_size ends before `partner` gets the uniform choice. */
+#define DSMC_PARTNER_UNIFORM 0
+#define DSMC_PARTNER_SUBCELL 1
+#define DSMC_PARTNER_NEAREST 2
 typedef struct {
     uint32_t struct_size;
     double mass, d_ref, T_ref, omega, F_N;
+    int32_t partner;        /* DSMC_PARTNER_* */
+    int32_t n_sub;          /* subcells per axis (DSMC_PARTNER_SUBCELL) */
 } dsmc_gas;
 
 /* One boundary segment.  Faces: 2 * axis + side (side 0 at coordinate 0,

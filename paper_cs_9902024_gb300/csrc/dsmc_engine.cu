@@ -147,6 +147,8 @@ static dsmc_status build_cfg(dsmc_ctx* ctx, double dt, uint64_t seed)
     const double omega = ctx->gas.omega;
     const double dref = ctx->gas.d_ref;
     c.hs = (omega == 0.5) ? 1 : 0;
+    c.partner = ctx->gas.partner;
+    c.n_sub = ctx->gas.partner == DSMC_PARTNER_SUBCELL ? ctx->gas.n_sub : 1;
     c.A_hs = M_PI * (dref * dref);
     const double mr = ctx->gas.mass / 2.0;
     c.K_vhs = M_PI * (dref * dref) * std::pow(2.0 * kB * ctx->gas.T_ref / mr, omega - 0.5) /
@@ -399,6 +401,9 @@ static StepArgs<T> args_for(const dsmc_ctx* ctx, int cur, int run0, int n)
         a.hot.plate_ix[pi] = pi < c.n_plate ? c.bc[c.plate_idx[pi]].plate_index : 0;
     }
     a.hot.hs = c.hs;
+    a.hot.dim = c.dim;
+    a.hot.partner = c.partner;
+    a.hot.n_sub = c.n_sub;
     a.hot.ncells_magic = c.ncells_magic;
     a.hot.seed = c.seed;
     a.hot.A_hs = (T)c.A_hs;
@@ -704,7 +709,7 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     if (!domain || !cells || !gas || (n_b > 0 && !b) || n_b < 0 || n_b > DSMC_MAX_BC)
         return DSMC_E_INVALID;
     if (domain->struct_size < sizeof(dsmc_domain) || cells->struct_size < sizeof(dsmc_cells) ||
-        gas->struct_size < sizeof(dsmc_gas) ||
+        gas->struct_size < offsetof(dsmc_gas, partner) ||
         (opt && opt->struct_size < offsetof(dsmc_options, checks)))
         return DSMC_E_INVALID;
     if (domain->dim != 2 && domain->dim != 3) return DSMC_E_INVALID;
@@ -715,6 +720,18 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     if (nc > (1 << 24)) return DSMC_E_INVALID;
     if (!(gas->mass > 0.0) || !(gas->d_ref >= 0.0) || !(gas->F_N > 0.0) || !(gas->T_ref > 0.0) ||
         !(gas->omega >= 0.5 && gas->omega <= 1.0))
+        return DSMC_E_INVALID;
+    // an older caller's gas ends before the partner choice: uniform
+    dsmc_gas g_in;
+    std::memset(&g_in, 0, sizeof(g_in));
+    std::memcpy(&g_in, gas, std::min<size_t>(gas->struct_size, sizeof(dsmc_gas)));
+    g_in.struct_size = sizeof(dsmc_gas);
+    if (gas->struct_size < sizeof(dsmc_gas)) {
+        g_in.partner = DSMC_PARTNER_UNIFORM;
+        g_in.n_sub = 1;
+    }
+    if (g_in.partner < DSMC_PARTNER_UNIFORM || g_in.partner > DSMC_PARTNER_NEAREST ||
+        (g_in.partner == DSMC_PARTNER_SUBCELL && (g_in.n_sub < 1 || g_in.n_sub > 64)))
         return DSMC_E_INVALID;
     if (domain->fill && !(domain->fill_n >= 0.0 && domain->fill_T > 0.0)) return DSMC_E_INVALID;
     for (int q = 0; q < n_b; ++q) {
@@ -755,7 +772,7 @@ dsmc_status dsmc_create(const dsmc_domain* domain, const dsmc_cells* cells, cons
     ctx->dom = *domain;
     ctx->cells = *cells;
     if (domain->dim == 2) ctx->cells.n[2] = 1;
-    ctx->gas = *gas;
+    ctx->gas = g_in;
     ctx->bcs.assign(b, b + n_b);
     std::memset(&ctx->opt, 0, sizeof(ctx->opt));
     ctx->opt.struct_size = sizeof(dsmc_options);
@@ -967,6 +984,11 @@ static std::string tune_key(const dsmc_ctx* ctx, int n_runs, int steps)
     h = fnv1a(h, ctx->cells.n, sizeof ctx->cells.n);
     const double g[5] = {ctx->gas.mass, ctx->gas.d_ref, ctx->gas.T_ref, ctx->gas.omega, ctx->gas.F_N};
     h = fnv1a(h, g, sizeof g);
+    if (ctx->gas.partner != DSMC_PARTNER_UNIFORM) {
+        const int32_t pv[2] = {ctx->gas.partner,
+                               ctx->gas.partner == DSMC_PARTNER_SUBCELL ? ctx->gas.n_sub : 1};
+        h = fnv1a(h, pv, sizeof pv);
+    }
     for (const dsmc_boundary& b : ctx->bcs) {
         const int32_t iv[8] = {b.kind, b.face, b.lo[0], b.lo[1], b.hi[0], b.hi[1], b.step_from, b.step_to};
         const double dv[5] = {b.n, b.T, b.U[0], b.U[1], b.U[2]};
@@ -1732,6 +1754,7 @@ static dsmc_status mixed_upload_args(dsmc_mixed* m, const int32_t* n_runs)
             const int i = m->order[k];
             dsmc_ctx* c = m->parts[i];
             h[k] = args_for<T>(c, p, (int)c->opt.run_offset, n_runs[i]);
+            if (h[k].hot.partner != DSMC_PARTNER_UNIFORM) ma.positional = 1;
             const int64_t cells = (int64_t)c->ncells * n_runs[i];
             ma.tile_base[k + 1] = ma.tile_base[k] + (int32_t)((cells + kTileCells - 1) / kTileCells);
             ma.ctile_base[k + 1] = ma.ctile_base[k] + (int32_t)((cells + kCollideCells - 1) / kCollideCells);

@@ -53,6 +53,7 @@ struct BcDev {
 
 struct Cfg {
     int32_t dim, n[3], ncells, n_bc, n_plate, hs, fill, pad_;
+    int32_t partner, n_sub;   // collision-partner choice (DSMC_PARTNER_*), subcells per axis
     int32_t plate_idx[DSMC_MAX_BC];
     double L[3], d[3], inv_d[3], Vc, dt, mass;
     double coef;         // F_N dt / Vc
@@ -100,6 +101,8 @@ struct Hot {
     int32_t plate_ax[4], plate_ix[4];   // plate axis and face index (plane
                                         // between cells plate_ix - 1 and plate_ix)
     int32_t hs;
+    int32_t dim;
+    int32_t partner, n_sub;  // collision-partner choice (DSMC_PARTNER_*), subcells per axis
     uint64_t ncells_magic;
     uint64_t seed;
     T A_hs, K_vhs, one_m_omega;
@@ -170,6 +173,7 @@ struct MultiArgs {
     uint32_t* queue;              // kQueueKinds claim counters, zeroed at each step's end
     int32_t n_parts;
     int32_t collide_stage;        // the collision CTAs' stage (every part's the same)
+    int32_t positional;           // some part chooses collision partners by position
     int32_t tile_base[kMaxParts + 1];     // sort/gather tiles before each part
     int32_t ctile_base[kMaxParts + 1];    // collision tiles before each part
     int32_t scan_base[kMaxParts + 1];     // scan CTAs before each part

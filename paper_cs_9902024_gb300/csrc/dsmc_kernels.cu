@@ -1304,6 +1304,79 @@ __device__ __forceinline__ uint32_t pick(uint32_t bits, uint32_t n)
     return (uint32_t)((m2 * (uint64_t)n) >> 24);
 }
 
+// Positions of one cell's particles in the next pool (offsets inside the
+// cell, LCR order); x[2] is read in 3-D only.
+template <typename T>
+struct CellPos {
+    const T* x[3];
+};
+
+// the subcell of a particle from its offsets: per axis floor(n_sub f / d),
+// clamped to the cell, axis 0 fastest
+template <typename T, class C>
+__device__ __forceinline__ uint32_t subcell_of(const C& c, const CellPos<T>& p, uint32_t m)
+{
+    const int ns = c.n_sub;
+    uint32_t s = 0;
+    for (int a = c.dim - 1; a >= 0; --a) {
+        int k = (int)dfloor(in_cells(c, a, p.x[a][m]) * (T)ns);
+        k = k < 0 ? 0 : (k > ns - 1 ? ns - 1 : k);
+        s = s * (uint32_t)ns + (uint32_t)k;
+    }
+    return s;
+}
+
+// The second particle of an NTC candidate whose first is i, among the N of
+// the cell, by the gas model's choice of partner: uniform over the other
+// N - 1 (the r-th other in LCR order, r from `bits`); uniform over the other
+// particles of i's subcell, or the uniform rule if i is alone there; the
+// nearest other particle (squared distance summed over the grid's axes in
+// axis order; the first of equal distances).  The cell's particles are read
+// from global memory, one pass per choice (two for a subcell draw).
+template <typename T, class C>
+__device__ uint32_t pick_partner(const C& c, const CellPos<T>& p, uint32_t N, uint32_t i,
+                                 uint32_t bits)
+{
+    if (c.partner == DSMC_PARTNER_NEAREST) {
+        const bool d3 = c.dim == 3;
+        const T a0 = p.x[0][i], a1 = p.x[1][i], a2 = d3 ? p.x[2][i] : (T)0;
+        T best = (T)0;
+        uint32_t j = 0xFFFFFFFFu;
+        for (uint32_t m = 0; m < N; ++m) {
+            if (m == i) continue;
+            const T e0 = p.x[0][m] - a0;
+            const T e1 = p.x[1][m] - a1;
+            T dd = e0 * e0;
+            dd = dd + e1 * e1;
+            if (d3) {
+                const T e2 = p.x[2][m] - a2;
+                dd = dd + e2 * e2;
+            }
+            if (j == 0xFFFFFFFFu || dd < best) {
+                best = dd;
+                j = m;
+            }
+        }
+        return j;
+    }
+    if (c.partner == DSMC_PARTNER_SUBCELL) {
+        const uint32_t si = subcell_of<T>(c, p, i);
+        uint32_t K = 0;
+        for (uint32_t m = 0; m < N; ++m) K += (m != i && subcell_of<T>(c, p, m) == si) ? 1u : 0u;
+        if (K > 0u) {
+            uint32_t r = pick(bits, K);
+            for (uint32_t m = 0; m < N; ++m) {
+                if (m == i || subcell_of<T>(c, p, m) != si) continue;
+                if (r == 0u) return m;
+                --r;
+            }
+        }
+    }
+    uint32_t j = pick(bits, N - 1u);
+    if (j >= i) j += 1u;
+    return j;
+}
+
 // NTC acceptance u < sigma c_r / (sigma c_r)_max: FP64 state divides, as the
 // oracle does; FP32 state compares u (sigma c_r)_max < sigma c_r (no
 // division; FP32 collision arithmetic)
@@ -1345,17 +1418,23 @@ __device__ __forceinline__ double warp_sum(double x)
 }
 
 // The draws of NTC candidate k of a cell with N particles: the pair (i, j),
-// the acceptance uniform, cos(chi) and the azimuth uniform.
-template <typename T, class C>
+// the acceptance uniform, cos(chi) and the azimuth uniform.  POS: the
+// partner j is chosen by pick_partner from the cell's positions xp.
+template <bool POS, typename T, class C>
 __device__ __forceinline__ void candidate_draws(const C& c, uint32_t run, uint32_t step,
-                                                uint32_t cell, int64_t k, uint32_t N, uint32_t& ci,
-                                                uint32_t& cj, T& u2, T& u3, T& ue)
+                                                uint32_t cell, int64_t k, uint32_t N,
+                                                const CellPos<T>& xp, uint32_t& ci, uint32_t& cj,
+                                                T& u2, T& u3, T& ue)
 {
     const uint4 r = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k));
     const uint4 r2 = draw_c(c, run, step, cell, kColl, (uint32_t)(2 * k + 1));
     ci = pick(r.x, N);
-    cj = pick(r.y, N - 1u);
-    if (cj >= ci) cj += 1u;
+    if constexpr (POS) {
+        cj = pick_partner<T>(c, xp, N, ci, r.y);
+    } else {
+        cj = pick(r.y, N - 1u);
+        if (cj >= ci) cj += 1u;
+    }
     u2 = u01<T>(r.z);
     u3 = u01<T>(r.w);
     ue = u01<T>(r2.x);
@@ -1403,10 +1482,10 @@ __device__ __forceinline__ void collide_candidate(const C& c, T* sv0, T* sv1, T*
 // particle still sees its collisions in candidate order: the result equals
 // applying the candidates one after another.  On return every lane holds
 // the warp's totals.
-template <typename T, class C>
-__device__ void collide_cell_warp(const C& c, T* sv0, T* sv1, T* sv2, uint32_t N, int64_t M,
-                                  T smax, uint32_t cell, uint32_t run, uint32_t step,
-                                  T& seen, uint32_t& nacc, uint32_t& nclamp)
+template <bool POS, typename T, class C>
+__device__ void collide_cell_warp(const C& c, T* sv0, T* sv1, T* sv2, const CellPos<T>& xp,
+                                  uint32_t N, int64_t M, T smax, uint32_t cell, uint32_t run,
+                                  uint32_t step, T& seen, uint32_t& nacc, uint32_t& nclamp)
 {
     const uint32_t lane = lane_id();
     T my_seen = (T)0;
@@ -1415,7 +1494,7 @@ __device__ void collide_cell_warp(const C& c, T* sv0, T* sv1, T* sv2, uint32_t N
         const int64_t k = kb + lane;
         uint32_t ci = 0xFFFFFFFFu, cj = 0xFFFFFFFEu;
         T u2 = (T)1, u3 = (T)0, ue = (T)0;
-        if (k < M) candidate_draws<T>(c, run, step, cell, k, N, ci, cj, u2, u3, ue);
+        if (k < M) candidate_draws<POS, T>(c, run, step, cell, k, N, xp, ci, cj, u2, u3, ue);
         uint32_t pending = __ballot_sync(0xFFFFFFFFu, k < M);
         while (pending) {
             bool blocked = false;
@@ -1744,10 +1823,11 @@ __global__ void __launch_bounds__(kTileCells, 4) k_cell(StepArgs<T> a)
 // velocity), which gives the thread two independent chains of work; the
 // azimuth draw is made only for an accepted pair.  The draws are those of
 // candidate_draws.
-template <typename T, class C>
-__device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2, uint32_t run,
-                                                 uint32_t step, uint32_t cell, uint32_t M, uint32_t N,
-                                                 T smax, T& seen, uint32_t& nacc, uint32_t& nclamp)
+template <bool POS, typename T, class C>
+__device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2,
+                                                 const CellPos<T>& xp, uint32_t run, uint32_t step,
+                                                 uint32_t cell, uint32_t M, uint32_t N, T smax,
+                                                 T& seen, uint32_t& nacc, uint32_t& nclamp)
 {
     if (M == 0u) return;
     uint4 r = draw_c(c, run, step, cell, kColl, 0u);
@@ -1756,8 +1836,13 @@ __device__ __forceinline__ void collide_cell_run(const C& c, T* v0, T* v1, T* v2
         const uint32_t kn = k + 1u < M ? k + 1u : k;
         const uint4 rn = draw_c(c, run, step, cell, kColl, 2u * kn);
         const uint32_t i = pick(r.x, N);
-        uint32_t j = pick(r.y, N - 1u);
-        if (j >= i) j += 1u;
+        uint32_t j;
+        if constexpr (POS) {
+            j = pick_partner<T>(c, xp, N, i, r.y);
+        } else {
+            j = pick(r.y, N - 1u);
+            if (j >= i) j += 1u;
+        }
         collide_pair<T>(c, v0, v1, v2, i, j, u01<T>(r.z), u01<T>(r.w), [&]() {
             return u01<T>(draw_c(c, run, step, cell, kColl, 2u * k + 1u).x);
         }, smax, seen, nacc, nclamp);
@@ -1797,8 +1882,9 @@ struct CollideSmem {
 // per-cell steps, cells tid, tid + kCollideThreads, ...; for the collisions,
 // positions of the tile's ascending candidate order taken in snake order
 // (tid, 2 kCollideThreads - 1 - tid, ...), so that a thread's light cells
-// offset its heavy ones.
-template <typename T>
+// offset its heavy ones.  POS: collision partners are chosen by position
+// (pick_partner), read from the next pool.
+template <typename T, bool POS>
 __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
                                              const CollideSmem<T>& sm, uint32_t& phase,
                                              CellTally& tl)
@@ -1943,14 +2029,18 @@ __device__ __forceinline__ void collide_tile(const StepArgs<T>& a, int64_t tile,
             T seen = (T)0;
             uint32_t nacc = 0, nclamp = 0;
             const uint32_t o = sh + (begq - b0);
+            CellPos<T> xp{};
+            if constexpr (POS) {
+                for (int ax = 0; ax < 3; ++ax) xp.x[ax] = a.xo[ax] ? a.xo[ax] + begq : nullptr;
+            }
             // one call per address space, so that staged cells use
             // shared-memory loads and stores
             if (stq)
-                collide_cell_run<T>(c, s0 + o, s1 + o, s2 + o, a.run0 + rl, step, cell, Mq, Nq, smax,
-                                    seen, nacc, nclamp);
+                collide_cell_run<POS, T>(c, s0 + o, s1 + o, s2 + o, xp, a.run0 + rl, step, cell, Mq,
+                                         Nq, smax, seen, nacc, nclamp);
             else
-                collide_cell_run<T>(c, a.vo[0] + begq, a.vo[1] + begq, a.vo[2] + begq, a.run0 + rl,
-                                    step, cell, Mq, Nq, smax, seen, nacc, nclamp);
+                collide_cell_run<POS, T>(c, a.vo[0] + begq, a.vo[1] + begq, a.vo[2] + begq, xp,
+                                         a.run0 + rl, step, cell, Mq, Nq, smax, seen, nacc, nclamp);
             if (seen > smax) a.smax[gq] = seen;
             if (a.cand) { a.cand[gq] = Mq; a.accd[gq] = nacc; }
             tl.cand += Mq;
@@ -2005,7 +2095,7 @@ __device__ __forceinline__ void flush_tally(Counters* ctr, const CellTally& tl)
     }
 }
 
-template <typename T>
+template <typename T, bool POS>
 __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>()) k_collide(StepArgs<T> a)
 {
     pdl_enter();
@@ -2022,7 +2112,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>()) k_co
     CellTally tl;
     const int64_t ntiles = (a.total_cells + kCollideCells - 1) / kCollideCells;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        collide_tile<T>(a, tile, sm, phase, tl);
+        collide_tile<T, POS>(a, tile, sm, phase, tl);
     flush_tally<T>(a.ctr, tl);
 }
 
@@ -2299,8 +2389,9 @@ __global__ void __launch_bounds__(kBigThreads, 2) k_cell_big(StepArgs<T> a)
 // velocities in the next pool (LCR order): NTC count, candidates applied by
 // collide_cell_warp (disjoint pairs side by side, in-order result), and the
 // cell's moments at sample steps.  Many large cells proceed at once.
-// the big cells of one problem, warp `wid` of `warps`
-template <typename T>
+// the big cells of one problem, warp `wid` of `warps` (POS: partners chosen
+// by position)
+template <typename T, bool POS>
 __device__ __forceinline__ void collide_big_part(const StepArgs<T>& a, uint32_t wid, uint32_t warps)
 {
     const Cfg& c = *a.cfg;
@@ -2324,9 +2415,13 @@ __device__ __forceinline__ void collide_big_part(const StepArgs<T>& a, uint32_t 
         T* v2 = a.vo[2] + beg;
         T seen = (T)0;
         uint32_t nacc = 0, nclamp = 0;
+        CellPos<T> xp{};
+        if constexpr (POS) {
+            for (int ax = 0; ax < 3; ++ax) xp.x[ax] = a.xo[ax] ? a.xo[ax] + beg : nullptr;
+        }
         if (M > 0)
-            collide_cell_warp<T>(c, v0, v1, v2, N, M, smax, cell, a.run0 + rl, step, seen, nacc,
-                                 nclamp);
+            collide_cell_warp<POS, T>(c, v0, v1, v2, xp, N, M, smax, cell, a.run0 + rl, step, seen,
+                                      nacc, nclamp);
         if (lane == 0) {
             a.rem[gcell] = rem;
             if (seen > smax) a.smax[gcell] = seen;
@@ -2348,12 +2443,12 @@ __device__ __forceinline__ void collide_big_part(const StepArgs<T>& a, uint32_t 
     }
 }
 
-template <typename T>
+template <typename T, bool POS>
 __global__ void __launch_bounds__(256) k_collide_big(StepArgs<T> a)
 {
     pdl_enter();
-    collide_big_part<T>(a, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
-                        gridDim.x * (blockDim.x >> 5));
+    collide_big_part<T, POS>(a, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                             gridDim.x * (blockDim.x >> 5));
 }
 
 // ---------------------------------------------------------------------------
@@ -2707,7 +2802,7 @@ __global__ void __launch_bounds__(kTileCells, 4) mk_cell(MultiArgs<T> m)
     });
 }
 
-template <typename T>
+template <typename T, bool POS>
 __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>() - (sizeof(T) == 4 ? 1 : 0))
     mk_collide(MultiArgs<T> m)
 {
@@ -2732,7 +2827,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>() - (si
             load_part(sa, m.parts, p);
             cur = p;
         }
-        collide_tile<T>(sa, (int64_t)(item - (uint32_t)m.ctile_base[p]), sm, phase, tl);
+        collide_tile<T, POS>(sa, (int64_t)(item - (uint32_t)m.ctile_base[p]), sm, phase, tl);
     });
     if (cur >= 0) flush_tally<T>(sa.ctr, tl);
 }
@@ -2749,14 +2844,14 @@ __global__ void __launch_bounds__(kBigThreads, 2) mk_cell_big(MultiArgs<T> m)
     }
 }
 
-template <typename T>
+template <typename T, bool POS>
 __global__ void __launch_bounds__(256) mk_collide_big(MultiArgs<T> m)
 {
     __shared__ StepArgs<T> sa;
     for (int p = 0; p < m.n_parts; ++p) {
         load_part(sa, m.parts, p);
-        collide_big_part<T>(sa, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
-                            gridDim.x * (blockDim.x >> 5));
+        collide_big_part<T, POS>(sa, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                 gridDim.x * (blockDim.x >> 5));
     }
 }
 
@@ -2918,11 +3013,20 @@ static size_t collide_smem(int prec, int stage)
     return (size_t)3 * collide_stage_pitch(stage) * (prec == DSMC_FP64 ? 8 : 4);
 }
 
+// the collision kernels choose partners by position only when the gas
+// model asks for it (pick_partner); the uniform choice keeps its own
+// instantiation
 void launch_collide(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
     constexpr int prec = DSMC_KPREC;
-    DISPATCH_PREC(prec, launch_pdl(ls, k_collide<T>, ls.collide_blocks, kCollideThreads,
-                                   collide_smem(prec, A<T>(args).collide_stage), s, A<T>(args)));
+    DISPATCH_PREC(prec, {
+        const StepArgs<T>& a = A<T>(args);
+        const size_t sm = collide_smem(prec, a.collide_stage);
+        if (a.hot.partner != DSMC_PARTNER_UNIFORM)
+            launch_pdl(ls, k_collide<T, true>, ls.collide_blocks, kCollideThreads, sm, s, a);
+        else
+            launch_pdl(ls, k_collide<T, false>, ls.collide_blocks, kCollideThreads, sm, s, a);
+    });
 }
 
 int big_cell_limit() { return big_max_of<DSMC_KT>(); }
@@ -2939,7 +3043,13 @@ void launch_cell_big(const void* args, const LaunchShape& ls, cudaStream_t s)
 void launch_collide_big(const void* args, const LaunchShape& ls, cudaStream_t s)
 {
     constexpr int prec = DSMC_KPREC;
-    DISPATCH_PREC(prec, launch_pdl(ls, k_collide_big<T>, ls.sms * 2, 256, 0, s, A<T>(args)));
+    DISPATCH_PREC(prec, {
+        const StepArgs<T>& a = A<T>(args);
+        if (a.hot.partner != DSMC_PARTNER_UNIFORM)
+            launch_pdl(ls, k_collide_big<T, true>, ls.sms * 2, 256, 0, s, a);
+        else
+            launch_pdl(ls, k_collide_big<T, false>, ls.sms * 2, 256, 0, s, a);
+    });
 }
 
 void launch_reduce(const void* args, const LaunchShape& ls, cudaStream_t s)
@@ -3005,7 +3115,13 @@ static cudaError_t raise_collide_smem_limit(int prec, int multi, size_t bytes)
     if (bytes <= cur) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     DISPATCH_PREC(prec, {
-        e = multi ? set_smem(mk_collide<T>, bytes) : set_smem(k_collide<T>, bytes);
+        if (multi) {
+            e = set_smem(mk_collide<T, false>, bytes);
+            if (e == cudaSuccess) e = set_smem(mk_collide<T, true>, bytes);
+        } else {
+            e = set_smem(k_collide<T, false>, bytes);
+            if (e == cudaSuccess) e = set_smem(k_collide<T, true>, bytes);
+        }
     });
     if (e == cudaSuccess) cur = bytes;
     return e;
@@ -3026,10 +3142,12 @@ int collide_stage_for(int per_sm, int multi)
         int b = 0;
         DISPATCH_PREC(prec, {
             if (multi)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mk_collide<T>, kCollideThreads,
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mk_collide<T, false>,
+                                                              kCollideThreads,
                                                               collide_smem(prec, stage));
             else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_collide<T>, kCollideThreads,
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_collide<T, false>,
+                                                              kCollideThreads,
                                                               collide_smem(prec, stage));
         });
         if (b >= per_sm) break;
@@ -3154,15 +3272,25 @@ void launch_m_cell_big(const void* margs, const LaunchShape& ls, cudaStream_t s)
 void launch_m_collide_big(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
     constexpr int prec = DSMC_KPREC;
-    DISPATCH_PREC(prec, (mk_collide_big<T><<<ls.sms * 2, 256, 0, s>>>(MA<T>(margs))));
+    DISPATCH_PREC(prec, {
+        if (MA<T>(margs).positional)
+            mk_collide_big<T, true><<<ls.sms * 2, 256, 0, s>>>(MA<T>(margs));
+        else
+            mk_collide_big<T, false><<<ls.sms * 2, 256, 0, s>>>(MA<T>(margs));
+    });
 }
 
 void launch_m_collide(const void* margs, const LaunchShape& ls, cudaStream_t s)
 {
     constexpr int prec = DSMC_KPREC;
-    DISPATCH_PREC(prec, (mk_collide<T><<<ls.collide_blocks, kCollideThreads,
-                                          collide_smem(prec, MA<T>(margs).collide_stage), s>>>(
-                             MA<T>(margs))));
+    DISPATCH_PREC(prec, {
+        const MultiArgs<T>& m = MA<T>(margs);
+        const size_t sm = collide_smem(prec, m.collide_stage);
+        if (m.positional)
+            mk_collide<T, true><<<ls.collide_blocks, kCollideThreads, sm, s>>>(m);
+        else
+            mk_collide<T, false><<<ls.collide_blocks, kCollideThreads, sm, s>>>(m);
+    });
 }
 
 void launch_m_reduce(const void* margs, const LaunchShape& ls, cudaStream_t s)

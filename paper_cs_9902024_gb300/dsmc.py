@@ -56,7 +56,8 @@ class Cells(C.Structure):
 
 class Gas(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("mass", C.c_double), ("d_ref", C.c_double),
-                ("T_ref", C.c_double), ("omega", C.c_double), ("F_N", C.c_double)]
+                ("T_ref", C.c_double), ("omega", C.c_double), ("F_N", C.c_double),
+                ("partner", C.c_int32), ("n_sub", C.c_int32)]
 
 
 class Boundary(C.Structure):
@@ -164,7 +165,8 @@ def _structs(w):
         cells.n[a] = w["ncell"][a] if a < w["dim"] else 1
     g = w["gas"]
     gas = Gas(struct_size=C.sizeof(Gas), mass=g["mass"], d_ref=g["d_ref"], T_ref=g["T_ref"],
-              omega=g["omega"], F_N=g["F_N"])
+              omega=g["omega"], F_N=g["F_N"], partner=g.get("partner", 0),
+              n_sub=g.get("n_sub", 1))
     nb = len(w["bcs"])
     if nb > MAX_BC:
         raise DsmcError(E_INVALID, "too many boundary segments")

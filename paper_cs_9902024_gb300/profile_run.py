@@ -4,12 +4,15 @@ launch shapes), for a profiler to capture chosen launches of it.
     python -m paper_cs_9902024_gb300.profile_run duct 256 301
     python -m paper_cs_9902024_gb300.profile_run duct 256 301 760,2432,3072,1216
     python -m paper_cs_9902024_gb300.profile_run jet 8 60
+    python -m paper_cs_9902024_gb300.profile_run duct 256 101 0,0,0,0 nearest
 
 Arguments: workload (duct: the 64x32 channel, HS, its 8 sample times; jet:
 the 256x128 pulsed jet, VHS; plate: the 128x64x64 box with a plate; mixed:
 runs on grids of 32x16 to 256x128 cells; the last three with 2 sample
 times), runs, steps, and optionally a launch shape (move CTAs, scatter
-CTAs, sort/gather tile budget, collision CTAs; 0 keeps a default).  Each step launches the step's kernels once, in
+CTAs, sort/gather tile budget, collision CTAs; 0 keeps a default) and the
+choice of collision partner (uniform, subcell: 2 per axis, nearest; not for
+mixed).  Each step launches the step's kernels once, in
 a fixed order, so the n-th launch of a kernel is its n-th step.  Prints the
 particle-steps done and the device error word (non-zero exit if set)."""
 import sys
@@ -26,6 +29,9 @@ def main(argv):
     if len(argv) > 3:
         from .dsmc import SHAPE_KEYS
         shape = dict(zip(SHAPE_KEYS, (int(v) for v in argv[3].split(","))))
+        if not any(shape.values()):
+            shape = None
+    partner = argv[4] if len(argv) > 4 else "uniform"
     if name == "mixed":
         m = W.mixed(grids=[(32, runs), (64, runs), (128, runs), (256, runs)], steps=steps,
                     n_samples=2)
@@ -37,6 +43,7 @@ def main(argv):
         else:
             make = {"jet": W.jet256x128_n64, "plate": W.plate128x64x64_n16}[name]
             w = make(runs=runs, steps=steps, n_samples=2)
+        w = W.with_partner(w, partner, 2)
         e = Ensemble(w, use_graph=False, shape=shape).run()
         st = e.stats()
         err = st["error_word"]

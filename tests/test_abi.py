@@ -49,12 +49,13 @@ def test_ctypes_layout_matches_header():
     int main(void) {
       printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dsmc_domain), sizeof(dsmc_cells),
              sizeof(dsmc_gas), sizeof(dsmc_boundary), sizeof(dsmc_options), sizeof(dsmc_stats));
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsmc_boundary, n),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsmc_boundary, n),
              offsetof(dsmc_options, stream), offsetof(dsmc_options, profile),
              offsetof(dsmc_options, autotune), offsetof(dsmc_options, shape),
              offsetof(dsmc_stats, ms_steps), offsetof(dsmc_stats, launches_kernel),
              offsetof(dsmc_stats, shape), offsetof(dsmc_options, checks),
-             offsetof(dsmc_options, tune_cache));
+             offsetof(dsmc_options, tune_cache), offsetof(dsmc_gas, partner),
+             offsetof(dsmc_gas, n_sub));
       return 0;
     }
     """
@@ -71,7 +72,8 @@ def test_ctypes_layout_matches_header():
     assert offs == [D.Boundary.n.offset, D.Options.stream.offset, D.Options.profile.offset,
                     D.Options.autotune.offset, D.Options.shape.offset,
                     D.Stats.ms_steps.offset, D.Stats.launches_kernel.offset, D.Stats.shape.offset,
-                    D.Options.checks.offset, D.Options.tune_cache.offset]
+                    D.Options.checks.offset, D.Options.tune_cache.offset,
+                    D.Gas.partner.offset, D.Gas.n_sub.offset]
 
 
 def _args():
@@ -104,6 +106,18 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     badg.omega = 1.5
     assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(badg), arr, nb, C.byref(opt),
                            C.byref(h)) == D.E_INVALID
+    # collision-partner choice out of range; subcells per axis out of range
+    for partner, n_sub in ((3, 1), (-1, 1), (1, 0), (1, 65)):
+        badg = D.Gas.from_buffer_copy(gas)
+        badg.partner, badg.n_sub = partner, n_sub
+        assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(badg), arr, nb,
+                               C.byref(opt), C.byref(h)) == D.E_INVALID
+    # a gas struct that ends before the partner fields is still accepted as
+    # far as the argument checks go (uniform choice); one shorter is not
+    badg = D.Gas.from_buffer_copy(gas)
+    badg.struct_size = D.Gas.partner.offset - 8
+    assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(badg), arr, nb, C.byref(opt),
+                           C.byref(h)) == D.E_INVALID
     badb = (D.Boundary * 1).from_buffer_copy(arr)
     badb[0].face = 5          # z face in 2-D
     assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(gas), badb, 1, C.byref(opt),
@@ -133,6 +147,19 @@ def test_create_without_gpu_reports_cuda_error(lib):
     opt = D.Options(struct_size=C.sizeof(D.Options))
     assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(gas), arr, nb, C.byref(opt),
                            C.byref(h)) == D.E_CUDA
+    # an older caller's gas (no partner fields) and valid partner choices
+    # pass the argument checks too
+    short = D.Gas.from_buffer_copy(gas)
+    short.struct_size = D.Gas.partner.offset
+    short.partner = 7        # beyond the caller's struct: not read
+    variants = [short]
+    for partner, n_sub in ((1, 1), (1, 64), (2, 0)):
+        g = D.Gas.from_buffer_copy(gas)
+        g.partner, g.n_sub = partner, n_sub
+        variants.append(g)
+    for g in variants:
+        assert lib.dsmc_create(C.byref(dom), C.byref(cells), C.byref(g), arr, nb, C.byref(opt),
+                               C.byref(h)) == D.E_CUDA
     assert not h.value
 
 

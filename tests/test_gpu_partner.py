@@ -1,0 +1,112 @@
+"""The collision-partner variants on the device (GPU): the second particle of
+an NTC candidate chosen within the first one's subcell, or as its nearest
+neighbour, against the FP64 oracle.
+
+FP64 device state takes every decision as the oracle does (the subcell of a
+particle and the nearest distance in double precision), so the LCR, the cell
+counts and the NTC candidate / accepted counts agree exactly every step, in
+the tile kernel (cells up to 128 particles), in the big-cell kernel and in
+3-D.  FP32 state is held to the oracle statistically.  A mixed-size ensemble
+whose parts choose partners differently equals each part run alone (the
+uniform part then runs in the positional instantiation of the kernels)."""
+import numpy as np
+import pytest
+
+from oracle import macro_from_acc, run_ensemble
+from paper_cs_9902024_gb300 import workloads as W
+from tests.parity import zscores
+from tests.test_gpu_parity import _assert_exact, _lockstep
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    import __graft_entry__ as g
+    g.build()
+    from paper_cs_9902024_gb300 import dsmc
+    return dsmc
+
+
+@pytest.mark.parametrize("scheme,n_sub", [("subcell", 2), ("subcell", 3), ("nearest", 1)])
+def test_fp64_duct_partner_every_step(D, scheme, n_sub):
+    """The filling duct, 3 runs x 30 steps, every step compared; the
+    counters equal the oracle's."""
+    w = W.with_partner(W.duct64x32_n8(runs=3), scheme, n_sub)
+    ens, orc, res = _lockstep(D, w, runs=3, steps=30)
+    _assert_exact(res)
+    assert res[-1][0]["n"] > 3000
+    st = ens.stats()
+    so = [orc.stats(r) for r in range(3)]
+    for k in ("candidates", "collisions", "clamps", "particle_steps", "wall_hits"):
+        assert st[k] == sum(s[k] for s in so), k
+    assert st["collisions"] > 1000
+
+
+@pytest.mark.parametrize("scheme", ["subcell", "nearest"])
+def test_fp64_jet_big_cells_partner(D, scheme):
+    """The VHS jet with cells of hundreds of particles near the orifice: the
+    big-cell kernel's warp draws 32 candidates at a time, each lane choosing
+    its own partner by position."""
+    w = W.with_partner(W.pulsed_jet(nx=24, ny=16, runs=2, steps=10, n_samples=2, orifice=4,
+                                    pulse=5, F_N=4.49e10 * 4), scheme, 2)
+    ens, orc, res = _lockstep(D, w, runs=2, steps=10)
+    _assert_exact(res, tol_x=1e-10, tol_v=1e-9)
+    assert res[4][0]["cnt"].max() > 128
+    assert ens.stats()["collisions"] > 0
+
+
+@pytest.mark.parametrize("scheme,n_sub", [("subcell", 3), ("nearest", 1)])
+def test_fp64_plate3d_partner(D, scheme, n_sub):
+    """3-D: subcells over three axes, distances over three axes."""
+    w = W.with_partner(W.plate3d(nx=24, ny=12, nz=12, plate=6, plate_x=8, ppc=8, runs=2,
+                                 steps=10, n_samples=2), scheme, n_sub)
+    ens, orc, res = _lockstep(D, w, runs=2, steps=10)
+    _assert_exact(res)
+    assert ens.stats()["collisions"] > 0
+
+
+@pytest.mark.parametrize("scheme", ["subcell", "nearest"])
+def test_fp32_duct_partner_within_3_combined_se(D, scheme):
+    """FP32 batched ensemble of the 8-run duct (200 steps, 4 samples) against
+    the FP64 oracle with the same partner choice: density, velocity and
+    temperature within 3 combined standard errors; collision counts within
+    2%."""
+    w = W.with_partner(W.duct64x32_n8(), scheme, 2)
+    acc_o, st_o = run_ensemble(w, threads=8)
+    mo = macro_from_acc(acc_o, w, w["runs"])
+    ens = D.Ensemble(w).run()
+    T = len(w["sample_steps"])
+    ms = [ens.macro(t) for t in range(T)]
+    mg = {k: np.stack([m[k] for m in ms]) for k in ms[0]}
+    raw = np.stack([ens.raw(t) for t in range(T)])
+    mask = np.minimum(raw[..., 0].sum(1), acc_o[..., 0].sum(1)) >= 40
+    z, excluded = zscores(mg, mo, mask)
+    assert excluded <= 0.01 * max(z.size, 1)
+    frac = np.mean(np.abs(z) > 3)
+    print("duct64x32_n8 %s fp32: %d comparisons, |z|>3 fraction %.4f" % (scheme, z.size, frac))
+    assert z.size > 10000 and frac < 0.01
+    st = ens.stats()
+    for k in ("generated", "particle_steps", "collisions"):
+        assert st[k] == pytest.approx(st_o[k], rel=0.02), k
+    ens.close()
+
+
+def test_mixed_parts_with_different_partner_choices(D):
+    """One part per grid, choosing partners uniformly, by subcell and by
+    nearest neighbour: the single-launch ensemble gives every part what its
+    own dsmc_run_ensemble gives it, bit for bit (FP32 and FP64)."""
+    m = W.mixed(grids=[(32, 3), (48, 2), (64, 3)], steps=30, n_samples=2)
+    m["groups"][0] = W.with_partner(m["groups"][0], "nearest")
+    m["groups"][2] = W.with_partner(m["groups"][2], "subcell", 2)
+    T = len(m["groups"][0]["sample_steps"])
+    for precision in ("fp32", "fp64"):
+        me = D.MixedEnsemble(m, precision=precision).run()
+        for gi, w in enumerate(m["groups"]):
+            alone = D.Ensemble(w, precision=precision, run_offset=w["run0"]).run()
+            for t in range(T):
+                assert np.array_equal(me.raw(gi, t), alone.raw(t)), (precision, gi, t)
+            assert alone.stats()["collisions"] == me.parts[gi].stats()["collisions"]
+            alone.close()
+        assert me.mixed_stats()["error_word"] == 0
+        me.close()

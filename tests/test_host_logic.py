@@ -1,9 +1,11 @@
 """Host-side logic without a GPU: the mixed-size ensemble's grouping and the
 bench's algorithmic-byte accounting."""
 import os
+import json
 import sys
 
 import numpy as np
+import pytest
 
 from paper_cs_9902024_gb300 import workloads as W
 
@@ -66,6 +68,52 @@ def test_algorithmic_bytes_split_between_tile_and_big_cell_kernels():
     w3 = W.plate3d(nx=8, ny=4, nz=4, runs=1)
     m3, _ = bench.algorithmic_bytes(w3, st0, steps=10, runs=1)
     assert m3["move"] == 900 * 40 and m3["cell"] == 1200 * 56
+
+
+def test_partner_variant_bytes_and_traffic_family(tmp_path):
+    """A positional partner choice adds one read of every particle's
+    position to Interaction (8 B in 2-D, 12 in 3-D); its traffic entry is a
+    family of its own, so the uniform choice's DRAM counters never stand in
+    for it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    st = {"particle_steps": 1000, "generated": 100, "pool_steps": 1200, "big_pool_steps": 300,
+          "collisions": 50}
+    w = W.duct64x32_n8()
+    mu, lu = bench.algorithmic_bytes(w, st, steps=10, runs=8)
+    for scheme in ("subcell", "nearest"):
+        wp = W.with_partner(w, scheme, 2)
+        mp, lp = bench.algorithmic_bytes(wp, st, steps=10, runs=8)
+        assert mp["collide"] + mp["collide_big"] == 1200 * (16 + 8)
+        assert lp["collide"] - lu["collide"] == 900 * 8
+        assert lp["collide_big"] - lu["collide_big"] == 300 * 8
+        assert mp["cell"] == mu["cell"] and lp["move"] == lu["move"]
+    w3 = W.with_partner(W.plate3d(nx=8, ny=4, nz=4, runs=1), "nearest")
+    m3, _ = bench.algorithmic_bytes(w3, dict(st, big_pool_steps=0), steps=10, runs=1)
+    assert m3["collide"] == 1200 * (16 + 12)
+    # the traffic of the uniform family is not used for a variant
+    tj = tmp_path / "traffic.json"
+    tj.write_text(json.dumps({"duct64x32": {"cell": {"kernel_hash": "h", "dram_bytes": 4.0e6,
+                                                     "particles": 1.0e5}}}))
+    prs = {"pool_steps": 2000, "big_pool_steps": 0, "launches_kernel": {"cell": 10}}
+    assert bench.traffic_per_launch("duct64x32_n512", "cell", prs, path=str(tj),
+                                    khash="h") == pytest.approx(40.0 * 2000 / 10)
+    assert bench.traffic_per_launch("duct64x32_n512", "cell", prs, path=str(tj), khash="h",
+                                    partner="nearest") is None
+
+
+def test_with_partner_keeps_the_workload():
+    w = W.duct64x32_n512()
+    for scheme, code in (("uniform", 0), ("subcell", 1), ("nearest", 2)):
+        wp = W.with_partner(w, scheme, n_sub=3)
+        assert wp["gas"]["partner"] == code
+        assert wp["gas"]["n_sub"] == (3 if scheme == "subcell" else 1)
+        for k in ("dim", "ncell", "L", "bcs", "runs", "steps", "dt", "sample_steps", "seed"):
+            assert wp[k] == w[k], k
+        for k in ("mass", "d_ref", "T_ref", "omega", "F_N"):
+            assert wp["gas"][k] == w["gas"][k]
+        assert (wp["name"] == w["name"]) == (scheme == "uniform")
+    assert "partner" not in w["gas"]
 
 
 def test_method_rows_are_bytes_over_summed_kernel_time():
