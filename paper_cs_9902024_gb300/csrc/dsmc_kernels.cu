@@ -1311,19 +1311,27 @@ struct CellPos {
     const T* x[3];
 };
 
-// the subcell of a particle from its offsets: per axis floor(n_sub f / d),
-// clamped to the cell, axis 0 fastest
+// the subcell index along axis a of offset f: floor(n_sub f / d), clamped
+// to the cell
+template <typename T, class C>
+__device__ __forceinline__ uint32_t subcell_axis(const C& c, int a, T f)
+{
+    const int ns = c.n_sub;
+    int k = (int)dfloor(in_cells(c, a, f) * (T)ns);
+    k = k < 0 ? 0 : (k > ns - 1 ? ns - 1 : k);
+    return (uint32_t)k;
+}
+
+// the subcell of particle m from its offsets, axis 0 fastest (positions are
+// read-only while the cells collide; the axes are spelt out so that the
+// position pointers stay in registers)
 template <typename T, class C>
 __device__ __forceinline__ uint32_t subcell_of(const C& c, const CellPos<T>& p, uint32_t m)
 {
-    const int ns = c.n_sub;
-    uint32_t s = 0;
-    for (int a = c.dim - 1; a >= 0; --a) {
-        int k = (int)dfloor(in_cells(c, a, p.x[a][m]) * (T)ns);
-        k = k < 0 ? 0 : (k > ns - 1 ? ns - 1 : k);
-        s = s * (uint32_t)ns + (uint32_t)k;
-    }
-    return s;
+    const uint32_t ns = (uint32_t)c.n_sub;
+    uint32_t s = c.dim == 3 ? subcell_axis<T>(c, 2, __ldg(p.x[2] + m)) : 0u;
+    s = s * ns + subcell_axis<T>(c, 1, __ldg(p.x[1] + m));
+    return s * ns + subcell_axis<T>(c, 0, __ldg(p.x[0] + m));
 }
 
 // The second particle of an NTC candidate whose first is i, among the N of
@@ -1331,30 +1339,46 @@ __device__ __forceinline__ uint32_t subcell_of(const C& c, const CellPos<T>& p, 
 // N - 1 (the r-th other in LCR order, r from `bits`); uniform over the other
 // particles of i's subcell, or the uniform rule if i is alone there; the
 // nearest other particle (squared distance summed over the grid's axes in
-// axis order; the first of equal distances).  The cell's particles are read
-// from global memory, one pass per choice (two for a subcell draw).
+// axis order; the first of equal distances).  The cell's positions are read
+// from global memory (read-only path), one pass per choice (two for a
+// subcell draw); the passes select without branches so that the loads of
+// consecutive particles overlap.
 template <typename T, class C>
-__device__ uint32_t pick_partner(const C& c, const CellPos<T>& p, uint32_t N, uint32_t i,
-                                 uint32_t bits)
+__device__ __forceinline__ uint32_t pick_partner(const C& c, const CellPos<T>& p, uint32_t N,
+                                                 uint32_t i, uint32_t bits)
 {
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
     if (c.partner == DSMC_PARTNER_NEAREST) {
-        const bool d3 = c.dim == 3;
-        const T a0 = p.x[0][i], a1 = p.x[1][i], a2 = d3 ? p.x[2][i] : (T)0;
+        const T* x0 = p.x[0];
+        const T* x1 = p.x[1];
+        const T a0 = __ldg(x0 + i), a1 = __ldg(x1 + i);
         T best = (T)0;
-        uint32_t j = 0xFFFFFFFFu;
-        for (uint32_t m = 0; m < N; ++m) {
-            if (m == i) continue;
-            const T e0 = p.x[0][m] - a0;
-            const T e1 = p.x[1][m] - a1;
-            T dd = e0 * e0;
-            dd = dd + e1 * e1;
-            if (d3) {
-                const T e2 = p.x[2][m] - a2;
+        uint32_t j = kNone;
+        if (c.dim == 3) {
+            const T* x2 = p.x[2];
+            const T a2 = __ldg(x2 + i);
+#pragma unroll 4
+            for (uint32_t m = 0; m < N; ++m) {
+                const T e0 = __ldg(x0 + m) - a0;
+                const T e1 = __ldg(x1 + m) - a1;
+                const T e2 = __ldg(x2 + m) - a2;
+                T dd = e0 * e0;
+                dd = dd + e1 * e1;
                 dd = dd + e2 * e2;
+                const bool take = m != i && (j == kNone || dd < best);
+                best = take ? dd : best;
+                j = take ? m : j;
             }
-            if (j == 0xFFFFFFFFu || dd < best) {
-                best = dd;
-                j = m;
+        } else {
+#pragma unroll 4
+            for (uint32_t m = 0; m < N; ++m) {
+                const T e0 = __ldg(x0 + m) - a0;
+                const T e1 = __ldg(x1 + m) - a1;
+                T dd = e0 * e0;
+                dd = dd + e1 * e1;
+                const bool take = m != i && (j == kNone || dd < best);
+                best = take ? dd : best;
+                j = take ? m : j;
             }
         }
         return j;
@@ -1362,14 +1386,18 @@ __device__ uint32_t pick_partner(const C& c, const CellPos<T>& p, uint32_t N, ui
     if (c.partner == DSMC_PARTNER_SUBCELL) {
         const uint32_t si = subcell_of<T>(c, p, i);
         uint32_t K = 0;
+#pragma unroll 4
         for (uint32_t m = 0; m < N; ++m) K += (m != i && subcell_of<T>(c, p, m) == si) ? 1u : 0u;
         if (K > 0u) {
-            uint32_t r = pick(bits, K);
+            const uint32_t r = pick(bits, K);
+            uint32_t seen = 0, j = kNone;
+#pragma unroll 4
             for (uint32_t m = 0; m < N; ++m) {
-                if (m == i || subcell_of<T>(c, p, m) != si) continue;
-                if (r == 0u) return m;
-                --r;
+                const bool mate = m != i && subcell_of<T>(c, p, m) == si;
+                j = (mate && seen == r) ? m : j;
+                seen += mate ? 1u : 0u;
             }
+            return j;
         }
     }
     uint32_t j = pick(bits, N - 1u);
