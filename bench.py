@@ -271,9 +271,10 @@ def algorithmic_bytes(w, st, steps, runs, cells=None):
         "cell": (pool - big) * gather + cells * steps * 4,
         "cell_big": big * gather,
         # per cell: start, NTC remainder (read + write), (sigma c_r)_max;
-        # every particle's velocity read once, both velocities of every
-        # collision written
-        # (positional partner choice: every particle's position read once)
+        # the velocity of every particle in cells up to 128 read once (the
+        # larger cells are the big-cell kernel's), both velocities of every
+        # collision written; a positional partner choice also reads every
+        # particle's position once
         "collide": (cells * steps * 24 + (pool - big) * (3 * t + pos)
                     + st["collisions"] * 2 * 3 * t),
         "collide_big": big * (3 * t + pos),
