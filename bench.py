@@ -329,16 +329,44 @@ def method_rows(method, kern_ms, peak):
 
 
 # ---------------------------------------------------------------------------
+def workload_config(w, args, runs=None):
+    """The workload part of the bench line's config, the same in both arms."""
+    if args.workload == "mixed_n1024":
+        return {"workload": w["name"] + " (" + WORKLOAD_TEXT["mixed_n1024"] + ")",
+                "runs": w["runs"], "grids": len(w["groups"]), "steps_per_run": w["steps"],
+                "sample_times": len(w["groups"][0]["sample_steps"])}
+    cells = 1
+    for a in range(w["dim"]):
+        cells *= w["ncell"][a]
+    return {"workload": w["name"] + " (" + WORKLOAD_TEXT[args.workload] + ")",
+            "runs_per_gpu": runs if runs is not None else w["runs"],
+            "steps_per_run": w["steps"], "cells_per_run": cells,
+            "sample_times": len(w["sample_steps"]),
+            "partner": args.partner + (" (%d subcells per axis)" % args.n_sub
+                                       if args.partner == "subcell" else "")}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     from oracle import run_ensemble
-    w = workload(name=args.workload, partner=args.partner, n_sub=args.n_sub)
     cores = min(cpu_cores(), 16)
-    sample_runs = min(64, w["runs"])
-    probe = ORACLE_PROBE_STEPS[args.workload]
-    sample_steps = w["steps"] if probe is None else min(w["steps"], 5 * probe)
+    if args.workload == "mixed_n1024":
+        # the mixed workload: the first steps of up to 16 runs of its median
+        # grid (as the measured arm's CPU leg)
+        from paper_cs_9902024_gb300 import workloads as W
+        m = W.by_name(args.workload)
+        cfg = workload_config(m, args)
+        w = m["groups"][len(m["groups"]) // 2]
+        sample_runs, sample_steps = min(16, w["runs"]), min(20, w["steps"])
+    else:
+        w = workload(args.runs, args.workload, args.partner, args.n_sub)
+        cfg = workload_config(w, args)
+        sample_runs = min(64, w["runs"])
+        probe = ORACLE_PROBE_STEPS[args.workload]
+        sample_steps = w["steps"] if probe is None else min(w["steps"], 5 * probe)
+    cfg.update(mode="FP64 oracle on the host cores, threads over run groups", state="fp64")
     wr = dict(w)
 
     def one():
@@ -362,8 +390,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": w["name"], "runs": w["runs"], "steps_per_run": w["steps"],
-                   "cells": w["ncell"][0] * w["ncell"][1], "sample_times": len(w["sample_steps"])},
+        "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -474,11 +501,10 @@ def bench_mixed(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": m["name"] + " (" + WORKLOAD_TEXT["mixed_n1024"] + ")",
-                   "runs": m["runs"], "grids": len(m["groups"]), "steps_per_run": steps,
-                   "sample_times": T, "mode": "one launch per kernel kind per step, work queues, "
-                   "CUDA graph per step", "state": "fp32", "sampling": "fp64 group sums",
-                   "l2": "inputs larger than L2 (pool ~30 GB)"},
+        "config": dict(workload_config(m, args),
+                       mode="one launch per kernel kind per step, work queues, CUDA graph per step",
+                       state="fp32", sampling="fp64 group sums",
+                       l2="inputs larger than L2 (pool ~30 GB)"),
         "clocks": clk.summary(),
         "e2e": {"value": ps * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
@@ -587,15 +613,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["name"] + " (" + WORKLOAD_TEXT[args.workload] + ")",
-                   "runs_per_gpu": runs, "steps_per_run": steps,
-                   "cells_per_run": int(np.prod([w["ncell"][a] for a in range(w["dim"])])),
-                   "sample_times": n_samples,
-                   "mode": "batched, CUDA graph per step", "state": "fp32",
-                   "sampling": "fp64 group sums", "l2": "inputs larger than L2 (pool ~1 GB)",
-                   "parallelism": "runs sharded over %d GPU(s)" % ws,
-                   "partner": args.partner + (" (%d subcells per axis)" % args.n_sub
-                                              if args.partner == "subcell" else "")},
+        "config": dict(workload_config(w, args, runs),
+                       mode="batched, CUDA graph per step", state="fp32",
+                       sampling="fp64 group sums", l2="inputs larger than L2 (pool ~1 GB)",
+                       parallelism="runs sharded over %d GPU(s)" % ws),
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
