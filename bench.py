@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--partner", default="uniform", choices=["uniform", "subcell", "nearest"],
                    help="choice of the second collision partner (gas model variant)")
     p.add_argument("--n-sub", type=int, default=2, help="subcells per axis (--partner subcell)")
+    p.add_argument("--window", type=int, default=1,
+                   help="time-averaged samples: each sample sums the last WINDOW steps up to its "
+                        "sample time (1: instantaneous samples)")
     return p.parse_args()
 
 
@@ -346,6 +349,19 @@ def workload_config(w, args, runs=None):
                                        if args.partner == "subcell" else "")}
 
 
+def sample_windows(w, L):
+    """Windows of L steps ending at the workload's sample times (None for
+    instantaneous samples); they must be disjoint."""
+    if L <= 1:
+        return None
+    ss = w["sample_steps"]
+    win = [(max(1, t - L + 1), t) for t in ss]
+    for (a, _), (_, b) in zip(win[1:], win[:-1]):
+        if a <= b:
+            raise SystemExit("windows of %d steps overlap at the sample times %s" % (L, ss))
+    return win
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -554,6 +570,7 @@ def main():
     steps = w["steps"]
     n_samples = len(w["sample_steps"])
     stream = torch.cuda.Stream(device=device)
+    win = sample_windows(w, args.window)
     ens = Ensemble(w, device=device, stream=stream, run_offset=shard.run_offset(rank, runs),
                    autotune=True)
 
@@ -562,7 +579,7 @@ def main():
             torch.distributed.barrier()
 
     for _ in range(max(args.warmup, 3)):
-        ens.run()
+        ens.run(windows=win)
     st = ens.stats()
     ps_per_step = st["particle_steps"]
     # fill: 6 launches (cells, counts, scan (two passes), particles, ids);
@@ -578,7 +595,7 @@ def main():
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            ens.run()
+            ens.run(windows=win)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -595,7 +612,7 @@ def main():
     h2d = d2h = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ens.run()
+        ens.run(windows=win)
         raws = np.stack([ens.raw(t) for t in range(n_samples)])
         if ws > 1:
             raws = shard.allreduce_group_sums(raws)
@@ -615,7 +632,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(w, args, runs),
                        mode="batched, CUDA graph per step", state="fp32",
-                       sampling="fp64 group sums", l2="inputs larger than L2 (pool ~1 GB)",
+                       sampling="fp64 group sums" + (
+                           ", each sample time-averaged over %d steps" % args.window
+                           if win else ""),
+                       l2="inputs larger than L2 (pool ~1 GB)",
                        parallelism="runs sharded over %d GPU(s)" % ws),
         "clocks": clocks,
         "e2e": e2e,
@@ -628,18 +648,18 @@ def main():
         #    the per-run loop's cost is the same for every run) ------------
         plain_runs = max(2, min(64, runs // 8))
         pe = Ensemble(w, mode="plain", device=device, stream=stream)
-        pe.run(runs=min(8, plain_runs))
+        pe.run(runs=min(8, plain_runs), windows=win)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        pe.run(runs=plain_runs)
+        pe.run(runs=plain_runs, windows=win)
         e1.record(stream)
         torch.cuda.synchronize()
         pst = pe.stats()
         pms = e0.elapsed_time(e1)
         # same-seed batched run of the same 64 runs: identical sums
-        be = Ensemble(w, device=device, stream=stream).run(runs=plain_runs)
+        be = Ensemble(w, device=device, stream=stream).run(runs=plain_runs, windows=win)
         same = all(np.array_equal(pe.raw(t), be.raw(t)) for t in range(n_samples))
         out["plain"] = {"value": pst["particle_steps"] / (pms / 1e3), "unit": UNIT,
                         "runs_timed": plain_runs, "ms": pms,
@@ -656,7 +676,7 @@ def main():
         pr = Ensemble(w, profile=True, device=device, stream=stream, shape=st["shape"])
         passes = []
         for _ in range(2):
-            pr.run()
+            pr.run(windows=win)
             passes.append(pr.stats())
         pr.close()
         prs = dict(passes[-1])

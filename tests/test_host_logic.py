@@ -102,6 +102,19 @@ def test_partner_variant_bytes_and_traffic_family(tmp_path):
                                     partner="nearest") is None
 
 
+def test_sample_windows_end_at_the_sample_times():
+    sys.path.insert(0, ROOT)
+    import bench
+    w = W.duct64x32_n512()
+    assert bench.sample_windows(w, 1) is None
+    win = bench.sample_windows(w, 25)
+    assert [b for _, b in win] == w["sample_steps"]
+    assert all(b - a + 1 == 25 for a, b in win)
+    assert len(bench.sample_windows(w, 50)) == 8       # 50-step gaps: just disjoint
+    with pytest.raises(SystemExit):
+        bench.sample_windows(w, 51)
+
+
 def test_with_partner_keeps_the_workload():
     w = W.duct64x32_n512()
     for scheme, code in (("uniform", 0), ("subcell", 1), ("nearest", 2)):
