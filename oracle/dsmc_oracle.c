@@ -570,7 +570,10 @@ static int64_t choose_partner(const orc_config* cfg, const double d[3], int c, c
 int64_t orc_partner(const orc_config* cfg, int c, const double* x, int64_t N, int64_t i,
                     double u1)
 {
-    if (!cfg || !x || N < 2 || i < 0 || i >= N) return -1;
+    if (!cfg || !x || N < 2 || i < 0 || i >= N ||
+        cfg->partner < ORC_PARTNER_UNIFORM || cfg->partner > ORC_PARTNER_NEAREST ||
+        (cfg->partner == ORC_PARTNER_SUBCELL && cfg->n_sub < 1))
+        return -1;
     double d[3];
     for (int a = 0; a < 3; ++a) d[a] = cfg->L[a] / (a < cfg->dim ? cfg->ncell[a] : 1);
     return choose_partner(cfg, d, c, (const char*)x, 3 * sizeof(double), N, i, u1);

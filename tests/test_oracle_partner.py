@@ -39,6 +39,19 @@ def _cell_geometry(w, c):
     return ci * d, d
 
 
+def test_invalid_partner_arguments():
+    w = _grid(2, "subcell", n_sub=2)
+    lo, d = _cell_geometry(w, 0)
+    x = lo + np.array([[0.1, 0.1, 0.5], [0.9, 0.9, 0.5]]) * d
+    assert partner(w, 0, x, 0, 0.5) == 1
+    assert partner(w, 0, x[:1], 0, 0.5) == -1          # one particle: no pair
+    assert partner(w, 0, x, 2, 0.5) == -1              # i out of range
+    bad = W.with_partner(w, "subcell", n_sub=0)
+    assert partner(bad, 0, x, 0, 0.5) == -1
+    bad = dict(w, gas=dict(w["gas"], partner=3))
+    assert partner(bad, 0, x, 0, 0.5) == -1
+
+
 def test_closed_forms():
     assert MEAN_DIST_SQUARE == pytest.approx(0.5214054331, abs=1e-9)
     assert MEAN_DIST_CUBE == pytest.approx(0.6617071822, abs=1e-9)
