@@ -1335,7 +1335,8 @@ __device__ __forceinline__ uint32_t subcell_of(const C& c, const CellPos<T>& p, 
 }
 
 // The second particle of an NTC candidate whose first is i, among the N of
-// the cell, by the gas model's choice of partner: uniform over the other
+// the cell, by the gas model's choice of partner (the Interaction step of
+// Sec. 1.1 leaves the pair selection to the gas model): uniform over the other
 // N - 1 (the r-th other in LCR order, r from `bits`); uniform over the other
 // particles of i's subcell, or the uniform rule if i is alone there; the
 // nearest other particle (squared distance summed over the grid's axes in
